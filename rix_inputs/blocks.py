@@ -1,0 +1,287 @@
+"""Seeded synthetic C, V and D blocks in the canonical packed layout.
+
+Canonical layout (the interchange format both the library and the oracle
+read; each side builds its own pair list and checks it against ``keys``):
+
+* pair list: all (A, B, n1, n2, n3) with |x_B + n.cell - x_A| < cutoff
+  (every pair when there is no cutoff; n = 0 for clusters), sorted
+  lexicographically.  The distance of a pair is evaluated in its
+  representative orientation (A < B, or A == B with n > 0
+  lexicographically), so the list is exactly symmetric.
+* C(A,B,n): [P][i][j], P runs over aux(A) then aux(B) (aux(A) only for the
+  on-site pair A == B, n == 0); i in basis(A), j in basis(B).
+  C(B,A,-n)[P'][j][i] = C(A,B,n)[P][i][j] with P' the same aux function.
+* V(A,B,n): [P][Q], P in aux(A), Q in aux(B) (the image of B at n).
+* D(A,B,n): [i][j].
+* blocks are stored back to back in pair-list order.
+
+Generators (per the workload definitions):
+* C amplitude N(0,1) * exp(-0.8 r_AB) (r in bohr), drawn for representative
+  pairs and mirrored; on-site blocks symmetric in (i, j).
+* V_PQ = [erf(R/g1) - erf(R/g2)] / R with g1 = sqrt(2(sP^2 + sQ^2)),
+  g2 = sqrt(g1^2 + 1/omega^2); series at small R (limit 2/sqrt(pi)(1/g1 - 1/g2)).
+* D = 2 sum_m c_m c_m^T over localised orbitals: coefficients
+  N(0,1) * exp(-r) on every basis function of the atoms within 4 A of the
+  orbital centre (nearest image), normalised to unit 2-norm.
+"""
+import math
+import numpy as np
+from scipy.special import erf
+
+from . import rng
+from .systems import OMEGA, ang2bohr, D_SUPPORT_ANGSTROM
+
+KEY_SHIFT_A = 44
+KEY_SHIFT_B = 24
+
+
+def pack_key(A, B, n):
+    n = np.asarray(n, dtype=np.int64)
+    return ((np.asarray(A, np.int64) << KEY_SHIFT_A) | (np.asarray(B, np.int64) << KEY_SHIFT_B)
+            | ((n[..., 0] + 128) << 16) | ((n[..., 1] + 128) << 8) | (n[..., 2] + 128))
+
+
+def unpack_key(k):
+    k = np.asarray(k, dtype=np.int64)
+    A = (k >> KEY_SHIFT_A) & 0xFFFFF
+    B = (k >> KEY_SHIFT_B) & 0xFFFFF
+    n = np.stack([((k >> 16) & 0xFF) - 128, ((k >> 8) & 0xFF) - 128, (k & 0xFF) - 128], axis=-1)
+    return A.astype(np.int32), B.astype(np.int32), n.astype(np.int32)
+
+
+def image_range(system):
+    """Largest |n_i| that can bring two atoms within the cutoff.
+
+    With h_i the spacing of lattice planes and w_i the spread of the atoms'
+    fractional coordinates along i, a pair at image n is at least
+    (|n_i| - w_i) h_i apart, so |n_i| <= floor(cutoff / h_i + w_i).
+    """
+    a = np.asarray(system.cell)
+    vol = abs(np.linalg.det(a))
+    h = np.array([vol / np.linalg.norm(np.cross(a[1], a[2])),
+                  vol / np.linalg.norm(np.cross(a[2], a[0])),
+                  vol / np.linalg.norm(np.cross(a[0], a[1]))])
+    frac = system.xyz @ np.linalg.inv(a)
+    w = frac.max(axis=0) - frac.min(axis=0)
+    return np.floor(system.cutoff / h + w).astype(int)
+
+
+def _is_rep(A, B, n):
+    npos = (n[:, 0] > 0) | ((n[:, 0] == 0) & ((n[:, 1] > 0) | ((n[:, 1] == 0) & (n[:, 2] > 0))))
+    return (A < B) | ((A == B) & npos)
+
+
+def _d2(xyz, cell, A, B, n):
+    """Squared distance in the exact operation order shared by all pair builders."""
+    if cell is None:
+        s = np.zeros((len(A), 3))
+    else:
+        nn = n.astype(np.float64)
+        s = (nn[:, 0:1] * cell[0][None, :] + nn[:, 1:2] * cell[1][None, :]) + nn[:, 2:3] * cell[2][None, :]
+    dx = (xyz[B] + s) - xyz[A]
+    return (dx[:, 0] * dx[:, 0] + dx[:, 1] * dx[:, 1]) + dx[:, 2] * dx[:, 2]
+
+
+def pair_distance2(system, A, B, n):
+    """d^2 of each pair evaluated in its representative orientation."""
+    A = np.asarray(A); B = np.asarray(B); n = np.asarray(n)
+    rep = _is_rep(A, B, n) | ((A == B) & (n == 0).all(axis=1))
+    Ar = np.where(rep, A, B)
+    Br = np.where(rep, B, A)
+    nr = np.where(rep[:, None], n, -n)
+    return _d2(system.xyz, system.cell, Ar, Br, nr)
+
+
+def pair_list(system):
+    """Sorted canonical pair list: keys, A, B, n.
+
+    Candidates come from a k-d tree over the periodic images (radius padded
+    by 1e-9 relative); every candidate is then decided by the exact d^2 test.
+    """
+    from scipy.spatial import cKDTree
+    nat = system.n_atoms
+    if system.cell is None:
+        if system.cutoff <= 0:
+            A, B = np.meshgrid(np.arange(nat), np.arange(nat), indexing="ij")
+            A = A.ravel(); B = B.ravel()
+            n = np.zeros((len(A), 3), dtype=np.int64)
+        else:
+            tree = cKDTree(system.xyz)
+            cand = tree.query_pairs(system.cutoff * (1 + 1e-9), output_type="ndarray")
+            A = np.concatenate([cand[:, 0], cand[:, 1], np.arange(nat)])
+            B = np.concatenate([cand[:, 1], cand[:, 0], np.arange(nat)])
+            n = np.zeros((len(A), 3), dtype=np.int64)
+            d2 = pair_distance2(system, A, B, n)
+            keep = d2 < system.cutoff * system.cutoff
+            A, B, n = A[keep], B[keep], n[keep]
+    else:
+        if system.cutoff <= 0:
+            raise ValueError("periodic systems need a cutoff")
+        nr = image_range(system)
+        imgs = np.stack(np.meshgrid(*[np.arange(-k, k + 1) for k in nr], indexing="ij"),
+                        axis=-1).reshape(-1, 3)
+        shift = imgs.astype(np.float64) @ system.cell
+        pts = (system.xyz[None, :, :] + shift[:, None, :]).reshape(-1, 3)
+        tree = cKDTree(pts)
+        lists = tree.query_ball_point(system.xyz, system.cutoff * (1 + 1e-9))
+        A = np.repeat(np.arange(nat), [len(l) for l in lists])
+        J = np.concatenate([np.asarray(l, dtype=np.int64) for l in lists])
+        B = J % nat
+        n = imgs[J // nat].astype(np.int64)
+        d2 = pair_distance2(system, A, B, n)
+        keep = d2 < system.cutoff * system.cutoff
+        A, B, n = A[keep], B[keep], n[keep]
+    keys = pack_key(A, B, n)
+    keys = np.unique(keys)
+    A, B, n = unpack_key(keys)
+    return keys, A, B, n
+
+
+def coulomb_sr(R, sP, sQ, omega):
+    """Short-range (erfc-screened) Coulomb interaction of two unit s-Gaussian
+    charges of widths sP, sQ at distance R (bohr); broadcasts."""
+    g1 = np.sqrt(2.0 * (sP * sP + sQ * sQ))
+    g2 = np.sqrt(g1 * g1 + 1.0 / (omega * omega))
+    small = R < 1e-3 * g1
+    Rs = np.where(small, 1.0, R)
+    full = (erf(Rs / g1) - erf(Rs / g2)) / Rs
+    ser = (2.0 / math.sqrt(math.pi)) * ((1.0 / g1 - 1.0 / g2) - (R * R / 3.0) * (1.0 / g1 ** 3 - 1.0 / g2 ** 3))
+    return np.where(small, ser, full)
+
+
+class Packed:
+    """Canonical packed C, V, D plus the pair list they are laid out on."""
+
+    def __init__(self, system, keys, A, B, n):
+        self.system = system
+        self.keys, self.A, self.B, self.n = keys, A, B, n
+        sp = system.species
+        nbA = system.nbas[sp[A]].astype(np.int64); nbB = system.nbas[sp[B]].astype(np.int64)
+        naA = system.naux[sp[A]].astype(np.int64); naB = system.naux[sp[B]].astype(np.int64)
+        self.onsite = (A == B) & (n == 0).all(axis=1)
+        self.sizeC = (naA + np.where(self.onsite, 0, naB)) * nbA * nbB
+        self.sizeV = naA * naB
+        self.sizeD = nbA * nbB
+        self.offC = np.concatenate([[0], np.cumsum(self.sizeC)]).astype(np.int64)
+        self.offV = np.concatenate([[0], np.cumsum(self.sizeV)]).astype(np.int64)
+        self.offD = np.concatenate([[0], np.cumsum(self.sizeD)]).astype(np.int64)
+        self.partner = np.searchsorted(keys, pack_key(B, A, -n))
+        assert (keys[self.partner] == pack_key(B, A, -n)).all(), "pair list not symmetric"
+        self.rep = _is_rep(A, B, n) | self.onsite
+        self.dist = np.sqrt(pair_distance2(system, A, B, n))
+        self.C = None
+        self.V = None
+        self.D = None
+
+    @property
+    def n_pairs(self):
+        return len(self.keys)
+
+    def _groups(self, mask):
+        sp = self.system.species
+        sA = sp[self.A]; sB = sp[self.B]
+        idx = np.nonzero(mask)[0]
+        if len(idx) == 0:
+            return
+        gk = (sA[idx].astype(np.int64) * 64 + sB[idx]) * 2 + self.onsite[idx]
+        for g in np.unique(gk):
+            sel = idx[gk == g]
+            yield int(sA[sel[0]]), int(sB[sel[0]]), bool(self.onsite[sel[0]]), sel
+
+    def gen_C(self):
+        s = self.system
+        C = np.empty(int(self.offC[-1]), dtype=np.float64)
+        for a, b, ons, sel in self._groups(self.rep):
+            nbA, nbB = int(s.nbas[a]), int(s.nbas[b])
+            naA, naB = int(s.naux[a]), int(s.naux[b])
+            rows = naA + (0 if ons else naB)
+            size = rows * nbA * nbB
+            for c0 in range(0, len(sel), max(1, (1 << 24) // size)):
+                ss = sel[c0:c0 + max(1, (1 << 24) // size)]
+                ctr = self.offC[ss][:, None] + np.arange(size)[None, :]
+                blk = rng.normal(s.seed, rng.STREAM_C, ctr) * np.exp(-0.8 * self.dist[ss])[:, None]
+                blk = blk.reshape(len(ss), rows, nbA, nbB)
+                if ons:
+                    iu = np.triu_indices(nbA)
+                    up = blk[:, :, iu[0], iu[1]]
+                    blk[:, :, iu[1], iu[0]] = up
+                C[self.offC[ss][:, None] + np.arange(size)[None, :]] = blk.reshape(len(ss), size)
+                if not ons:
+                    part = self.partner[ss]
+                    pb = np.concatenate([blk[:, naA:], blk[:, :naA]], axis=1).transpose(0, 1, 3, 2)
+                    C[self.offC[part][:, None] + np.arange(size)[None, :]] = pb.reshape(len(ss), size)
+        self.C = C
+        return C
+
+    def gen_V(self):
+        s = self.system
+        V = np.empty(int(self.offV[-1]), dtype=np.float64)
+        for a, b, ons, sel in self._groups(self.rep):
+            blk = coulomb_sr(self.dist[sel][:, None, None], s.sigma[a][None, :, None],
+                             s.sigma[b][None, None, :], OMEGA)
+            na_a, na_b = blk.shape[1], blk.shape[2]
+            V[self.offV[sel][:, None] + np.arange(na_a * na_b)[None, :]] = blk.reshape(len(sel), -1)
+            part = self.partner[sel]
+            V[self.offV[part][:, None] + np.arange(na_a * na_b)[None, :]] = \
+                blk.transpose(0, 2, 1).reshape(len(sel), -1)
+        self.V = V
+        return V
+
+    def orbitals(self):
+        """Support of each orbital: list of (atoms, image vectors, distances in bohr)."""
+        s = self.system
+        rmax = ang2bohr(D_SUPPORT_ANGSTROM)
+        out = []
+        for c in s.orbital_centres:
+            d = s.xyz - s.xyz[c][None, :]
+            if s.cell is None:
+                img = np.zeros((s.n_atoms, 3), dtype=np.int64)
+            else:
+                frac = d @ np.linalg.inv(s.cell)
+                img = -np.rint(frac).astype(np.int64)
+                d = d + img @ s.cell
+            r = np.sqrt((d * d).sum(axis=1))
+            sel = np.nonzero(r <= rmax)[0]
+            out.append((sel, img[sel], r[sel]))
+        return out
+
+    def gen_D(self):
+        s = self.system
+        D = np.zeros(int(self.offD[-1]), dtype=np.float64)
+        nb = s.nbas[s.species].astype(np.int64)
+        dropped = 0
+        for m, (atoms, img, r) in enumerate(self.orbitals()):
+            nbs = nb[atoms]
+            nloc = int(nbs.sum())
+            c = rng.normal(s.seed, rng.STREAM_D, (m << 20) + np.arange(nloc))
+            c = c * np.repeat(np.exp(-r), nbs)
+            c = c / np.linalg.norm(c)
+            na = len(atoms)
+            X, Y = np.meshgrid(np.arange(na), np.arange(na), indexing="ij")
+            keys = pack_key(atoms[X], atoms[Y], img[Y] - img[X])
+            pos = np.minimum(np.searchsorted(self.keys, keys), len(self.keys) - 1)
+            ok = self.keys[pos] == keys
+            dropped += int((~ok).sum())
+            loc = np.concatenate([[0], np.cumsum(nbs)])
+            aof = np.repeat(np.arange(na), nbs)           # atom of each local function
+            iof = np.arange(nloc) - loc[aof]              # index within its atom
+            pr = pos[aof[:, None], aof[None, :]]
+            okr = ok[aof[:, None], aof[None, :]]
+            dst = self.offD[pr] + iof[:, None] * nbs[aof][None, :] + iof[None, :]
+            val = 2.0 * np.outer(c, c)
+            D[dst[okr]] += val[okr]
+        self.D = D
+        self.D_dropped = dropped
+        return D
+
+
+def generate(system, C=True, V=True, D=True):
+    keys, A, B, n = pair_list(system)
+    pk = Packed(system, keys, A, B, n)
+    if C:
+        pk.gen_C()
+    if V:
+        pk.gen_V()
+    if D:
+        pk.gen_D()
+    return pk
