@@ -1,0 +1,299 @@
+#!/usr/bin/env python
+"""Benchmark of the exchange build: K-build time per SCF iteration.
+
+One step = one rix_build_K + rix_energy on the resident inputs of the
+workload (default: the (H2O)64 cluster, 192 atoms, nbasis 1536, 8 A cutoff).
+Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config 1] [--precision fp64|mixed]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on a bounded row sample)
+
+Inputs are synthetic (seeded), larger than L2 (C alone is 0.87 GB for the
+default workload), so no L2 flush is needed between steps.  With N > 1 (one
+process per GPU under torchrun) every rank runs an independent replica of the
+whole build (the build is not sharded across GPUs).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "K-build ms per SCF iteration (rix_build_K + rix_energy)"
+WORKLOAD_NAMES = {
+    0: "(H2O)8 cluster, 24 atoms, nbasis 192, no cutoff",
+    1: "(H2O)64 cluster, 192 atoms, nbasis 1536, 8 A cutoff, tau 1e-10",
+    2: "ice-like periodic, 768 atoms (256 H2O), nbasis 6144, 8 A images",
+    3: "perovskite-like periodic, 1536 atoms, nbasis 24911, 8 A images",
+    4: "ice-like periodic, 3072 atoms (1024 H2O), nbasis 24576, 8 A images",
+}
+STAGE_KERNEL = {"flags": "k_flags", "T": "k_T", "U2": "k_U2", "X12": "k_X12", "Z": "k_Z", "X34": "k_X34",
+                "sym": "k_sym"}
+STAGE_FLOP_INDEX = {"T": 0, "U2": 1, "X12": 2, "Z": 3, "X34": 4}
+# FP64 peak of GB300 (recipe table: FP64 1.25 TFLOP/s), used when no measured FP64 peak exists.
+FP64_PEAK_TFLOPS_NOMINAL = 1.25
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax = float(f[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(system, pk, rows):
+    """Time the FP64 oracle on a row sample; return (seconds, sample FLOPs, full FLOPs, threads)."""
+    from oracle.oracle import Oracle
+    o = Oracle(system)
+    o.set_data(pk.C, pk.V, pk.D)
+    o.kpattern()
+    o.build_K(dry=True)
+    full = o.flops()
+    o.kpattern(rows)
+    t0 = time.perf_counter()
+    o.build_K()
+    dt = time.perf_counter() - t0
+    return dt, o.flops(), full, Oracle.threads()
+
+
+def sample_rows(system, n_mol=1):
+    """A whole molecule (or the first atoms) near the middle of the atom list."""
+    mid = (system.n_atoms // 2) // 3 * 3
+    return list(range(mid, min(system.n_atoms, mid + 3 * n_mol)))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import rix_inputs as ri
+    s = ri.config(args.config)
+    pk = ri.generate(s)
+    rows = sample_rows(s)
+    for _ in range(args.warmup):
+        oracle_sample(s, pk, rows[:1])
+    times, sf, ff, thr = [], 0, 0, 1
+    for _ in range(args.steps):
+        dt, sf, ff, thr = oracle_sample(s, pk, rows)
+        times.append(dt * ff / sf * 1e3)
+    ms = float(np.mean(times))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAMES[args.config], "precision": "fp64", "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": ms, "unit": "ms", "cores": thr, "kind": "oracle",
+                         "sample": f"rows {rows} of {s.n_atoms} ({sf:.3g} of {ff:.3g} FLOP), "
+                                   f"time scaled by the oracle's own FLOP ratio"},
+        "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def run_rix(args):
+    import torch
+    import torch.distributed as dist
+    import rix_inputs as ri
+    from paper_2403_10343_gb300.rix import Exchange
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    s = ri.config(args.config)
+    pk = ri.generate(s)
+    ex = Exchange.from_system(s, precision=args.precision, profile=1)
+    assert np.array_equal(ex.pair_keys(), pk.keys)
+    C = torch.from_numpy(pk.C).to(dev)
+    V = torch.from_numpy(pk.V).to(dev)
+    D = torch.from_numpy(pk.D).to(dev)
+    ex.set_CV(C, V)
+    K = torch.empty(ex.k_elems, dtype=torch.float64, device=dev)
+    Ex = torch.empty(1, dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream()
+
+    def step(Dd):
+        ex.build_K(Dd, K)
+        ex.energy(Dd, K, Ex)
+
+    for _ in range(args.warmup):
+        step(D)
+    torch.cuda.synchronize()
+    ex.stage_times()  # drop the warm-up events
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step(D)
+    e1.record(st)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    stage_ms, nb = ex.stage_times()
+    stage_ms = {k: v / max(1, nb) for k, v in stage_ms.items()}
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+
+    # end to end through the same API with host buffers: D in, K and E_x out, every step
+    Dh = torch.from_numpy(pk.D).pin_memory()
+    Kh = torch.empty(ex.k_elems, dtype=torch.float64).pin_memory()
+    Exh = torch.empty(1, dtype=torch.float64).pin_memory()
+    Dd = torch.empty_like(D)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(args.steps):
+        Dd.copy_(Dh, non_blocking=True)
+        step(Dd)
+        Kh.copy_(K, non_blocking=True)
+        Exh.copy_(Ex, non_blocking=True)
+    e1.record(st)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    ex.stage_times()
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = t.item()
+
+    stats = ex.stats()
+    pk_peaks, src = peaks()
+    dom = max((k for k in stage_ms if k in STAGE_FLOP_INDEX), key=lambda k: stage_ms[k])
+    flops = stats["flops_stage"][STAGE_FLOP_INDEX[dom]]
+    achieved = flops / (stage_ms[dom] * 1e-3) / 1e12
+    if args.precision == "fp64":
+        peak = pk_peaks.get("fp64_tflops", FP64_PEAK_TFLOPS_NOMINAL)
+        roof = {"bound": "alu", "kernel": STAGE_KERNEL[dom], "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "FP64 pipe, nominal (recipe table)" if "fp64_tflops" not in pk_peaks
+                else "FP64 pipe, measured"}
+    else:
+        peak = pk_peaks["bf16_tflops_sustained"]
+        tensor_fl = stats["tensor_flops"] * (stage_ms[dom] / sum(stage_ms.values()))
+        roof = {"bound": "tensor", "kernel": STAGE_KERNEL[dom], "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"bf16 sustained ({src})"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rows = sample_rows(s)
+        dt, sf, ff, thr = oracle_sample(s, pk, rows)
+        cpu = {"value": dt * ff / sf * 1e3, "unit": "ms", "cores": thr, "kind": "oracle",
+               "sample": f"rows {rows} of {s.n_atoms} ({sf:.3g} of {ff:.3g} FLOP, {dt:.1f} s), "
+                         f"scaled to a full build by the oracle's own FLOP ratio"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": ms / world, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16-slices+f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAMES[args.config], "precision": args.precision,
+                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
+            "e2e": {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": int(D.numel() * 8),
+                    "d2h_bytes_per_step": int(K.numel() * 8 + 8)},
+            "gpu_launches": 9 * args.steps,
+            "clocks": clocks,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+            "alg_flops": stats["flops_fp64"],
+            "alg_tflops": stats["flops_fp64"] / (ms * 1e-3) / 1e12,
+            "E_x": Ex.item(),
+        }
+        print(json.dumps(line))
+    ex.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--impl", default="rix", choices=["rix", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        from paper_2403_10343_gb300 import build
+        build.build()
+        run_rix(args)
+
+
+if __name__ == "__main__":
+    main()

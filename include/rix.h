@@ -1,0 +1,178 @@
+/*
+ * rix -- RI-LVL real-space exact-exchange build on one NVIDIA GB300 (sm_103a).
+ *
+ * C ABI of librix.so.  Plain pointers and sizes only; no C++ or framework
+ * types cross this boundary.  Every entry point returns a rix_status and
+ * never aborts; device-side work is enqueued on the caller's CUDA stream and
+ * the compute entry points never synchronise the host.
+ *
+ * The operation (Kokott et al., arXiv:2403.10343, Sec. "Description of the
+ * real-space formalism", Eq. 117-121 with the RI-LVL restriction Eq. 127-135):
+ *
+ *   K_il(n) = sum_{jk} sum_{PQ} C^P_ij V_PQ C^Q_kl D_jk
+ *   E_x     = -1/4 sum_il D_li K_il            (-1/4 Tr(D K), one cell)
+ *
+ * i is a basis function of atom A in cell 0, l of atom E in cell n; P is an
+ * auxiliary function on the atom of i or of j, Q on the atom of k or of l.
+ *
+ * ---------------------------------------------------------------------------
+ * Block-sparse packed format (shared by C, V, D, K and the gradients)
+ * ---------------------------------------------------------------------------
+ * A pair (A, B, n1, n2, n3) joins atom A in cell 0 to atom B in cell
+ * n = n1 a1 + n2 a2 + n3 a3.  The pair list holds every pair with
+ * |x_B + n - x_A| < cutoff (every pair at n = 0 when cutoff <= 0, cluster only),
+ * sorted lexicographically by (A, B, n1, n2, n3), and is exactly symmetric:
+ * the distance is evaluated in the orientation with A < B (or A == B and
+ * n > 0 lexicographically) as dx_c = (x_B,c + s_c) - x_A,c with
+ * s_c = (n1 a1_c + n2 a2_c) + n3 a3_c and d^2 = (dx_0^2 + dx_1^2) + dx_2^2,
+ * without fused multiply-add.
+ *
+ *   C(A,B,n): [P][i][j] row-major, P over aux(A) then aux(B) (aux(A) only for
+ *             the on-site pair A == B, n == 0); i in basis(A), j in basis(B).
+ *             Must satisfy C(B,A,-n)[P][j][i] == C(A,B,n)[P][i][j] bit for bit
+ *             (the translational/pair symmetry the paper uses, Eq. 157-181).
+ *   V(A,B,n): [P][Q], P in aux(A), Q in aux(B at n); V(B,A,-n) = V(A,B,n)^T.
+ *   D(A,B,n): [i][j]; D(B,A,-n) = D(A,B,n)^T (not checked).
+ *   K(A,E,n): [i][l] on the K pattern: every (A, E, n) reachable from A by at
+ *             most three pair hops (the reach of the four RI-LVL terms).
+ *
+ * Blocks are stored back to back in list order; rix_layout returns each
+ * list's keys and element offsets.  A key packs (A, B, n) as
+ * A << 44 | B << 24 | (n1+128) << 16 | (n2+128) << 8 | (n3+128).
+ *
+ * Input screening (paper Sec. "Initialization": compression of C and V
+ * below 1e-10; Sec. "Evaluation of the EXX matrix": norm screening): a C,
+ * V or D block whose largest |element| is below screen_tau contributes zero.
+ *
+ * Ownership: host arrays passed to rix_setup are copied.  Device buffers
+ * passed to rix_set_CV are copied into library-owned storage.  D, K, E_x and
+ * gradient buffers are caller-owned device memory that must stay valid until
+ * the enqueued work has finished on the stream.  Everything else (pair lists,
+ * plans, workspaces) is owned by the context and freed by rix_destroy.
+ */
+#ifndef RIX_H
+#define RIX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rix_ctx rix_ctx;
+
+typedef enum {
+  RIX_OK = 0,
+  RIX_EINVAL = 1,        /* bad argument or inconsistent sizes */
+  RIX_ENOMEM = 2,        /* device or host allocation failed, or plan exceeds the memory limit */
+  RIX_ECUDA = 3,         /* a CUDA call failed; rix_last_error() has the message */
+  RIX_ENOTSYM = 4,       /* C or V violates the pair symmetry */
+  RIX_ETIMEOUT = 5,      /* a bounded device wait ran out */
+  RIX_EUNSUPPORTED = 6,  /* valid request this build does not support */
+  RIX_ESTATE = 7         /* call out of order (e.g. build before set_CV) */
+} rix_status;
+
+typedef enum {
+  RIX_FP64 = 0,          /* every product and sum in IEEE double */
+  RIX_MIXED_BF16 = 1     /* tensor-core products on error-free BF16 slices, FP64 sums */
+} rix_precision;
+
+/* Lists returned by rix_layout: the pair list with the C, V or D element
+ * offsets, or the K list with the K offsets. */
+enum { RIX_LIST_C = 0, RIX_LIST_V = 1, RIX_LIST_D = 2, RIX_LIST_K = 3 };
+
+typedef struct {
+  int32_t n_atoms;
+  const double *xyz_bohr;          /* [n_atoms][3], host */
+  const int32_t *species;          /* [n_atoms] species index, host */
+  int32_t n_species;
+  const int32_t *nbas_per_species; /* [n_species] basis functions (1..64) */
+  const int32_t *naux_per_species; /* [n_species] aux functions (1..256) */
+  const double *cell_bohr;         /* [3][3] rows = lattice vectors; NULL = cluster */
+  double cutoff_bohr;              /* pair cutoff; <= 0 = all pairs (cluster only) */
+  double screen_tau;               /* block screening threshold; <= 0 = none */
+} rix_system;
+
+typedef struct {
+  int32_t precision;               /* rix_precision */
+  int32_t n_slices;                /* mixed mode: BF16 slices per operand (0 = default) */
+  int64_t max_workspace_bytes;     /* 0 = no limit beyond the device's free memory */
+  int32_t verbose;                 /* 0 = silent */
+  int32_t profile;                 /* 1 = record a CUDA event after every stage of rix_build_K */
+} rix_options;
+
+typedef struct {
+  int64_t n_atoms, n_pairs, n_pairs2, n_kblocks;
+  int64_t c_elems, v_elems, d_elems, k_elems;
+  double flops_fp64;               /* algorithmic FLOPs of one rix_build_K (unpadded products) */
+  double flops_stage[6];           /* T, U2, X12 (terms 1+2), Z (term 4), X34, symmetrise */
+  double min_bytes;                /* 8 (nnz C + V + D) + 8 nnz K */
+  double tensor_flops;             /* mixed mode: tensor-core FLOPs issued per build */
+  int64_t workspace_bytes;         /* library-owned device memory */
+} rix_stats_t;
+
+/* Set up a system: copies the host arrays, builds the pair list on the device
+ * (a1: cutoff over image-resolved pairs), derives the 2- and 3-hop lists and
+ * the product plan, and allocates workspaces.  Synchronous.  Errors: EINVAL
+ * (sizes, species tables, periodic without cutoff, images beyond +-127),
+ * ENOMEM, ECUDA.  On error *out is NULL. */
+rix_status rix_setup(const rix_system *sys, const rix_options *opt, rix_ctx **out);
+
+/* Host views of a list: number of blocks, keys [n] and element offsets [n+1]
+ * (block b occupies [offsets[b], offsets[b+1]) of the packed array).  which
+ * is one of RIX_LIST_C/V/D (same keys, per-array offsets) or RIX_LIST_K.
+ * The arrays belong to the context and live until rix_destroy. */
+rix_status rix_layout(const rix_ctx *ctx, int32_t which, int64_t *n_blocks,
+                      const int64_t **keys, const int64_t **offsets);
+
+/* Element counts of the packed C, V, D and K arrays. */
+rix_status rix_layout_sizes(const rix_ctx *ctx, int64_t *c_elems, int64_t *v_elems,
+                            int64_t *d_elems, int64_t *k_elems);
+
+/* Load C and V (device pointers, packed format, FP64).  Copies them into
+ * library storage, checks the pair symmetry of C and V (ENOTSYM), computes
+ * the screening flags and, in mixed mode, the BF16 slices.  Enqueued on
+ * `stream` (cudaStream_t, NULL = legacy default stream); synchronises the
+ * stream once to read the symmetry verdict. */
+rix_status rix_set_CV(rix_ctx *ctx, const double *C_dev, const double *V_dev, void *stream);
+
+/* K = exchange matrix of D (device, packed, FP64) into K_dev (device, packed
+ * on the K list, FP64, fully overwritten).  Asynchronous on `stream`; no host
+ * synchronisation, no allocation; may be captured in a CUDA graph once one
+ * call has completed.  ESTATE before rix_set_CV. */
+rix_status rix_build_K(rix_ctx *ctx, const double *D_dev, double *K_dev, void *stream);
+
+/* *Ex_dev = -1/4 sum over the D pattern of <D(E,A,-n), K(A,E,n)>_F, a
+ * deterministic FP64 tree reduction.  Ex_dev is one device double. */
+rix_status rix_energy(rix_ctx *ctx, const double *D_dev, const double *K_dev,
+                      double *Ex_dev, void *stream);
+
+/* Adjoint of E_x scaled by gEx (host scalar): dD_dev [d_elems] = gEx * dE/dD
+ * = -gEx K(D)/2 per stored D entry, dC_dev [c_elems] = gEx * dE/dC per stored
+ * C entry, dV_dev [v_elems] = gEx * dE/dV per stored V entry (partials with
+ * every stored entry an independent variable; symmetric partners each carry
+ * their own).  Any output pointer may be NULL to skip it.  Intermediates are
+ * recomputed, not stored.  Asynchronous. */
+rix_status rix_backward(rix_ctx *ctx, const double *D_dev, double gEx,
+                        double *dD_dev, double *dC_dev, double *dV_dev, void *stream);
+
+/* Gamma-point fold of an image-resolved K: Kdense[I][L] = sum_n K(A,E,n)[i][l]
+ * (I, L global basis indices), row-major nbasis x nbasis.  Asynchronous. */
+rix_status rix_fold_gamma(rix_ctx *ctx, const double *K_dev, double *Kdense_dev, void *stream);
+
+rix_status rix_stats(const rix_ctx *ctx, rix_stats_t *out);
+
+/* Device time of each stage of rix_build_K (ms), summed over the builds since
+ * the previous call, and the number of builds: ms[0..6] = screening flags,
+ * T, U2, terms 1+2, Z, terms 3+4, symmetrise.  Needs rix_options.profile = 1
+ * (the events are recorded on the build's stream); synchronises on the last
+ * recorded event.  EUNSUPPORTED without profiling. */
+rix_status rix_stage_times(rix_ctx *ctx, double *ms, int32_t n, int32_t *n_builds);
+const char *rix_strerror(rix_status s);
+const char *rix_last_error(const rix_ctx *ctx);
+void rix_destroy(rix_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RIX_H */

@@ -55,6 +55,10 @@ def _load():
             lib.orc_destroy.argtypes = [P]
             lib.orc_threads.restype = ctypes.c_int
             lib.orc_set_terms.argtypes = [P, ctypes.c_int]
+            lib.orc_build_K_ex.restype = ctypes.c_int
+            lib.orc_build_K_ex.argtypes = [P, P, ctypes.c_int]
+            lib.orc_flops.restype = ctypes.c_double
+            lib.orc_flops.argtypes = [P]
             _lib = lib
     return _lib
 
@@ -126,11 +130,16 @@ class Oracle:
         self.lib.orc_kkeys(self.h, _ptr(k))
         return k
 
-    def build_K(self):
+    def build_K(self, dry=False):
+        """K for the rows of the last kpattern(); dry=True only counts the work."""
         K = np.empty(self.lib.orc_ksize(self.h), dtype=np.float64)
-        if self.lib.orc_build_K(self.h, _ptr(K)) != 0:
+        if self.lib.orc_build_K_ex(self.h, _ptr(K), 1 if dry else 0) != 0:
             raise RuntimeError("oracle: build_K before set_data/kpattern")
         return K
+
+    def flops(self):
+        """FLOPs (2 per multiply-add) the last build_K did or, dry, would do."""
+        return self.lib.orc_flops(self.h)
 
     def energy(self, K, per_row=False):
         nr = self.system.n_atoms if self._rows is None else len(self._rows)

@@ -109,6 +109,8 @@ typedef struct {
     int nrows; int32_t *rows;
     int64_t nk; uint64_t *kkeys; int64_t *offK; int64_t *krow; /* krow[nrows+1] */
     int terms;  /* bit t-1 enables term t (all four by default) */
+    int dry;    /* 1: count the multiply-adds of a build without doing them */
+    double flops;  /* FLOPs (2 per multiply-add) of the last build */
 } orc;
 
 static inline int NB(const orc *o, int a) { return o->nbs[o->sp[a]]; }
@@ -418,7 +420,7 @@ static int64_t ns_find(const nodestore *s, int atom, int m1, int m2, int m3) {
  *   term 3: Z += V(B,E') S(B,E'),  S^Q_jl = sum_{G'} sum_k D(B,G')_jk C(G',E')^{Q on E'}_kl
  *   term 4: Z += sum_{G' != E'} V(B,G') Y,  Y^Q_jl = sum_k D(B,G')_jk C(G',E')^{Q on G'}_kl
  * (the paper's H = F D and G pieces for P on the second atom). */
-static void build_Z(const orc *o, int b, nodestore *Z) {
+static void build_Z(const orc *o, int b, nodestore *Z, double *fl) {
     int nbB = NB(o, b), naB = NA(o, b);
     nodestore S; ns_init(&S);
     double *Y = NULL; int64_t ycap = 0;
@@ -440,6 +442,8 @@ static void build_Z(const orc *o, int b, nodestore *Z) {
             if ((o->terms & 4) && pbe >= 0 && o->keepV[pbe]) {
                 int64_t so = ns_block(&S, e, m1, m2, m3, (int64_t)naE * nbB * nbE);
                 double *s = S.buf + so;
+                *fl += 2.0 * naE * nbB * nbE * nbG;
+                if (!o->dry)
                 for (int q = 0; q < naE; q++)
                     for (int j = 0; j < nbB; j++)
                         for (int l = 0; l < nbE; l++) {
@@ -453,6 +457,8 @@ static void build_Z(const orc *o, int b, nodestore *Z) {
             if ((o->terms & 8) && !o->onsite[p3] && o->keepV[p2]) {
                 int64_t ysz = (int64_t)naG * nbB * nbE;
                 if (ysz > ycap) { free(Y); ycap = ysz; Y = (double *)malloc(sizeof(double) * ycap); }
+                *fl += 2.0 * naG * nbB * nbE * nbG + 2.0 * naB * nbB * nbE * naG;
+                if (!o->dry)
                 for (int q = 0; q < naG; q++)
                     for (int j = 0; j < nbB; j++)
                         for (int l = 0; l < nbE; l++) {
@@ -463,6 +469,7 @@ static void build_Z(const orc *o, int b, nodestore *Z) {
                         }
                 int64_t zo = ns_block(Z, e, m1, m2, m3, (int64_t)naB * nbB * nbE);
                 double *z = Z->buf + zo;
+                if (!o->dry)
                 for (int pp = 0; pp < naB; pp++)
                     for (int j = 0; j < nbB; j++)
                         for (int l = 0; l < nbE; l++) {
@@ -483,6 +490,8 @@ static void build_Z(const orc *o, int b, nodestore *Z) {
         const double *s = S.buf + S.off[id];
         int64_t zo = ns_block(Z, e, m[0], m[1], m[2], (int64_t)naB * nbB * nbE);
         double *z = Z->buf + zo;
+        *fl += 2.0 * naB * nbB * nbE * naE;
+        if (!o->dry)
         for (int pp = 0; pp < naB; pp++)
             for (int j = 0; j < nbB; j++)
                 for (int l = 0; l < nbE; l++) {
@@ -506,7 +515,7 @@ static int64_t kfind(const orc *o, int64_t lo, int64_t hi, uint64_t key) {
 }
 
 /* ---------------------------------------------------------- one K row */
-static void k_row(const orc *o, int r, nodestore *Zs, const uint8_t *haveZ, double *K) {
+static void k_row(const orc *o, int r, nodestore *Zs, const uint8_t *haveZ, double *K, double *fl) {
     int a = o->rows[r];
     int nbA = NB(o, a), naA = NA(o, a);
     int64_t k0 = o->krow[r], k1 = o->krow[r + 1];
@@ -526,6 +535,8 @@ static void k_row(const orc *o, int r, nodestore *Zs, const uint8_t *haveZ, doub
             const double *Dbg = o->D + o->offD[p2];
             int64_t to = ns_block(&T, g, n1[0] + n2[0], n1[1] + n2[1], n1[2] + n2[2], (int64_t)naA * nbA * nbG);
             double *t = T.buf + to;
+            *fl += 2.0 * naA * nbA * nbG * nbB;
+            if (!o->dry)
             for (int pp = 0; pp < naA; pp++)
                 for (int i = 0; i < nbA; i++)
                     for (int k = 0; k < nbG; k++) {
@@ -550,6 +561,8 @@ static void k_row(const orc *o, int r, nodestore *Zs, const uint8_t *haveZ, doub
             int64_t sz = (int64_t)naG * nbA * nbG;
             if (sz > u2cap) { free(U2); u2cap = sz; U2 = (double *)malloc(sizeof(double) * sz); }
             const double *Vag = o->V + o->offV[pag];
+            *fl += 2.0 * naG * nbA * nbG * naA;
+            if (!o->dry)
             for (int q = 0; q < naG; q++)
                 for (int i = 0; i < nbA; i++)
                     for (int k = 0; k < nbG; k++) {
@@ -572,6 +585,8 @@ static void k_row(const orc *o, int r, nodestore *Zs, const uint8_t *haveZ, doub
                 int64_t sz = (int64_t)naE * nbA * nbG;
                 if (sz > u1cap) { free(U1); u1cap = sz; U1 = (double *)malloc(sizeof(double) * sz); }
                 const double *Vae = o->V + o->offV[pae];
+                *fl += 2.0 * naE * nbA * nbG * naA + 2.0 * nbA * nbE * naE * nbG;
+                if (!o->dry)
                 for (int q = 0; q < naE; q++)
                     for (int i = 0; i < nbA; i++)
                         for (int k = 0; k < nbG; k++) {
@@ -581,6 +596,7 @@ static void k_row(const orc *o, int r, nodestore *Zs, const uint8_t *haveZ, doub
                             U1[((int64_t)q * nbA + i) * nbG + k] = acc;
                         }
                 int qE0 = o->onsite[p3] ? 0 : naG;
+                if (!o->dry)
                 for (int i = 0; i < nbA; i++)
                     for (int l = 0; l < nbE; l++) {
                         double acc = 0;
@@ -592,6 +608,8 @@ static void k_row(const orc *o, int r, nodestore *Zs, const uint8_t *haveZ, doub
             }
             /* term 2: P on A, Q on G' != E' */
             if (have2 && !o->onsite[p3]) {
+                *fl += 2.0 * nbA * nbE * naG * nbG;
+                if (!o->dry)
                 for (int i = 0; i < nbA; i++)
                     for (int l = 0; l < nbE; l++) {
                         double acc = 0;
@@ -618,6 +636,8 @@ static void k_row(const orc *o, int r, nodestore *Zs, const uint8_t *haveZ, doub
             int nbE = NB(o, e);
             const double *z = Z->buf + Z->off[id];
             double *kb = K + o->offK[KBLOCK(e, n1[0] + m[0], n1[1] + m[1], n1[2] + m[2])];
+            *fl += 2.0 * nbA * nbE * naB * nbB;
+            if (!o->dry)
             for (int i = 0; i < nbA; i++)
                 for (int l = 0; l < nbE; l++) {
                     double acc = 0;
@@ -631,10 +651,12 @@ static void k_row(const orc *o, int r, nodestore *Zs, const uint8_t *haveZ, doub
 #undef KBLOCK
 }
 
-/* Exchange matrix rows for the pattern set by orc_kpattern; K is [ksize]. */
-int orc_build_K(void *h, double *K) {
+/* Exchange matrix rows for the pattern set by orc_kpattern; K is [ksize].
+ * With dry = 1 the loops only count their multiply-adds (K is left zero). */
+int orc_build_K_ex(void *h, double *K, int dry) {
     orc *o = (orc *)h;
     if (!o->C || !o->kkeys) return -1;
+    o->dry = dry;
     memset(K, 0, sizeof(double) * o->offK[o->nk]);
     /* Z(B;.) for every B adjacent to a selected row */
     uint8_t *need = (uint8_t *)calloc(o->nat, 1);
@@ -643,18 +665,23 @@ int orc_build_K(void *h, double *K) {
         for (int64_t p = o->rowptr[a]; p < o->rowptr[a + 1]; p++) need[o->pB[p]] = 1;
     }
     nodestore *Zs = (nodestore *)calloc(o->nat, sizeof(nodestore));
-    #pragma omp parallel for schedule(dynamic, 1)
+    double fl = 0;
+    #pragma omp parallel for schedule(dynamic, 1) reduction(+ : fl)
     for (int b = 0; b < o->nat; b++) {
         if (!need[b]) continue;
         ns_init(&Zs[b]);
-        build_Z(o, b, &Zs[b]);
+        build_Z(o, b, &Zs[b], &fl);
     }
-    #pragma omp parallel for schedule(dynamic, 1)
-    for (int r = 0; r < o->nrows; r++) k_row(o, r, Zs, need, K);
+    #pragma omp parallel for schedule(dynamic, 1) reduction(+ : fl)
+    for (int r = 0; r < o->nrows; r++) k_row(o, r, Zs, need, K, &fl);
     for (int b = 0; b < o->nat; b++) if (need[b]) ns_free(&Zs[b]);
     free(Zs); free(need);
+    o->flops = fl;
+    o->dry = 0;
     return 0;
 }
+int orc_build_K(void *h, double *K) { return orc_build_K_ex(h, K, 0); }
+double orc_flops(void *h) { return ((orc *)h)->flops; }
 
 /* Per-row energy contributions e_r = -1/4 sum_{l} sum_{i in row atom} D_li K_il,
  * D_li taken from the block D(E,A,-n) (the transpose partner of D(A,E,n));

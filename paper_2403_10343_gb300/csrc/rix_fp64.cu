@@ -1,0 +1,622 @@
+// FP64 path of the exchange build and the shared small kernels.
+//
+// The build runs the paper's grouping of the RI-LVL sum by the atoms that
+// carry the two auxiliary functions (Eq. 157-172).  With i on A, j on B',
+// k on G', l on E' it computes
+//
+//   T(A,G')   = sum_B' C(A,B')^{P on A} D(B',G')                (E = C*D)
+//   U2(A,G')  = V(A,G')^T T(A,G')                               (G = E'*V)
+//   X(A,E')   = 1/2 sum_G' [V(A,E')^T T(A,G')]^{Q on E'} C(G',E')^{Q on E'}   term 1
+//             +     sum_G'!=E' U2(A,G') C(G',E')^{Q on G'}                     term 2
+//   Z(B,E')   = 1/2 sum_G'!=E' [V(B,G') C(G',E')^{Q on G'}] applied to D(B,G') (H = F*D)
+//   X(A,E')  +=     sum_B'!=A C(A,B')^{P on B'} Z(B,E')                        term 4
+//   K(A,E',n) = X(A,E',n) + X(E',A,-n)^T
+//
+// Term 3 (P on B', Q on E') equals term 2 transposed (the pair symmetry of C,
+// V and D, Eq. 181; the paper's "2G"), and terms 1 and 4 are symmetric by
+// themselves, so the last line restores all four terms exactly.
+//
+// Each kernel is output-stationary: one CTA owns an output block (or a row
+// tile of it), walks its product list and keeps the sums in registers, so no
+// atomics are needed and every run sums in the same order.
+#include <cstdio>
+
+#include "rix_internal.h"
+
+using namespace rix;
+
+namespace {
+
+constexpr int NT = 256;      // threads per CTA
+constexpr int MAXE = 32;     // output elements per thread in tiled kernels (NT * MAXE = 8192)
+constexpr int XMAXE = 16;    // output elements per thread for K blocks (64 x 64 / 256)
+constexpr int SM_BIG = 12288;  // doubles of dynamic shared memory for stage tiles (96 KB)
+
+// ------------------------------------------------------------------ pair list (a1)
+__device__ __forceinline__ double d2_raw(const double *xyz, const double *cell, int periodic, int a, int b,
+                                         int n1, int n2, int n3) {
+  double s[3] = {0.0, 0.0, 0.0};
+  if (periodic) {
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+      s[c] = __dadd_rn(__dadd_rn(__dmul_rn((double)n1, cell[c]), __dmul_rn((double)n2, cell[3 + c])),
+                       __dmul_rn((double)n3, cell[6 + c]));
+  }
+  double dx[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) dx[c] = __dsub_rn(__dadd_rn(xyz[3 * b + c], s[c]), xyz[3 * a + c]);
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx[0], dx[0]), __dmul_rn(dx[1], dx[1])), __dmul_rn(dx[2], dx[2]));
+}
+
+__device__ __forceinline__ bool is_rep(int a, int b, int n1, int n2, int n3) {
+  if (a != b) return a < b;
+  if (n1 != 0) return n1 > 0;
+  if (n2 != 0) return n2 > 0;
+  return n3 >= 0;
+}
+
+// One warp per atom A; candidates (B, n1, n2, n3) in lexicographic order, so
+// the kept pairs come out sorted.  Pass 1 counts, pass 2 writes the keys.
+__global__ void k_pairs(int nat, const double *xyz, const double *cell, int periodic, int nr0, int nr1,
+                        int nr2, double rc2, int cut, int64_t *counts, const int64_t *rowptr, int64_t *keys) {
+  int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  int lane = threadIdx.x & 31;
+  if (warp >= nat) return;
+  const int a = warp;
+  const int N1 = 2 * nr0 + 1, N2 = 2 * nr1 + 1, N3 = 2 * nr2 + 1;
+  const int64_t total = (int64_t)nat * N1 * N2 * N3;
+  int64_t pos = rowptr ? rowptr[a] : 0;
+  int64_t cnt = 0;
+  for (int64_t base = 0; base < total; base += 32) {
+    int64_t c = base + lane;
+    bool keep = false;
+    int b = 0, n1 = 0, n2 = 0, n3 = 0;
+    if (c < total) {
+      int64_t r = c;
+      n3 = (int)(r % N3) - nr2; r /= N3;
+      n2 = (int)(r % N2) - nr1; r /= N2;
+      n1 = (int)(r % N1) - nr0; r /= N1;
+      b = (int)r;
+      if (!cut) {
+        keep = true;
+      } else {
+        double d2 = is_rep(a, b, n1, n2, n3) ? d2_raw(xyz, cell, periodic, a, b, n1, n2, n3)
+                                             : d2_raw(xyz, cell, periodic, b, a, -n1, -n2, -n3);
+        keep = d2 < rc2;
+      }
+    }
+    unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (keys && keep) keys[pos + __popc(m & ((1u << lane) - 1u))] = pair_key(a, b, n1, n2, n3);
+    pos += __popc(m);
+    cnt += __popc(m);
+  }
+  if (counts && lane == 0) counts[a] = cnt;
+}
+
+// ------------------------------------------------------------------ screening flags
+// keep[b] = max |block b| >= tau (always 1 when tau <= 0); one warp per block.
+__global__ void k_flags(const double *arr, const int64_t *off, int64_t n, double tau, uint8_t *keep) {
+  int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  if (!(tau > 0)) {
+    if (lane == 0) keep[w] = 1;
+    return;
+  }
+  double m = 0;
+  for (int64_t i = off[w] + lane; i < off[w + 1]; i += 32) m = fmax(m, fabs(arr[i]));
+  for (int s = 16; s; s >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, s));
+  if (lane == 0) keep[w] = m >= tau;
+}
+
+// ------------------------------------------------------------------ symmetry check of C and V
+// C(B,A,-n)[P'][j][i] == C(A,B,n)[P][i][j] with P' the same aux function, and
+// V(B,A,-n) == V(A,B,n)^T, bit for bit.  One warp per pair; sets *flag on a mismatch.
+__global__ void k_symcheck(int64_t np, const int32_t *pA, const int32_t *pB, const int32_t *partner,
+                           const uint8_t *onsite, const int32_t *nb, const int32_t *na, const double *C,
+                           const int64_t *offC, const double *V, const int64_t *offV, int32_t *flag) {
+  int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (p >= np) return;
+  int a = pA[p], b = pB[p];
+  int64_t q = partner[p];
+  int nbA = nb[a], nbB = nb[b], naA = na[a], naB = na[b];
+  bool bad = false;
+  const double *c = C + offC[p], *cq = C + offC[q];
+  int rows = naA + (onsite[p] ? 0 : naB);
+  int64_t n = (int64_t)rows * nbA * nbB;
+  for (int64_t e = lane; e < n; e += 32) {
+    int P = (int)(e / (nbA * nbB));
+    int r = (int)(e % (nbA * nbB));
+    int i = r / nbB, j = r % nbB;
+    int Pq = onsite[p] ? P : (P < naA ? P + naB : P - naA);
+    if (c[e] != cq[((int64_t)Pq * nbB + j) * nbA + i]) bad = true;
+  }
+  const double *v = V + offV[p], *vq = V + offV[q];
+  for (int e = lane; e < naA * naB; e += 32) {
+    int P = e / naB, Q = e % naB;
+    if (v[e] != vq[Q * naA + P]) bad = true;
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1);
+}
+
+// ------------------------------------------------------------------ stage T
+// T(A,G')[P][i][k] for P in [p0, p0+pt): sum over (C(A,B'), D(B',G')) entries.
+__global__ void __launch_bounds__(NT) k_T(const int2 *items, const int64_t *ptrT, const int2 *LT,
+                                          const int32_t *atomA2, const int32_t *atomB2, const int64_t *off2,
+                                          const int32_t *pB, const int32_t *nb, const int32_t *na,
+                                          const double *__restrict__ C, const int64_t *offC,
+                                          const double *__restrict__ D, const int64_t *offD,
+                                          const uint8_t *keepC, const uint8_t *keepD, double *T) {
+  extern __shared__ double sm[];
+  const int tid = threadIdx.x;
+  const int2 it = items[blockIdx.x];
+  const int t = it.x, p0 = it.y;
+  const int a = atomA2[t], g = atomB2[t];
+  const int nbA = nb[a], naA = na[a], nbG = nb[g];
+  const int per = nbA * nbG;
+  const int pt = max(1, NT * MAXE / per);
+  const int pe = min(naA, p0 + pt);
+  const int nel = (pe - p0) * per;
+  double acc[MAXE];
+#pragma unroll
+  for (int r = 0; r < MAXE; r++) acc[r] = 0.0;
+  for (int64_t e = ptrT[t]; e < ptrT[t + 1]; e++) {
+    const int2 en = LT[e];
+    if (!keepC[en.x] || !keepD[en.y]) continue;
+    const int nbB = nb[pB[en.x]];
+    const double *Dg = D + offD[en.y];
+    __syncthreads();
+    for (int i = tid; i < nbB * nbG; i += NT) sm[i] = Dg[i];
+    __syncthreads();
+    const double *Cr = C + offC[en.x] + (int64_t)p0 * nbA * nbB;
+#pragma unroll
+    for (int r = 0; r < MAXE; r++) {
+      const int el = tid + r * NT;
+      if (el < nel) {
+        const int row = el / nbG, col = el - row * nbG;
+        const double *cr = Cr + (int64_t)row * nbB;
+        double s = acc[r];
+        for (int j = 0; j < nbB; j++) s = fma(__ldg(cr + j), sm[j * nbG + col], s);
+        acc[r] = s;
+      }
+    }
+  }
+  double *out = T + off2[t] + (int64_t)p0 * per;
+#pragma unroll
+  for (int r = 0; r < MAXE; r++) {
+    const int el = tid + r * NT;
+    if (el < nel) out[el] = acc[r];
+  }
+}
+
+// ------------------------------------------------------------------ stage U2
+// U2(A,G')[Q][i][k] = sum_P V(A,G')[P][Q] T(A,G')[P][i][k] for Q in [q0, q0+qt).
+__global__ void __launch_bounds__(NT) k_U2(const int2 *items, const int32_t *pA, const int32_t *pB,
+                                           const int32_t *nb, const int32_t *na, const double *__restrict__ V,
+                                           const int64_t *offV, const uint8_t *keepV, const int32_t *map1to2,
+                                           const double *__restrict__ T, const int64_t *off2,
+                                           const int64_t *offU, double *U) {
+  const int2 it = items[blockIdx.x];
+  const int p = it.x, q0 = it.y;
+  if (!keepV[p]) return;
+  const int a = pA[p], g = pB[p];
+  const int nbA = nb[a], naA = na[a], nbG = nb[g], naG = na[g];
+  const int per = nbA * nbG;
+  const int qt = max(1, NT * MAXE / per);
+  const int qe = min(naG, q0 + qt);
+  const int nel = (qe - q0) * per;
+  const double *Vb = V + offV[p];
+  const double *Tt = T + off2[map1to2[p]];
+  double *out = U + offU[p] + (int64_t)q0 * per;
+  for (int el = threadIdx.x; el < nel; el += NT) {
+    const int q = q0 + el / per, c = el % per;
+    double s = 0.0;
+    for (int P = 0; P < naA; P++) s = fma(__ldg(Vb + P * naG + q), __ldg(Tt + (int64_t)P * per + c), s);
+    out[el] = s;
+  }
+}
+
+// ------------------------------------------------------------------ terms 1 and 2
+__global__ void __launch_bounds__(NT) k_X12(const int32_t *ord, const int64_t *ptr, const X12Entry *L,
+                                            const int32_t *atomA2, const int32_t *atomB2,
+                                            const int32_t *map2to1, const int32_t *map2to3,
+                                            const int32_t *pA, const uint8_t *onsite, const int32_t *nb,
+                                            const int32_t *na, const double *__restrict__ C,
+                                            const int64_t *offC, const double *__restrict__ V,
+                                            const int64_t *offV, const uint8_t *keepC, const uint8_t *keepV,
+                                            const double *__restrict__ T, const int64_t *off2,
+                                            const double *__restrict__ U, const int64_t *offU,
+                                            const int64_t *offK, double *X) {
+  extern __shared__ double sm[];
+  const int tid = threadIdx.x;
+  const int s = ord[blockIdx.x];
+  const int a = atomA2[s], e = atomB2[s];
+  const int nbA = nb[a], naA = na[a], nbE = nb[e], naE = na[e];
+  const int nel = nbA * nbE;
+  const int pae = map2to1[s];
+  const bool has1 = pae >= 0 && keepV[pae];
+  double acc[XMAXE];
+#pragma unroll
+  for (int r = 0; r < XMAXE; r++) acc[r] = 0.0;
+  for (int64_t it = ptr[s]; it < ptr[s + 1]; it++) {
+    const X12Entry en = L[it];
+    if (!keepC[en.p3]) continue;
+    const int g = pA[en.p3];
+    const int nbG = nb[g], naG = na[g];
+    const double *Cge = C + offC[en.p3];
+    if (en.t1 && has1) {
+      // term 1: U1[Q][i][k] = sum_P V(A,E')[P][Q] T(A,G')[P][i][k], Q on E', in tiles of Q
+      const int qE0 = onsite[en.p3] ? 0 : naG;
+      const double *Tt = T + off2[en.t];
+      const double *Vae = V + offV[pae];
+      const int per = nbA * nbG;
+      const int qt = min(naE, max(1, SM_BIG / per));
+      for (int q0 = 0; q0 < naE; q0 += qt) {
+        const int qn = min(qt, naE - q0);
+        __syncthreads();
+        for (int el = tid; el < qn * per; el += NT) {
+          const int q = el / per, c = el - q * per;
+          double u = 0.0;
+          for (int P = 0; P < naA; P++) u = fma(__ldg(Vae + P * naE + q0 + q), __ldg(Tt + (int64_t)P * per + c), u);
+          sm[el] = u;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < XMAXE; r++) {
+          const int el = tid + r * NT;
+          if (el < nel) {
+            const int i = el / nbE, l = el - i * nbE;
+            double v = 0.0;
+            for (int q = 0; q < qn; q++) {
+              const double *cq = Cge + ((int64_t)(qE0 + q0 + q) * nbG) * nbE + l;
+              const double *uq = sm + (q * nbA + i) * nbG;
+              for (int k = 0; k < nbG; k++) v = fma(uq[k], __ldg(cq + k * nbE), v);
+            }
+            acc[r] = fma(0.5, v, acc[r]);
+          }
+        }
+      }
+    }
+    if (en.u2 >= 0 && keepV[en.u2]) {
+      // term 2: X += U2(A,G')[Q][i][k] C(G',E')[Q on G'][k][l]
+      const double *U2 = U + offU[en.u2];
+#pragma unroll
+      for (int r = 0; r < XMAXE; r++) {
+        const int el = tid + r * NT;
+        if (el < nel) {
+          const int i = el / nbE, l = el - i * nbE;
+          double v = acc[r];
+          for (int q = 0; q < naG; q++) {
+            const double *cq = Cge + ((int64_t)q * nbG) * nbE + l;
+            const double *uq = U2 + ((int64_t)q * nbA + i) * nbG;
+            for (int k = 0; k < nbG; k++) v = fma(__ldg(uq + k), __ldg(cq + k * nbE), v);
+          }
+          acc[r] = v;
+        }
+      }
+    }
+  }
+  double *out = X + offK[map2to3[s]];
+#pragma unroll
+  for (int r = 0; r < XMAXE; r++) {
+    const int el = tid + r * NT;
+    if (el < nel) out[el] += acc[r];
+  }
+}
+
+// ------------------------------------------------------------------ term 4 intermediate
+// Z(B,E')[P][j][l] = 1/2 sum over (pair (B,G'), pair (G',E') not on-site) of
+//   sum_k D(B,G')[j][k] F[P][k][l],  F[P][k][l] = sum_Q V(B,G')[P][Q] C(G',E')[Q on G'][k][l].
+__global__ void __launch_bounds__(NT) k_Z(const int2 *items, const int64_t *ptrZ, const int2 *LZ,
+                                          const int32_t *atomA2, const int32_t *atomB2, const int64_t *off2,
+                                          const int32_t *pB, const int32_t *nb, const int32_t *na,
+                                          const double *__restrict__ C, const int64_t *offC,
+                                          const double *__restrict__ V, const int64_t *offV,
+                                          const double *__restrict__ D, const int64_t *offD,
+                                          const uint8_t *keepC, const uint8_t *keepV, const uint8_t *keepD,
+                                          double *Z) {
+  extern __shared__ double sm[];
+  const int tid = threadIdx.x;
+  const int2 it = items[blockIdx.x];
+  const int z = it.x, p0 = it.y;
+  const int b = atomA2[z], e = atomB2[z];
+  const int nbB = nb[b], naB = na[b], nbE = nb[e];
+  const int per = nbB * nbE;
+  const int pt = max(1, NT * MAXE / per);
+  const int pe = min(naB, p0 + pt);
+  const int nel = (pe - p0) * per;
+  double acc[MAXE];
+#pragma unroll
+  for (int r = 0; r < MAXE; r++) acc[r] = 0.0;
+  for (int64_t x = ptrZ[z]; x < ptrZ[z + 1]; x++) {
+    const int2 en = LZ[x];
+    if (!keepD[en.x] || !keepV[en.x] || !keepC[en.y]) continue;
+    const int g = pB[en.x];
+    const int nbG = nb[g], naG = na[g];
+    const double *Dbg = D + offD[en.x];
+    const double *Vbg = V + offV[en.x];
+    const double *Cge = C + offC[en.y];
+    const int fper = nbG * nbE;
+    const int ft = max(1, min(pe - p0, SM_BIG / fper));
+    for (int ps = p0; ps < pe; ps += ft) {
+      const int fn = min(ft, pe - ps);
+      __syncthreads();
+      for (int el = tid; el < fn * fper; el += NT) {
+        const int pp = el / fper, c = el - pp * fper;
+        const double *vr = Vbg + (int64_t)(ps + pp) * naG;
+        double f = 0.0;
+        for (int Q = 0; Q < naG; Q++) f = fma(__ldg(vr + Q), __ldg(Cge + (int64_t)Q * fper + c), f);
+        sm[el] = f;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < MAXE; r++) {
+        const int el = tid + r * NT;
+        if (el < nel) {
+          const int P = el / per;               // relative to p0
+          const int pr = P - (ps - p0);
+          if (pr >= 0 && pr < fn) {
+            const int rem = el - P * per;
+            const int j = rem / nbE, l = rem - j * nbE;
+            const double *dj = Dbg + j * nbG;
+            const double *fp = sm + pr * fper + l;
+            double v = acc[r];
+            for (int k = 0; k < nbG; k++) v = fma(__ldg(dj + k), fp[k * nbE], v);
+            acc[r] = v;
+          }
+        }
+      }
+    }
+  }
+  double *out = Z + off2[z] + (int64_t)p0 * per;
+#pragma unroll
+  for (int r = 0; r < MAXE; r++) {
+    const int el = tid + r * NT;
+    if (el < nel) out[el] = 0.5 * acc[r];
+  }
+}
+
+// ------------------------------------------------------------------ term 4 (and term 3 via the transpose)
+// X(A,E') += sum over (C(A,B') not on-site, Z(B,E'')) of C(A,B')[P on B'][i][j] Z[P][j][l].
+__global__ void __launch_bounds__(NT) k_X34(const int32_t *ord, const int64_t *ptr, const int2 *L,
+                                            const int32_t *atomA3, const int32_t *atomB3, const int32_t *pB,
+                                            const int32_t *nb, const int32_t *na,
+                                            const double *__restrict__ C, const int64_t *offC,
+                                            const uint8_t *keepC, const double *__restrict__ Z,
+                                            const int64_t *off2, const int64_t *offK, double *X) {
+  extern __shared__ double sm[];
+  const int tid = threadIdx.x;
+  const int x = ord[blockIdx.x];
+  const int a = atomA3[x], e = atomB3[x];
+  const int nbA = nb[a], naA = na[a], nbE = nb[e];
+  const int nel = nbA * nbE;
+  double acc[XMAXE];
+#pragma unroll
+  for (int r = 0; r < XMAXE; r++) acc[r] = 0.0;
+  for (int64_t it = ptr[x]; it < ptr[x + 1]; it++) {
+    const int2 en = L[it];
+    if (!keepC[en.x]) continue;
+    const int b = pB[en.x];
+    const int nbB = nb[b], naB = na[b];
+    const double *Cb = C + offC[en.x] + (int64_t)naA * nbA * nbB;
+    const double *Zb = Z + off2[en.y];
+    const int csz = nbA * nbB, zsz = nbB * nbE;
+    const int pc = max(1, min(naB, SM_BIG / (csz + zsz)));
+    for (int P0 = 0; P0 < naB; P0 += pc) {
+      const int pn = min(pc, naB - P0);
+      __syncthreads();
+      for (int i = tid; i < pn * csz; i += NT) sm[i] = Cb[(int64_t)P0 * csz + i];
+      for (int i = tid; i < pn * zsz; i += NT) sm[pn * csz + i] = Zb[(int64_t)P0 * zsz + i];
+      __syncthreads();
+      const double *Zs = sm + pn * csz;
+#pragma unroll
+      for (int r = 0; r < XMAXE; r++) {
+        const int el = tid + r * NT;
+        if (el < nel) {
+          const int i = el / nbE, l = el - i * nbE;
+          double v = acc[r];
+          for (int P = 0; P < pn; P++) {
+            const double *cr = sm + (P * nbA + i) * nbB;
+            const double *zr = Zs + P * zsz + l;
+            for (int j = 0; j < nbB; j++) v = fma(cr[j], zr[j * nbE], v);
+          }
+          acc[r] = v;
+        }
+      }
+    }
+  }
+  double *out = X + offK[x];
+#pragma unroll
+  for (int r = 0; r < XMAXE; r++) {
+    const int el = tid + r * NT;
+    if (el < nel) out[el] += acc[r];
+  }
+}
+
+// ------------------------------------------------------------------ K = X + X^T (image flipped)
+__global__ void k_sym(int64_t nk, const int32_t *atomA3, const int32_t *atomB3, const int32_t *partner3,
+                      const int32_t *nb, const int64_t *offK, const double *__restrict__ X, double *K) {
+  const int64_t x = blockIdx.x;
+  if (x >= nk) return;
+  const int nbA = nb[atomA3[x]], nbE = nb[atomB3[x]];
+  const double *xa = X + offK[x], *xb = X + offK[partner3[x]];
+  double *k = K + offK[x];
+  for (int el = threadIdx.x; el < nbA * nbE; el += blockDim.x) {
+    const int i = el / nbE, l = el - i * nbE;
+    k[el] = xa[el] + xb[l * nbA + i];
+  }
+}
+
+// ------------------------------------------------------------------ energy
+// Pair p contributes sum_il D(B,A,-n)[l][i] K(A,B,n)[i][l]; each thread owns
+// one pair, each CTA reduces its 256 pairs in a fixed tree.
+__global__ void k_energy(int64_t np, const int32_t *pA, const int32_t *pB, const int32_t *partner,
+                         const int32_t *map1to3, const int32_t *nb, const double *__restrict__ D,
+                         const int64_t *offD, const uint8_t *keepD, const double *__restrict__ K,
+                         const int64_t *offK, double *part) {
+  __shared__ double red[256];
+  const int64_t p = blockIdx.x * (int64_t)256 + threadIdx.x;
+  double s = 0.0;
+  if (p < np) {
+    const int64_t q = partner[p];
+    if (keepD[q]) {
+      const int nbA = nb[pA[p]], nbB = nb[pB[p]];
+      const double *dq = D + offD[q];
+      const double *kb = K + offK[map1to3[p]];
+      for (int i = 0; i < nbA; i++)
+        for (int l = 0; l < nbB; l++) s = fma(dq[l * nbA + i], kb[i * nbB + l], s);
+    }
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_energy_final(int64_t n, const double *part, double *Ex) {
+  __shared__ double red[1024];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += 1024) s += part[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 512; w; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *Ex = -0.25 * red[0];
+}
+
+// ------------------------------------------------------------------ Gamma fold
+__global__ void k_fold(int64_t ng, const int64_t *fold, const int32_t *atomA3, const int32_t *atomB3,
+                       const int32_t *nb, const int64_t *offK, const int64_t *bofs, int64_t nbasis,
+                       const double *__restrict__ K, double *Kd) {
+  const int64_t gi = blockIdx.x;
+  if (gi >= ng) return;
+  const int64_t x0 = fold[gi], x1 = fold[gi + 1];
+  const int a = atomA3[x0], e = atomB3[x0];
+  const int nbA = nb[a], nbE = nb[e];
+  for (int el = threadIdx.x; el < nbA * nbE; el += blockDim.x) {
+    double s = 0.0;
+    for (int64_t x = x0; x < x1; x++) s += K[offK[x] + el];
+    const int i = el / nbE, l = el - i * nbE;
+    Kd[(bofs[a] + i) * nbasis + bofs[e] + l] = s;
+  }
+}
+
+rix_status last(rix_ctx *ctx, const char *what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    ctx->last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return RIX_ECUDA;
+  }
+  return RIX_OK;
+}
+
+bool g_attr_done = false;
+
+}  // namespace
+
+rix_status rix_launch_pairs(rix_ctx *ctx, const double *d_xyz, const double *d_cell, const int nr[3],
+                            int64_t *d_counts, const int64_t *d_rowptr, int64_t *d_keys, cudaStream_t st) {
+  const int nat = ctx->nat;
+  const int threads = 256;
+  const int64_t blocks = ((int64_t)nat * 32 + threads - 1) / threads;
+  k_pairs<<<(unsigned)blocks, threads, 0, st>>>(nat, d_xyz, d_cell, ctx->periodic ? 1 : 0, nr[0], nr[1], nr[2],
+                                                ctx->rc * ctx->rc, ctx->rc > 0 ? 1 : 0, d_counts, d_rowptr, d_keys);
+  return last(ctx, "k_pairs");
+}
+
+rix_status rix_launch_flags(rix_ctx *ctx, const double *arr, const int64_t *off, int64_t n, uint8_t *keep,
+                            cudaStream_t st) {
+  if (n == 0) return RIX_OK;
+  const int64_t blocks = (n * 32 + 255) / 256;
+  k_flags<<<(unsigned)blocks, 256, 0, st>>>(arr, off, n, ctx->tau, keep);
+  return last(ctx, "k_flags");
+}
+
+rix_status rix_launch_symcheck(rix_ctx *ctx, cudaStream_t st) {
+  RIX_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(int32_t), st));
+  const int64_t blocks = (ctx->np * 32 + 255) / 256;
+  k_symcheck<<<(unsigned)blocks, 256, 0, st>>>(ctx->np, ctx->d_pA, ctx->d_pB, ctx->d_partner1, ctx->d_onsite,
+                                               ctx->d_nb, ctx->d_na, ctx->d_C, ctx->d_offC, ctx->d_V,
+                                               ctx->d_offV, ctx->d_flag);
+  return last(ctx, "k_symcheck");
+}
+
+rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t st) {
+  if (!g_attr_done) {
+    cudaFuncSetAttribute(k_X12, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_BIG * 8);
+    cudaFuncSetAttribute(k_Z, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_BIG * 8);
+    cudaFuncSetAttribute(k_X34, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_BIG * 8);
+    g_attr_done = true;
+  }
+  rix_status s;
+  if ((s = rix_prof_mark(ctx, 0, st)) != RIX_OK) return s;
+  if ((s = rix_launch_flags(ctx, D, ctx->d_offD, ctx->np, ctx->d_keepD, st)) != RIX_OK) return s;
+  if ((s = rix_prof_mark(ctx, 1, st)) != RIX_OK) return s;
+  if (ctx->n_itT) {
+    k_T<<<(unsigned)ctx->n_itT, NT, 64 * 64 * 8, st>>>(
+        ctx->d_itT, ctx->d_ptrT, ctx->d_LT, ctx->d_atomA2, ctx->d_atomB2, ctx->d_off2, ctx->d_pB, ctx->d_nb,
+        ctx->d_na, ctx->d_C, ctx->d_offC, D, ctx->d_offD, ctx->d_keepC, ctx->d_keepD, ctx->d_T);
+    if ((s = last(ctx, "k_T")) != RIX_OK) return s;
+  }
+  if ((s = rix_prof_mark(ctx, 2, st)) != RIX_OK) return s;
+  if (ctx->n_itU) {
+    k_U2<<<(unsigned)ctx->n_itU, NT, 0, st>>>(ctx->d_itU, ctx->d_pA, ctx->d_pB, ctx->d_nb, ctx->d_na, ctx->d_V,
+                                              ctx->d_offV, ctx->d_keepV, ctx->d_map1to2, ctx->d_T, ctx->d_off2,
+                                              ctx->d_offU, ctx->d_U);
+    if ((s = last(ctx, "k_U2")) != RIX_OK) return s;
+  }
+  if ((s = rix_prof_mark(ctx, 3, st)) != RIX_OK) return s;
+  RIX_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_X, 0, sizeof(double) * ctx->offK[ctx->nk], st));
+  if (ctx->n_ordX12) {
+    k_X12<<<(unsigned)ctx->n_ordX12, NT, SM_BIG * 8, st>>>(
+        ctx->d_ordX12, ctx->d_ptrX12, ctx->d_LX12, ctx->d_atomA2, ctx->d_atomB2, ctx->d_map2to1,
+        ctx->d_map2to3, ctx->d_pA, ctx->d_onsite, ctx->d_nb, ctx->d_na, ctx->d_C, ctx->d_offC, ctx->d_V,
+        ctx->d_offV, ctx->d_keepC, ctx->d_keepV, ctx->d_T, ctx->d_off2, ctx->d_U, ctx->d_offU, ctx->d_offK,
+        ctx->d_X);
+    if ((s = last(ctx, "k_X12")) != RIX_OK) return s;
+  }
+  if ((s = rix_prof_mark(ctx, 4, st)) != RIX_OK) return s;
+  if (ctx->n_itZ) {
+    k_Z<<<(unsigned)ctx->n_itZ, NT, SM_BIG * 8, st>>>(
+        ctx->d_itZ, ctx->d_ptrZ, ctx->d_LZ, ctx->d_atomA2, ctx->d_atomB2, ctx->d_off2, ctx->d_pB, ctx->d_nb,
+        ctx->d_na, ctx->d_C, ctx->d_offC, ctx->d_V, ctx->d_offV, D, ctx->d_offD, ctx->d_keepC, ctx->d_keepV,
+        ctx->d_keepD, ctx->d_Z);
+    if ((s = last(ctx, "k_Z")) != RIX_OK) return s;
+  }
+  if ((s = rix_prof_mark(ctx, 5, st)) != RIX_OK) return s;
+  if (ctx->n_ordX34) {
+    k_X34<<<(unsigned)ctx->n_ordX34, NT, SM_BIG * 8, st>>>(
+        ctx->d_ordX34, ctx->d_ptrX34, ctx->d_LX34, ctx->d_atomA3, ctx->d_atomB3, ctx->d_pB, ctx->d_nb, ctx->d_na,
+        ctx->d_C, ctx->d_offC, ctx->d_keepC, ctx->d_Z, ctx->d_off2, ctx->d_offK, ctx->d_X);
+    if ((s = last(ctx, "k_X34")) != RIX_OK) return s;
+  }
+  if ((s = rix_prof_mark(ctx, 6, st)) != RIX_OK) return s;
+  k_sym<<<(unsigned)ctx->nk, 128, 0, st>>>(ctx->nk, ctx->d_atomA3, ctx->d_atomB3, ctx->d_partner3, ctx->d_nb,
+                                           ctx->d_offK, ctx->d_X, K);
+  if ((s = last(ctx, "k_sym")) != RIX_OK) return s;
+  return rix_prof_mark(ctx, 7, st);
+}
+
+rix_status rix_launch_energy(rix_ctx *ctx, const double *D, const double *K, double *Ex, cudaStream_t st) {
+  rix_status s;
+  if ((s = rix_launch_flags(ctx, D, ctx->d_offD, ctx->np, ctx->d_keepD, st)) != RIX_OK) return s;
+  k_energy<<<(unsigned)ctx->n_epart, 256, 0, st>>>(ctx->np, ctx->d_pA, ctx->d_pB, ctx->d_partner1, ctx->d_map1to3,
+                                                   ctx->d_nb, D, ctx->d_offD, ctx->d_keepD, K, ctx->d_offK,
+                                                   ctx->d_epart);
+  if ((s = last(ctx, "k_energy")) != RIX_OK) return s;
+  k_energy_final<<<1, 1024, 0, st>>>(ctx->n_epart, ctx->d_epart, Ex);
+  return last(ctx, "k_energy_final");
+}
+
+rix_status rix_launch_fold(rix_ctx *ctx, const double *K, double *Kd, cudaStream_t st) {
+  RIX_CUDA_TRY(ctx, cudaMemsetAsync(Kd, 0, sizeof(double) * ctx->nbasis * ctx->nbasis, st));
+  k_fold<<<(unsigned)ctx->n_fold, 128, 0, st>>>(ctx->n_fold, ctx->d_fold, ctx->d_atomA3, ctx->d_atomB3, ctx->d_nb,
+                                                ctx->d_offK, ctx->d_bofs, ctx->nbasis, K, Kd);
+  return last(ctx, "k_fold");
+}

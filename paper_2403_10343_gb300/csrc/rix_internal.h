@@ -1,0 +1,157 @@
+// Internal structures of librix (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/rix.h"
+
+#define RIX_CUDA_TRY(ctx, call)                                                  \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      (ctx)->last_error = std::string(#call) + ": " + cudaGetErrorString(e_);     \
+      return RIX_ECUDA;                                                           \
+    }                                                                             \
+  } while (0)
+
+namespace rix {
+
+// Pair key: A << 44 | B << 24 | (n1+128) << 16 | (n2+128) << 8 | (n3+128).
+__host__ __device__ inline int64_t pair_key(int64_t a, int64_t b, int n1, int n2, int n3) {
+  return (a << 44) | (b << 24) | ((int64_t)(n1 + 128) << 16) | ((int64_t)(n2 + 128) << 8) |
+         (int64_t)(n3 + 128);
+}
+__host__ __device__ inline int key_a(int64_t k) { return (int)((k >> 44) & 0xFFFFF); }
+__host__ __device__ inline int key_b(int64_t k) { return (int)((k >> 24) & 0xFFFFF); }
+__host__ __device__ inline int key_n(int64_t k, int c) {
+  return (int)((k >> (16 - 8 * c)) & 0xFF) - 128;
+}
+
+// One entry of the term-1/2 product list (output = a 2-hop block (A,E)).
+struct X12Entry {
+  int32_t t;     // T block (A, G') in the 2-hop list
+  int32_t p3;    // pair (G', E') carrying C
+  int32_t u2;    // pair (A, G') whose U2 block feeds term 2, -1 if no term 2
+  int32_t t1;    // 1 if term 1 uses this entry
+};
+
+// Device allocation tracked for the workspace statistics.
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace rix
+
+struct rix_ctx {
+  // ------------------------------------------------------------ system
+  int32_t nat = 0, nsp = 0;
+  bool periodic = false;
+  double cell[9] = {0};
+  double rc = 0, tau = 0;
+  std::vector<double> xyz;
+  std::vector<int32_t> sp, nbs, nas;   // species of each atom, per-species sizes
+  std::vector<int32_t> nb_at, na_at;   // per atom
+  rix_options opt{};
+  std::string last_error;
+  bool have_cv = false;
+
+  // ------------------------------------------------------------ lists (host)
+  int64_t np = 0;                      // 1-hop pairs
+  std::vector<int64_t> keys1, offC, offV, offD, row1;
+  std::vector<int32_t> pA, pB;
+  std::vector<int8_t> pn;              // [np][3]
+  std::vector<uint8_t> onsite;
+  std::vector<int32_t> partner1;
+  int64_t n2 = 0;                      // 2-hop blocks (T and Z)
+  std::vector<int64_t> keys2, off2, row2;
+  int64_t nk = 0;                      // 3-hop blocks (K and X)
+  std::vector<int64_t> keys3, offK, row3;
+
+  // ------------------------------------------------------------ device
+  std::vector<rix::DevBuf> bufs;
+  size_t dev_bytes = 0;
+  // atoms
+  int32_t *d_nb = nullptr, *d_na = nullptr;
+  // pair list
+  int32_t *d_pA = nullptr, *d_pB = nullptr, *d_partner1 = nullptr;
+  uint8_t *d_onsite = nullptr;
+  int64_t *d_offC = nullptr, *d_offV = nullptr, *d_offD = nullptr, *d_offU = nullptr;
+  int32_t *d_map1to2 = nullptr, *d_map1to3 = nullptr;
+  // 2-hop and 3-hop lists
+  int32_t *d_atomA2 = nullptr, *d_atomB2 = nullptr;   // (A, G) of a 2-hop block
+  int64_t *d_off2 = nullptr;
+  int32_t *d_map2to1 = nullptr, *d_map2to3 = nullptr;
+  int32_t *d_atomA3 = nullptr, *d_atomB3 = nullptr;
+  int64_t *d_offK = nullptr;
+  int32_t *d_partner3 = nullptr;
+  // product lists (CSR over outputs) and launch orders
+  int64_t *d_ptrT = nullptr; int2 *d_LT = nullptr;
+  int64_t *d_ptrX12 = nullptr; rix::X12Entry *d_LX12 = nullptr;
+  int64_t *d_ptrZ = nullptr; int2 *d_LZ = nullptr;
+  int64_t *d_ptrX34 = nullptr; int2 *d_LX34 = nullptr;
+  // tiled work items: (output, first row) per launch
+  int2 *d_itT = nullptr; int64_t n_itT = 0;
+  int2 *d_itZ = nullptr; int64_t n_itZ = 0;
+  int2 *d_itU = nullptr; int64_t n_itU = 0;
+  int32_t *d_ordX12 = nullptr; int64_t n_ordX12 = 0;
+  int32_t *d_ordX34 = nullptr; int64_t n_ordX34 = 0;
+  // inputs and intermediates
+  double *d_C = nullptr, *d_V = nullptr;
+  uint8_t *d_keepC = nullptr, *d_keepV = nullptr, *d_keepD = nullptr;
+  double *d_T = nullptr, *d_Z = nullptr, *d_U = nullptr, *d_X = nullptr;
+  double *d_epart = nullptr;            // energy partial sums
+  int32_t *d_flag = nullptr;            // device status word
+  int64_t n_epart = 0;
+  // fold-gamma groups (consecutive K blocks with the same atom pair)
+  int64_t n_fold = 0;
+  int64_t *d_fold = nullptr;
+  int64_t nbasis = 0;
+  int64_t *d_bofs = nullptr;            // global basis offset of each atom
+  // tile sizes (rows of P per work item)
+  int32_t tileT = 0, tileZ = 0;
+
+  rix_stats_t stats{};
+
+  // stage timing (rix_options.profile): 8 events per build, pooled
+  static constexpr int NSTAGE = 7;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<cudaEvent_t> ev_pending;  // NSTAGE + 1 per recorded build
+};
+
+// record the stage boundary `i` of the current build (no-op without profiling)
+rix_status rix_prof_mark(rix_ctx *ctx, int i, cudaStream_t st);
+
+// helpers shared across translation units
+rix_status rix_dev_alloc(rix_ctx *ctx, void **p, size_t bytes);
+template <class T>
+inline rix_status rix_alloc(rix_ctx *ctx, T **p, size_t n) {
+  return rix_dev_alloc(ctx, (void **)p, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
+}
+template <class T>
+inline rix_status rix_upload(rix_ctx *ctx, T **p, const std::vector<T> &v) {
+  rix_status s = rix_alloc(ctx, p, v.size());
+  if (s != RIX_OK) return s;
+  if (!v.empty()) {
+    cudaError_t e = cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      ctx->last_error = std::string("upload: ") + cudaGetErrorString(e);
+      return RIX_ECUDA;
+    }
+  }
+  return RIX_OK;
+}
+
+// FP64 path launches (rix_fp64.cu)
+rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t st);
+rix_status rix_launch_flags(rix_ctx *ctx, const double *arr, const int64_t *off, int64_t n,
+                            uint8_t *keep, cudaStream_t st);
+rix_status rix_launch_symcheck(rix_ctx *ctx, cudaStream_t st);
+rix_status rix_launch_energy(rix_ctx *ctx, const double *D, const double *K, double *Ex,
+                             cudaStream_t st);
+rix_status rix_launch_fold(rix_ctx *ctx, const double *K, double *Kd, cudaStream_t st);
+rix_status rix_launch_pairs(rix_ctx *ctx, const double *d_xyz, const double *d_cell,
+                            const int nr[3], int64_t *d_counts, const int64_t *d_rowptr,
+                            int64_t *d_keys, cudaStream_t st);

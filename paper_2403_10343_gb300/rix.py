@@ -1,0 +1,253 @@
+"""Python binding of librix (ctypes; argument marshalling only).
+
+Every function forwards to the C entry point of the same name in
+``include/rix.h``; device buffers are torch CUDA tensors passed by
+``data_ptr()`` together with the current CUDA stream.  There is no CPU
+fallback: if the shared library cannot be loaded, import fails.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librix.so")
+
+RIX_OK, RIX_EINVAL, RIX_ENOMEM, RIX_ECUDA, RIX_ENOTSYM, RIX_ETIMEOUT, RIX_EUNSUPPORTED, RIX_ESTATE = range(8)
+RIX_FP64, RIX_MIXED_BF16 = 0, 1
+RIX_LIST_C, RIX_LIST_V, RIX_LIST_D, RIX_LIST_K = 0, 1, 2, 3
+PRECISIONS = {"fp64": RIX_FP64, "mixed": RIX_MIXED_BF16, "bf16": RIX_MIXED_BF16}
+
+
+class RixError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"rix status {status}: {msg}")
+
+
+class _System(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int32), ("xyz_bohr", ctypes.c_void_p), ("species", ctypes.c_void_p),
+                ("n_species", ctypes.c_int32), ("nbas_per_species", ctypes.c_void_p),
+                ("naux_per_species", ctypes.c_void_p), ("cell_bohr", ctypes.c_void_p),
+                ("cutoff_bohr", ctypes.c_double), ("screen_tau", ctypes.c_double)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("n_slices", ctypes.c_int32),
+                ("max_workspace_bytes", ctypes.c_int64), ("verbose", ctypes.c_int32),
+                ("profile", ctypes.c_int32)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int64), ("n_pairs", ctypes.c_int64), ("n_pairs2", ctypes.c_int64),
+                ("n_kblocks", ctypes.c_int64), ("c_elems", ctypes.c_int64), ("v_elems", ctypes.c_int64),
+                ("d_elems", ctypes.c_int64), ("k_elems", ctypes.c_int64), ("flops_fp64", ctypes.c_double),
+                ("flops_stage", ctypes.c_double * 6), ("min_bytes", ctypes.c_double),
+                ("tensor_flops", ctypes.c_double), ("workspace_bytes", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load():
+    """Load librix.so (built by ``paper_2403_10343_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"librix.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    lib.rix_setup.argtypes = [ctypes.POINTER(_System), ctypes.POINTER(_Options), ctypes.POINTER(P)]
+    lib.rix_layout.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                               ctypes.POINTER(ctypes.POINTER(ctypes.c_int64)),
+                               ctypes.POINTER(ctypes.POINTER(ctypes.c_int64))]
+    lib.rix_layout_sizes.argtypes = [P] + [ctypes.POINTER(ctypes.c_int64)] * 4
+    lib.rix_set_CV.argtypes = [P, P, P, P]
+    lib.rix_build_K.argtypes = [P, P, P, P]
+    lib.rix_energy.argtypes = [P, P, P, P, P]
+    lib.rix_backward.argtypes = [P, P, ctypes.c_double, P, P, P, P]
+    lib.rix_fold_gamma.argtypes = [P, P, P, P]
+    lib.rix_stats.argtypes = [P, ctypes.POINTER(_Stats)]
+    lib.rix_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
+                                    ctypes.POINTER(ctypes.c_int32)]
+    lib.rix_strerror.restype = ctypes.c_char_p
+    lib.rix_strerror.argtypes = [I]
+    lib.rix_last_error.restype = ctypes.c_char_p
+    lib.rix_last_error.argtypes = [P]
+    lib.rix_destroy.argtypes = [P]
+    for f in ("rix_setup", "rix_layout", "rix_layout_sizes", "rix_set_CV", "rix_build_K", "rix_energy",
+              "rix_backward", "rix_fold_gamma", "rix_stats", "rix_stage_times"):
+        getattr(lib, f).restype = I
+    _lib = lib
+    return lib
+
+
+def _check(st, ctx=None):
+    if st != RIX_OK:
+        lib = load()
+        msg = lib.rix_strerror(st).decode()
+        if ctx is not None:
+            msg += ": " + lib.rix_last_error(ctx).decode()
+        raise RixError(st, msg)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t, name, dtype_size=8):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def setup(xyz_bohr, species, nbas, naux, cell_bohr=None, cutoff_bohr=0.0, screen_tau=0.0,
+          precision="fp64", n_slices=0, max_workspace_bytes=0, verbose=0, profile=0):
+    """rix_setup: returns an opaque context handle (int)."""
+    lib = load()
+    keep = [np.ascontiguousarray(xyz_bohr, dtype=np.float64), np.ascontiguousarray(species, dtype=np.int32),
+            np.ascontiguousarray(nbas, dtype=np.int32), np.ascontiguousarray(naux, dtype=np.int32)]
+    cell = None if cell_bohr is None else np.ascontiguousarray(cell_bohr, dtype=np.float64)
+    sysd = _System(len(keep[1]), keep[0].ctypes.data, keep[1].ctypes.data, len(keep[2]), keep[2].ctypes.data,
+                   keep[3].ctypes.data, None if cell is None else cell.ctypes.data,
+                   float(cutoff_bohr), float(screen_tau))
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    opt = _Options(prec, int(n_slices), int(max_workspace_bytes), int(verbose), int(profile))
+    h = ctypes.c_void_p()
+    _check(lib.rix_setup(ctypes.byref(sysd), ctypes.byref(opt), ctypes.byref(h)))
+    return h.value
+
+
+def layout(ctx, which):
+    """rix_layout: (keys int64[n], offsets int64[n+1]) copied to numpy."""
+    lib = load()
+    n = ctypes.c_int64()
+    k = ctypes.POINTER(ctypes.c_int64)()
+    o = ctypes.POINTER(ctypes.c_int64)()
+    _check(lib.rix_layout(ctx, which, ctypes.byref(n), ctypes.byref(k), ctypes.byref(o)), ctx)
+    keys = np.ctypeslib.as_array(k, shape=(n.value,)).copy() if n.value else np.zeros(0, np.int64)
+    offs = np.ctypeslib.as_array(o, shape=(n.value + 1,)).copy()
+    return keys, offs
+
+
+def layout_sizes(ctx):
+    lib = load()
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(lib.rix_layout_sizes(ctx, *[ctypes.byref(x) for x in v]), ctx)
+    return tuple(x.value for x in v)
+
+
+def set_CV(ctx, C, V, stream=None):
+    _check(load().rix_set_CV(ctx, _dptr(C, "C"), _dptr(V, "V"), _stream(stream)), ctx)
+
+
+def build_K(ctx, D, K, stream=None):
+    _check(load().rix_build_K(ctx, _dptr(D, "D"), _dptr(K, "K"), _stream(stream)), ctx)
+
+
+def energy(ctx, D, K, Ex, stream=None):
+    _check(load().rix_energy(ctx, _dptr(D, "D"), _dptr(K, "K"), _dptr(Ex, "Ex"), _stream(stream)), ctx)
+
+
+def backward(ctx, D, gEx, dD=None, dC=None, dV=None, stream=None):
+    _check(load().rix_backward(ctx, _dptr(D, "D"), float(gEx), _dptr(dD, "dD"), _dptr(dC, "dC"),
+                               _dptr(dV, "dV"), _stream(stream)), ctx)
+
+
+def fold_gamma(ctx, K, Kdense, stream=None):
+    _check(load().rix_fold_gamma(ctx, _dptr(K, "K"), _dptr(Kdense, "Kdense"), _stream(stream)), ctx)
+
+
+def stats(ctx):
+    s = _Stats()
+    _check(load().rix_stats(ctx, ctypes.byref(s)), ctx)
+    d = {f: getattr(s, f) for f, _ in _Stats._fields_ if f != "flops_stage"}
+    d["flops_stage"] = list(s.flops_stage)
+    return d
+
+
+STAGES = ("flags", "T", "U2", "X12", "Z", "X34", "sym")
+
+
+def stage_times(ctx):
+    """rix_stage_times: (dict stage -> summed ms, number of builds)."""
+    ms = (ctypes.c_double * len(STAGES))()
+    nb = ctypes.c_int32()
+    _check(load().rix_stage_times(ctx, ms, len(STAGES), ctypes.byref(nb)), ctx)
+    return dict(zip(STAGES, list(ms))), nb.value
+
+
+def destroy(ctx):
+    if ctx:
+        load().rix_destroy(ctx)
+
+
+class Exchange:
+    """Convenience owner of one rix context plus its device-resident C and V."""
+
+    def __init__(self, xyz_bohr, species, nbas, naux, cell_bohr=None, cutoff_bohr=0.0, screen_tau=0.0,
+                 precision="fp64", n_slices=0, max_workspace_bytes=0, verbose=0, profile=0):
+        self.ctx = setup(xyz_bohr, species, nbas, naux, cell_bohr, cutoff_bohr, screen_tau, precision,
+                         n_slices, max_workspace_bytes, verbose, profile)
+        self.c_elems, self.v_elems, self.d_elems, self.k_elems = layout_sizes(self.ctx)
+
+    @classmethod
+    def from_system(cls, system, **kw):
+        return cls(system.xyz, system.species, system.nbas, system.naux, system.cell, system.cutoff,
+                   system.tau, **kw)
+
+    def pair_keys(self):
+        return layout(self.ctx, RIX_LIST_C)[0]
+
+    def k_keys(self):
+        return layout(self.ctx, RIX_LIST_K)[0]
+
+    def set_CV(self, C, V, stream=None):
+        set_CV(self.ctx, C, V, stream)
+
+    def build_K(self, D, K=None, stream=None):
+        import torch
+        if K is None:
+            K = torch.empty(self.k_elems, dtype=torch.float64, device=D.device)
+        build_K(self.ctx, D, K, stream)
+        return K
+
+    def energy(self, D, K, Ex=None, stream=None):
+        import torch
+        if Ex is None:
+            Ex = torch.empty(1, dtype=torch.float64, device=D.device)
+        energy(self.ctx, D, K, Ex, stream)
+        return Ex
+
+    def fold_gamma(self, K, nbasis, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((nbasis, nbasis), dtype=torch.float64, device=K.device)
+        fold_gamma(self.ctx, K, out, stream)
+        return out
+
+    def stats(self):
+        return stats(self.ctx)
+
+    def stage_times(self):
+        return stage_times(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
