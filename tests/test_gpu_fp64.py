@@ -131,13 +131,16 @@ def test_full_size_sampled_rows(cfg, rows):
     nb = s.nbas[s.species]
     for r, e_ref in zip(rows, e_rows_ref):
         e = 0.0
+        scale = 0.0
         for p in np.nonzero(A == r)[0]:
             q = pk.partner[p]
             x = kidx[int(pk.keys[p])]
             kb = K[koff[x]:koff[x + 1]].reshape(nb[r], nb[B[p]])
             dq = pk.D[pk.offD[q]:pk.offD[q + 1]].reshape(nb[B[p]], nb[r])
             e += np.sum(dq.T * kb)
-        assert abs(-0.25 * e - e_ref) < 1e-11 * abs(e_ref)
+            scale += np.sum(np.abs(dq.T * kb))
+        # a row's energy can nearly cancel; compare against the size of its terms
+        assert abs(-0.25 * e - e_ref) < 1e-12 * 0.25 * scale
     # the device energy reduction against a host sum over the device K
     A3, E3, n3 = ri.unpack_key(keys)
     host_e = 0.0
