@@ -147,6 +147,19 @@ rix_status rix_build_K(rix_ctx *ctx, const double *D_dev, double *K_dev, void *s
 rix_status rix_energy(rix_ctx *ctx, const double *D_dev, const double *K_dev,
                       double *Ex_dev, void *stream);
 
+/* The same energy as rix_energy, for callers that must not allocate device
+ * memory when they ask for it (a framework whose caching allocator already
+ * holds the GPU's free memory, or an SCF loop that forbids allocation and the
+ * synchronisation it can cause).  No counterpart in the paper: it only moves
+ * the reduction's scratch (one partial sum per 256 pairs) into a fixed
+ * 512 KB device array owned by the library (kept on every GPU that loads it
+ * until exit).  Contexts with more than 16,777,216 pairs are rejected
+ * (RIX_EINVAL).  Every call on a device shares that array: calls whose work
+ * overlaps on the GPU race.  The first call on a device looks up the array's
+ * address, so make it before any stream capture begins.  Asynchronous. */
+rix_status rix_energy_noalloc(rix_ctx *ctx, const double *D_dev, const double *K_dev,
+                              double *Ex_dev, void *stream);
+
 /* Adjoint of E_x scaled by gEx (host scalar): dD_dev [d_elems] = gEx * dE/dD
  * = -gEx K(D)/2 per stored D entry, dC_dev [c_elems] = gEx * dE/dC per stored
  * C entry, dV_dev [v_elems] = gEx * dE/dV per stored V entry (partials with

@@ -614,6 +614,20 @@ rix_status rix_launch_energy(rix_ctx *ctx, const double *D, const double *K, dou
   return last(ctx, "k_energy_final");
 }
 
+// Same energy reduction as rix_launch_energy, with the per-CTA partial sums in
+// a caller-supplied device buffer of at least ctx->n_epart doubles.
+rix_status rix_launch_energy_partials(rix_ctx *ctx, const double *D, const double *K, double *Ex, double *partials,
+                                      cudaStream_t st) {
+  rix_status s;
+  if ((s = rix_launch_flags(ctx, D, ctx->d_offD, ctx->np, ctx->d_keepD, st)) != RIX_OK) return s;
+  k_energy<<<(unsigned)ctx->n_epart, 256, 0, st>>>(ctx->np, ctx->d_pA, ctx->d_pB, ctx->d_partner1, ctx->d_map1to3,
+                                                   ctx->d_nb, D, ctx->d_offD, ctx->d_keepD, K, ctx->d_offK,
+                                                   partials);
+  if ((s = last(ctx, "k_energy")) != RIX_OK) return s;
+  k_energy_final<<<1, 1024, 0, st>>>(ctx->n_epart, partials, Ex);
+  return last(ctx, "k_energy_final");
+}
+
 rix_status rix_launch_fold(rix_ctx *ctx, const double *K, double *Kd, cudaStream_t st) {
   RIX_CUDA_TRY(ctx, cudaMemsetAsync(Kd, 0, sizeof(double) * ctx->nbasis * ctx->nbasis, st));
   k_fold<<<(unsigned)ctx->n_fold, 128, 0, st>>>(ctx->n_fold, ctx->d_fold, ctx->d_atomA3, ctx->d_atomB3, ctx->d_nb,

@@ -67,6 +67,7 @@ def load():
     lib.rix_set_CV.argtypes = [P, P, P, P]
     lib.rix_build_K.argtypes = [P, P, P, P]
     lib.rix_energy.argtypes = [P, P, P, P, P]
+    lib.rix_energy_noalloc.argtypes = [P, P, P, P, P]
     lib.rix_backward.argtypes = [P, P, ctypes.c_double, P, P, P, P]
     lib.rix_fold_gamma.argtypes = [P, P, P, P]
     lib.rix_stats.argtypes = [P, ctypes.POINTER(_Stats)]
@@ -78,6 +79,7 @@ def load():
     lib.rix_last_error.argtypes = [P]
     lib.rix_destroy.argtypes = [P]
     for f in ("rix_setup", "rix_layout", "rix_layout_sizes", "rix_set_CV", "rix_build_K", "rix_energy",
+              "rix_energy_noalloc",
               "rix_backward", "rix_fold_gamma", "rix_stats", "rix_stage_times"):
         getattr(lib, f).restype = I
     _lib = lib
@@ -156,6 +158,11 @@ def build_K(ctx, D, K, stream=None):
 
 def energy(ctx, D, K, Ex, stream=None):
     _check(load().rix_energy(ctx, _dptr(D, "D"), _dptr(K, "K"), _dptr(Ex, "Ex"), _stream(stream)), ctx)
+
+
+def energy_noalloc(ctx, D, K, Ex, stream=None):
+    """rix_energy_noalloc: the energy reduction without any device allocation."""
+    _check(load().rix_energy_noalloc(ctx, _dptr(D, "D"), _dptr(K, "K"), _dptr(Ex, "Ex"), _stream(stream)), ctx)
 
 
 def backward(ctx, D, gEx, dD=None, dC=None, dV=None, stream=None):
