@@ -99,6 +99,7 @@ typedef struct {
   int64_t max_workspace_bytes;     /* 0 = no limit beyond the device's free memory */
   int32_t verbose;                 /* 0 = silent */
   int32_t profile;                 /* 1 = record a CUDA event after every stage of rix_build_K */
+  int32_t backward;                /* 1 = also plan rix_backward (extra product lists) */
 } rix_options;
 
 typedef struct {

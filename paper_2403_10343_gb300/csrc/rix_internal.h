@@ -37,6 +37,14 @@ struct X12Entry {
   int32_t t1;    // 1 if term 1 uses this entry
 };
 
+// One entry of the backward term-1/2 list grouped by the C pair (G',E').
+struct BX12Entry {
+  int32_t t;     // T block (A, G')
+  int32_t s;     // output block (A, E') in the 2-hop list (a pair-list block)
+  int32_t u2;    // pair (A, G') for term 2, -1 if none
+  int32_t t1;    // 1 if term 1
+};
+
 // Device allocation tracked for the workspace statistics.
 struct DevBuf {
   void *p = nullptr;
@@ -112,6 +120,21 @@ struct rix_ctx {
   int64_t *d_bofs = nullptr;            // global basis offset of each atom
   // tile sizes (rows of P per work item)
   int32_t tileT = 0, tileZ = 0;
+
+  // ------------------------------------------------------------ backward plan (opt.backward)
+  bool have_bwd = false;
+  int64_t *d_ptrBC34 = nullptr; int2 *d_LBC34 = nullptr;   // per pair (A,B'): (pair (A,E'), Z(B,E'))
+  int64_t *d_ptrBZ34 = nullptr; int2 *d_LBZ34 = nullptr;   // per Z block: (pair (A,B'), pair (A,E'))
+  int64_t *d_ptrBZV = nullptr; int2 *d_LBZV = nullptr;     // per pair (B,G'): (pair (G',E'), Z(B,E'))
+  int64_t *d_ptrBZC = nullptr; int2 *d_LBZC = nullptr;     // per pair (G',E'): (pair (B,G'), Z(B,E'))
+  int64_t *d_ptrBU2 = nullptr; int2 *d_LBU2 = nullptr;     // per pair (A,G'): (block (A,E'), pair (G',E'))
+  int64_t *d_ptrBT1 = nullptr; int2 *d_LBT1 = nullptr;     // per T block: (block (A,E'), pair (G',E'))
+  int64_t *d_ptrBC12 = nullptr; rix::BX12Entry *d_LBC12 = nullptr;  // per pair (G',E')
+  int64_t *d_ptrBTC = nullptr; int2 *d_LBTC = nullptr;     // per pair (A,B'): (pair (B',G'), T block)
+  int4 *d_itB[9] = {nullptr};                              // tiled work items per backward kernel
+  int64_t n_itB[9] = {0};
+  double *d_Zbar = nullptr, *d_Tbar = nullptr, *d_U2bar = nullptr, *d_Kbuf = nullptr;
+  double bwd_flops = 0;
 
   rix_stats_t stats{};
 

@@ -101,6 +101,188 @@ void group_by(int64_t lo, int64_t hi, const std::vector<int64_t> &keys, const st
 }  // namespace
 
 // --------------------------------------------------------------------------
+// Group (key, payload) records into CSR order, keeping input order within a key.
+template <class P>
+static void csr_group(int64_t nkeys, const std::vector<int64_t> &key, const std::vector<P> &pay,
+                      std::vector<int64_t> &ptr, std::vector<P> &out) {
+  ptr.assign(nkeys + 1, 0);
+  for (int64_t k : key) ptr[k + 1]++;
+  for (int64_t i = 0; i < nkeys; i++) ptr[i + 1] += ptr[i];
+  std::vector<int64_t> pos(ptr.begin(), ptr.end() - 1);
+  out.resize(key.size());
+  for (size_t e = 0; e < key.size(); e++) out[pos[key[e]]++] = pay[e];
+}
+
+// Work items (output, first row) over `rows` rows of `per` elements each, rows per item
+// chosen by the same rule as the kernels.
+static void add_items(std::vector<int4> &it, int64_t out, int64_t rows, int64_t rt) {
+  for (int64_t r0 = 0; r0 < rows; r0 += rt) it.push_back(make_int4((int)out, (int)r0, 0, 0));
+}
+
+// Product lists of the adjoint (reverse order of the stages of rix_build_K).  Only
+// output blocks (A,E') on the pair list carry a nonzero adjoint, so every list is
+// restricted to them.
+static rix_status build_backward_lists(rix_ctx *ctx, const std::vector<int2> &LT, const std::vector<int64_t> &ptrT,
+                                       const std::vector<X12Entry> &LX12, const std::vector<int64_t> &ptrX12,
+                                       const std::vector<int2> &LZ, const std::vector<int64_t> &ptrZ,
+                                       const std::vector<int32_t> &map1to2, const std::vector<int32_t> &map2to1,
+                                       const std::vector<int32_t> &atomA2, const std::vector<int32_t> &atomB2) {
+  const int nat = ctx->nat;
+  const int64_t np = ctx->np, n2 = ctx->n2;
+  auto &pA = ctx->pA, &pB = ctx->pB;
+  auto &pn = ctx->pn;
+  auto &row1 = ctx->row1, &row2 = ctx->row2;
+  auto &keys2 = ctx->keys2;
+  auto NB = [&](int a) { return (int64_t)ctx->nb_at[a]; };
+  auto NA = [&](int a) { return (int64_t)ctx->na_at[a]; };
+  auto find2 = [&](int64_t key) { int a = key_a(key); return find_in(keys2, row2[a], row2[a + 1], key); };
+  const int64_t CAP = 8192, SMB = 12288;
+  double fl = 0;
+
+  // (pair (A,B') not on-site, pair (A,E')) -> Z(B, E'-n1)
+  std::vector<int64_t> kBC, kBZ;
+  std::vector<int2> vBC, vBZ;
+  for (int a = 0; a < nat; a++)
+    for (int64_t p1 = row1[a]; p1 < row1[a + 1]; p1++) {
+      if (ctx->onsite[p1]) continue;
+      int b = pB[p1];
+      for (int64_t pae = row1[a]; pae < row1[a + 1]; pae++) {
+        int e = pB[pae];
+        int8_t m[3];
+        bool ok = true;
+        for (int c = 0; c < 3; c++) m[c] = (int8_t)(pn[3 * pae + c] - pn[3 * p1 + c]);
+        int64_t z = find2(pair_key(b, e, m[0], m[1], m[2]));
+        if (z < 0 || ptrZ[z + 1] == ptrZ[z] || !ok) continue;
+        kBC.push_back(p1); vBC.push_back(make_int2((int)pae, (int)z));
+        kBZ.push_back(z); vBZ.push_back(make_int2((int)p1, (int)pae));
+        fl += 4.0 * NA(b) * NB(a) * NB(b) * NB(e);
+      }
+    }
+  std::vector<int64_t> ptrBC, ptrBZ;
+  std::vector<int2> LBC, LBZ;
+  csr_group(np, kBC, vBC, ptrBC, LBC);
+  csr_group(n2, kBZ, vBZ, ptrBZ, LBZ);
+  std::vector<int64_t>().swap(kBC); std::vector<int2>().swap(vBC);
+  std::vector<int64_t>().swap(kBZ); std::vector<int2>().swap(vBZ);
+
+  // (pair (B,G'), pair (G',E') not on-site) for Z blocks that carry an adjoint
+  std::vector<int64_t> kZV, kZC;
+  std::vector<int2> vZV, vZC;
+  for (int64_t z = 0; z < n2; z++) {
+    if (ptrBZ[z + 1] == ptrBZ[z]) continue;
+    int b = atomA2[z], e = atomB2[z];
+    for (int64_t x = ptrZ[z]; x < ptrZ[z + 1]; x++) {
+      int2 en = LZ[x];
+      int g = pB[en.x];
+      kZV.push_back(en.x); vZV.push_back(make_int2(en.y, (int)z));
+      kZC.push_back(en.y); vZC.push_back(make_int2(en.x, (int)z));
+      fl += 2.0 * NA(b) * NA(g) * NB(g) * NB(e) * 2 + 2.0 * NA(b) * NB(b) * NB(g) * NB(e) * 2;
+    }
+  }
+  std::vector<int64_t> ptrZV, ptrZC;
+  std::vector<int2> LZV, LZC;
+  csr_group(np, kZV, vZV, ptrZV, LZV);
+  csr_group(np, kZC, vZC, ptrZC, LZC);
+  std::vector<int64_t>().swap(kZV); std::vector<int2>().swap(vZV);
+  std::vector<int64_t>().swap(kZC); std::vector<int2>().swap(vZC);
+
+  // terms 1 and 2, outputs on the pair list only
+  std::vector<int64_t> kU2, kT1, kC12;
+  std::vector<int2> vU2, vT1;
+  std::vector<BX12Entry> vC12;
+  std::vector<uint8_t> hasT1(np, 0);
+  for (int64_t s = 0; s < n2; s++) {
+    int64_t pae = map2to1[s];
+    if (pae < 0) continue;
+    int a = atomA2[s], e = atomB2[s];
+    for (int64_t x = ptrX12[s]; x < ptrX12[s + 1]; x++) {
+      const X12Entry &en = LX12[x];
+      int g = pA[en.p3];
+      if (en.u2 >= 0) {
+        kU2.push_back(en.u2); vU2.push_back(make_int2((int)s, en.p3));
+        fl += 2.0 * NA(g) * NB(a) * NB(g) * NB(e) * 2;
+      }
+      if (en.t1) {
+        kT1.push_back(en.t); vT1.push_back(make_int2((int)s, en.p3));
+        hasT1[pae] = 1;
+        fl += 2.0 * NA(e) * NB(a) * NB(g) * NB(e) * 2 + 2.0 * NA(a) * NA(e) * NB(a) * NB(g) * 3;
+      }
+      kC12.push_back(en.p3); vC12.push_back({en.t, (int32_t)s, en.u2, en.t1});
+    }
+  }
+  std::vector<int64_t> ptrU2, ptrT1, ptrC12;
+  std::vector<int2> LU2, LT1;
+  std::vector<BX12Entry> LC12;
+  csr_group(np, kU2, vU2, ptrU2, LU2);
+  csr_group(n2, kT1, vT1, ptrT1, LT1);
+  csr_group(np, kC12, vC12, ptrC12, LC12);
+  std::vector<int64_t>().swap(kU2); std::vector<int2>().swap(vU2);
+  std::vector<int64_t>().swap(kT1); std::vector<int2>().swap(vT1);
+  std::vector<int64_t>().swap(kC12); std::vector<BX12Entry>().swap(vC12);
+
+  // T adjoint -> C(A,B') own block: (pair (B',G'), T block)
+  std::vector<int64_t> kTC;
+  std::vector<int2> vTC;
+  for (int64_t t = 0; t < n2; t++)
+    for (int64_t x = ptrT[t]; x < ptrT[t + 1]; x++) {
+      kTC.push_back(LT[x].x); vTC.push_back(make_int2(LT[x].y, (int)t));
+      int a = atomA2[t], g = atomB2[t], b = pB[LT[x].x];
+      fl += 2.0 * NA(a) * NB(a) * NB(b) * NB(g);
+    }
+  std::vector<int64_t> ptrTC;
+  std::vector<int2> LTC;
+  csr_group(np, kTC, vTC, ptrTC, LTC);
+  std::vector<int64_t>().swap(kTC); std::vector<int2>().swap(vTC);
+
+  // ------------------------------------------------------------ tiled work items
+  std::vector<int4> it[9];
+  for (int64_t p = 0; p < np; p++) {
+    int a = pA[p], x = pB[p];
+    if (ptrBC[p + 1] > ptrBC[p]) add_items(it[0], p, NA(x), std::max<int64_t>(1, CAP / (NB(a) * NB(x))));
+    if (ptrZV[p + 1] > ptrZV[p]) add_items(it[2], p, NA(a), std::max<int64_t>(1, CAP / NA(x)));
+    if (ptrZC[p + 1] > ptrZC[p]) add_items(it[3], p, NA(a), std::max<int64_t>(1, CAP / (NB(a) * NB(x))));
+    if (ptrU2[p + 1] > ptrU2[p]) add_items(it[4], p, NA(x), std::max<int64_t>(1, CAP / (NB(a) * NB(x))));
+    if (hasT1[p] || ptrU2[p + 1] > ptrU2[p]) add_items(it[6], p, NA(a), std::max<int64_t>(1, CAP / NA(x)));
+    if (ptrC12[p + 1] > ptrC12[p]) {
+      int64_t rows = NA(a) + (ctx->onsite[p] ? 0 : NA(x));
+      int64_t per = NB(a) * NB(x);
+      add_items(it[7], p, rows, std::max<int64_t>(1, std::min(CAP / per, SMB / (64 * NB(a)))));
+    }
+    if (ptrTC[p + 1] > ptrTC[p]) add_items(it[8], p, NA(a), std::max<int64_t>(1, CAP / (NB(a) * NB(x))));
+  }
+  for (int64_t z = 0; z < n2; z++) {
+    int b = atomA2[z], e = atomB2[z];
+    if (ptrBZ[z + 1] > ptrBZ[z]) add_items(it[1], z, NA(b), std::max<int64_t>(1, CAP / (NB(b) * NB(e))));
+    bool needT = ptrT1[z + 1] > ptrT1[z];
+    int64_t pag = map2to1[z];
+    if (pag >= 0 && ptrU2[pag + 1] > ptrU2[pag]) needT = true;
+    if (needT) add_items(it[5], z, NA(b), std::max<int64_t>(1, CAP / (NB(b) * NB(e))));
+  }
+  (void)map1to2;
+  ctx->bwd_flops = fl;
+
+  TRY(rix_upload(ctx, &ctx->d_ptrBC34, ptrBC)); TRY(rix_upload(ctx, &ctx->d_LBC34, LBC));
+  TRY(rix_upload(ctx, &ctx->d_ptrBZ34, ptrBZ)); TRY(rix_upload(ctx, &ctx->d_LBZ34, LBZ));
+  TRY(rix_upload(ctx, &ctx->d_ptrBZV, ptrZV)); TRY(rix_upload(ctx, &ctx->d_LBZV, LZV));
+  TRY(rix_upload(ctx, &ctx->d_ptrBZC, ptrZC)); TRY(rix_upload(ctx, &ctx->d_LBZC, LZC));
+  TRY(rix_upload(ctx, &ctx->d_ptrBU2, ptrU2)); TRY(rix_upload(ctx, &ctx->d_LBU2, LU2));
+  TRY(rix_upload(ctx, &ctx->d_ptrBT1, ptrT1)); TRY(rix_upload(ctx, &ctx->d_LBT1, LT1));
+  TRY(rix_upload(ctx, &ctx->d_ptrBC12, ptrC12)); TRY(rix_upload(ctx, &ctx->d_LBC12, LC12));
+  TRY(rix_upload(ctx, &ctx->d_ptrBTC, ptrTC)); TRY(rix_upload(ctx, &ctx->d_LBTC, LTC));
+  for (int k = 0; k < 9; k++) {
+    TRY(rix_upload(ctx, &ctx->d_itB[k], it[k]));
+    ctx->n_itB[k] = it[k].size();
+  }
+  TRY(rix_alloc(ctx, &ctx->d_Zbar, ctx->off2[n2]));
+  TRY(rix_alloc(ctx, &ctx->d_Tbar, ctx->off2[n2]));
+  int64_t nU = 0;
+  for (int64_t p = 0; p < np; p++) nU += NA(pB[p]) * NB(pA[p]) * NB(pB[p]);
+  TRY(rix_alloc(ctx, &ctx->d_U2bar, nU));
+  TRY(rix_alloc(ctx, &ctx->d_Kbuf, ctx->offK[ctx->nk]));
+  ctx->have_bwd = true;
+  return RIX_OK;
+}
+
 static rix_status build_lists(rix_ctx *ctx) {
   const int nat = ctx->nat;
   const int64_t np = ctx->np;
@@ -384,6 +566,13 @@ static rix_status build_lists(rix_ctx *ctx) {
       std::vector<int64_t>().swap(lxp[a]);
     }
     ptrX34[nk] = base;
+  }
+
+  // ---------------------------------------------------------------- backward plan
+  if (ctx->opt.backward) {
+    rix_status sb = build_backward_lists(ctx, LT, ptrT, LX12, ptrX12, LZ, ptrZ, map1to2, map2to1, atomA2,
+                                         atomB2);
+    if (sb != RIX_OK) return sb;
   }
 
   // ---------------------------------------------------------------- work items and launch orders
@@ -698,13 +887,6 @@ extern "C" rix_status rix_energy(rix_ctx *ctx, const double *D, const double *K,
 extern "C" rix_status rix_fold_gamma(rix_ctx *ctx, const double *K, double *Kd, void *stream) {
   if (!ctx || !K || !Kd) return RIX_EINVAL;
   return rix_launch_fold(ctx, K, Kd, (cudaStream_t)stream);
-}
-
-extern "C" rix_status rix_backward(rix_ctx *ctx, const double *D, double gEx, double *dD, double *dC,
-                                   double *dV, void *stream) {
-  (void)D; (void)gEx; (void)dD; (void)dC; (void)dV; (void)stream;
-  if (!ctx) return RIX_EINVAL;
-  return RIX_EUNSUPPORTED;
 }
 
 extern "C" rix_status rix_stats(const rix_ctx *ctx, rix_stats_t *out) {

@@ -1,0 +1,195 @@
+"""Adjoint (rix_backward) against central finite differences.
+
+E_x is quadratic in C and in D and linear in V, so a central difference
+(E(x+h) - E(x-h)) / 2h equals the derivative up to rounding for any h.
+Stored entries come in transpose pairs (C(A,B)[P][i][j] <-> C(B,A)[P][j][i],
+V(X,Y)[P][Q] <-> V(Y,X)[Q][P], D(A,B)[i][j] <-> D(B,A)[j][i]); a perturbation
+moves both partners (keeping the inputs symmetric) and is compared with the
+sum of the two reported partials.
+"""
+import numpy as np
+import pytest
+
+import rix_inputs as ri
+import rix_inputs.systems as S
+from oracle.oracle import Oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2403_10343_gb300.rix import Exchange  # noqa: E402
+from paper_2403_10343_gb300.autograd import exchange_energy  # noqa: E402
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda")
+
+
+def _small_pbc(seed=11, side=4.6, cut=4.8, nmol=1):
+    o = np.array([[1.0, 1.2, 0.8], [3.9, 3.1, 3.3]])[:nmol]
+    xyz, spc = S._waters(o, seed)
+    names = ["O", "H"]
+    nb, na = S._species_arrays(names)
+    return S.System(name="pbc", seed=seed, xyz=ri.ang2bohr(xyz), species=spc, species_names=names,
+                    nbas=nb, naux=na, sigma=S._aux_widths(seed, names), cell=ri.ang2bohr(np.eye(3) * side),
+                    cutoff=ri.ang2bohr(cut), tau=0.0,
+                    orbital_centres=np.repeat(np.arange(0, len(spc), 3), 5).astype(np.int32))
+
+
+def _partner_C(pk, s, p, e):
+    """Index (absolute) of the transpose partner of C element e of pair p."""
+    sp = s.species
+    a, b = pk.A[p], pk.B[p]
+    nbA, nbB, naA, naB = s.nbas[sp[a]], s.nbas[sp[b]], s.naux[sp[a]], s.naux[sp[b]]
+    P, r = divmod(e, nbA * nbB)
+    i, j = divmod(r, nbB)
+    q = pk.partner[p]
+    if pk.onsite[p]:
+        return pk.offC[p] + (P * nbA + j) * nbB + i
+    Pq = P + naB if P < naA else P - naA
+    return pk.offC[q] + (Pq * nbB + j) * nbA + i
+
+
+def _partner_V(pk, s, p, e):
+    sp = s.species
+    naA, naB = s.naux[sp[pk.A[p]]], s.naux[sp[pk.B[p]]]
+    P, Q = divmod(e, naB)
+    return pk.offV[pk.partner[p]] + Q * naA + P
+
+
+def _partner_D(pk, s, p, e):
+    sp = s.species
+    nbA, nbB = s.nbas[sp[pk.A[p]]], s.nbas[sp[pk.B[p]]]
+    i, j = divmod(e, nbB)
+    return pk.offD[pk.partner[p]] + j * nbA + i
+
+
+def _entries(pk, s, which, n, rng):
+    off = {"C": pk.offC, "V": pk.offV, "D": pk.offD}[which]
+    part = {"C": _partner_C, "V": _partner_V, "D": _partner_D}[which]
+    out = []
+    while len(out) < n:
+        p = int(rng.integers(pk.n_pairs))
+        e = int(rng.integers(off[p + 1] - off[p]))
+        g = int(off[p] + e)
+        out.append((g, int(part(pk, s, p, e))))
+    return out
+
+
+def _fd_check(s, pk, n=12, h=1e-3, seed=0, tol=1e-7):
+    ex = Exchange.from_system(s, backward=1)
+    C, V, D = _dev(pk.C), _dev(pk.V), _dev(pk.D)
+    ex.set_CV(C, V)
+    dD, dC, dV = ex.backward(D, 1.0)
+    torch.cuda.synchronize()
+    grads = {"C": dC.cpu().numpy(), "V": dV.cpu().numpy(), "D": dD.cpu().numpy()}
+    base = {"C": pk.C, "V": pk.V, "D": pk.D}
+
+    def energy(arrs):
+        ex.set_CV(_dev(arrs["C"]), _dev(arrs["V"]))
+        Dd = _dev(arrs["D"])
+        return ex.energy(Dd, ex.build_K(Dd)).item()
+
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    for which in ("C", "V", "D"):
+        g = grads[which]
+        scale = np.abs(g).max()
+        for (e1, e2) in _entries(pk, s, which, n, rng):
+            arrs = {k: v.copy() for k, v in base.items()}
+            arrs[which][e1] += h
+            if e2 != e1:
+                arrs[which][e2] += h
+            ep = energy(arrs)
+            arrs[which][e1] -= 2 * h
+            if e2 != e1:
+                arrs[which][e2] -= 2 * h
+            em = energy(arrs)
+            fd = (ep - em) / (2 * h)
+            an = g[e1] + (g[e2] if e2 != e1 else 0.0)
+            err = abs(fd - an) / scale
+            worst = max(worst, err)
+            assert err < tol, (which, e1, e2, fd, an, scale)
+            if e2 != e1:
+                assert g[e1] == g[e2], "reported partials of transpose partners differ"
+    ex.close()
+    return worst
+
+
+def test_grad_fd_cluster24():
+    s = ri.config(0)
+    pk = ri.generate(s)
+    _fd_check(s, pk, n=16)
+
+
+def test_grad_fd_periodic_self_images():
+    s = _small_pbc()
+    pk = ri.generate(s)
+    assert any((pk.A == pk.B) & ~pk.onsite)
+    _fd_check(s, pk, n=16, seed=1)
+
+
+def test_grad_fd_periodic_two_waters():
+    s = _small_pbc(nmol=2, side=6.0, cut=4.0)
+    pk = ri.generate(s)
+    _fd_check(s, pk, n=12, seed=2)
+
+
+def test_grad_fd_heavy_species():
+    s = S.perovskite(1, 1, 1, 31)
+    s.cutoff = ri.ang2bohr(5.0)
+    pk = ri.generate(s)
+    _fd_check(s, pk, n=8, seed=3)
+
+
+def test_dD_is_minus_half_K_and_oracle_fd():
+    """dE/dD = -K/2 entrywise; a few C and V partials against central differences of the oracle."""
+    s = ri.config(0)
+    pk = ri.generate(s)
+    ex = Exchange.from_system(s, backward=1)
+    ex.set_CV(_dev(pk.C), _dev(pk.V))
+    D = _dev(pk.D)
+    dD, dC, dV = ex.backward(D, 2.0)
+    K = ex.build_K(D).cpu().numpy()
+    torch.cuda.synchronize()
+    kidx = {int(k): x for x, k in enumerate(ex.k_keys())}
+    A, E, _ = ri.unpack_key(ex.k_keys())
+    nb = s.nbas[s.species]
+    koff = np.concatenate([[0], np.cumsum(nb[A].astype(np.int64) * nb[E])])
+    dDh = dD.cpu().numpy()
+    for p in range(0, pk.n_pairs, 7):
+        x = kidx[int(pk.keys[p])]
+        assert np.allclose(dDh[pk.offD[p]:pk.offD[p + 1]], -1.0 * K[koff[x]:koff[x + 1]], rtol=0, atol=1e-13 * np.abs(K).max())
+    o = Oracle(s)
+    o.kpattern()
+    rng = np.random.default_rng(5)
+    h = 1e-3
+    for which, g, part in (("C", dC.cpu().numpy() / 2, _partner_C), ("V", dV.cpu().numpy() / 2, _partner_V)):
+        for (e1, e2) in _entries(pk, s, which, 3, rng):
+            arrs = {"C": pk.C.copy(), "V": pk.V.copy(), "D": pk.D}
+            vals = []
+            for sgn in (1, -1):
+                a = {k: v.copy() for k, v in arrs.items()}
+                a[which][e1] += sgn * h
+                if e2 != e1:
+                    a[which][e2] += sgn * h
+                o.set_data(a["C"], a["V"], a["D"])
+                vals.append(o.energy(o.build_K()))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            an = g[e1] + (g[e2] if e2 != e1 else 0.0)
+            assert abs(fd - an) < 1e-7 * np.abs(g).max(), (which, fd, an)
+
+
+def test_autograd_function():
+    s = ri.config(0)
+    pk = ri.generate(s)
+    ex = Exchange.from_system(s, backward=1)
+    C = _dev(pk.C).requires_grad_(True)
+    V = _dev(pk.V).requires_grad_(True)
+    D = _dev(pk.D).requires_grad_(True)
+    E = exchange_energy(D, C, V, ex)
+    E.backward()
+    dD, dC, dV = ex.backward(D.detach(), 1.0)
+    torch.cuda.synchronize()
+    assert torch.equal(D.grad, dD) and torch.equal(C.grad, dC) and torch.equal(V.grad, dV)
+    assert E.item() < 0
