@@ -174,6 +174,18 @@ rix_status rix_backward(rix_ctx *ctx, const double *D_dev, double gEx,
  * (I, L global basis indices), row-major nbasis x nbasis.  Asynchronous. */
 rix_status rix_fold_gamma(rix_ctx *ctx, const double *K_dev, double *Kdense_dev, void *stream);
 
+/* C = A B for FP64 device matrices (row-major, leading dimensions in elements;
+ * C overwritten) computed on the BF16 tensor cores by error-free slicing: each
+ * row of A and column of B is scaled by its own power of two and cut into
+ * n_slices 7-bit integer digits (1..8); the slice products with s + t <=
+ * n_slices + 1 are accumulated exactly and combined in 64-bit fixed point.
+ * Error about 2^(-7 n_slices) of (row scale x column scale x K).  The splitting
+ * is Ozaki, Ogita, Oishi, Rump (2012); the paper itself uses FP64 BLAS
+ * (Sec. "Improvements of other relevant code parts").  Allocates its slice
+ * buffers on `stream` and synchronises it.  ETIMEOUT if a device wait ran out. */
+rix_status rix_gemm_sliced(const double *A, int64_t lda, const double *B, int64_t ldb, double *C,
+                           int64_t ldc, int32_t M, int32_t N, int32_t K, int32_t n_slices, void *stream);
+
 rix_status rix_stats(const rix_ctx *ctx, rix_stats_t *out);
 
 /* Device time of each stage of rix_build_K (ms), summed over the builds since

@@ -71,6 +71,8 @@ def load():
     lib.rix_backward.argtypes = [P, P, ctypes.c_double, P, P, P, P]
     lib.rix_fold_gamma.argtypes = [P, P, P, P]
     lib.rix_stats.argtypes = [P, ctypes.POINTER(_Stats)]
+    lib.rix_gemm_sliced.argtypes = [P, ctypes.c_int64, P, ctypes.c_int64, P, ctypes.c_int64, ctypes.c_int32,
+                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P]
     lib.rix_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
                                     ctypes.POINTER(ctypes.c_int32)]
     lib.rix_strerror.restype = ctypes.c_char_p
@@ -80,7 +82,7 @@ def load():
     lib.rix_destroy.argtypes = [P]
     for f in ("rix_setup", "rix_layout", "rix_layout_sizes", "rix_set_CV", "rix_build_K", "rix_energy",
               "rix_energy_noalloc",
-              "rix_backward", "rix_fold_gamma", "rix_stats", "rix_stage_times"):
+              "rix_backward", "rix_fold_gamma", "rix_stats", "rix_stage_times", "rix_gemm_sliced"):
         getattr(lib, f).restype = I
     _lib = lib
     return lib
@@ -180,6 +182,19 @@ def stats(ctx):
     d = {f: getattr(s, f) for f, _ in _Stats._fields_ if f != "flops_stage"}
     d["flops_stage"] = list(s.flops_stage)
     return d
+
+
+def gemm_sliced(A, B, n_slices, C=None, stream=None):
+    """rix_gemm_sliced: C = A @ B (FP64 CUDA matrices) on the BF16 tensor cores."""
+    import torch
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2
+    if C is None:
+        C = torch.empty((M, N), dtype=torch.float64, device=A.device)
+    _check(load().rix_gemm_sliced(_dptr(A, "A"), A.stride(0), _dptr(B, "B"), B.stride(0), _dptr(C, "C"),
+                                  C.stride(0), M, N, K, int(n_slices), _stream(stream)))
+    return C
 
 
 STAGES = ("flags", "T", "U2", "X12", "Z", "X34", "sym")
