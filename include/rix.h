@@ -110,6 +110,7 @@ typedef struct {
   double min_bytes;                /* 8 (nnz C + V + D) + 8 nnz K */
   double tensor_flops;             /* mixed mode: tensor-core FLOPs issued per build */
   int64_t workspace_bytes;         /* library-owned device memory */
+  int32_t n_row_blocks;            /* row blocks of the memory plan (1 = all intermediates resident) */
 } rix_stats_t;
 
 /* Set up a system: copies the host arrays, builds the pair list on the device

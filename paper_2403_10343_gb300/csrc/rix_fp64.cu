@@ -147,7 +147,8 @@ __global__ void __launch_bounds__(NT) k_T(const int2 *items, const int64_t *ptrT
                                           const int32_t *pB, const int32_t *nb, const int32_t *na,
                                           const double *__restrict__ C, const int64_t *offC,
                                           const double *__restrict__ D, const int64_t *offD,
-                                          const uint8_t *keepC, const uint8_t *keepD, double *T) {
+                                          const uint8_t *keepC, const uint8_t *keepD, double *T,
+                                          int64_t tbase) {
   extern __shared__ double sm[];
   const int tid = threadIdx.x;
   const int2 it = items[blockIdx.x];
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(NT) k_T(const int2 *items, const int64_t *ptrT
       }
     }
   }
-  double *out = T + off2[t] + (int64_t)p0 * per;
+  double *out = T + (off2[t] - tbase) + (int64_t)p0 * per;
 #pragma unroll
   for (int r = 0; r < MAXE; r++) {
     const int el = tid + r * NT;
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(NT) k_U2(const int2 *items, const int32_t *pA,
                                            const int32_t *nb, const int32_t *na, const double *__restrict__ V,
                                            const int64_t *offV, const uint8_t *keepV, const int32_t *map1to2,
                                            const double *__restrict__ T, const int64_t *off2,
-                                           const int64_t *offU, double *U) {
+                                           const int64_t *offU, double *U, int64_t tbase) {
   const int2 it = items[blockIdx.x];
   const int p = it.x, q0 = it.y;
   if (!keepV[p]) return;
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(NT) k_U2(const int2 *items, const int32_t *pA,
   const int qe = min(naG, q0 + qt);
   const int nel = (qe - q0) * per;
   const double *Vb = V + offV[p];
-  const double *Tt = T + off2[map1to2[p]];
+  const double *Tt = T + (off2[map1to2[p]] - tbase);
   double *out = U + offU[p] + (int64_t)q0 * per;
   for (int el = threadIdx.x; el < nel; el += NT) {
     const int q = q0 + el / per, c = el % per;
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(NT) k_X12(const int32_t *ord, const int64_t *p
                                             const int64_t *offV, const uint8_t *keepC, const uint8_t *keepV,
                                             const double *__restrict__ T, const int64_t *off2,
                                             const double *__restrict__ U, const int64_t *offU,
-                                            const int64_t *offK, double *X) {
+                                            const int64_t *offK, double *X, int64_t tbase) {
   extern __shared__ double sm[];
   const int tid = threadIdx.x;
   const int s = ord[blockIdx.x];
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(NT) k_X12(const int32_t *ord, const int64_t *p
     if (en.t1 && has1) {
       // term 1: U1[Q][i][k] = sum_P V(A,E')[P][Q] T(A,G')[P][i][k], Q on E', in tiles of Q
       const int qE0 = onsite[en.p3] ? 0 : naG;
-      const double *Tt = T + off2[en.t];
+      const double *Tt = T + (off2[en.t] - tbase);
       const double *Vae = V + offV[pae];
       const int per = nbA * nbG;
       const int qt = min(naE, max(1, SM_BIG / per));
@@ -315,7 +316,7 @@ __global__ void __launch_bounds__(NT) k_Z(const int2 *items, const int64_t *ptrZ
                                           const double *__restrict__ V, const int64_t *offV,
                                           const double *__restrict__ D, const int64_t *offD,
                                           const uint8_t *keepC, const uint8_t *keepV, const uint8_t *keepD,
-                                          double *Z) {
+                                          double *Z, int64_t zbase) {
   extern __shared__ double sm[];
   const int tid = threadIdx.x;
   const int2 it = items[blockIdx.x];
@@ -369,7 +370,7 @@ __global__ void __launch_bounds__(NT) k_Z(const int2 *items, const int64_t *ptrZ
       }
     }
   }
-  double *out = Z + off2[z] + (int64_t)p0 * per;
+  double *out = Z + (off2[z] - zbase) + (int64_t)p0 * per;
 #pragma unroll
   for (int r = 0; r < MAXE; r++) {
     const int el = tid + r * NT;
@@ -384,7 +385,8 @@ __global__ void __launch_bounds__(NT) k_X34(const int32_t *ord, const int64_t *p
                                             const int32_t *nb, const int32_t *na,
                                             const double *__restrict__ C, const int64_t *offC,
                                             const uint8_t *keepC, const double *__restrict__ Z,
-                                            const int64_t *off2, const int64_t *offK, double *X) {
+                                            const int64_t *off2, const int64_t *offK, double *X, int64_t zbase,
+                                            int64_t zlo, int64_t zhi) {
   extern __shared__ double sm[];
   const int tid = threadIdx.x;
   const int x = ord[blockIdx.x];
@@ -396,11 +398,11 @@ __global__ void __launch_bounds__(NT) k_X34(const int32_t *ord, const int64_t *p
   for (int r = 0; r < XMAXE; r++) acc[r] = 0.0;
   for (int64_t it = ptr[x]; it < ptr[x + 1]; it++) {
     const int2 en = L[it];
-    if (!keepC[en.x]) continue;
+    if (!keepC[en.x] || en.y < zlo || en.y >= zhi) continue;
     const int b = pB[en.x];
     const int nbB = nb[b], naB = na[b];
     const double *Cb = C + offC[en.x] + (int64_t)naA * nbA * nbB;
-    const double *Zb = Z + off2[en.y];
+    const double *Zb = Z + (off2[en.y] - zbase);
     const int csz = nbA * nbB, zsz = nbB * nbE;
     const int pc = max(1, min(naB, SM_BIG / (csz + zsz)));
     for (int P0 = 0; P0 < naB; P0 += pc) {
@@ -558,43 +560,58 @@ rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t
   if ((s = rix_prof_mark(ctx, 0, st)) != RIX_OK) return s;
   if ((s = rix_launch_flags(ctx, D, ctx->d_offD, ctx->np, ctx->d_keepD, st)) != RIX_OK) return s;
   if ((s = rix_prof_mark(ctx, 1, st)) != RIX_OK) return s;
-  if (ctx->n_itT) {
-    k_T<<<(unsigned)ctx->n_itT, NT, 64 * 64 * 8, st>>>(
-        ctx->d_itT, ctx->d_ptrT, ctx->d_LT, ctx->d_atomA2, ctx->d_atomB2, ctx->d_off2, ctx->d_pB, ctx->d_nb,
-        ctx->d_na, ctx->d_C, ctx->d_offC, D, ctx->d_offD, ctx->d_keepC, ctx->d_keepD, ctx->d_T);
-    if ((s = last(ctx, "k_T")) != RIX_OK) return s;
-  }
-  if ((s = rix_prof_mark(ctx, 2, st)) != RIX_OK) return s;
-  if (ctx->n_itU) {
-    k_U2<<<(unsigned)ctx->n_itU, NT, 0, st>>>(ctx->d_itU, ctx->d_pA, ctx->d_pB, ctx->d_nb, ctx->d_na, ctx->d_V,
-                                              ctx->d_offV, ctx->d_keepV, ctx->d_map1to2, ctx->d_T, ctx->d_off2,
-                                              ctx->d_offU, ctx->d_U);
-    if ((s = last(ctx, "k_U2")) != RIX_OK) return s;
-  }
-  if ((s = rix_prof_mark(ctx, 3, st)) != RIX_OK) return s;
   RIX_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_X, 0, sizeof(double) * ctx->offK[ctx->nk], st));
-  if (ctx->n_ordX12) {
-    k_X12<<<(unsigned)ctx->n_ordX12, NT, SM_BIG * 8, st>>>(
-        ctx->d_ordX12, ctx->d_ptrX12, ctx->d_LX12, ctx->d_atomA2, ctx->d_atomB2, ctx->d_map2to1,
-        ctx->d_map2to3, ctx->d_pA, ctx->d_onsite, ctx->d_nb, ctx->d_na, ctx->d_C, ctx->d_offC, ctx->d_V,
-        ctx->d_offV, ctx->d_keepC, ctx->d_keepV, ctx->d_T, ctx->d_off2, ctx->d_U, ctx->d_offU, ctx->d_offK,
-        ctx->d_X);
-    if ((s = last(ctx, "k_X12")) != RIX_OK) return s;
+  // terms 1 and 2, one block of row atoms at a time (T resident for the block)
+  for (int b = 0; b < ctx->nblk; b++) {
+    const int64_t tbase = ctx->blk_base[b];
+    const int64_t nT = ctx->segT[b + 1] - ctx->segT[b];
+    if (nT) {
+      k_T<<<(unsigned)nT, NT, 64 * 64 * 8, st>>>(
+          ctx->d_itT + ctx->segT[b], ctx->d_ptrT, ctx->d_LT, ctx->d_atomA2, ctx->d_atomB2, ctx->d_off2, ctx->d_pB,
+          ctx->d_nb, ctx->d_na, ctx->d_C, ctx->d_offC, D, ctx->d_offD, ctx->d_keepC, ctx->d_keepD, ctx->d_T, tbase);
+      if ((s = last(ctx, "k_T")) != RIX_OK) return s;
+    }
+    if (b == 0 && (s = rix_prof_mark(ctx, 2, st)) != RIX_OK) return s;
+    const int64_t nU = ctx->segU[b + 1] - ctx->segU[b];
+    if (nU) {
+      k_U2<<<(unsigned)nU, NT, 0, st>>>(ctx->d_itU + ctx->segU[b], ctx->d_pA, ctx->d_pB, ctx->d_nb, ctx->d_na,
+                                        ctx->d_V, ctx->d_offV, ctx->d_keepV, ctx->d_map1to2, ctx->d_T, ctx->d_off2,
+                                        ctx->d_offU, ctx->d_U, tbase);
+      if ((s = last(ctx, "k_U2")) != RIX_OK) return s;
+    }
+    if (b == 0 && (s = rix_prof_mark(ctx, 3, st)) != RIX_OK) return s;
+    const int64_t nX = ctx->segX12[b + 1] - ctx->segX12[b];
+    if (nX) {
+      k_X12<<<(unsigned)nX, NT, SM_BIG * 8, st>>>(
+          ctx->d_ordX12 + ctx->segX12[b], ctx->d_ptrX12, ctx->d_LX12, ctx->d_atomA2, ctx->d_atomB2, ctx->d_map2to1,
+          ctx->d_map2to3, ctx->d_pA, ctx->d_onsite, ctx->d_nb, ctx->d_na, ctx->d_C, ctx->d_offC, ctx->d_V,
+          ctx->d_offV, ctx->d_keepC, ctx->d_keepV, ctx->d_T, ctx->d_off2, ctx->d_U, ctx->d_offU, ctx->d_offK,
+          ctx->d_X, tbase);
+      if ((s = last(ctx, "k_X12")) != RIX_OK) return s;
+    }
+    if (b == 0 && (s = rix_prof_mark(ctx, 4, st)) != RIX_OK) return s;
   }
-  if ((s = rix_prof_mark(ctx, 4, st)) != RIX_OK) return s;
-  if (ctx->n_itZ) {
-    k_Z<<<(unsigned)ctx->n_itZ, NT, SM_BIG * 8, st>>>(
-        ctx->d_itZ, ctx->d_ptrZ, ctx->d_LZ, ctx->d_atomA2, ctx->d_atomB2, ctx->d_off2, ctx->d_pB, ctx->d_nb,
-        ctx->d_na, ctx->d_C, ctx->d_offC, ctx->d_V, ctx->d_offV, D, ctx->d_offD, ctx->d_keepC, ctx->d_keepV,
-        ctx->d_keepD, ctx->d_Z);
-    if ((s = last(ctx, "k_Z")) != RIX_OK) return s;
-  }
-  if ((s = rix_prof_mark(ctx, 5, st)) != RIX_OK) return s;
-  if (ctx->n_ordX34) {
-    k_X34<<<(unsigned)ctx->n_ordX34, NT, SM_BIG * 8, st>>>(
-        ctx->d_ordX34, ctx->d_ptrX34, ctx->d_LX34, ctx->d_atomA3, ctx->d_atomB3, ctx->d_pB, ctx->d_nb, ctx->d_na,
-        ctx->d_C, ctx->d_offC, ctx->d_keepC, ctx->d_Z, ctx->d_off2, ctx->d_offK, ctx->d_X);
-    if ((s = last(ctx, "k_X34")) != RIX_OK) return s;
+  // terms 3 and 4, one block of middle atoms B at a time (Z resident for the block)
+  for (int b = 0; b < ctx->nblk; b++) {
+    const int64_t zbase = ctx->blk_base[b];
+    const int64_t nZ = ctx->segZ[b + 1] - ctx->segZ[b];
+    if (nZ) {
+      k_Z<<<(unsigned)nZ, NT, SM_BIG * 8, st>>>(
+          ctx->d_itZ + ctx->segZ[b], ctx->d_ptrZ, ctx->d_LZ, ctx->d_atomA2, ctx->d_atomB2, ctx->d_off2, ctx->d_pB,
+          ctx->d_nb, ctx->d_na, ctx->d_C, ctx->d_offC, ctx->d_V, ctx->d_offV, D, ctx->d_offD, ctx->d_keepC,
+          ctx->d_keepV, ctx->d_keepD, ctx->d_Z, zbase);
+      if ((s = last(ctx, "k_Z")) != RIX_OK) return s;
+    }
+    if (b == 0 && (s = rix_prof_mark(ctx, 5, st)) != RIX_OK) return s;
+    if (ctx->have_mx) {
+      if ((s = rix_mixed_x34(ctx, ctx->blk_atom[b], ctx->blk_atom[b + 1], zbase, st)) != RIX_OK) return s;
+    } else if (ctx->n_ordX34) {
+      const int64_t zlo = ctx->row2[ctx->blk_atom[b]], zhi = ctx->row2[ctx->blk_atom[b + 1]];
+      k_X34<<<(unsigned)ctx->n_ordX34, NT, SM_BIG * 8, st>>>(
+          ctx->d_ordX34, ctx->d_ptrX34, ctx->d_LX34, ctx->d_atomA3, ctx->d_atomB3, ctx->d_pB, ctx->d_nb, ctx->d_na,
+          ctx->d_C, ctx->d_offC, ctx->d_keepC, ctx->d_Z, ctx->d_off2, ctx->d_offK, ctx->d_X, zbase, zlo, zhi);
+      if ((s = last(ctx, "k_X34")) != RIX_OK) return s;
+    }
   }
   if ((s = rix_prof_mark(ctx, 6, st)) != RIX_OK) return s;
   k_sym<<<(unsigned)ctx->nk, 128, 0, st>>>(ctx->nk, ctx->d_atomA3, ctx->d_atomB3, ctx->d_partner3, ctx->d_nb,

@@ -606,6 +606,7 @@ static rix_status build_lists(rix_ctx *ctx) {
     int64_t qt = std::max<int64_t>(1, CAP / per);
     for (int64_t q0 = 0; q0 < NA(g); q0 += qt) itU.push_back(make_int2((int)p, (int)q0));
   }
+  // launch order: most expensive first (longest processing time first)
   auto order_by = [](std::vector<int2> &it, const std::vector<double> &cost) {
     std::vector<int64_t> idx(it.size());
     std::iota(idx.begin(), idx.end(), 0);
@@ -617,16 +618,16 @@ static rix_status build_lists(rix_ctx *ctx) {
   order_by(itT, cT);
   order_by(itZ, cZ);
   std::vector<int32_t> ordX12, ordX34;
+  std::vector<double> cX12;
+  for (int64_t s = 0; s < n2; s++)
+    if (ptrX12[s + 1] > ptrX12[s]) {
+      ordX12.push_back((int32_t)s);
+      cX12.push_back((double)(ptrX12[s + 1] - ptrX12[s]) * NA(atomA2[s]) * NB(atomA2[s]));
+    }
   {
-    std::vector<double> c;
-    for (int64_t s = 0; s < n2; s++)
-      if (ptrX12[s + 1] > ptrX12[s]) {
-        ordX12.push_back((int32_t)s);
-        c.push_back((double)(ptrX12[s + 1] - ptrX12[s]) * NA(atomA2[s]) * NB(atomA2[s]));
-      }
     std::vector<int64_t> idx(ordX12.size());
     std::iota(idx.begin(), idx.end(), 0);
-    std::stable_sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) { return c[x] > c[y]; });
+    std::stable_sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) { return cX12[x] > cX12[y]; });
     std::vector<int32_t> o(idx.size());
     for (size_t i = 0; i < idx.size(); i++) o[i] = ordX12[idx[i]];
     ordX12.swap(o);
@@ -689,21 +690,87 @@ static rix_status build_lists(rix_ctx *ctx) {
   TRY(rix_upload(ctx, &ctx->d_LZ, LZ));
   TRY(rix_upload(ctx, &ctx->d_ptrX34, ptrX34));
   TRY(rix_upload(ctx, &ctx->d_LX34, LX34));
-  TRY(rix_upload(ctx, &ctx->d_itT, itT)); ctx->n_itT = itT.size();
-  TRY(rix_upload(ctx, &ctx->d_itZ, itZ)); ctx->n_itZ = itZ.size();
-  TRY(rix_upload(ctx, &ctx->d_itU, itU)); ctx->n_itU = itU.size();
-  TRY(rix_upload(ctx, &ctx->d_ordX12, ordX12)); ctx->n_ordX12 = ordX12.size();
-  TRY(rix_upload(ctx, &ctx->d_ordX34, ordX34)); ctx->n_ordX34 = ordX34.size();
   TRY(rix_upload(ctx, &ctx->d_fold, fold)); ctx->n_fold = (int64_t)fold.size() - 1;
   TRY(rix_upload(ctx, &ctx->d_bofs, bofs));
-  // workspaces
-  TRY(rix_alloc(ctx, &ctx->d_T, ctx->off2[n2]));
-  TRY(rix_alloc(ctx, &ctx->d_Z, ctx->off2[n2]));
   TRY(rix_alloc(ctx, &ctx->d_U, offU[np]));
   TRY(rix_alloc(ctx, &ctx->d_X, ctx->offK[nk]));
   ctx->n_epart = (np + 255) / 256;
   TRY(rix_alloc(ctx, &ctx->d_epart, ctx->n_epart + 1));
   TRY(rix_alloc(ctx, &ctx->d_flag, 4));
+
+  // ---------------------------------------------------------------- memory plan (row blocks)
+  // T and Z need off2[n2] doubles each.  If both do not fit in what is left, the
+  // rows are processed in blocks of consecutive atoms (the paper's Fock-matrix
+  // blocks): T, U2 and terms 1+2 per block of row atoms A, Z and terms 3+4 per
+  // block of middle atoms B, with T and Z buffers sized for the largest block.
+  std::vector<int64_t> asz(nat);
+  for (int a = 0; a < nat; a++) asz[a] = ctx->off2[row2[a + 1]] - ctx->off2[row2[a]];
+  int64_t avail;
+  {
+    size_t fr = 0, to = 0;
+    cudaMemGetInfo(&fr, &to);
+    avail = (int64_t)fr - ((int64_t)4 << 30);
+    if (ctx->opt.max_workspace_bytes > 0)
+      avail = std::min<int64_t>(avail, ctx->opt.max_workspace_bytes - (int64_t)ctx->dev_bytes);
+    if (ctx->opt.precision == RIX_MIXED_BF16) avail -= rix_mixed_bytes(ctx, ptrZ);
+  }
+  const int64_t per_buf = std::max<int64_t>(0, avail / 2 / (int64_t)sizeof(double));
+  ctx->blk_atom.assign(1, 0);
+  {
+    int64_t cur = 0;
+    for (int a = 0; a < nat; a++) {
+      if (asz[a] > per_buf) {
+        ctx->last_error = "workspace too small for the intermediates of one atom";
+        return RIX_ENOMEM;
+      }
+      if (cur + asz[a] > per_buf) {
+        ctx->blk_atom.push_back(a);
+        cur = 0;
+      }
+      cur += asz[a];
+    }
+    ctx->blk_atom.push_back(nat);
+  }
+  const int nblk = (int)ctx->blk_atom.size() - 1;
+  std::vector<int> blk_of(nat);
+  int64_t maxbuf = 0;
+  ctx->blk_base.assign(nblk, 0);
+  for (int b = 0; b < nblk; b++) {
+    for (int a = ctx->blk_atom[b]; a < ctx->blk_atom[b + 1]; a++) blk_of[a] = b;
+    ctx->blk_base[b] = ctx->off2[row2[ctx->blk_atom[b]]];
+    maxbuf = std::max(maxbuf, ctx->off2[row2[ctx->blk_atom[b + 1]]] - ctx->blk_base[b]);
+  }
+  // items of one block are contiguous, in cost order within the block
+  auto seg_sort = [&](std::vector<int2> &it, auto blk_of_item, std::vector<int64_t> &seg) {
+    std::stable_sort(it.begin(), it.end(), [&](const int2 &x, const int2 &y) { return blk_of_item(x) < blk_of_item(y); });
+    seg.assign(nblk + 1, 0);
+    for (auto &v : it) seg[blk_of_item(v) + 1]++;
+    for (int b = 0; b < nblk; b++) seg[b + 1] += seg[b];
+  };
+  seg_sort(itT, [&](const int2 &v) { return blk_of[atomA2[v.x]]; }, ctx->segT);
+  seg_sort(itZ, [&](const int2 &v) { return blk_of[atomA2[v.x]]; }, ctx->segZ);
+  seg_sort(itU, [&](const int2 &v) { return blk_of[pA[v.x]]; }, ctx->segU);
+  {
+    std::stable_sort(ordX12.begin(), ordX12.end(),
+                     [&](int32_t x, int32_t y) { return blk_of[atomA2[x]] < blk_of[atomA2[y]]; });
+    ctx->segX12.assign(nblk + 1, 0);
+    for (auto v : ordX12) ctx->segX12[blk_of[atomA2[v]] + 1]++;
+    for (int b = 0; b < nblk; b++) ctx->segX12[b + 1] += ctx->segX12[b];
+  }
+  ctx->nblk = nblk;
+  TRY(rix_upload(ctx, &ctx->d_itT, itT)); ctx->n_itT = itT.size();
+  TRY(rix_upload(ctx, &ctx->d_itZ, itZ)); ctx->n_itZ = itZ.size();
+  TRY(rix_upload(ctx, &ctx->d_itU, itU)); ctx->n_itU = itU.size();
+  TRY(rix_upload(ctx, &ctx->d_ordX12, ordX12)); ctx->n_ordX12 = ordX12.size();
+  TRY(rix_upload(ctx, &ctx->d_ordX34, ordX34)); ctx->n_ordX34 = ordX34.size();
+  if (nblk > 1 && ctx->opt.backward) {
+    ctx->last_error = "rix_backward needs T and Z resident (workspace too small)";
+    return RIX_ENOMEM;
+  }
+  TRY(rix_alloc(ctx, &ctx->d_T, maxbuf));
+  TRY(rix_alloc(ctx, &ctx->d_Z, maxbuf));
+  if (ctx->opt.precision == RIX_MIXED_BF16) TRY(rix_mixed_plan(ctx, ptrZ));
+  if (ctx->opt.verbose) fprintf(stderr, "rix: %d row block(s), T/Z buffers %.3g GB each\n", nblk, maxbuf * 8e-9);
   return RIX_OK;
 }
 
@@ -869,6 +936,7 @@ extern "C" rix_status rix_set_CV(rix_ctx *ctx, const double *C, const double *V,
   }
   if ((s = rix_launch_flags(ctx, ctx->d_C, ctx->d_offC, ctx->np, ctx->d_keepC, st)) != RIX_OK) return s;
   if ((s = rix_launch_flags(ctx, ctx->d_V, ctx->d_offV, ctx->np, ctx->d_keepV, st)) != RIX_OK) return s;
+  if ((s = rix_mixed_pack_C(ctx, st)) != RIX_OK) return s;
   ctx->have_cv = true;
   return RIX_OK;
 }
@@ -893,6 +961,7 @@ extern "C" rix_status rix_stats(const rix_ctx *ctx, rix_stats_t *out) {
   if (!ctx || !out) return RIX_EINVAL;
   *out = ctx->stats;
   out->workspace_bytes = (int64_t)ctx->dev_bytes;
+  out->n_row_blocks = ctx->nblk;
   return RIX_OK;
 }
 

@@ -204,6 +204,16 @@ __global__ void k_pack(const double *X, int64_t sr, int64_t sk, int R, int Kd, i
 }
 
 // ------------------------------------------------------------------ the GEMM
+// One problem of a batched launch: its packed operands, exponents and the
+// scatter maps of its output (rows (row block q, i), columns (col block z, l)).
+struct Prob {
+  int64_t aoff, boff;      // byte offsets of the A and B slice planes
+  int64_t eaoff, eboff;    // offsets into the exponent arrays
+  int64_t rowoff, coloff;  // offsets into rowinfo / colinfo
+  int64_t xoff;            // offset into xmap ([nq][nz])
+  int32_t Mpad, Npad, Kpad, M, N, nz, drop, pad_;
+};
+
 struct GemmArgs {
   const __nv_bfloat16 *A;  // planes [S][Mpad/128][Kpad/32] tiles
   const __nv_bfloat16 *B;  // planes [S][Npad/64][Kpad/32] tiles
@@ -214,6 +224,14 @@ struct GemmArgs {
   int accumulate;          // 1: C += result
   int drop;                // low bits dropped from the fixed-point sum (keeps it in 63 bits)
   int *err;                // set to 1 on a timed-out wait
+  // batched scatter mode (tiles != nullptr): C, ldc, M, N, Mpad, Npad, Kpad, drop come from Prob
+  const int4 *tiles;       // (problem, mt, nt, -)
+  const Prob *probs;
+  const int2 *rowinfo;     // (q, i) per packed row; q < 0 for padding
+  const int4 *colinfo;     // (z, l, nbE, -) per packed column; z < 0 for padding
+  const int32_t *xmap;     // output block index per (q, z)
+  const int64_t *offK;
+  double *X;               // X[offK[x] + i * nbE + l] += value (atomic)
 };
 
 // Bits the fixed-point sum needs: products below 2^14, at most Kpad of them per
@@ -238,11 +256,26 @@ __global__ void __launch_bounds__(256, 1) k_gemm_sliced(GemmArgs g) {
   int *abort_flag = (int *)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int mt = blockIdx.x, nt = blockIdx.y;
-  const int nk = g.Kpad / KC;
+  int mt = blockIdx.x, nt = blockIdx.y;
+  const __nv_bfloat16 *gA = g.A, *gB = g.B;
+  const int *geA = g.eA, *geB = g.eB;
+  int Mpad = g.Mpad, Npad = g.Npad, Kpad = g.Kpad, Mrows = g.M, Ncols = g.N, drop = g.drop;
+  const Prob *pr = nullptr;
+  if (g.tiles) {
+    const int4 t = g.tiles[blockIdx.x];
+    pr = g.probs + t.x;
+    mt = t.y;
+    nt = t.z;
+    gA = (const __nv_bfloat16 *)((const char *)g.A + pr->aoff);
+    gB = (const __nv_bfloat16 *)((const char *)g.B + pr->boff);
+    geA = g.eA + pr->eaoff;
+    geB = g.eB + pr->eboff;
+    Mpad = pr->Mpad; Npad = pr->Npad; Kpad = pr->Kpad; Mrows = pr->M; Ncols = pr->N; drop = pr->drop;
+  }
+  const int nk = Kpad / KC;
   const int ngroups = (nk + GROUP - 1) / GROUP;
-  const int64_t a_tiles = (int64_t)(g.Mpad / TM) * nk;  // tiles per A plane
-  const int64_t b_tiles = (int64_t)(g.Npad / TN) * nk;
+  const int64_t a_tiles = (int64_t)(Mpad / TM) * nk;  // tiles per A plane
+  const int64_t b_tiles = (int64_t)(Npad / TN) * nk;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < NSTAGE; i++) {
@@ -279,9 +312,9 @@ __global__ void __launch_bounds__(256, 1) k_gemm_sliced(GemmArgs g) {
       uint8_t *sb = sa + S * A_TILE;
       mbar_expect_tx(&full[st], (uint32_t)stage_bytes);
       for (int s = 0; s < S; s++) {
-        const char *ga = (const char *)g.A + ((int64_t)s * a_tiles + (int64_t)mt * nk + c) * A_TILE;
+        const char *ga = (const char *)gA + ((int64_t)s * a_tiles + (int64_t)mt * nk + c) * A_TILE;
         bulk_g2s(sa + s * A_TILE, ga, A_TILE, &full[st]);
-        const char *gb = (const char *)g.B + ((int64_t)s * b_tiles + (int64_t)nt * nk + c) * B_TILE;
+        const char *gb = (const char *)gB + ((int64_t)s * b_tiles + (int64_t)nt * nk + c) * B_TILE;
         bulk_g2s(sb + s * B_TILE, gb, B_TILE, &full[st]);
       }
     }
@@ -337,7 +370,7 @@ __global__ void __launch_bounds__(256, 1) k_gemm_sliced(GemmArgs g) {
       }
       tc_fence_after();
       for (int d = 2; d <= S + 1; d++) {
-        const int sh = 7 * (S + 1 - d) - g.drop;
+        const int sh = 7 * (S + 1 - d) - drop;
 #pragma unroll
         for (int n0 = 0; n0 < TN; n0 += 16) {
           uint32_t r[16];
@@ -355,16 +388,32 @@ __global__ void __launch_bounds__(256, 1) k_gemm_sliced(GemmArgs g) {
     }
     if (ok) {
       const int gr = mt * TM + row;
-      if (gr < g.M) {
-        const int er = g.eA[gr];
-        for (int n = 0; n < TN; n++) {
-          const int gc = nt * TN + n;
-          if (gc >= g.N) break;
-          const int sc = er + g.eB[gc] - 7 * (S + 1) + g.drop;
-          double v = ldexp((double)acc[n], sc);
-          double *dst = g.C + (int64_t)gr * g.ldc + gc;
-          if (g.accumulate) *dst += v;
-          else *dst = v;
+      if (gr < Mrows) {
+        const int er = geA[gr];
+        if (!pr) {
+          for (int n = 0; n < TN; n++) {
+            const int gc = nt * TN + n;
+            if (gc >= Ncols) break;
+            const int sc = er + geB[gc] - 7 * (S + 1) + drop;
+            double v = ldexp((double)acc[n], sc);
+            double *dst = g.C + (int64_t)gr * g.ldc + gc;
+            if (g.accumulate) *dst += v;
+            else *dst = v;
+          }
+        } else {
+          const int2 ri = g.rowinfo[pr->rowoff + gr];
+          if (ri.x >= 0) {
+            const int32_t *xrow = g.xmap + pr->xoff + (int64_t)ri.x * pr->nz;
+            for (int n = 0; n < TN; n++) {
+              const int gc = nt * TN + n;
+              if (gc >= Ncols) break;
+              const int4 ci = g.colinfo[pr->coloff + gc];
+              if (ci.x < 0) continue;
+              const int sc = er + geB[gc] - 7 * (S + 1) + drop;
+              const double v = ldexp((double)acc[n], sc);
+              atomicAdd(g.X + g.offK[xrow[ci.x]] + (int64_t)ri.y * ci.z + ci.y, v);
+            }
+          }
         }
       }
     }
@@ -415,7 +464,8 @@ extern "C" rix_status rix_gemm_sliced(const double *A, int64_t lda, const double
     const int64_t n = (int64_t)Npad * Kpad;
     k_pack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(B, 1, ldb, N, K, Npad, Kpad, eB, S, TN, Bp);
   }
-  GemmArgs g{Ap, Bp, eA, eB, C, ldc, M, N, Mpad, Npad, Kpad, S, 0, fixed_point_drop(Kpad, S), err};
+  GemmArgs g{Ap, Bp, eA, eB, C, ldc, M, N, Mpad, Npad, Kpad, S, 0, fixed_point_drop(Kpad, S), err,
+             nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   const int smem = NSTAGE * S * (A_TILE + B_TILE) + 8 * (2 * NSTAGE + 2) + 16;
   cudaFuncSetAttribute(k_gemm_sliced, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   k_gemm_sliced<<<dim3(Mpad / TM, Npad / TN), 256, smem, st>>>(g);
@@ -426,5 +476,337 @@ extern "C" rix_status rix_gemm_sliced(const double *A, int64_t lda, const double
   cudaFreeAsync(buf, st);
   if (e != cudaSuccess) return RIX_ECUDA;
   if (herr) return RIX_ETIMEOUT;
+  return RIX_OK;
+}
+
+// ==========================================================================
+// Terms 3+4 on the tensor cores: X(A,E') += sum_{P on B, j} C(A,B')[P][i][j] Z(B,E')[P][j][l]
+// as one sliced GEMM per middle atom B: rows (A', i) over B's neighbours A'
+// (not B itself), K = (P, j) on B, columns (E', l) over B's 2-hop blocks.
+// The C operand is constant and sliced once in rix_set_CV; Z is sliced per
+// build.  Results are added to X with FP64 atomics.
+// ==========================================================================
+namespace rixtc {
+
+// One warp per packed row (A operand) or column (B operand): exponent of the
+// row's largest |x| over K, then its S digits into the tile positions.
+__global__ void k_pack_C34(int64_t nrows, const int64_t *rowprob, const Prob *probs, const int2 *rowsrc,
+                           const int32_t *pA, const int32_t *pB, const int32_t *nb, const int32_t *na,
+                           const double *__restrict__ C, const int64_t *offC, const uint8_t *keepC, int S,
+                           __nv_bfloat16 *planes, int *eA) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= nrows) return;
+  const Prob pr = probs[rowprob[w]];
+  const int r = (int)(w - pr.rowoff);
+  const int2 src = rowsrc[w];
+  const int nkt = pr.Kpad / KC;
+  char *base = (char *)planes + pr.aoff;
+  const int64_t ptile = (int64_t)(pr.Mpad / TM) * nkt * A_TILE;  // bytes per plane
+  if (src.x < 0 || !keepC[src.x]) {
+    if (lane == 0) eA[pr.eaoff + r] = -2000;
+    return;  // planes start zeroed
+  }
+  const int p1 = src.x, i = src.y;
+  const int a = pA[p1], b = pB[p1];
+  const int nbA = nb[a], naA = na[a], nbB = nb[b], naB = na[b];
+  const int K = naB * nbB;
+  const double *row = C + offC[p1] + ((int64_t)naA * nbA + i) * nbB;  // [P][.][j] with stride nbA*nbB over P
+  int m = -2000;
+  for (int k = lane; k < K; k += 32) {
+    const int P = k / nbB, j = k - P * nbB;
+    m = max(m, exp_of(fabs(row[(int64_t)P * nbA * nbB + j])));
+  }
+  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) eA[pr.eaoff + r] = m;
+  for (int k = lane; k < K; k += 32) {
+    const int P = k / nbB, j = k - P * nbB;
+    float d[MAXS];
+    digits_of(row[(int64_t)P * nbA * nbB + j], m, S, d);
+    const int64_t off = ((int64_t)(r / TM) * nkt + k / KC) * A_TILE + tile_off(r % TM, k % KC);
+    for (int s = 0; s < S; s++) *(__nv_bfloat16 *)(base + s * ptile + off) = __float2bfloat16_rn(d[s]);
+  }
+}
+
+__global__ void k_pack_Z34(int64_t c0, int64_t ncols, const int64_t *colprob, const Prob *probs,
+                           const int4 *colsrc, const int32_t *atomA2, const int32_t *nb, const int32_t *na,
+                           const double *__restrict__ Z, const int64_t *off2, int64_t zbase, int64_t bbase, int S,
+                           __nv_bfloat16 *planes, int *eB) {
+  const int64_t w = c0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= c0 + ncols) return;
+  const Prob pr = probs[colprob[w]];
+  const int c = (int)(w - pr.coloff);
+  const int4 src = colsrc[w];  // (z, l, nbE, -)
+  const int nkt = pr.Kpad / KC;
+  char *base = (char *)planes + (pr.boff - bbase);
+  const int64_t ptile = (int64_t)(pr.Npad / TN) * nkt * B_TILE;
+  if (src.x < 0) {
+    if (lane == 0) eB[pr.eboff + c] = -2000;
+    return;
+  }
+  const int b = atomA2[src.x];
+  const int nbB = nb[b], naB = na[b];
+  const int K = naB * nbB, nbE = src.z, l = src.y;
+  const double *zc = Z + (off2[src.x] - zbase) + l;  // element k at zc[k * nbE]
+  int m = -2000;
+  for (int k = lane; k < K; k += 32) m = max(m, exp_of(fabs(zc[(int64_t)k * nbE])));
+  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) eB[pr.eboff + c] = m;
+  for (int k = lane; k < K; k += 32) {
+    float d[MAXS];
+    digits_of(zc[(int64_t)k * nbE], m, S, d);
+    const int64_t off = ((int64_t)(c / TN) * nkt + k / KC) * B_TILE + tile_off(c % TN, k % KC);
+    for (int s = 0; s < S; s++) *(__nv_bfloat16 *)(base + s * ptile + off) = __float2bfloat16_rn(d[s]);
+  }
+}
+
+}  // namespace rixtc
+
+#include <algorithm>
+#include <vector>
+
+// Build the batched plan for terms 3+4 on the tensor cores (called by rix_setup in
+// mixed precision).  ptrZ marks the Z blocks that receive products.
+rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
+  using namespace rix;
+  const int nat = ctx->nat, S = ctx->opt.n_slices > 0 ? ctx->opt.n_slices : 6;
+  if (S > MAXS) {
+    ctx->last_error = "n_slices above 8";
+    return RIX_EINVAL;
+  }
+  ctx->mx_S = S;
+  auto &row1 = ctx->row1, &row2 = ctx->row2, &row3 = ctx->row3;
+  auto find3 = [&](int64_t key) {
+    const int a = key_a(key);
+    auto it = std::lower_bound(ctx->keys3.begin() + row3[a], ctx->keys3.begin() + row3[a + 1], key);
+    return (it == ctx->keys3.begin() + row3[a + 1] || *it != key) ? (int64_t)-1 : (int64_t)(it - ctx->keys3.begin());
+  };
+  std::vector<Prob> probs(nat);
+  std::vector<int2> rowinfo, rowsrc;
+  std::vector<int4> colinfo, colsrc;
+  std::vector<int64_t> rowprob, colprob;
+  std::vector<int32_t> xmap;
+  std::vector<int4> tiles;
+  int64_t aoff = 0, eaoff = 0, eboff = 0;
+  std::vector<int64_t> bbytes(nat);
+  double tflops = 0;
+  const int npairs = S * (S + 1) / 2;
+  for (int b = 0; b < nat; b++) {
+    Prob &pr = probs[b];
+    std::vector<int64_t> qs, zs;
+    for (int64_t q = row1[b]; q < row1[b + 1]; q++)
+      if (!ctx->onsite[q]) qs.push_back(q);
+    for (int64_t z = row2[b]; z < row2[b + 1]; z++)
+      if (ptrZ[z + 1] > ptrZ[z]) zs.push_back(z);
+    int M = 0, N = 0;
+    for (auto q : qs) M += ctx->nb_at[ctx->pB[q]];
+    for (auto z : zs) N += ctx->nb_at[key_b(ctx->keys2[z])];
+    const int K = ctx->na_at[b] * ctx->nb_at[b];
+    pr.M = M; pr.N = N;
+    pr.Mpad = std::max(TM, (M + TM - 1) / TM * TM);
+    pr.Npad = std::max(TN, (N + TN - 1) / TN * TN);
+    pr.Kpad = (K + KC - 1) / KC * KC;
+    pr.nz = (int32_t)zs.size();
+    pr.drop = fixed_point_drop(pr.Kpad, S);
+    pr.aoff = aoff;
+    pr.eaoff = eaoff;
+    pr.eboff = eboff;
+    pr.rowoff = (int64_t)rowinfo.size();
+    pr.coloff = (int64_t)colinfo.size();
+    pr.xoff = (int64_t)xmap.size();
+    aoff += (int64_t)S * pr.Mpad * pr.Kpad * 2;
+    bbytes[b] = (int64_t)S * pr.Npad * pr.Kpad * 2;
+    eaoff += pr.Mpad;
+    eboff += pr.Npad;
+    for (int qi = 0; qi < (int)qs.size(); qi++) {
+      const int64_t q = qs[qi];
+      const int a = ctx->pB[q];
+      for (int i = 0; i < ctx->nb_at[a]; i++) {
+        rowinfo.push_back(make_int2(qi, i));
+        rowsrc.push_back(make_int2(ctx->partner1[q], i));
+        rowprob.push_back(b);
+      }
+    }
+    for (int r = M; r < pr.Mpad; r++) {
+      rowinfo.push_back(make_int2(-1, 0));
+      rowsrc.push_back(make_int2(-1, 0));
+      rowprob.push_back(b);
+    }
+    for (int zi = 0; zi < (int)zs.size(); zi++) {
+      const int e = key_b(ctx->keys2[zs[zi]]);
+      for (int l = 0; l < ctx->nb_at[e]; l++) {
+        colinfo.push_back(make_int4(zi, l, ctx->nb_at[e], 0));
+        colsrc.push_back(make_int4((int)zs[zi], l, ctx->nb_at[e], 0));
+        colprob.push_back(b);
+      }
+    }
+    for (int c = N; c < pr.Npad; c++) {
+      colinfo.push_back(make_int4(-1, 0, 0, 0));
+      colsrc.push_back(make_int4(-1, 0, 0, 0));
+      colprob.push_back(b);
+    }
+    // output block of (row block q, column block z): atom A at -n_q from B, E' at n_z from B
+    for (auto q : qs) {
+      const int a = ctx->pB[q];
+      for (auto z : zs) {
+        const int64_t kz = ctx->keys2[z];
+        const int n0 = key_n(kz, 0) - ctx->pn[3 * q], n1 = key_n(kz, 1) - ctx->pn[3 * q + 1],
+                  n2 = key_n(kz, 2) - ctx->pn[3 * q + 2];
+        const int64_t x = find3(pair_key(a, key_b(kz), n0, n1, n2));
+        if (x < 0) {
+          ctx->last_error = "mixed plan: output block outside the K pattern";
+          return RIX_EINVAL;
+        }
+        xmap.push_back((int32_t)x);
+      }
+    }
+    for (int nt = 0; nt < pr.Npad / TN; nt++)
+      for (int mt = 0; mt < pr.Mpad / TM; mt++) tiles.push_back(make_int4(b, mt, nt, 0));
+    tflops += 2.0 * pr.Mpad * pr.Npad * pr.Kpad * npairs;
+  }
+  // groups of consecutive B inside one memory-plan block, B slices within a budget
+  const int64_t budget = std::max<int64_t>(bbytes.empty() ? 0 : *std::max_element(bbytes.begin(), bbytes.end()),
+                                           (int64_t)16 << 30);
+  ctx->mx_grp.clear();
+  ctx->mx_grp.push_back(0);
+  int64_t cur = 0, maxgrp = 0;
+  int blk = 0;
+  for (int b = 0; b < nat; b++) {
+    while (b >= ctx->blk_atom[blk + 1]) blk++;
+    const bool new_blk = b == ctx->blk_atom[blk] && b > 0;
+    if (b > 0 && (new_blk || cur + bbytes[b] > budget)) {
+      ctx->mx_grp.push_back(b);
+      maxgrp = std::max(maxgrp, cur);
+      cur = 0;
+    }
+    probs[b].boff = cur;  // relative to the group's buffer
+    cur += bbytes[b];
+  }
+  maxgrp = std::max(maxgrp, cur);
+  ctx->mx_grp.push_back(nat);
+  // tile and column ranges per group (tiles and columns are ordered by B)
+  ctx->mx_tile_seg.assign(ctx->mx_grp.size(), 0);
+  ctx->mx_col_seg.assign(ctx->mx_grp.size(), 0);
+  {
+    size_t gi = 0, ti = 0, ci = 0;
+    for (gi = 0; gi + 1 < ctx->mx_grp.size(); gi++) {
+      const int bend = ctx->mx_grp[gi + 1];
+      while (ti < tiles.size() && tiles[ti].x < bend) ti++;
+      while (ci < colprob.size() && colprob[ci] < bend) ci++;
+      ctx->mx_tile_seg[gi + 1] = ti;
+      ctx->mx_col_seg[gi + 1] = ci;
+    }
+  }
+  ctx->stats.tensor_flops = tflops;
+  ctx->mx_nrows = (int64_t)rowinfo.size();
+  ctx->mx_ncols = (int64_t)colinfo.size();
+  rix_status s;
+  if ((s = rix_upload(ctx, (Prob **)&ctx->d_mx_probs, probs)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &ctx->d_mx_rowinfo, rowinfo)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &ctx->d_mx_rowsrc, rowsrc)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &ctx->d_mx_rowprob, rowprob)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &ctx->d_mx_colinfo, colinfo)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &ctx->d_mx_colsrc, colsrc)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &ctx->d_mx_colprob, colprob)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &ctx->d_mx_xmap, xmap)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &ctx->d_mx_tiles, tiles)) != RIX_OK) return s;
+  if ((s = rix_alloc(ctx, &ctx->d_mx_eA, std::max<int64_t>(eaoff, 1))) != RIX_OK) return s;
+  if ((s = rix_alloc(ctx, &ctx->d_mx_eB, std::max<int64_t>(eboff, 1))) != RIX_OK) return s;
+  if ((s = rix_alloc(ctx, &ctx->d_mx_err, 4)) != RIX_OK) return s;
+  if ((s = rix_dev_alloc(ctx, (void **)&ctx->d_mx_A, std::max<int64_t>(aoff, 16))) != RIX_OK) return s;
+  if ((s = rix_dev_alloc(ctx, (void **)&ctx->d_mx_B, std::max<int64_t>(maxgrp, 16))) != RIX_OK) return s;
+  ctx->mx_A_bytes = aoff;
+  ctx->mx_B_bytes = maxgrp;
+  RIX_CUDA_TRY(ctx, cudaMemset(ctx->d_mx_A, 0, std::max<int64_t>(aoff, 16)));
+  RIX_CUDA_TRY(ctx, cudaMemset(ctx->d_mx_B, 0, std::max<int64_t>(maxgrp, 16)));
+  RIX_CUDA_TRY(ctx, cudaMemset(ctx->d_mx_err, 0, 4));
+  ctx->have_mx = true;
+  if (ctx->opt.verbose)
+    fprintf(stderr, "rix mixed: %zu GEMM tiles, C slices %.3g GB, Z slice buffer %.3g GB, %zu group(s)\n",
+            tiles.size(), aoff * 1e-9, maxgrp * 1e-9, ctx->mx_grp.size() - 1);
+  return RIX_OK;
+}
+
+// Device bytes the mixed plan will need (slices of C, one group of Z slices, maps).
+int64_t rix_mixed_bytes(const rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
+  const int S = ctx->opt.n_slices > 0 ? ctx->opt.n_slices : 6;
+  int64_t a = 0, bmax = 0, btot = 0, maps = 0;
+  for (int b = 0; b < ctx->nat; b++) {
+    int64_t M = 0, N = 0, nq = 0, nz = 0;
+    for (int64_t q = ctx->row1[b]; q < ctx->row1[b + 1]; q++)
+      if (!ctx->onsite[q]) { M += ctx->nb_at[ctx->pB[q]]; nq++; }
+    for (int64_t z = ctx->row2[b]; z < ctx->row2[b + 1]; z++)
+      if (ptrZ[z + 1] > ptrZ[z]) { N += ctx->nb_at[rix::key_b(ctx->keys2[z])]; nz++; }
+    const int64_t K = (int64_t)ctx->na_at[b] * ctx->nb_at[b];
+    const int64_t Mp = std::max<int64_t>(rixtc::TM, (M + rixtc::TM - 1) / rixtc::TM * rixtc::TM);
+    const int64_t Np = std::max<int64_t>(rixtc::TN, (N + rixtc::TN - 1) / rixtc::TN * rixtc::TN);
+    const int64_t Kp = (K + rixtc::KC - 1) / rixtc::KC * rixtc::KC;
+    a += S * Mp * Kp * 2;
+    bmax = std::max(bmax, S * Np * Kp * 2);
+    btot += S * Np * Kp * 2;
+    maps += nq * nz * 4 + (Mp * 3 + Np * 5) * 8 + (Mp / rixtc::TM) * (Np / rixtc::TN) * 16;
+  }
+  return a + std::min(btot, std::max(bmax, (int64_t)16 << 30)) + maps;
+}
+
+// Slice the constant C operand (after rix_set_CV has loaded C and its flags).
+rix_status rix_mixed_pack_C(rix_ctx *ctx, cudaStream_t st) {
+  using namespace rixtc;
+  if (!ctx->have_mx || ctx->mx_nrows == 0) return RIX_OK;
+  const int64_t blocks = (ctx->mx_nrows * 32 + 255) / 256;
+  k_pack_C34<<<(unsigned)blocks, 256, 0, st>>>(ctx->mx_nrows, ctx->d_mx_rowprob, (const Prob *)ctx->d_mx_probs,
+                                               ctx->d_mx_rowsrc, ctx->d_pA, ctx->d_pB, ctx->d_nb, ctx->d_na,
+                                               ctx->d_C, ctx->d_offC, ctx->d_keepC, ctx->mx_S,
+                                               (__nv_bfloat16 *)ctx->d_mx_A, ctx->d_mx_eA);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    ctx->last_error = std::string("k_pack_C34: ") + cudaGetErrorString(e);
+    return RIX_ECUDA;
+  }
+  return RIX_OK;
+}
+
+// Terms 3+4 for the middle atoms [b0, b1) of one memory-plan block: slice their Z
+// blocks and run the batched GEMM into X.
+rix_status rix_mixed_x34(rix_ctx *ctx, int b0, int b1, int64_t zbase, cudaStream_t st) {
+  using namespace rixtc;
+  static bool attr = false;
+  const int S = ctx->mx_S;
+  const int smem = NSTAGE * S * (A_TILE + B_TILE) + 8 * (2 * NSTAGE + 2) + 16;
+  if (!attr) {
+    cudaFuncSetAttribute(k_gemm_sliced, cudaFuncAttributeMaxDynamicSharedMemorySize, NSTAGE * MAXS * (A_TILE + B_TILE) + 64);
+    attr = true;
+  }
+  for (size_t gi = 0; gi + 1 < ctx->mx_grp.size(); gi++) {
+    const int g0 = ctx->mx_grp[gi], g1 = ctx->mx_grp[gi + 1];
+    if (g1 <= b0 || g0 >= b1) continue;
+    const int64_t c0 = ctx->mx_col_seg[gi], c1 = ctx->mx_col_seg[gi + 1];
+    const int64_t t0 = ctx->mx_tile_seg[gi], t1 = ctx->mx_tile_seg[gi + 1];
+    const Prob *probs = (const Prob *)ctx->d_mx_probs;
+    int64_t bbase = 0;
+    {
+      // byte offset of the group's first problem in the per-group buffer is 0 by construction
+      bbase = 0;
+    }
+    if (c1 > c0) {
+      const int64_t blocks = ((c1 - c0) * 32 + 255) / 256;
+      k_pack_Z34<<<(unsigned)blocks, 256, 0, st>>>(c0, c1 - c0, ctx->d_mx_colprob, probs, ctx->d_mx_colsrc,
+                                                   ctx->d_atomA2, ctx->d_nb, ctx->d_na, ctx->d_Z, ctx->d_off2, zbase,
+                                                   bbase, S, (__nv_bfloat16 *)ctx->d_mx_B, ctx->d_mx_eB);
+    }
+    if (t1 > t0) {
+      GemmArgs g{(const __nv_bfloat16 *)ctx->d_mx_A, (const __nv_bfloat16 *)ctx->d_mx_B, ctx->d_mx_eA,
+                 ctx->d_mx_eB, nullptr, 0, 0, 0, 0, 0, 0, S, 1, 0, ctx->d_mx_err,
+                 ctx->d_mx_tiles + t0, probs, ctx->d_mx_rowinfo, ctx->d_mx_colinfo, ctx->d_mx_xmap, ctx->d_offK,
+                 ctx->d_X};
+      k_gemm_sliced<<<(unsigned)(t1 - t0), 256, smem, st>>>(g);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      ctx->last_error = std::string("mixed terms 3+4: ") + cudaGetErrorString(e);
+      return RIX_ECUDA;
+    }
+  }
   return RIX_OK;
 }

@@ -43,7 +43,8 @@ class _Stats(ctypes.Structure):
                 ("n_kblocks", ctypes.c_int64), ("c_elems", ctypes.c_int64), ("v_elems", ctypes.c_int64),
                 ("d_elems", ctypes.c_int64), ("k_elems", ctypes.c_int64), ("flops_fp64", ctypes.c_double),
                 ("flops_stage", ctypes.c_double * 6), ("min_bytes", ctypes.c_double),
-                ("tensor_flops", ctypes.c_double), ("workspace_bytes", ctypes.c_int64)]
+                ("tensor_flops", ctypes.c_double), ("workspace_bytes", ctypes.c_int64),
+                ("n_row_blocks", ctypes.c_int32)]
 
 
 _lib = None

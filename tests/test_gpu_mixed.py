@@ -1,0 +1,88 @@
+"""Mixed precision (terms 3+4 on the BF16 tensor cores by error-free slicing).
+
+Bar for the mixed path: K within 1e-8 relative Frobenius of the FP64 oracle
+and |dE_x| <= 1e-6 Ha.  The error against the FP64 path is also reported.
+"""
+import numpy as np
+import pytest
+
+import rix_inputs as ri
+import rix_inputs.systems as S
+from oracle.oracle import exchange
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2403_10343_gb300.rix import Exchange  # noqa: E402
+
+K_TOL = 1e-8
+E_TOL_HA = 1e-6
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda")
+
+
+def _run(s, pk, **kw):
+    ex = Exchange.from_system(s, **kw)
+    ex.set_CV(_dev(pk.C), _dev(pk.V))
+    D = _dev(pk.D)
+    K = ex.build_K(D)
+    E = ex.energy(D, K)
+    torch.cuda.synchronize()
+    return ex, ex.k_keys(), K.cpu().numpy(), E.item()
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("case", ["cluster24", "pbc_selfimage", "heavy"])
+def test_mixed_against_oracle(case):
+    if case == "cluster24":
+        s = ri.config(0)
+    elif case == "pbc_selfimage":
+        o = np.array([[1.0, 1.2, 0.8]])
+        xyz, spc = S._waters(o, 11)
+        nb, na = S._species_arrays(["O", "H"])
+        s = S.System(name="p", seed=11, xyz=ri.ang2bohr(xyz), species=spc, species_names=["O", "H"], nbas=nb,
+                     naux=na, sigma=S._aux_widths(11, ["O", "H"]), cell=ri.ang2bohr(np.eye(3) * 4.6),
+                     cutoff=ri.ang2bohr(4.8), tau=0.0,
+                     orbital_centres=np.repeat(np.arange(0, len(spc), 3), 5).astype(np.int32))
+    else:
+        s = S.perovskite(1, 1, 1, 31)
+        s.cutoff = ri.ang2bohr(6.5)
+    pk = ri.generate(s)
+    kk, K_ref, E_ref, _ = exchange(s, pk)
+    ex, keys, K, E = _run(s, pk, precision="mixed")
+    assert np.array_equal(keys, kk)
+    err = _rel(K, K_ref)
+    print(f"{case}: mixed K rel err {err:.2e}, |dE| {abs(E - E_ref):.2e} Ha")
+    assert err < K_TOL
+    assert abs(E - E_ref) < E_TOL_HA
+    assert ex.stats()["tensor_flops"] > 0
+
+
+def test_mixed_slices_converge():
+    s = ri.config(0)
+    pk = ri.generate(s)
+    _, _, K64, E64 = _run(s, pk)
+    errs = []
+    for nsl in (3, 4, 5, 6):
+        _, _, K, E = _run(s, pk, precision="mixed", n_slices=nsl)
+        errs.append(_rel(K, K64))
+    print("mixed error vs slices 3..6:", errs)
+    assert errs[-1] < errs[0]
+    assert errs[-1] < 1e-10
+
+
+def test_mixed_full_size_cluster():
+    s = ri.config(1)
+    pk = ri.generate(s)
+    _, keys, K64, E64 = _run(s, pk)
+    _, keys2, K, E = _run(s, pk, precision="mixed")
+    assert np.array_equal(keys, keys2)
+    err = _rel(K, K64)
+    print(f"(H2O)64 mixed vs FP64: K rel err {err:.2e}, dE {E - E64:.2e} Ha")
+    assert err < K_TOL
+    assert abs(E - E64) < E_TOL_HA
