@@ -7,7 +7,7 @@
  * the compute entry points never synchronise the host.
  *
  * The operation (Kokott et al., arXiv:2403.10343, Sec. "Description of the
- * real-space formalism", Eq. 117-121 with the RI-LVL restriction Eq. 127-135):
+ * real-space formalism", Eq. 4 with the RI-LVL restriction of Eqs. 6-7):
  *
  *   K_il(n) = sum_{jk} sum_{PQ} C^P_ij V_PQ C^Q_kl D_jk
  *   E_x     = -1/4 sum_il D_li K_il            (-1/4 Tr(D K), one cell)
@@ -30,7 +30,7 @@
  *   C(A,B,n): [P][i][j] row-major, P over aux(A) then aux(B) (aux(A) only for
  *             the on-site pair A == B, n == 0); i in basis(A), j in basis(B).
  *             Must satisfy C(B,A,-n)[P][j][i] == C(A,B,n)[P][i][j] bit for bit
- *             (the translational/pair symmetry the paper uses, Eq. 157-181).
+ *             (the translational/pair symmetry the paper uses with Eqs. 11-12).
  *   V(A,B,n): [P][Q], P in aux(A), Q in aux(B at n); V(B,A,-n) = V(A,B,n)^T.
  *   D(A,B,n): [i][j]; D(B,A,-n) = D(A,B,n)^T (not checked).
  *   K(A,E,n): [i][l] on the K pattern: every (A, E, n) reachable from A by at

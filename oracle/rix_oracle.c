@@ -7,15 +7,16 @@
  *
  * What it computes (paper, Sec. "Description of the real-space formalism"):
  *
- *   K_il = sum_{jk} sum_{PQ} C^P_ij V_PQ C^Q_kl D_jk            (Eq. 117-121)
+ *   K_il = sum_{jk} sum_{PQ} C^P_ij V_PQ C^Q_kl D_jk            (Eq. 4)
  *   E_x  = -1/4 sum_il D_li K_il                                   (-1/4 Tr(D K))
  *
  * with the RI-LVL restriction C^P_ij = 0 unless P sits on the atom of i or the
- * atom of j (Eq. 127-135), image-resolved lattice sums (Eq. 117-121) and the
+ * atom of j (Eqs. 6-7), image-resolved lattice sums (Eq. 4) and the
  * translational symmetry C^{mu(R')}_{i(0) k(R')} = C^{mu(0)}_{k(0) i(-R')}.
  *
  * The sum is taken in the paper's grouping by which atom carries P and which
- * carries Q (Eq. 157-172; i on A, j on B, k on G, l on E):
+ * carries Q (Eq. 11 with the intermediates of Eqs. 12a-12d; i on A, j on B,
+ * k on G, l on E):
  *   term 1  P on A, Q on E         : T = C D (E = C*D), U = V^T T, K += U C
  *   term 2  P on A, Q on G (G!=E)  : U = V(A,G)^T T,   K += U C
  *   term 3  P on B (B!=A), Q on E  : S = D C, Z3 = V S, K += C Z3

@@ -1,7 +1,7 @@
 // FP64 path of the exchange build and the shared small kernels.
 //
 // The build runs the paper's grouping of the RI-LVL sum by the atoms that
-// carry the two auxiliary functions (Eq. 157-172).  With i on A, j on B',
+// carry the two auxiliary functions (Eq. 11, Eqs. 12a-12d).  With i on A, j on B',
 // k on G', l on E' it computes
 //
 //   T(A,G')   = sum_B' C(A,B')^{P on A} D(B',G')                (E = C*D)
@@ -13,7 +13,7 @@
 //   K(A,E',n) = X(A,E',n) + X(E',A,-n)^T
 //
 // Term 3 (P on B', Q on E') equals term 2 transposed (the pair symmetry of C,
-// V and D, Eq. 181; the paper's "2G"), and terms 1 and 4 are symmetric by
+// V and D stated after Eqs. 12a-12d; the paper's "2G"), and terms 1 and 4 are symmetric by
 // themselves, so the last line restores all four terms exactly.
 //
 // Each kernel is output-stationary: one CTA owns an output block (or a row

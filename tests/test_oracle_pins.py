@@ -76,7 +76,7 @@ def test_dense_chain_24_atoms():
 
 @pytest.mark.parametrize("nmol,side,cut", [(2, 6.0, 4.0), (1, 4.6, 4.8)])
 def test_periodic_definition(nmol, side, cut):
-    """Image-resolved K(A,E,n) against the per-quadruple definition (Eq. 117-121).
+    """Image-resolved K(A,E,n) against the per-quadruple definition (Eq. 4).
 
     The second case has the atom's own periodic images inside the cutoff
     (pairs (A, A, n != 0) with two aux sets)."""
