@@ -57,6 +57,8 @@ def _load():
             lib.orc_set_terms.argtypes = [P, ctypes.c_int]
             lib.orc_build_K_ex.restype = ctypes.c_int
             lib.orc_build_K_ex.argtypes = [P, P, ctypes.c_int]
+            lib.orc_kpattern_blocks.restype = ctypes.c_int64
+            lib.orc_kpattern_blocks.argtypes = [P, ctypes.c_int64, P]
             lib.orc_flops.restype = ctypes.c_double
             lib.orc_flops.argtypes = [P]
             _lib = lib
@@ -129,6 +131,16 @@ class Oracle:
         k = np.empty(nk, dtype=np.int64)
         self.lib.orc_kkeys(self.h, _ptr(k))
         return k
+
+    def kpattern_blocks(self, keys):
+        """Sampled mode: only the listed K blocks (A, E', n); returns them sorted."""
+        k = np.ascontiguousarray(keys, dtype=np.int64)
+        self._rows = None
+        self._sampled = k
+        n = self.lib.orc_kpattern_blocks(self.h, len(k), k.ctypes.data_as(ctypes.c_void_p))
+        out = np.empty(n, dtype=np.int64)
+        self.lib.orc_kkeys(self.h, out.ctypes.data_as(ctypes.c_void_p))
+        return out
 
     def build_K(self, dry=False):
         """K for the rows of the last kpattern(); dry=True only counts the work."""

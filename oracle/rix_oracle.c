@@ -112,6 +112,8 @@ typedef struct {
     int terms;  /* bit t-1 enables term t (all four by default) */
     int dry;    /* 1: count the multiply-adds of a build without doing them */
     double flops;  /* FLOPs (2 per multiply-add) of the last build */
+    int sampled;   /* 1: K only for the blocks listed in kkeys (orc_kpattern_blocks) */
+    hmap needZ;    /* sampled mode: Z blocks (B, E', m) some listed K block uses */
 } orc;
 
 static inline int NB(const orc *o, int a) { return o->nbs[o->sp[a]]; }
@@ -301,6 +303,7 @@ static int cmp_u64(const void *a, const void *b) {
 int64_t orc_kpattern(void *h, int nrows, const int32_t *rows) {
     orc *o = (orc *)h;
     free(o->rows); free(o->kkeys); free(o->offK); free(o->krow);
+    if (o->sampled) { hm_free(&o->needZ); o->sampled = 0; }
     if (nrows < 0) {
         o->nrows = o->nat;
         o->rows = (int32_t *)malloc(sizeof(int32_t) * o->nat);
@@ -368,6 +371,46 @@ int64_t orc_kpattern(void *h, int nrows, const int32_t *rows) {
     }
     return o->nk;
 }
+/* K pattern = an explicit list of blocks (A, E', n) (sampled mode): only these
+ * blocks are computed, with T and Z restricted to what they need.  Returns the
+ * number of blocks; their order follows orc_kkeys (sorted). */
+static int cmp_u64b(const void *a, const void *b) {
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return x < y ? -1 : x > y;
+}
+int64_t orc_kpattern_blocks(void *h, int64_t n, const int64_t *keys) {
+    orc *o = (orc *)h;
+    free(o->rows); free(o->kkeys); free(o->offK); free(o->krow);
+    if (o->sampled) hm_free(&o->needZ);
+    o->sampled = 1;
+    o->kkeys = (uint64_t *)malloc(sizeof(uint64_t) * (n + 1));
+    memcpy(o->kkeys, keys, sizeof(uint64_t) * n);
+    qsort(o->kkeys, n, sizeof(uint64_t), cmp_u64b);
+    o->nk = n;
+    o->rows = (int32_t *)malloc(sizeof(int32_t) * (n + 1));
+    o->krow = (int64_t *)malloc(sizeof(int64_t) * (n + 2));
+    o->nrows = 0;
+    for (int64_t x = 0; x < n; x++) {
+        int a = (int)((o->kkeys[x] >> 44) & 0xFFFFF);
+        if (o->nrows == 0 || o->rows[o->nrows - 1] != a) { o->rows[o->nrows] = a; o->krow[o->nrows] = x; o->nrows++; }
+    }
+    o->krow[o->nrows] = n;
+    o->offK = (int64_t *)malloc(sizeof(int64_t) * (n + 1));
+    o->offK[0] = 0;
+    hm_init(&o->needZ, 4096);
+    for (int64_t x = 0; x < n; x++) {
+        int a = (int)((o->kkeys[x] >> 44) & 0xFFFFF), e = (int)((o->kkeys[x] >> 24) & 0xFFFFF);
+        int m1 = (int)((o->kkeys[x] >> 16) & 0xFF) - 128, m2 = (int)((o->kkeys[x] >> 8) & 0xFF) - 128,
+            m3 = (int)(o->kkeys[x] & 0xFF) - 128;
+        o->offK[x + 1] = o->offK[x] + (int64_t)NB(o, a) * NB(o, e);
+        for (int64_t p = o->rowptr[a]; p < o->rowptr[a + 1]; p++) {
+            const int32_t *n1 = o->pn + 3 * p;
+            hm_get_or_put(&o->needZ, pair_key(o->pB[p], e, m1 - n1[0], m2 - n1[1], m3 - n1[2]), 1);
+        }
+    }
+    return n;
+}
+
 void orc_kkeys(void *h, int64_t *keys) {
     orc *o = (orc *)h;
     memcpy(keys, o->kkeys, sizeof(int64_t) * o->nk);
@@ -438,6 +481,7 @@ static void build_Z(const orc *o, int b, nodestore *Z, double *fl) {
             int m1 = n2[0] + n3[0], m2 = n2[1] + n3[1], m3 = n2[2] + n3[2];
             const double *Cge = o->C + o->offC[p3];
             int qE0 = o->onsite[p3] ? 0 : naG;  /* first row of aux(E') in C(G',E') */
+            if (o->sampled && hm_get(&o->needZ, pair_key(b, e, m1, m2, m3)) < 0) continue;
             /* term 3: S(B,E') if V(B,E') is present */
             int64_t pbe = find_pair(o, b, e, m1, m2, m3);
             if ((o->terms & 4) && pbe >= 0 && o->keepV[pbe]) {
@@ -508,11 +552,13 @@ static void build_Z(const orc *o, int b, nodestore *Z, double *fl) {
 
 /* index of a K block in a row (the pattern holds every node the terms reach) */
 static int64_t kfind(const orc *o, int64_t lo, int64_t hi, uint64_t key) {
+    const int64_t end = hi;
     while (lo < hi) {
         int64_t mid = (lo + hi) / 2;
         if (o->kkeys[mid] < key) lo = mid + 1; else hi = mid;
     }
-    return lo;  /* the pattern contains every node the terms reach */
+    if (lo < end && o->kkeys[lo] == key) return lo;
+    return o->sampled ? -1 : lo;  /* a full pattern contains every node the terms reach */
 }
 
 /* ---------------------------------------------------------- one K row */
@@ -522,6 +568,18 @@ static void k_row(const orc *o, int r, nodestore *Zs, const uint8_t *haveZ, doub
     int64_t k0 = o->krow[r], k1 = o->krow[r + 1];
     /* K blocks of this row: binary search in the sorted row keys */
 #define KBLOCK(E, M1, M2, M3) kfind(o, k0, k1, pair_key(a, (E), (M1), (M2), (M3)))
+    /* sampled mode: T only for the nodes G' next to a listed E' of this row */
+    hmap needT; hm_init(&needT, 64);
+    if (o->sampled)
+        for (int64_t x = k0; x < k1; x++) {
+            int e = (int)((o->kkeys[x] >> 24) & 0xFFFFF);
+            int m1 = (int)((o->kkeys[x] >> 16) & 0xFF) - 128, m2 = (int)((o->kkeys[x] >> 8) & 0xFF) - 128,
+                m3 = (int)(o->kkeys[x] & 0xFF) - 128;
+            for (int64_t q = o->rowptr[e]; q < o->rowptr[e + 1]; q++) {
+                const int32_t *nq = o->pn + 3 * q;
+                hm_get_or_put(&needT, node_key(o->pB[q], m1 + nq[0], m2 + nq[1], m3 + nq[2]), 1);
+            }
+        }
     /* term 1/2 intermediate T(A,G') [P in aux(A)][i][k] = sum_{B'} C(A,B')^{P on A} D(B',G') */
     nodestore T; ns_init(&T);
     for (int64_t p1 = o->rowptr[a]; p1 < o->rowptr[a + 1]; p1++) {
@@ -534,6 +592,7 @@ static void k_row(const orc *o, int r, nodestore *Zs, const uint8_t *haveZ, doub
             int g = o->pB[p2]; const int32_t *n2 = o->pn + 3 * p2;
             int nbG = NB(o, g);
             const double *Dbg = o->D + o->offD[p2];
+            if (o->sampled && hm_get(&needT, node_key(g, n1[0] + n2[0], n1[1] + n2[1], n1[2] + n2[2])) < 0) continue;
             int64_t to = ns_block(&T, g, n1[0] + n2[0], n1[1] + n2[1], n1[2] + n2[2], (int64_t)naA * nbA * nbG);
             double *t = T.buf + to;
             *fl += 2.0 * naA * nbA * nbG * nbB;
@@ -579,7 +638,9 @@ static void k_row(const orc *o, int r, nodestore *Zs, const uint8_t *haveZ, doub
             int nbE = NB(o, e), naE = NA(o, e);
             int e1 = m[0] + n3[0], e2 = m[1] + n3[1], e3 = m[2] + n3[2];
             const double *Cge = o->C + o->offC[p3];
-            double *kb = K + o->offK[KBLOCK(e, e1, e2, e3)];
+            const int64_t kx = KBLOCK(e, e1, e2, e3);
+            if (kx < 0) continue;
+            double *kb = K + o->offK[kx];
             /* term 1: P on A, Q on E' */
             int64_t pae = find_pair(o, a, e, e1, e2, e3);
             if ((o->terms & 1) && pae >= 0 && o->keepV[pae]) {
@@ -636,7 +697,9 @@ static void k_row(const orc *o, int r, nodestore *Zs, const uint8_t *haveZ, doub
             int e = Z->atom[id]; const int32_t *m = Z->img + 3 * id;
             int nbE = NB(o, e);
             const double *z = Z->buf + Z->off[id];
-            double *kb = K + o->offK[KBLOCK(e, n1[0] + m[0], n1[1] + m[1], n1[2] + m[2])];
+            const int64_t kx = KBLOCK(e, n1[0] + m[0], n1[1] + m[1], n1[2] + m[2]);
+            if (kx < 0) continue;
+            double *kb = K + o->offK[kx];
             *fl += 2.0 * nbA * nbE * naB * nbB;
             if (!o->dry)
             for (int i = 0; i < nbA; i++)
@@ -649,6 +712,7 @@ static void k_row(const orc *o, int r, nodestore *Zs, const uint8_t *haveZ, doub
                 }
         }
     }
+    hm_free(&needT);
 #undef KBLOCK
 }
 
@@ -700,6 +764,7 @@ double orc_energy(void *h, const double *K, double *per_row) {
             int b = o->pB[p]; const int32_t *n = o->pn + 3 * p;
             int nbB = NB(o, b);
             int64_t x = kfind(o, o->krow[r], o->krow[r + 1], pair_key(a, b, n[0], n[1], n[2]));
+            if (x < 0) continue;  /* sampled mode: block not listed */
             const double *kb = K + o->offK[x];
             const double *dq = o->D + o->offD[q];   /* D(B,A,-n) [l][i] */
             for (int i = 0; i < nbA; i++)

@@ -329,3 +329,24 @@ def test_coulomb_generator_limits():
     assert np.array_equal(coulomb_sr(R, sP, sQ, 0.11), coulomb_sr(R, sQ, sP, 0.11))
     far = coulomb_sr(np.array([10.0, 20.0, 30.0]), sP, sQ, 0.11)
     assert far[0] > far[1] > far[2] > 0
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_sampled_blocks_equal_full_rows(periodic):
+    """Block-sampled mode (only listed K blocks) gives exactly the full build's blocks."""
+    if periodic:
+        s = _waters_system([[1.0, 1.2, 0.8], [3.9, 3.1, 3.3]], seed=29, cell_side=6.0, cutoff_ang=4.5)
+    else:
+        s = ri.config(0)
+    pk = ri.generate(s)
+    kk, K, E, _ = _full(s, pk)
+    full = k_blocks(s, kk, K)
+    pick = np.random.default_rng(4).choice(len(kk), 12, replace=False)
+    o = Oracle(s)
+    o.set_data(pk.C, pk.V, pk.D)
+    ks = o.kpattern_blocks(kk[pick])
+    Ks = o.build_K()
+    got = k_blocks(s, ks, Ks)
+    assert set(got) == {k for k in full if int(ri.pack_key(k[0], k[1], np.array(k[2]))) in set(kk[pick].tolist())}
+    for key, blk in got.items():
+        assert np.array_equal(blk, full[key])
