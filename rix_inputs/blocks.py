@@ -24,12 +24,50 @@ Generators (per the workload definitions):
   N(0,1) * exp(-r) on every basis function of the atoms within 4 A of the
   orbital centre (nearest image), normalised to unit 2-norm.
 """
+import ctypes
 import math
+import os
+import subprocess
+import threading
+
 import numpy as np
 from scipy.special import erf
 
 from . import rng
 from .systems import OMEGA, ang2bohr, D_SUPPORT_ANGSTROM
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_GEN_SRC = os.path.join(_HERE, "_gen.c")
+_GEN_LIB = os.path.join(_HERE, "_build", "libgen.so")
+_gen_lock = threading.Lock()
+_gen = None
+
+
+def build_gen(force=False):
+    """Compile the C fill helper (gcc, OpenMP, no FMA contraction)."""
+    os.makedirs(os.path.dirname(_GEN_LIB), exist_ok=True)
+    if force or not os.path.exists(_GEN_LIB) or os.path.getmtime(_GEN_LIB) < os.path.getmtime(_GEN_SRC):
+        tmp = _GEN_LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-o", tmp, _GEN_SRC, "-lm"])
+        os.replace(tmp, _GEN_LIB)
+    return _GEN_LIB
+
+
+def _genlib():
+    global _gen
+    with _gen_lock:
+        if _gen is None:
+            lib = ctypes.CDLL(build_gen())
+            P = ctypes.c_void_p
+            lib.fill_C.argtypes = [ctypes.c_int64] + [P] * 9 + [ctypes.c_uint64, ctypes.c_uint64, P]
+            lib.fill_V.argtypes = [ctypes.c_int64] + [P] * 9 + [ctypes.c_double, P]
+            _gen = lib
+    return _gen
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
 
 KEY_SHIFT_A = 44
 KEY_SHIFT_B = 24
@@ -188,42 +226,43 @@ class Packed:
             sel = idx[gk == g]
             yield int(sA[sel[0]]), int(sB[sel[0]]), bool(self.onsite[sel[0]]), sel
 
+    def _pair_sizes(self):
+        s = self.system
+        sp = s.species
+        return (np.ascontiguousarray(s.naux[sp[self.A]], dtype=np.int32),
+                np.ascontiguousarray(s.naux[sp[self.B]], dtype=np.int32),
+                np.ascontiguousarray(s.nbas[sp[self.A]], dtype=np.int32),
+                np.ascontiguousarray(s.nbas[sp[self.B]], dtype=np.int32))
+
     def gen_C(self):
         s = self.system
         C = np.empty(int(self.offC[-1]), dtype=np.float64)
-        for a, b, ons, sel in self._groups(self.rep):
-            nbA, nbB = int(s.nbas[a]), int(s.nbas[b])
-            naA, naB = int(s.naux[a]), int(s.naux[b])
-            rows = naA + (0 if ons else naB)
-            size = rows * nbA * nbB
-            for c0 in range(0, len(sel), max(1, (1 << 24) // size)):
-                ss = sel[c0:c0 + max(1, (1 << 24) // size)]
-                ctr = self.offC[ss][:, None] + np.arange(size)[None, :]
-                blk = rng.normal(s.seed, rng.STREAM_C, ctr) * np.exp(-0.8 * self.dist[ss])[:, None]
-                blk = blk.reshape(len(ss), rows, nbA, nbB)
-                if ons:
-                    iu = np.triu_indices(nbA)
-                    up = blk[:, :, iu[0], iu[1]]
-                    blk[:, :, iu[1], iu[0]] = up
-                C[self.offC[ss][:, None] + np.arange(size)[None, :]] = blk.reshape(len(ss), size)
-                if not ons:
-                    part = self.partner[ss]
-                    pb = np.concatenate([blk[:, naA:], blk[:, :naA]], axis=1).transpose(0, 1, 3, 2)
-                    C[self.offC[part][:, None] + np.arange(size)[None, :]] = pb.reshape(len(ss), size)
+        naA, naB, nbA, nbB = self._pair_sizes()
+        rep = np.ascontiguousarray(self.rep, dtype=np.uint8)
+        ons = np.ascontiguousarray(self.onsite, dtype=np.uint8)
+        part = np.ascontiguousarray(self.partner, dtype=np.int64)
+        dist = np.ascontiguousarray(self.dist, dtype=np.float64)
+        offC = np.ascontiguousarray(self.offC, dtype=np.int64)
+        _genlib().fill_C(self.n_pairs, _p(offC), _p(rep), _p(ons), _p(part), _p(naA), _p(naB), _p(nbA), _p(nbB),
+                         _p(dist), s.seed, rng.STREAM_C, _p(C))
         self.C = C
         return C
 
     def gen_V(self):
         s = self.system
         V = np.empty(int(self.offV[-1]), dtype=np.float64)
-        for a, b, ons, sel in self._groups(self.rep):
-            blk = coulomb_sr(self.dist[sel][:, None, None], s.sigma[a][None, :, None],
-                             s.sigma[b][None, None, :], OMEGA)
-            na_a, na_b = blk.shape[1], blk.shape[2]
-            V[self.offV[sel][:, None] + np.arange(na_a * na_b)[None, :]] = blk.reshape(len(sel), -1)
-            part = self.partner[sel]
-            V[self.offV[part][:, None] + np.arange(na_a * na_b)[None, :]] = \
-                blk.transpose(0, 2, 1).reshape(len(sel), -1)
+        naA, naB, _, _ = self._pair_sizes()
+        sig = np.ascontiguousarray(np.concatenate(s.sigma), dtype=np.float64)
+        sig_off = np.concatenate([[0], np.cumsum([len(x) for x in s.sigma])]).astype(np.int64)
+        sp = s.species
+        sigA = np.ascontiguousarray(sig_off[sp[self.A]], dtype=np.int64)
+        sigB = np.ascontiguousarray(sig_off[sp[self.B]], dtype=np.int64)
+        rep = np.ascontiguousarray(self.rep, dtype=np.uint8)
+        part = np.ascontiguousarray(self.partner, dtype=np.int64)
+        dist = np.ascontiguousarray(self.dist, dtype=np.float64)
+        offV = np.ascontiguousarray(self.offV, dtype=np.int64)
+        _genlib().fill_V(self.n_pairs, _p(offV), _p(rep), _p(part), _p(naA), _p(naB), _p(sigA), _p(sigB), _p(sig),
+                         _p(dist), OMEGA, _p(V))
         self.V = V
         return V
 
