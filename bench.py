@@ -5,7 +5,11 @@ One step = one rix_build_K + rix_energy on the resident inputs of the
 workload (default: the (H2O)64 cluster, 192 atoms, nbasis 1536, 8 A cutoff).
 Prints one JSON line.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--config 1] [--precision fp64|mixed]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config 1] [--precision both|fp64|mixed]
+
+By default both paths run; the headline value is the mixed path (terms 3+4 on
+the BF16 tensor cores by error-free slicing), with the FP64 path's time and the
+mixed-vs-FP64 errors in the same line.
   python bench.py --impl reference ...   (the FP64 CPU oracle on a bounded row sample)
 
 Inputs are synthetic (seeded), larger than L2 (C alone is 0.87 GB for the
@@ -36,6 +40,7 @@ WORKLOAD_NAMES = {
 }
 STAGE_KERNEL = {"flags": "k_flags", "T": "k_T", "U2": "k_U2", "X12": "k_X12", "Z": "k_Z", "X34": "k_X34",
                 "sym": "k_sym"}
+# in mixed precision the X34 stage is k_pack_Z34 + k_gemm_sliced
 STAGE_FLOP_INDEX = {"T": 0, "U2": 1, "X12": 2, "Z": 3, "X34": 4}
 # FP64 peak of GB300 (recipe table: FP64 1.25 TFLOP/s), used when no measured FP64 peak exists.
 FP64_PEAK_TFLOPS_NOMINAL = 1.25
@@ -149,28 +154,19 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def run_rix(args):
+def measure(args, s, pk, precision, dev, world, rank, local):
+    """Warm up, time args.steps builds (+ energy) and the end-to-end variant; returns a dict."""
     import torch
     import torch.distributed as dist
-    import rix_inputs as ri
     from paper_2403_10343_gb300.rix import Exchange
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", local)
-
-    s = ri.config(args.config)
-    pk = ri.generate(s)
-    ex = Exchange.from_system(s, precision=args.precision, profile=1)
+    ex = Exchange.from_system(s, precision=precision, profile=1)
     assert np.array_equal(ex.pair_keys(), pk.keys)
     C = torch.from_numpy(pk.C).to(dev)
     V = torch.from_numpy(pk.V).to(dev)
     D = torch.from_numpy(pk.D).to(dev)
     ex.set_CV(C, V)
+    del C, V
     K = torch.empty(ex.k_elems, dtype=torch.float64, device=dev)
     Ex = torch.empty(1, dtype=torch.float64, device=dev)
     st = torch.cuda.current_stream()
@@ -203,7 +199,6 @@ def run_rix(args):
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = t.item()
-
     # end to end through the same API with host buffers: D in, K and E_x out, every step
     Dh = torch.from_numpy(pk.D).pin_memory()
     Kh = torch.empty(ex.k_elems, dtype=torch.float64).pin_memory()
@@ -226,25 +221,68 @@ def run_rix(args):
         t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = t.item()
-
     stats = ex.stats()
+    nblk = stats["n_row_blocks"]
+    launches = 2 + 3 * nblk + nblk * (3 if precision == "mixed" else 2) + 3  # build + energy kernels
+    out = {"ms": ms, "e2e_ms": e2e_ms, "stage_ms": stage_ms, "stats": stats, "clocks": clocks,
+           "E_x": Ex.item(), "K": K, "launches": launches, "h2d": int(D.numel() * 8), "d2h": int(K.numel() * 8 + 8)}
+    ex.close()
+    return out
+
+
+def roofline(args, precision, r):
+    stats, stage_ms = r["stats"], r["stage_ms"]
     pk_peaks, src = peaks()
     dom = max((k for k in stage_ms if k in STAGE_FLOP_INDEX), key=lambda k: stage_ms[k])
     flops = stats["flops_stage"][STAGE_FLOP_INDEX[dom]]
     achieved = flops / (stage_ms[dom] * 1e-3) / 1e12
-    if args.precision == "fp64":
-        peak = pk_peaks.get("fp64_tflops", FP64_PEAK_TFLOPS_NOMINAL)
-        roof = {"bound": "alu", "kernel": STAGE_KERNEL[dom], "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": "FP64 pipe, nominal (recipe table)" if "fp64_tflops" not in pk_peaks
-                else "FP64 pipe, measured"}
-    else:
-        peak = pk_peaks["bf16_tflops_sustained"]
-        tensor_fl = stats["tensor_flops"] * (stage_ms[dom] / sum(stage_ms.values()))
-        roof = {"bound": "tensor", "kernel": STAGE_KERNEL[dom], "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": f"bf16 sustained ({src})"}
+    roof_tc = None
+    if precision == "mixed" and stage_ms.get("X34", 0) > 0:
+        # terms 3+4 on the tensor cores: issued BF16 FLOPs (all slice pairs, padded tiles)
+        tc = stats["tensor_flops"] / (stage_ms["X34"] * 1e-3) / 1e12
+        peak_tc = pk_peaks["bf16_tflops_sustained"]
+        roof_tc = {"bound": "tensor", "kernel": "k_gemm_sliced (+ k_pack_Z34)", "achieved": tc, "peak": peak_tc,
+                   "unit": "TFLOP/s", "frac": tc / peak_tc, "traffic": None,
+                   "peak_source": f"bf16 sustained, {src}",
+                   "fp64_equivalent_tflops": stats["flops_stage"][STAGE_FLOP_INDEX["X34"]] / (stage_ms["X34"] * 1e-3) / 1e12}
+    if precision == "mixed" and dom == "X34":
+        return roof_tc, roof_tc
+    peak = pk_peaks.get("fp64_tflops", FP64_PEAK_TFLOPS_NOMINAL)
+    roof = {"bound": "alu", "kernel": STAGE_KERNEL[dom], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_source": "FP64 pipe, nominal 1.25 TFLOP/s (recipe table); measured DFMA 1.01, DMMA 1.06"}
+    return roof, roof_tc
 
+
+def run_rix(args):
+    import torch
+    import torch.distributed as dist
+    import rix_inputs as ri
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    s = ri.config(args.config)
+    pk = ri.generate(s)
+    precs = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    res = {p: measure(args, s, pk, p, dev, world, rank, local) for p in precs}
+    head = "mixed" if "mixed" in res else "fp64"
+    r = res[head]
+    roof, roof_tc = roofline(args, head, r)
+    extra = {}
+    if len(res) == 2:
+        K64, Km = res["fp64"]["K"], res["mixed"]["K"]
+        extra["fp64"] = {"ms": res["fp64"]["ms"], "e2e_ms": res["fp64"]["e2e_ms"], "E_x": res["fp64"]["E_x"],
+                         "stage_ms": {k: round(v, 4) for k, v in res["fp64"]["stage_ms"].items()},
+                         "roofline": roofline(args, "fp64", res["fp64"])[0]}
+        extra["mixed_vs_fp64"] = {"dE_x_Ha": res["mixed"]["E_x"] - res["fp64"]["E_x"],
+                                  "K_rel_fro": float(torch.linalg.norm(Km - K64) / torch.linalg.norm(K64)),
+                                  "speedup": res["fp64"]["ms"] / res["mixed"]["ms"]}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rows = sample_rows(s)
@@ -253,26 +291,29 @@ def run_rix(args):
                "sample": f"rows {rows} of {s.n_atoms} ({sf:.3g} of {ff:.3g} FLOP, {dt:.1f} s), "
                          f"scaled to a full build by the oracle's own FLOP ratio"}
     if rank == 0:
+        stats = r["stats"]
         line = {
-            "metric": METRIC, "value": ms / world, "unit": "ms", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16-slices+f64",
+            "metric": METRIC, "value": r["ms"] / world, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if head == "fp64" else "bf16-slices+f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAMES[args.config], "precision": args.precision,
+            "config": {"workload": WORKLOAD_NAMES[args.config], "precision": head,
+                       "n_slices": 6 if head == "mixed" else None,
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
-            "e2e": {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": int(D.numel() * 8),
-                    "d2h_bytes_per_step": int(K.numel() * 8 + 8)},
-            "gpu_launches": 9 * args.steps,
-            "clocks": clocks,
+            "e2e": {"value": r["e2e_ms"] / world, "unit": "ms", "h2d_bytes_per_step": r["h2d"],
+                    "d2h_bytes_per_step": r["d2h"]},
+            "gpu_launches": r["launches"] * args.steps,
+            "clocks": r["clocks"],
             "roofline": roof,
+            "roofline_tensor_stage": roof_tc,
             "cpu_baseline": cpu,
-            "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+            "stage_ms": {k: round(v, 4) for k, v in r["stage_ms"].items()},
             "alg_flops": stats["flops_fp64"],
-            "alg_tflops": stats["flops_fp64"] / (ms * 1e-3) / 1e12,
-            "E_x": Ex.item(),
+            "alg_tflops": stats["flops_fp64"] / (r["ms"] * 1e-3) / 1e12,
+            "E_x": r["E_x"],
         }
+        line.update(extra)
         print(json.dumps(line))
-    ex.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -283,7 +324,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--config", type=int, default=1)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
     ap.add_argument("--impl", default="rix", choices=["rix", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -37,12 +37,21 @@ constexpr int TN = 64;          // output columns per tile
 constexpr int KC = 32;          // K per pipeline stage
 constexpr int GROUP = 4;        // stages per exact accumulation group (128 K)
 constexpr int MAXS = 8;         // slices supported
-constexpr int NSTAGE = 2;
 constexpr uint64_t WAIT_NS = 2000000000ull;  // a wait gives up after 2 s
 
 // bytes of one packed tile (no-swizzle K-major core matrices, 8 rows x 16 B)
 constexpr int A_TILE = TM * KC * 2;  // 8 KB
 constexpr int B_TILE = TN * KC * 2;  // 4 KB
+
+constexpr int NSTAGE = 3;            // pipeline stages when they fit in shared memory
+constexpr int SMEM_LIMIT = 227 * 1024;
+
+// stages that fit for S slices, and the dynamic shared memory they need
+__host__ __device__ inline int n_stages(int S) {
+  const int st = S * (A_TILE + B_TILE);
+  return (SMEM_LIMIT - 256) / st >= NSTAGE ? NSTAGE : 2;
+}
+__host__ __device__ inline int smem_bytes(int S) { return n_stages(S) * S * (A_TILE + B_TILE) + 8 * (2 * NSTAGE + 2) + 16; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -248,7 +257,8 @@ __global__ void __launch_bounds__(256, 1) k_gemm_sliced(GemmArgs g) {
   // layout: [stage][A tiles S][B tiles S], then barriers, then TMEM address
   const int S = g.S;
   const int stage_bytes = S * (A_TILE + B_TILE);
-  uint64_t *full = (uint64_t *)(smem + NSTAGE * stage_bytes);
+  const int nst = n_stages(S);
+  uint64_t *full = (uint64_t *)(smem + nst * stage_bytes);
   uint64_t *empty = full + NSTAGE;
   uint64_t *accfull = empty + NSTAGE;
   uint64_t *accempty = accfull + 1;
@@ -278,7 +288,7 @@ __global__ void __launch_bounds__(256, 1) k_gemm_sliced(GemmArgs g) {
   const int64_t b_tiles = (int64_t)(Npad / TN) * nk;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < NSTAGE; i++) {
+    for (int i = 0; i < nst; i++) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
     }
@@ -302,8 +312,8 @@ __global__ void __launch_bounds__(256, 1) k_gemm_sliced(GemmArgs g) {
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ producer
     for (int c = 0; c < nk; c++) {
-      const int st = c % NSTAGE;
-      if (c >= NSTAGE && !mbar_wait(&empty[st], ((c / NSTAGE) - 1) & 1)) {
+      const int st = c % nst;
+      if (c >= nst && !mbar_wait(&empty[st], ((c / nst) - 1) & 1)) {
         atomicExch(abort_flag, 1);
         break;
       }
@@ -322,13 +332,13 @@ __global__ void __launch_bounds__(256, 1) k_gemm_sliced(GemmArgs g) {
     // ------------------------------------------------------------ MMA issuer
     const uint32_t idesc = idesc_bf16(TM, TN);
     for (int c = 0; c < nk; c++) {
-      const int st = c % NSTAGE;
+      const int st = c % nst;
       const int grp = c / GROUP;
       if (c % GROUP == 0 && grp > 0 && !mbar_wait(accempty, (grp - 1) & 1)) {
         atomicExch(abort_flag, 1);
         break;
       }
-      if (!mbar_wait(&full[st], (c / NSTAGE) & 1)) {
+      if (!mbar_wait(&full[st], (c / nst) & 1)) {
         atomicExch(abort_flag, 1);
         break;
       }
@@ -390,28 +400,34 @@ __global__ void __launch_bounds__(256, 1) k_gemm_sliced(GemmArgs g) {
       const int gr = mt * TM + row;
       if (gr < Mrows) {
         const int er = geA[gr];
+        // fully unrolled with predicates so acc[] stays in registers
         if (!pr) {
+#pragma unroll
           for (int n = 0; n < TN; n++) {
             const int gc = nt * TN + n;
-            if (gc >= Ncols) break;
-            const int sc = er + geB[gc] - 7 * (S + 1) + drop;
-            double v = ldexp((double)acc[n], sc);
-            double *dst = g.C + (int64_t)gr * g.ldc + gc;
-            if (g.accumulate) *dst += v;
-            else *dst = v;
+            if (gc < Ncols) {
+              const int sc = er + geB[gc] - 7 * (S + 1) + drop;
+              const double v = ldexp((double)acc[n], sc);
+              double *dst = g.C + (int64_t)gr * g.ldc + gc;
+              if (g.accumulate) *dst += v;
+              else *dst = v;
+            }
           }
         } else {
           const int2 ri = g.rowinfo[pr->rowoff + gr];
           if (ri.x >= 0) {
             const int32_t *xrow = g.xmap + pr->xoff + (int64_t)ri.x * pr->nz;
+#pragma unroll
             for (int n = 0; n < TN; n++) {
               const int gc = nt * TN + n;
-              if (gc >= Ncols) break;
-              const int4 ci = g.colinfo[pr->coloff + gc];
-              if (ci.x < 0) continue;
-              const int sc = er + geB[gc] - 7 * (S + 1) + drop;
-              const double v = ldexp((double)acc[n], sc);
-              atomicAdd(g.X + g.offK[xrow[ci.x]] + (int64_t)ri.y * ci.z + ci.y, v);
+              if (gc < Ncols) {
+                const int4 ci = g.colinfo[pr->coloff + gc];
+                if (ci.x >= 0) {
+                  const int sc = er + geB[gc] - 7 * (S + 1) + drop;
+                  const double v = ldexp((double)acc[n], sc);
+                  atomicAdd(g.X + g.offK[xrow[ci.x]] + (int64_t)ri.y * ci.z + ci.y, v);
+                }
+              }
             }
           }
         }
@@ -466,7 +482,7 @@ extern "C" rix_status rix_gemm_sliced(const double *A, int64_t lda, const double
   }
   GemmArgs g{Ap, Bp, eA, eB, C, ldc, M, N, Mpad, Npad, Kpad, S, 0, fixed_point_drop(Kpad, S), err,
              nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  const int smem = NSTAGE * S * (A_TILE + B_TILE) + 8 * (2 * NSTAGE + 2) + 16;
+  const int smem = smem_bytes(S);
   cudaFuncSetAttribute(k_gemm_sliced, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   k_gemm_sliced<<<dim3(Mpad / TM, Npad / TN), 256, smem, st>>>(g);
   cudaError_t e = cudaGetLastError();
@@ -773,9 +789,9 @@ rix_status rix_mixed_x34(rix_ctx *ctx, int b0, int b1, int64_t zbase, cudaStream
   using namespace rixtc;
   static bool attr = false;
   const int S = ctx->mx_S;
-  const int smem = NSTAGE * S * (A_TILE + B_TILE) + 8 * (2 * NSTAGE + 2) + 16;
+  const int smem = smem_bytes(S);
   if (!attr) {
-    cudaFuncSetAttribute(k_gemm_sliced, cudaFuncAttributeMaxDynamicSharedMemorySize, NSTAGE * MAXS * (A_TILE + B_TILE) + 64);
+    cudaFuncSetAttribute(k_gemm_sliced, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
     attr = true;
   }
   for (size_t gi = 0; gi + 1 < ctx->mx_grp.size(); gi++) {
