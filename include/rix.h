@@ -131,11 +131,14 @@ rix_status rix_layout(const rix_ctx *ctx, int32_t which, int64_t *n_blocks,
 rix_status rix_layout_sizes(const rix_ctx *ctx, int64_t *c_elems, int64_t *v_elems,
                             int64_t *d_elems, int64_t *k_elems);
 
-/* Load C and V (device pointers, packed format, FP64).  Copies them into
- * library storage, checks the pair symmetry of C and V (ENOTSYM), computes
- * the screening flags and, in mixed mode, the BF16 slices.  Enqueued on
- * `stream` (cudaStream_t, NULL = legacy default stream); synchronises the
- * stream once to read the symmetry verdict. */
+/* Load C and V (packed format, FP64).  Each pointer may be device memory or
+ * host memory (pinned or pageable; the copy direction follows from the
+ * address), so a caller whose C does not fit twice on the device can load it
+ * straight from the host.  Copies them into library storage, checks the pair
+ * symmetry of C and V (ENOTSYM), computes the screening flags and, in mixed
+ * mode, the BF16 slices.  Enqueued on `stream` (cudaStream_t, NULL = legacy
+ * default stream); synchronises the stream once to read the symmetry
+ * verdict. */
 rix_status rix_set_CV(rix_ctx *ctx, const double *C_dev, const double *V_dev, void *stream);
 
 /* K = exchange matrix of D (device, packed, FP64) into K_dev (device, packed

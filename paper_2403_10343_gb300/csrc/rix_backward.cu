@@ -4,7 +4,10 @@
 // E = -1/4 sum_p <D(partner p)^T, K(p)> and K = X + X^T, the adjoint of X is
 // Xbar(A,E') = -1/2 gEx D(A,E') on the pair list and zero elsewhere, so only
 // outputs on the pair list propagate.  The forward intermediates T, U2 and Z
-// are recomputed by a forward pass (nothing is kept between calls).  The
+// are recomputed by a forward pass (nothing is kept between calls); when the
+// memory plan splits the row atoms into blocks, T and Z are recomputed once
+// more per block, and Tbar and Zbar overwrite T and Z in the same buffers
+// after their last reader has run.  The
 // paper obtains forces and stress by differentiating the same contraction
 // (Sec. "EXX force and stress contributions"); dE/dC and dE/dV are the
 // quantities those chain through.
@@ -28,13 +31,20 @@ constexpr int SM_BIG = 12288;
 
 __device__ __forceinline__ int tile_rows(int per) { return max(1, CAP / per); }
 
+// The 2-hop blocks [lo, hi) resident in the T or Z buffer (one block of row
+// atoms); block i sits at off2[i] - base in the buffer.
+struct Win {
+  int64_t lo, hi, base;
+};
+__device__ __forceinline__ bool in_win(const Win &w, int64_t i) { return i >= w.lo && i < w.hi; }
+
 // ---------------------------------------------------------------- Cbar(A,B')[P on B']
 // += sum over (pair (A,E'), Z(B,E')) of sum_l Xbar(A,E')[i][l] Z[P][j][l]
 __global__ void __launch_bounds__(NT) kb_C34(const int4 *items, const int64_t *ptr, const int2 *L, const int32_t *pA,
                                              const int32_t *pB, const int32_t *nb, const int32_t *na,
                                              const double *__restrict__ D, const int64_t *offD,
                                              const double *__restrict__ Z, const int64_t *off2, const int64_t *offC,
-                                             const uint8_t *keepC, double sX, double *dC) {
+                                             const uint8_t *keepC, double sX, Win w, double *dC) {
   const int4 it = items[blockIdx.x];
   const int p1 = it.x, p0 = it.y;
   if (!keepC[p1]) return;
@@ -48,10 +58,11 @@ __global__ void __launch_bounds__(NT) kb_C34(const int4 *items, const int64_t *p
   for (int r = 0; r < MAXE; r++) acc[r] = 0.0;
   for (int64_t x = ptr[p1]; x < ptr[p1 + 1]; x++) {
     const int2 en = L[x];
+    if (!in_win(w, en.y)) continue;
     const int e = pB[en.x];
     const int nbE = nb[e];
     const double *Xb = D + offD[en.x];
-    const double *Zb = Z + off2[en.y];
+    const double *Zb = Z + (off2[en.y] - w.base);
 #pragma unroll
     for (int r = 0; r < MAXE; r++) {
       const int el = threadIdx.x + r * NT;
@@ -81,9 +92,10 @@ __global__ void __launch_bounds__(NT) kb_Z34(const int4 *items, const int64_t *p
                                              const int32_t *nb, const int32_t *na, const double *__restrict__ C,
                                              const int64_t *offC, const uint8_t *keepC,
                                              const double *__restrict__ D, const int64_t *offD,
-                                             const int64_t *off2, double sX, double *Zbar) {
+                                             const int64_t *off2, double sX, Win w, double *Zbar) {
   const int4 it = items[blockIdx.x];
   const int z = it.x, p0 = it.y;
+  if (!in_win(w, z)) return;
   const int b = atomA2[z], e = atomB2[z];
   const int nbB = nb[b], naB = na[b], nbE = nb[e];
   const int per = nbB * nbE;
@@ -112,7 +124,7 @@ __global__ void __launch_bounds__(NT) kb_Z34(const int4 *items, const int64_t *p
       }
     }
   }
-  double *out = Zbar + off2[z] + (int64_t)p0 * per;
+  double *out = Zbar + (off2[z] - w.base) + (int64_t)p0 * per;
 #pragma unroll
   for (int r = 0; r < MAXE; r++) {
     const int el = threadIdx.x + r * NT;
@@ -128,7 +140,7 @@ __global__ void __launch_bounds__(NT) kb_ZV(const int4 *items, const int64_t *pt
                                             const double *__restrict__ D, const int64_t *offD,
                                             const uint8_t *keepC, const uint8_t *keepV, const uint8_t *keepD,
                                             const double *__restrict__ Zbar, const int64_t *off2,
-                                            const int64_t *offV, double *dV) {
+                                            const int64_t *offV, Win w, double *dV) {
   extern __shared__ double sm[];
   const int4 it = items[blockIdx.x];
   const int p2 = it.x, p0 = it.y;
@@ -144,11 +156,11 @@ __global__ void __launch_bounds__(NT) kb_ZV(const int4 *items, const int64_t *pt
   for (int r = 0; r < MAXE; r++) acc[r] = 0.0;
   for (int64_t x = ptr[p2]; x < ptr[p2 + 1]; x++) {
     const int2 en = L[x];
-    if (!keepC[en.x]) continue;
+    if (!keepC[en.x] || !in_win(w, en.y)) continue;
     const int e = pB[en.x];
     const int nbE = nb[e];
     const double *Cg = C + offC[en.x];
-    const double *Zb = Zbar + off2[en.y];
+    const double *Zb = Zbar + (off2[en.y] - w.base);
     const int fper = nbG * nbE;
     const int ft = max(1, min(pe - p0, SM_BIG / fper));
     for (int ps = p0; ps < pe; ps += ft) {
@@ -197,7 +209,7 @@ __global__ void __launch_bounds__(NT) kb_ZC(const int4 *items, const int64_t *pt
                                             const double *__restrict__ D, const int64_t *offD,
                                             const uint8_t *keepC, const uint8_t *keepV, const uint8_t *keepD,
                                             const double *__restrict__ Zbar, const int64_t *off2,
-                                            const int64_t *offC, double *dC) {
+                                            const int64_t *offC, Win w, double *dC) {
   extern __shared__ double sm[];
   const int4 it = items[blockIdx.x];
   const int p3 = it.x, q0 = it.y;
@@ -212,12 +224,12 @@ __global__ void __launch_bounds__(NT) kb_ZC(const int4 *items, const int64_t *pt
   for (int r = 0; r < MAXE; r++) acc[r] = 0.0;
   for (int64_t x = ptr[p3]; x < ptr[p3 + 1]; x++) {
     const int2 en = L[x];
-    if (!keepD[en.x] || !keepV[en.x]) continue;
+    if (!keepD[en.x] || !keepV[en.x] || !in_win(w, en.y)) continue;
     const int b = pA[en.x];
     const int nbB = nb[b], naB = na[b];
     const double *Dbg = D + offD[en.x];
     const double *Vbg = V + offV[en.x];
-    const double *Zb = Zbar + off2[en.y];
+    const double *Zb = Zbar + (off2[en.y] - w.base);
     const int pc = max(1, min(naB, SM_BIG / per));
     for (int P0 = 0; P0 < naB; P0 += pc) {
       const int pn = min(pc, naB - P0);
@@ -310,10 +322,11 @@ __global__ void __launch_bounds__(NT) kb_T(const int4 *items, const int64_t *ptr
                                            const double *__restrict__ D, const int64_t *offD,
                                            const uint8_t *keepC, const uint8_t *keepV, const int64_t *ptrU2,
                                            const double *__restrict__ U2bar, const int64_t *offU,
-                                           const int64_t *off2, double sX, double *Tbar) {
+                                           const int64_t *off2, double sX, Win w, double *Tbar) {
   extern __shared__ double sm[];
   const int4 it = items[blockIdx.x];
   const int t = it.x, p0 = it.y;
+  if (!in_win(w, t)) return;
   const int a = atomA2[t], g = atomB2[t];
   const int nbA = nb[a], naA = na[a], nbG = nb[g], naG = na[g];
   const int per = nbA * nbG;
@@ -374,7 +387,7 @@ __global__ void __launch_bounds__(NT) kb_T(const int4 *items, const int64_t *ptr
       }
     }
   }
-  double *out = Tbar + off2[t] + (int64_t)p0 * per;
+  double *out = Tbar + (off2[t] - w.base) + (int64_t)p0 * per;
 #pragma unroll
   for (int r = 0; r < MAXE; r++) {
     const int el = threadIdx.x + r * NT;
@@ -393,11 +406,14 @@ __global__ void __launch_bounds__(NT) kb_V12(const int4 *items, const int64_t *p
                                              const uint8_t *keepC, const uint8_t *keepV,
                                              const double *__restrict__ T, const int64_t *off2,
                                              const int64_t *ptrU2, const double *__restrict__ U2bar,
-                                             const int64_t *offU, const int64_t *offV, double sX, double *dV) {
+                                             const int64_t *offU, const int64_t *offV, double sX, Win w,
+                                             double *dV) {
   extern __shared__ double sm[];
   const int4 it = items[blockIdx.x];
   const int p = it.x, p0 = it.y;
-  if (!keepV[p]) return;
+  // every T block this item reads has the row atom of pair p: it is resident iff T(A,X) is
+  const int s = map1to2[p];
+  if (!keepV[p] || !in_win(w, s)) return;
   const int a = pA[p], xa = pB[p];
   const int nbA = nb[a], naA = na[a], naX = na[xa], nbX = nb[xa];
   const int per = naX;
@@ -407,7 +423,6 @@ __global__ void __launch_bounds__(NT) kb_V12(const int4 *items, const int64_t *p
   double acc[MAXE];
 #pragma unroll
   for (int r = 0; r < MAXE; r++) acc[r] = 0.0;
-  const int s = map1to2[p];
   const double *Xb = D + offD[p];
   for (int64_t x = ptrX12[s]; x < ptrX12[s + 1]; x++) {
     const X12Entry en = LX12[x];
@@ -417,7 +432,7 @@ __global__ void __launch_bounds__(NT) kb_V12(const int4 *items, const int64_t *p
     const int qE0 = onsite[en.p3] ? 0 : naG;
     const int uper = nbA * nbG;
     const double *Ce = C + offC[en.p3] + (int64_t)qE0 * nbG * nbX;
-    const double *Tt = T + off2[en.t];
+    const double *Tt = T + (off2[en.t] - w.base);
     const int qt = max(1, min(naX, SM_BIG / uper));
     for (int q0 = 0; q0 < naX; q0 += qt) {
       const int qn = min(qt, naX - q0);
@@ -450,7 +465,7 @@ __global__ void __launch_bounds__(NT) kb_V12(const int4 *items, const int64_t *p
   }
   if (ptrU2[p + 1] > ptrU2[p]) {
     const int uper = nbA * nbX;
-    const double *Tt = T + off2[s];
+    const double *Tt = T + (off2[s] - w.base);
     const double *Ub = U2bar + offU[p];
 #pragma unroll
     for (int r = 0; r < MAXE; r++) {
@@ -484,7 +499,7 @@ __global__ void __launch_bounds__(NT) kb_C12(const int4 *items, const int64_t *p
                                              const uint8_t *keepC, const uint8_t *keepV,
                                              const double *__restrict__ T, const int64_t *off2,
                                              const double *__restrict__ U, const int64_t *offU,
-                                             const int64_t *offC, double sX, double *dC) {
+                                             const int64_t *offC, double sX, Win w, double *dC) {
   extern __shared__ double sm[];
   const int4 it = items[blockIdx.x];
   const int p3 = it.x, r0 = it.y;
@@ -504,13 +519,14 @@ __global__ void __launch_bounds__(NT) kb_C12(const int4 *items, const int64_t *p
   const int q1lo = max(r0, qE0) - qE0, q1hi = re - qE0;  // Q range [q1lo, q1hi)
   for (int64_t x = ptr[p3]; x < ptr[p3 + 1]; x++) {
     const BX12Entry en = L[x];
+    if (!in_win(w, en.t)) continue;  // uniform across the CTA
     const int a = atomA2[en.t];
     const int nbA = nb[a], naA = na[a];
     const int pae = map2to1[en.s];
     const double *Xb = D + offD[pae];
     if (en.t1 && keepV[pae] && q1hi > q1lo) {
       const int uper = nbA * nbG;
-      const double *Tt = T + off2[en.t];
+      const double *Tt = T + (off2[en.t] - w.base);
       const double *Vae = V + offV[pae];
       const int qn = q1hi - q1lo;
       __syncthreads();
@@ -570,7 +586,7 @@ __global__ void __launch_bounds__(NT) kb_TC(const int4 *items, const int64_t *pt
                                             const double *__restrict__ D, const int64_t *offD,
                                             const uint8_t *keepC, const uint8_t *keepD,
                                             const double *__restrict__ Tbar, const int64_t *off2,
-                                            const int64_t *offC, double *dC) {
+                                            const int64_t *offC, Win w, double *dC) {
   const int4 it = items[blockIdx.x];
   const int p1 = it.x, p0 = it.y;
   if (!keepC[p1]) return;
@@ -584,11 +600,11 @@ __global__ void __launch_bounds__(NT) kb_TC(const int4 *items, const int64_t *pt
   for (int r = 0; r < MAXE; r++) acc[r] = 0.0;
   for (int64_t x = ptr[p1]; x < ptr[p1 + 1]; x++) {
     const int2 en = L[x];
-    if (!keepD[en.x]) continue;
+    if (!keepD[en.x] || !in_win(w, en.y)) continue;
     const int g = pB[en.x];
     const int nbG = nb[g];
     const double *Dbg = D + offD[en.x];
-    const double *Tb = Tbar + off2[en.y];
+    const double *Tb = Tbar + (off2[en.y] - w.base);
 #pragma unroll
     for (int r = 0; r < MAXE; r++) {
       const int el = threadIdx.x + r * NT;
@@ -703,7 +719,7 @@ extern "C" rix_status rix_backward(rix_ctx *ctx, const double *D, double gEx, do
     cudaFuncSetAttribute(kb_C12, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_BIG * 8);
     g_bwd_attr = true;
   }
-  // forward recompute: flags, T, U2, Z and K
+  // forward recompute: flags, T, U2, Z and K (U2 stays complete; T and Z hold the last block)
   rix_status s = rix_fp64_build(ctx, D, ctx->d_Kbuf, st);
   if (s != RIX_OK) return s;
   const double sX = -0.5 * gEx;
@@ -714,75 +730,87 @@ extern "C" rix_status rix_backward(rix_ctx *ctx, const double *D, double gEx, do
     if ((s = last_err(ctx, "kb_dD")) != RIX_OK) return s;
   }
   if (!dC && !dV) return RIX_OK;
-  // Zbar (terms 3+4 adjoint) and U2bar, Tbar (terms 1+2, T adjoint)
-  if (ctx->n_itB[1]) {
-    kb_Z34<<<(unsigned)ctx->n_itB[1], NT, 0, st>>>(ctx->d_itB[1], ctx->d_ptrBZ34, ctx->d_LBZ34, ctx->d_atomA2,
-                                                   ctx->d_atomB2, ctx->d_pA, ctx->d_nb, ctx->d_na, ctx->d_C,
-                                                   ctx->d_offC, ctx->d_keepC, D, ctx->d_offD, ctx->d_off2, sX,
-                                                   ctx->d_Zbar);
-    if ((s = last_err(ctx, "kb_Z34")) != RIX_OK) return s;
-  }
+  // U2bar (term 2 adjoint) is per pair and needs no T
   if (ctx->n_itB[4]) {
     kb_U2<<<(unsigned)ctx->n_itB[4], NT, 0, st>>>(ctx->d_itB[4], ctx->d_ptrBU2, ctx->d_LBU2, ctx->d_pA, ctx->d_pB,
                                                   ctx->d_nb, ctx->d_na, ctx->d_map2to1, ctx->d_C, ctx->d_offC,
                                                   ctx->d_keepC, D, ctx->d_offD, ctx->d_offU, sX, ctx->d_U2bar);
     if ((s = last_err(ctx, "kb_U2")) != RIX_OK) return s;
   }
-  if (dC) {
-    RIX_CUDA_TRY(ctx, cudaMemsetAsync(dC, 0, sizeof(double) * ctx->offC[np], st));
-    if (ctx->n_itB[5]) {
-      kb_T<<<(unsigned)ctx->n_itB[5], NT, SM_BIG * 8, st>>>(
-          ctx->d_itB[5], ctx->d_ptrBT1, ctx->d_LBT1, ctx->d_atomA2, ctx->d_atomB2, ctx->d_map2to1, ctx->d_pA,
-          ctx->d_onsite, ctx->d_nb, ctx->d_na, ctx->d_C, ctx->d_offC, ctx->d_V, ctx->d_offV, D, ctx->d_offD,
-          ctx->d_keepC, ctx->d_keepV, ctx->d_ptrBU2, ctx->d_U2bar, ctx->d_offU, ctx->d_off2, sX, ctx->d_Tbar);
-      if ((s = last_err(ctx, "kb_T")) != RIX_OK) return s;
-    }
-    if (ctx->n_itB[0]) {
-      kb_C34<<<(unsigned)ctx->n_itB[0], NT, 0, st>>>(ctx->d_itB[0], ctx->d_ptrBC34, ctx->d_LBC34, ctx->d_pA,
-                                                     ctx->d_pB, ctx->d_nb, ctx->d_na, D, ctx->d_offD, ctx->d_Z,
-                                                     ctx->d_off2, ctx->d_offC, ctx->d_keepC, sX, dC);
-      if ((s = last_err(ctx, "kb_C34")) != RIX_OK) return s;
-    }
-    if (ctx->n_itB[3]) {
-      kb_ZC<<<(unsigned)ctx->n_itB[3], NT, SM_BIG * 8, st>>>(
-          ctx->d_itB[3], ctx->d_ptrBZC, ctx->d_LBZC, ctx->d_pA, ctx->d_pB, ctx->d_nb, ctx->d_na, ctx->d_V,
-          ctx->d_offV, D, ctx->d_offD, ctx->d_keepC, ctx->d_keepV, ctx->d_keepD, ctx->d_Zbar, ctx->d_off2,
-          ctx->d_offC, dC);
-      if ((s = last_err(ctx, "kb_ZC")) != RIX_OK) return s;
-    }
-    if (ctx->n_itB[7]) {
+  if (dC) RIX_CUDA_TRY(ctx, cudaMemsetAsync(dC, 0, sizeof(double) * ctx->offC[np], st));
+  if (dV) RIX_CUDA_TRY(ctx, cudaMemsetAsync(dV, 0, sizeof(double) * ctx->offV[np], st));
+  const int nblk = ctx->nblk;
+  // terms 1 and 2, one block of row atoms at a time: T (recomputed when the plan
+  // has several blocks), its consumers, then Tbar into the same buffer
+  for (int b = 0; b < nblk; b++) {
+    const Win w{ctx->row2[ctx->blk_atom[b]], ctx->row2[ctx->blk_atom[b + 1]], ctx->blk_base[b]};
+    if (nblk > 1 && (s = rix_launch_T_block(ctx, D, b, st)) != RIX_OK) return s;
+    if (dC && ctx->n_itB[7]) {
       kb_C12<<<(unsigned)ctx->n_itB[7], NT, SM_BIG * 8, st>>>(
           ctx->d_itB[7], ctx->d_ptrBC12, ctx->d_LBC12, ctx->d_atomA2, ctx->d_map2to1, ctx->d_pA, ctx->d_pB,
           ctx->d_onsite, ctx->d_nb, ctx->d_na, ctx->d_V, ctx->d_offV, D, ctx->d_offD, ctx->d_keepC, ctx->d_keepV,
-          ctx->d_T, ctx->d_off2, ctx->d_U, ctx->d_offU, ctx->d_offC, sX, dC);
+          ctx->d_T, ctx->d_off2, ctx->d_U, ctx->d_offU, ctx->d_offC, sX, w, dC);
       if ((s = last_err(ctx, "kb_C12")) != RIX_OK) return s;
     }
-    if (ctx->n_itB[8]) {
-      kb_TC<<<(unsigned)ctx->n_itB[8], NT, 0, st>>>(ctx->d_itB[8], ctx->d_ptrBTC, ctx->d_LBTC, ctx->d_pA, ctx->d_pB,
-                                                    ctx->d_nb, ctx->d_na, D, ctx->d_offD, ctx->d_keepC,
-                                                    ctx->d_keepD, ctx->d_Tbar, ctx->d_off2, ctx->d_offC, dC);
-      if ((s = last_err(ctx, "kb_TC")) != RIX_OK) return s;
+    if (dV && ctx->n_itB[6]) {
+      kb_V12<<<(unsigned)ctx->n_itB[6], NT, SM_BIG * 8, st>>>(
+          ctx->d_itB[6], ctx->d_ptrX12, ctx->d_LX12, ctx->d_map1to2, ctx->d_pA, ctx->d_pB, ctx->d_onsite, ctx->d_nb,
+          ctx->d_na, ctx->d_C, ctx->d_offC, D, ctx->d_offD, ctx->d_keepC, ctx->d_keepV, ctx->d_T, ctx->d_off2,
+          ctx->d_ptrBU2, ctx->d_U2bar, ctx->d_offU, ctx->d_offV, sX, w, dV);
+      if ((s = last_err(ctx, "kb_V12")) != RIX_OK) return s;
     }
+    if (dC && ctx->n_itB[5]) {
+      kb_T<<<(unsigned)ctx->n_itB[5], NT, SM_BIG * 8, st>>>(
+          ctx->d_itB[5], ctx->d_ptrBT1, ctx->d_LBT1, ctx->d_atomA2, ctx->d_atomB2, ctx->d_map2to1, ctx->d_pA,
+          ctx->d_onsite, ctx->d_nb, ctx->d_na, ctx->d_C, ctx->d_offC, ctx->d_V, ctx->d_offV, D, ctx->d_offD,
+          ctx->d_keepC, ctx->d_keepV, ctx->d_ptrBU2, ctx->d_U2bar, ctx->d_offU, ctx->d_off2, sX, w, ctx->d_T);
+      if ((s = last_err(ctx, "kb_T")) != RIX_OK) return s;
+      if (ctx->n_itB[8]) {
+        kb_TC<<<(unsigned)ctx->n_itB[8], NT, 0, st>>>(ctx->d_itB[8], ctx->d_ptrBTC, ctx->d_LBTC, ctx->d_pA,
+                                                      ctx->d_pB, ctx->d_nb, ctx->d_na, D, ctx->d_offD, ctx->d_keepC,
+                                                      ctx->d_keepD, ctx->d_T, ctx->d_off2, ctx->d_offC, w, dC);
+        if ((s = last_err(ctx, "kb_TC")) != RIX_OK) return s;
+      }
+    }
+  }
+  // terms 3 and 4, one block of middle atoms at a time: Z, its consumer, then Zbar
+  for (int b = 0; b < nblk; b++) {
+    const Win w{ctx->row2[ctx->blk_atom[b]], ctx->row2[ctx->blk_atom[b + 1]], ctx->blk_base[b]};
+    if (nblk > 1 && (s = rix_launch_Z_block(ctx, D, b, st)) != RIX_OK) return s;
+    if (dC && ctx->n_itB[0]) {
+      kb_C34<<<(unsigned)ctx->n_itB[0], NT, 0, st>>>(ctx->d_itB[0], ctx->d_ptrBC34, ctx->d_LBC34, ctx->d_pA,
+                                                     ctx->d_pB, ctx->d_nb, ctx->d_na, D, ctx->d_offD, ctx->d_Z,
+                                                     ctx->d_off2, ctx->d_offC, ctx->d_keepC, sX, w, dC);
+      if ((s = last_err(ctx, "kb_C34")) != RIX_OK) return s;
+    }
+    if (ctx->n_itB[1]) {
+      kb_Z34<<<(unsigned)ctx->n_itB[1], NT, 0, st>>>(ctx->d_itB[1], ctx->d_ptrBZ34, ctx->d_LBZ34, ctx->d_atomA2,
+                                                     ctx->d_atomB2, ctx->d_pA, ctx->d_nb, ctx->d_na, ctx->d_C,
+                                                     ctx->d_offC, ctx->d_keepC, D, ctx->d_offD, ctx->d_off2, sX, w,
+                                                     ctx->d_Z);
+      if ((s = last_err(ctx, "kb_Z34")) != RIX_OK) return s;
+    }
+    if (dC && ctx->n_itB[3]) {
+      kb_ZC<<<(unsigned)ctx->n_itB[3], NT, SM_BIG * 8, st>>>(
+          ctx->d_itB[3], ctx->d_ptrBZC, ctx->d_LBZC, ctx->d_pA, ctx->d_pB, ctx->d_nb, ctx->d_na, ctx->d_V,
+          ctx->d_offV, D, ctx->d_offD, ctx->d_keepC, ctx->d_keepV, ctx->d_keepD, ctx->d_Z, ctx->d_off2,
+          ctx->d_offC, w, dC);
+      if ((s = last_err(ctx, "kb_ZC")) != RIX_OK) return s;
+    }
+    if (dV && ctx->n_itB[2]) {
+      kb_ZV<<<(unsigned)ctx->n_itB[2], NT, SM_BIG * 8, st>>>(
+          ctx->d_itB[2], ctx->d_ptrBZV, ctx->d_LBZV, ctx->d_pA, ctx->d_pB, ctx->d_nb, ctx->d_na, ctx->d_C,
+          ctx->d_offC, D, ctx->d_offD, ctx->d_keepC, ctx->d_keepV, ctx->d_keepD, ctx->d_Z, ctx->d_off2,
+          ctx->d_offV, w, dV);
+      if ((s = last_err(ctx, "kb_ZV")) != RIX_OK) return s;
+    }
+  }
+  if (dC) {
     kb_symC<<<(unsigned)np, 128, 0, st>>>(np, ctx->d_pA, ctx->d_pB, ctx->d_partner1, ctx->d_onsite, ctx->d_nb,
                                          ctx->d_na, ctx->d_offC, dC);
     if ((s = last_err(ctx, "kb_symC")) != RIX_OK) return s;
   }
   if (dV) {
-    RIX_CUDA_TRY(ctx, cudaMemsetAsync(dV, 0, sizeof(double) * ctx->offV[np], st));
-    if (ctx->n_itB[2]) {
-      kb_ZV<<<(unsigned)ctx->n_itB[2], NT, SM_BIG * 8, st>>>(
-          ctx->d_itB[2], ctx->d_ptrBZV, ctx->d_LBZV, ctx->d_pA, ctx->d_pB, ctx->d_nb, ctx->d_na, ctx->d_C,
-          ctx->d_offC, D, ctx->d_offD, ctx->d_keepC, ctx->d_keepV, ctx->d_keepD, ctx->d_Zbar, ctx->d_off2,
-          ctx->d_offV, dV);
-      if ((s = last_err(ctx, "kb_ZV")) != RIX_OK) return s;
-    }
-    if (ctx->n_itB[6]) {
-      kb_V12<<<(unsigned)ctx->n_itB[6], NT, SM_BIG * 8, st>>>(
-          ctx->d_itB[6], ctx->d_ptrX12, ctx->d_LX12, ctx->d_map1to2, ctx->d_pA, ctx->d_pB, ctx->d_onsite, ctx->d_nb,
-          ctx->d_na, ctx->d_C, ctx->d_offC, D, ctx->d_offD, ctx->d_keepC, ctx->d_keepV, ctx->d_T, ctx->d_off2,
-          ctx->d_ptrBU2, ctx->d_U2bar, ctx->d_offU, ctx->d_offV, sX, dV);
-      if ((s = last_err(ctx, "kb_V12")) != RIX_OK) return s;
-    }
     kb_symV<<<(unsigned)np, 128, 0, st>>>(np, ctx->d_pA, ctx->d_pB, ctx->d_partner1, ctx->d_na, ctx->d_offV, dV);
     if ((s = last_err(ctx, "kb_symV")) != RIX_OK) return s;
   }

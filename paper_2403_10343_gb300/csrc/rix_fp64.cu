@@ -549,6 +549,34 @@ rix_status rix_launch_symcheck(rix_ctx *ctx, cudaStream_t st) {
   return last(ctx, "k_symcheck");
 }
 
+// T(A,G') for the row atoms of block b (T buffer holds that block).
+rix_status rix_launch_T_block(rix_ctx *ctx, const double *D, int b, cudaStream_t st) {
+  const int64_t nT = ctx->segT[b + 1] - ctx->segT[b];
+  if (!nT) return RIX_OK;
+  k_T<<<(unsigned)nT, NT, 64 * 64 * 8, st>>>(ctx->d_itT + ctx->segT[b], ctx->d_ptrT, ctx->d_LT, ctx->d_atomA2,
+                                             ctx->d_atomB2, ctx->d_off2, ctx->d_pB, ctx->d_nb, ctx->d_na, ctx->d_C,
+                                             ctx->d_offC, D, ctx->d_offD, ctx->d_keepC, ctx->d_keepD, ctx->d_T,
+                                             ctx->blk_base[b]);
+  return last(ctx, "k_T");
+}
+
+// Z(B;E') for the middle atoms of block b (Z buffer holds that block).
+rix_status rix_launch_Z_block(rix_ctx *ctx, const double *D, int b, cudaStream_t st) {
+  if (!g_attr_done) {
+    cudaFuncSetAttribute(k_X12, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_BIG * 8);
+    cudaFuncSetAttribute(k_Z, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_BIG * 8);
+    cudaFuncSetAttribute(k_X34, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_BIG * 8);
+    g_attr_done = true;
+  }
+  const int64_t nZ = ctx->segZ[b + 1] - ctx->segZ[b];
+  if (!nZ) return RIX_OK;
+  k_Z<<<(unsigned)nZ, NT, SM_BIG * 8, st>>>(ctx->d_itZ + ctx->segZ[b], ctx->d_ptrZ, ctx->d_LZ, ctx->d_atomA2,
+                                            ctx->d_atomB2, ctx->d_off2, ctx->d_pB, ctx->d_nb, ctx->d_na, ctx->d_C,
+                                            ctx->d_offC, ctx->d_V, ctx->d_offV, D, ctx->d_offD, ctx->d_keepC,
+                                            ctx->d_keepV, ctx->d_keepD, ctx->d_Z, ctx->blk_base[b]);
+  return last(ctx, "k_Z");
+}
+
 rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t st) {
   if (!g_attr_done) {
     cudaFuncSetAttribute(k_X12, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_BIG * 8);
@@ -564,13 +592,7 @@ rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t
   // terms 1 and 2, one block of row atoms at a time (T resident for the block)
   for (int b = 0; b < ctx->nblk; b++) {
     const int64_t tbase = ctx->blk_base[b];
-    const int64_t nT = ctx->segT[b + 1] - ctx->segT[b];
-    if (nT) {
-      k_T<<<(unsigned)nT, NT, 64 * 64 * 8, st>>>(
-          ctx->d_itT + ctx->segT[b], ctx->d_ptrT, ctx->d_LT, ctx->d_atomA2, ctx->d_atomB2, ctx->d_off2, ctx->d_pB,
-          ctx->d_nb, ctx->d_na, ctx->d_C, ctx->d_offC, D, ctx->d_offD, ctx->d_keepC, ctx->d_keepD, ctx->d_T, tbase);
-      if ((s = last(ctx, "k_T")) != RIX_OK) return s;
-    }
+    if ((s = rix_launch_T_block(ctx, D, b, st)) != RIX_OK) return s;
     if (b == 0 && (s = rix_prof_mark(ctx, 2, st)) != RIX_OK) return s;
     const int64_t nU = ctx->segU[b + 1] - ctx->segU[b];
     if (nU) {
@@ -594,14 +616,7 @@ rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t
   // terms 3 and 4, one block of middle atoms B at a time (Z resident for the block)
   for (int b = 0; b < ctx->nblk; b++) {
     const int64_t zbase = ctx->blk_base[b];
-    const int64_t nZ = ctx->segZ[b + 1] - ctx->segZ[b];
-    if (nZ) {
-      k_Z<<<(unsigned)nZ, NT, SM_BIG * 8, st>>>(
-          ctx->d_itZ + ctx->segZ[b], ctx->d_ptrZ, ctx->d_LZ, ctx->d_atomA2, ctx->d_atomB2, ctx->d_off2, ctx->d_pB,
-          ctx->d_nb, ctx->d_na, ctx->d_C, ctx->d_offC, ctx->d_V, ctx->d_offV, D, ctx->d_offD, ctx->d_keepC,
-          ctx->d_keepV, ctx->d_keepD, ctx->d_Z, zbase);
-      if ((s = last(ctx, "k_Z")) != RIX_OK) return s;
-    }
+    if ((s = rix_launch_Z_block(ctx, D, b, st)) != RIX_OK) return s;
     if (b == 0 && (s = rix_prof_mark(ctx, 5, st)) != RIX_OK) return s;
     if (ctx->have_mx) {
       if ((s = rix_mixed_x34(ctx, ctx->blk_atom[b], ctx->blk_atom[b + 1], zbase, st)) != RIX_OK) return s;

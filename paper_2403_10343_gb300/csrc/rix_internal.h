@@ -150,7 +150,7 @@ struct rix_ctx {
   int64_t *d_ptrBTC = nullptr; int2 *d_LBTC = nullptr;     // per pair (A,B'): (pair (B',G'), T block)
   int4 *d_itB[9] = {nullptr};                              // tiled work items per backward kernel
   int64_t n_itB[9] = {0};
-  double *d_Zbar = nullptr, *d_Tbar = nullptr, *d_U2bar = nullptr, *d_Kbuf = nullptr;
+  double *d_U2bar = nullptr, *d_Kbuf = nullptr;   // Tbar and Zbar reuse the T and Z buffers
   double bwd_flops = 0;
 
   rix_stats_t stats{};
@@ -192,6 +192,8 @@ rix_status rix_mixed_x34(rix_ctx *ctx, int b0, int b1, int64_t zbase, cudaStream
 
 // FP64 path launches (rix_fp64.cu)
 rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t st);
+rix_status rix_launch_T_block(rix_ctx *ctx, const double *D, int b, cudaStream_t st);
+rix_status rix_launch_Z_block(rix_ctx *ctx, const double *D, int b, cudaStream_t st);
 rix_status rix_launch_flags(rix_ctx *ctx, const double *arr, const int64_t *off, int64_t n,
                             uint8_t *keep, cudaStream_t st);
 rix_status rix_launch_symcheck(rix_ctx *ctx, cudaStream_t st);

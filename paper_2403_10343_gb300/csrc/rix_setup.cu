@@ -273,8 +273,6 @@ static rix_status build_backward_lists(rix_ctx *ctx, const std::vector<int2> &LT
     TRY(rix_upload(ctx, &ctx->d_itB[k], it[k]));
     ctx->n_itB[k] = it[k].size();
   }
-  TRY(rix_alloc(ctx, &ctx->d_Zbar, ctx->off2[n2]));
-  TRY(rix_alloc(ctx, &ctx->d_Tbar, ctx->off2[n2]));
   int64_t nU = 0;
   for (int64_t p = 0; p < np; p++) nU += NA(pB[p]) * NB(pA[p]) * NB(pB[p]);
   TRY(rix_alloc(ctx, &ctx->d_U2bar, nU));
@@ -763,10 +761,6 @@ static rix_status build_lists(rix_ctx *ctx) {
   TRY(rix_upload(ctx, &ctx->d_itU, itU)); ctx->n_itU = itU.size();
   TRY(rix_upload(ctx, &ctx->d_ordX12, ordX12)); ctx->n_ordX12 = ordX12.size();
   TRY(rix_upload(ctx, &ctx->d_ordX34, ordX34)); ctx->n_ordX34 = ordX34.size();
-  if (nblk > 1 && ctx->opt.backward) {
-    ctx->last_error = "rix_backward needs T and Z resident (workspace too small)";
-    return RIX_ENOMEM;
-  }
   TRY(rix_alloc(ctx, &ctx->d_T, maxbuf));
   TRY(rix_alloc(ctx, &ctx->d_Z, maxbuf));
   if (ctx->opt.precision == RIX_MIXED_BF16) TRY(rix_mixed_plan(ctx, ptrZ));
@@ -922,8 +916,9 @@ extern "C" rix_status rix_layout_sizes(const rix_ctx *ctx, int64_t *c, int64_t *
 extern "C" rix_status rix_set_CV(rix_ctx *ctx, const double *C, const double *V, void *stream) {
   if (!ctx || !C || !V) return RIX_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  RIX_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_C, C, sizeof(double) * ctx->offC[ctx->np], cudaMemcpyDeviceToDevice, st));
-  RIX_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_V, V, sizeof(double) * ctx->offV[ctx->np], cudaMemcpyDeviceToDevice, st));
+  // host or device sources: the direction follows from the (unified) address
+  RIX_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_C, C, sizeof(double) * ctx->offC[ctx->np], cudaMemcpyDefault, st));
+  RIX_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_V, V, sizeof(double) * ctx->offV[ctx->np], cudaMemcpyDefault, st));
   rix_status s = rix_launch_symcheck(ctx, st);
   if (s != RIX_OK) return s;
   int32_t bad = 0;

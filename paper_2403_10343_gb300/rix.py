@@ -151,8 +151,22 @@ def layout_sizes(ctx):
     return tuple(x.value for x in v)
 
 
+def _any_ptr(x, name):
+    """Device tensor, or a host array (numpy or CPU tensor) for rix_set_CV."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags.c_contiguous:
+            raise ValueError(f"{name} must be a contiguous float64 array")
+        return ctypes.c_void_p(x.ctypes.data)
+    if not x.is_cuda:
+        if not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        return ctypes.c_void_p(x.data_ptr())
+    return _dptr(x, name)
+
+
 def set_CV(ctx, C, V, stream=None):
-    _check(load().rix_set_CV(ctx, _dptr(C, "C"), _dptr(V, "V"), _stream(stream)), ctx)
+    """rix_set_CV; C and V may be CUDA tensors or host arrays (copied either way)."""
+    _check(load().rix_set_CV(ctx, _any_ptr(C, "C"), _any_ptr(V, "V"), _stream(stream)), ctx)
 
 
 def build_K(ctx, D, K, stream=None):

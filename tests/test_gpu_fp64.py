@@ -245,3 +245,16 @@ def test_row_blocked_memory_plan(case):
         assert abs(E - E_ref) < E_TOL * abs(E_ref)
         ex.close()
     assert max(seen) >= 2, seen
+
+
+def test_set_CV_from_host_arrays():
+    """rix_set_CV takes host arrays as well as device buffers; K is identical."""
+    s = ri.config(0)
+    pk = ri.generate(s)
+    ex, keys, K1, E1, (C, V, D) = run_gpu(s, pk)
+    ex2 = Exchange.from_system(s)
+    ex2.set_CV(np.ascontiguousarray(pk.C), np.ascontiguousarray(pk.V))
+    K2 = ex2.build_K(D).cpu().numpy()
+    assert np.array_equal(K1, K2)
+    ex.close()
+    ex2.close()

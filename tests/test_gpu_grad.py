@@ -13,11 +13,13 @@ import pytest
 import rix_inputs as ri
 import rix_inputs.systems as S
 from oracle.oracle import Oracle
+from oracle.grad import DenseCluster
+from partners import entries as _entries, partner_C as _partner_C, partner_V as _partner_V
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from paper_2403_10343_gb300.rix import Exchange  # noqa: E402
+from paper_2403_10343_gb300.rix import Exchange, RixError  # noqa: E402
 from paper_2403_10343_gb300.autograd import exchange_energy  # noqa: E402
 
 
@@ -34,46 +36,6 @@ def _small_pbc(seed=11, side=4.6, cut=4.8, nmol=1):
                     nbas=nb, naux=na, sigma=S._aux_widths(seed, names), cell=ri.ang2bohr(np.eye(3) * side),
                     cutoff=ri.ang2bohr(cut), tau=0.0,
                     orbital_centres=np.repeat(np.arange(0, len(spc), 3), 5).astype(np.int32))
-
-
-def _partner_C(pk, s, p, e):
-    """Index (absolute) of the transpose partner of C element e of pair p."""
-    sp = s.species
-    a, b = pk.A[p], pk.B[p]
-    nbA, nbB, naA, naB = s.nbas[sp[a]], s.nbas[sp[b]], s.naux[sp[a]], s.naux[sp[b]]
-    P, r = divmod(e, nbA * nbB)
-    i, j = divmod(r, nbB)
-    q = pk.partner[p]
-    if pk.onsite[p]:
-        return pk.offC[p] + (P * nbA + j) * nbB + i
-    Pq = P + naB if P < naA else P - naA
-    return pk.offC[q] + (Pq * nbB + j) * nbA + i
-
-
-def _partner_V(pk, s, p, e):
-    sp = s.species
-    naA, naB = s.naux[sp[pk.A[p]]], s.naux[sp[pk.B[p]]]
-    P, Q = divmod(e, naB)
-    return pk.offV[pk.partner[p]] + Q * naA + P
-
-
-def _partner_D(pk, s, p, e):
-    sp = s.species
-    nbA, nbB = s.nbas[sp[pk.A[p]]], s.nbas[sp[pk.B[p]]]
-    i, j = divmod(e, nbB)
-    return pk.offD[pk.partner[p]] + j * nbA + i
-
-
-def _entries(pk, s, which, n, rng):
-    off = {"C": pk.offC, "V": pk.offV, "D": pk.offD}[which]
-    part = {"C": _partner_C, "V": _partner_V, "D": _partner_D}[which]
-    out = []
-    while len(out) < n:
-        p = int(rng.integers(pk.n_pairs))
-        e = int(rng.integers(off[p + 1] - off[p]))
-        g = int(off[p] + e)
-        out.append((g, int(part(pk, s, p, e))))
-    return out
 
 
 def _fd_check(s, pk, n=12, h=1e-3, seed=0, tol=1e-7):
@@ -193,3 +155,71 @@ def test_autograd_function():
     torch.cuda.synchronize()
     assert torch.equal(D.grad, dD) and torch.equal(C.grad, dC) and torch.equal(V.grad, dV)
     assert E.item() < 0
+
+
+@pytest.mark.parametrize("case", ["cluster24", "pbc2"])
+def test_backward_row_blocked_plan(case):
+    """A workspace too small for T and Z splits the adjoint into row blocks
+    (T and Z recomputed per block); the gradients are unchanged."""
+    if case == "cluster24":
+        s = ri.config(0)
+    else:
+        s = _small_pbc(seed=11, side=6.0, cut=4.0, nmol=2)
+    pk = ri.generate(s)
+    D = _dev(pk.D)
+    full = Exchange.from_system(s, backward=1)
+    full.set_CV(_dev(pk.C), _dev(pk.V))
+    assert full.stats()["n_row_blocks"] == 1
+    ref = [x.cpu().numpy() for x in full.backward(D, 1.0)]
+    w0 = full.stats()["workspace_bytes"]
+    full.close()
+    seen = set()
+    for frac in (0.9, 0.8, 0.7, 0.6):
+        try:
+            ex = Exchange.from_system(s, backward=1, max_workspace_bytes=int(w0 * frac))
+        except RixError:
+            continue
+        ex.set_CV(_dev(pk.C), _dev(pk.V))
+        seen.add(ex.stats()["n_row_blocks"])
+        got = [x.cpu().numpy() for x in ex.backward(D, 1.0)]
+        for g, r in zip(got, ref):
+            assert np.linalg.norm(g - r) <= 1e-13 * np.linalg.norm(r)
+        ex.close()
+    assert max(seen) >= 2, seen
+
+
+def test_grad_config1_against_dense_definition():
+    """(H2O)64 cluster, 192 atoms, 8 A cutoff: rix_backward partials at random
+    stored C and V entries against the dense four-index definition of the
+    gradient; the mixed-precision context's dD against -1/2 K of the FP64 path."""
+    s = ri.config(1)
+    pk = ri.generate(s)
+    dc = DenseCluster(s, pk)
+    D = _dev(pk.D)
+    ex = Exchange.from_system(s, backward=1)
+    ex.set_CV(_dev(pk.C), _dev(pk.V))
+    dD, dC, dV = [x.cpu().numpy() for x in ex.backward(D, 1.0)]
+    ex.close()
+    rng = np.random.default_rng(7)
+    got, ref = [], []
+    for _ in range(16):
+        p = int(rng.integers(pk.n_pairs))
+        a, b = pk.A[p], pk.B[p]
+        rows = dc.na[a] + (0 if pk.onsite[p] else dc.na[b])
+        r, i, j = int(rng.integers(rows)), int(rng.integers(dc.nb[a])), int(rng.integers(dc.nb[b]))
+        got.append(dC[pk.offC[p] + (r * dc.nb[a] + i) * dc.nb[b] + j])
+        ref.append(dc.dC(p, r, i, j))
+    for _ in range(16):
+        p = int(rng.integers(pk.n_pairs))
+        P, Q = int(rng.integers(dc.na[pk.A[p]])), int(rng.integers(dc.na[pk.B[p]]))
+        got.append(dV[pk.offV[p] + P * dc.na[pk.B[p]] + Q])
+        ref.append(dc.dV(p, P, Q))
+    got, ref = np.array(got), np.array(ref)
+    scale = np.abs(ref).max()
+    print("dense-definition gradient check: max |diff| / max |ref| =", np.abs(got - ref).max() / scale)
+    assert np.all(np.abs(got - ref) <= 1e-11 * np.abs(ref) + 1e-13 * scale)
+    mx = Exchange.from_system(s, backward=1, precision="mixed")
+    mx.set_CV(_dev(pk.C), _dev(pk.V))
+    dDm = mx.backward(D, 1.0, want=("D",))[0].cpu().numpy()
+    mx.close()
+    assert np.linalg.norm(dD - dDm) <= 1e-8 * np.linalg.norm(dD)

@@ -1,0 +1,226 @@
+"""Full-size periodic workloads on one GPU.
+
+* Perovskite-like cell: 1,536 atoms (Pb/I/C/N/H), nbasis 24,911, C = 70.7 GB.
+* Ice-like supercell: 3,072 atoms (1,024 H2O), nbasis 24,576, C = 24.6 GB,
+  with the adjoint (dE/dD, dE/dC, dE/dV) through torch.autograd.
+
+Each case holds ~100 GB of host memory and runs for minutes, so the module
+runs only when RIX_LARGE=1.  C and V are loaded from host memory (the
+device would not hold two copies of C).  Parity is checked on sampled K
+blocks: the oracle's block-sampled build computes exactly the listed blocks
+(T and Z restricted to the nodes they need), for a few row atoms of every
+species, against the FP64 path (relative Frobenius <= 1e-12) and the mixed
+path (<= 1e-8); the mixed path must agree with the FP64 path in K (1e-8) and
+in E_x (1e-6 Ha).  Timings are printed (run with -s).
+"""
+import os
+import time
+
+import numpy as np
+import pytest
+
+import rix_inputs as ri
+from oracle.oracle import Oracle
+from partners import entries
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow,
+              pytest.mark.skipif(os.environ.get("RIX_LARGE") != "1", reason="full-size runs need RIX_LARGE=1")]
+
+from paper_2403_10343_gb300.rix import Exchange  # noqa: E402
+from paper_2403_10343_gb300.autograd import exchange_energy  # noqa: E402
+
+K_TOL_FP64 = 1e-12
+K_TOL_MIXED = 1e-8
+E_TOL_HA = 1e-6
+GB = 1 << 30
+
+
+def _offsets(s, keys):
+    A, E, _ = ri.unpack_key(keys)
+    nb = s.nbas[s.species].astype(np.int64)
+    return np.concatenate([[0], np.cumsum(nb[A] * nb[E])])
+
+
+def _workspace_cap(user_bytes):
+    """Leave room on the device for the caller's own tensors."""
+    free = torch.cuda.mem_get_info()[0]
+    return int(free - user_bytes - 6 * GB)
+
+
+def _sample_keys(s, keys, rng, per_species=2, per_row=6):
+    """A few K blocks of a few row atoms of every species (always the diagonal block)."""
+    A, E, n = ri.unpack_key(keys)
+    pick = []
+    for sp in range(len(s.nbas)):
+        atoms = np.nonzero(s.species == sp)[0]
+        for a in rng.choice(atoms, min(per_species, len(atoms)), replace=False):
+            rows = np.nonzero(A == a)[0]
+            diag = rows[(E[rows] == a) & (n[rows] == 0).all(axis=1)]
+            pick += list(diag) + list(rng.choice(rows, min(per_row, len(rows)), replace=False))
+    return np.unique(keys[np.array(pick)])
+
+
+def _blocks(keys_all, off, K, want):
+    idx = np.searchsorted(keys_all, want)
+    assert np.array_equal(keys_all[idx], want)
+    return np.concatenate([K[off[x]:off[x + 1]] for x in idx])
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _host_energy(s, pk, keys, off, K):
+    """-1/4 sum over pairs of <D(partner), K> from host arrays."""
+    nb = s.nbas[s.species].astype(np.int64)
+    x = np.searchsorted(keys, pk.keys)
+    e = 0.0
+    for p in range(pk.n_pairs):
+        a, b = pk.A[p], pk.B[p]
+        q = pk.partner[p]
+        kb = K[off[x[p]]:off[x[p] + 1]].reshape(nb[a], nb[b])
+        dq = pk.D[pk.offD[q]:pk.offD[q + 1]].reshape(nb[b], nb[a])
+        e += float(np.sum(dq.T * kb))
+    return -0.25 * e
+
+
+def _forward(s, pk, precision, **kw):
+    # room for D and K (7 GB at these sizes) next to the library's workspace
+    ex = Exchange.from_system(s, precision=precision, verbose=1, max_workspace_bytes=_workspace_cap(16 * GB), **kw)
+    t0 = time.time()
+    ex.set_CV(pk.C, pk.V)
+    torch.cuda.synchronize()
+    t_load = time.time() - t0
+    D = torch.from_numpy(pk.D).cuda()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    K = ex.build_K(D)
+    E = ex.energy(D, K)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    st = ex.stats()
+    print(f"[{s.name} {precision}] build+energy {ms / 1e3:.2f} s, set_CV {t_load:.1f} s, "
+          f"{st['n_row_blocks']} row block(s), workspace {st['workspace_bytes'] / GB:.1f} GiB, "
+          f"alg {st['flops_fp64']:.3e} FLOP ({st['flops_fp64'] / ms / 1e9:.3f} TFLOP/s), E_x {E.item():.10f}",
+          flush=True)
+    return ex, D, K, E.item(), ms
+
+
+def _parity(s, pk, res, rng):
+    keys64, K64, E64 = res["fp64"]
+    off = _offsets(s, keys64)
+    orc = Oracle(s)
+    assert np.array_equal(keys64, orc.kpattern()), "K pattern differs from the oracle's"
+    orc.set_data(pk.C, pk.V, pk.D)
+    want = _sample_keys(s, keys64, rng)
+    t0 = time.time()
+    kk = orc.kpattern_blocks(want)
+    Kref = orc.build_K()
+    print(f"[{s.name}] oracle: {len(kk)} sampled K blocks in {time.time() - t0:.1f} s", flush=True)
+    assert np.array_equal(kk, want)
+    e64 = _rel(_blocks(keys64, off, K64, kk), Kref)
+    keysm, Km, Em = res["mixed"]
+    assert np.array_equal(keysm, keys64)
+    em = _rel(_blocks(keysm, off, Km, kk), Kref)
+    kdiff = _rel(Km, K64)
+    print(f"[{s.name}] sampled blocks vs oracle: FP64 {e64:.2e}, mixed {em:.2e}; "
+          f"mixed vs FP64: K {kdiff:.2e}, dE {Em - E64:.3e} Ha", flush=True)
+    assert e64 < K_TOL_FP64
+    assert em < K_TOL_MIXED
+    assert kdiff < K_TOL_MIXED
+    assert abs(Em - E64) < E_TOL_HA
+    eh = _host_energy(s, pk, keys64, off, K64)
+    assert abs(eh - E64) < 1e-12 * abs(E64)
+
+
+def test_perovskite_1536_atoms():
+    s = ri.config(3)
+    t0 = time.time()
+    pk = ri.generate(s)
+    print(f"[{s.name}] inputs generated in {time.time() - t0:.1f} s: C {pk.C.nbytes / 1e9:.1f} GB", flush=True)
+    res = {}
+    for prec in ("fp64", "mixed"):
+        ex, D, K, E, _ = _forward(s, pk, prec)
+        res[prec] = (ex.k_keys(), K.cpu().numpy(), E)
+        del K, D
+        ex.close()
+        torch.cuda.empty_cache()
+    _parity(s, pk, res, np.random.default_rng(3))
+
+
+def test_ice_3072_atoms_forward_and_adjoint():
+    s = ri.config(4)
+    t0 = time.time()
+    pk = ri.generate(s)
+    print(f"[{s.name}] inputs generated in {time.time() - t0:.1f} s: C {pk.C.nbytes / 1e9:.1f} GB", flush=True)
+    res = {}
+    ex, D, K, E, _ = _forward(s, pk, "fp64")
+    res["fp64"] = (ex.k_keys(), K.cpu().numpy(), E)
+    del K, D
+    ex.close()
+    torch.cuda.empty_cache()
+
+    # mixed forward and the adjoint through torch.autograd (T and Z recomputed)
+    C = torch.from_numpy(pk.C).cuda().requires_grad_()
+    V = torch.from_numpy(pk.V).cuda().requires_grad_()
+    D = torch.from_numpy(pk.D).cuda().requires_grad_()
+    grads_bytes = (C.numel() + V.numel() + D.numel()) * 8
+    ex = Exchange.from_system(s, precision="mixed", backward=1, verbose=1,
+                              max_workspace_bytes=_workspace_cap(grads_bytes + 16 * GB))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    E = exchange_energy(D, C, V, ex)
+    ev[1].record()
+    E.backward()
+    ev[2].record()
+    torch.cuda.synchronize()
+    st = ex.stats()
+    print(f"[{s.name} mixed] forward {ev[0].elapsed_time(ev[1]) / 1e3:.2f} s, backward "
+          f"{ev[1].elapsed_time(ev[2]) / 1e3:.2f} s, {st['n_row_blocks']} row block(s), "
+          f"workspace {st['workspace_bytes'] / GB:.1f} GiB", flush=True)
+    Km = ex.build_K(D.detach())
+    res["mixed"] = (ex.k_keys(), Km.cpu().numpy(), E.item())
+    del Km
+    gD, gC, gV = D.grad.cpu().numpy(), C.grad.cpu().numpy(), V.grad.cpu().numpy()
+    assert np.isfinite(gC).all() and np.isfinite(gV).all() and np.isfinite(gD).all()
+
+    # central difference (h = 1e-5) along one direction over 32 random entries of C, V and D,
+    # each moved together with its transpose partner
+    rng = np.random.default_rng(11)
+    tens = {"C": C, "V": V, "D": D}
+    moves = {"C": {}, "V": {}, "D": {}}      # entry -> weight
+    an = 0.0
+    scale = 0.0
+    for which, n, g in (("C", 12, gC), ("V", 10, gV), ("D", 10, gD)):
+        for e1, e2 in entries(pk, s, which, n, rng):
+            w = float(rng.choice([-1.0, 1.0]))
+            for e in {e1, e2}:
+                moves[which][e] = moves[which].get(e, 0.0) + w
+                an += w * g[e]
+                scale += abs(g[e])
+    h = 1e-5
+
+    def energy_at(sign):
+        with torch.no_grad():
+            saved = {}
+            for which, mv in moves.items():
+                idx = torch.tensor(sorted(mv), dtype=torch.int64, device="cuda")
+                w = torch.tensor([mv[e] for e in sorted(mv)], dtype=torch.float64, device="cuda")
+                saved[which] = (idx, tens[which][idx].clone())
+                tens[which][idx] += sign * h * w
+            e = exchange_energy(D.detach(), C.detach(), V.detach(), ex).item()
+            for which, (idx, old) in saved.items():
+                tens[which][idx] = old
+            return e
+
+    fd = (energy_at(1.0) - energy_at(-1.0)) / (2 * h)
+    print(f"[{s.name} mixed] directional derivative over 32 entries (h = {h}): FD {fd:.10e}, "
+          f"adjoint {an:.10e}, |diff| / sum|g| = {abs(fd - an) / scale:.2e}", flush=True)
+    # E_x ~ 1e6 Ha: its rounding (~1e-8 Ha) over 2h bounds what the difference can resolve
+    assert abs(fd - an) <= 1e-4 * scale
+    ex.close()
+    del C, V, D
+    torch.cuda.empty_cache()
+    _parity(s, pk, res, np.random.default_rng(5))
