@@ -2,8 +2,10 @@
 """Benchmark of the exchange build: K-build time per SCF iteration.
 
 One step = one rix_build_K + rix_energy on the resident inputs of the
-workload (default: the (H2O)64 cluster, 192 atoms, nbasis 1536, 8 A cutoff).
-Prints one JSON line.
+workload (default: the (H2O)64 cluster, 192 atoms, nbasis 1536, 8 A cutoff),
+captured once into a CUDA graph and replayed (--graph 0: eager launches).
+Prints one JSON line; per-stage times come from CUDA events of the eager
+warm-up steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--config 1] [--precision both|fp64|mixed]
 
@@ -160,25 +162,50 @@ def measure(args, s, pk, precision, dev, world, rank, local):
     import torch.distributed as dist
     from paper_2403_10343_gb300.rix import Exchange
 
-    ex = Exchange.from_system(s, precision=precision, profile=1)
+    # leave room for the caller's D and K (and the end-to-end copies) beside the library's workspace
+    cap = 0
+    if s.n_atoms > 1000:
+        cap = int(torch.cuda.mem_get_info(dev)[0] - (24 << 30))
+    ex = Exchange.from_system(s, precision=precision, profile=1, max_workspace_bytes=cap)
     assert np.array_equal(ex.pair_keys(), pk.keys)
-    C = torch.from_numpy(pk.C).to(dev)
-    V = torch.from_numpy(pk.V).to(dev)
+    ex.set_CV(pk.C, pk.V)          # straight from host memory (copied into library storage)
     D = torch.from_numpy(pk.D).to(dev)
-    ex.set_CV(C, V)
-    del C, V
     K = torch.empty(ex.k_elems, dtype=torch.float64, device=dev)
     Ex = torch.empty(1, dtype=torch.float64, device=dev)
-    st = torch.cuda.current_stream()
+    tiles = None
+    if args.autotune:
+        # tile budgets of the FP64 contraction kernels, timed on this system (not in the timed region)
+        tiles = ex.autotune(D, os.path.join(tempfile.gettempdir(), "rix_tiles.txt"))
 
     def step(Dd):
         ex.build_K(Dd, K)
         ex.energy(Dd, K, Ex)
 
+    # warm-up steps run eagerly and carry the per-stage CUDA events
     for _ in range(args.warmup):
         step(D)
     torch.cuda.synchronize()
-    ex.stage_times()  # drop the warm-up events
+    stage_ms, nb = ex.stage_times()
+    stage_ms = {k: v / max(1, nb) for k, v in stage_ms.items()}
+    eager_ms = None
+    if args.graph:
+        # one step captured into a CUDA graph; the timed steps are replays
+        g = torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream(device=dev)
+        cs.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(cs):
+            step(D)
+        torch.cuda.current_stream().wait_stream(cs)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            step(D)
+        torch.cuda.synchronize()
+        run = g.replay
+        ex.stage_times()
+    else:
+        def run():
+            step(D)
+    st = torch.cuda.current_stream()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -188,13 +215,12 @@ def measure(args, s, pk, precision, dev, world, rank, local):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(st)
     for _ in range(args.steps):
-        step(D)
+        run()
     e1.record(st)
     torch.cuda.synchronize()
     clocks = clk.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    stage_ms, nb = ex.stage_times()
-    stage_ms = {k: v / max(1, nb) for k, v in stage_ms.items()}
+    ex.stage_times()
     if world > 1:
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -210,7 +236,11 @@ def measure(args, s, pk, precision, dev, world, rank, local):
     e0.record(st)
     for _ in range(args.steps):
         Dd.copy_(Dh, non_blocking=True)
-        step(Dd)
+        if args.graph:
+            D.copy_(Dd)        # the graph reads D
+            run()
+        else:
+            step(Dd)
         Kh.copy_(K, non_blocking=True)
         Exh.copy_(Ex, non_blocking=True)
     e1.record(st)
@@ -224,7 +254,8 @@ def measure(args, s, pk, precision, dev, world, rank, local):
     stats = ex.stats()
     nblk = stats["n_row_blocks"]
     launches = 2 + 3 * nblk + nblk * (3 if precision == "mixed" else 2) + 3  # build + energy kernels
-    out = {"ms": ms, "e2e_ms": e2e_ms, "stage_ms": stage_ms, "stats": stats, "clocks": clocks,
+    out = {"ms": ms, "e2e_ms": e2e_ms, "stage_ms": stage_ms, "stats": stats, "clocks": clocks, "graph": args.graph,
+           "tiles": tiles,
            "E_x": Ex.item(), "K": K, "launches": launches, "h2d": int(D.numel() * 8), "d2h": int(K.numel() * 8 + 8)}
     ex.close()
     return out
@@ -254,6 +285,29 @@ def roofline(args, precision, r):
     return roof, roof_tc
 
 
+def stage_roofline(precision, r):
+    """Every stage: algorithmic FP64-equivalent FLOPs over its event time, against the pipe it runs on."""
+    stats, stage_ms = r["stats"], r["stage_ms"]
+    pk_peaks, src = peaks()
+    out = {}
+    for st, idx in STAGE_FLOP_INDEX.items():
+        ms = stage_ms.get(st, 0.0)
+        if ms <= 0:
+            continue
+        fl = stats["flops_stage"][idx]
+        ach = fl / (ms * 1e-3) / 1e12
+        if precision == "mixed" and st == "X34":
+            tc = stats["tensor_flops"] / (ms * 1e-3) / 1e12
+            peak = pk_peaks["bf16_tflops_sustained"]
+            out[st] = {"ms": round(ms, 4), "pipe": "tensor (bf16 slices)", "issued_tflops": round(tc, 2),
+                       "peak": peak, "frac": round(tc / peak, 4), "fp64_equivalent_tflops": round(ach, 3)}
+        else:
+            peak = pk_peaks.get("fp64_tflops", FP64_PEAK_TFLOPS_NOMINAL)
+            out[st] = {"ms": round(ms, 4), "pipe": "fp64", "achieved_tflops": round(ach, 4), "peak": peak,
+                       "frac": round(ach / peak, 4)}
+    return out
+
+
 def run_rix(args):
     import torch
     import torch.distributed as dist
@@ -279,7 +333,8 @@ def run_rix(args):
         K64, Km = res["fp64"]["K"], res["mixed"]["K"]
         extra["fp64"] = {"ms": res["fp64"]["ms"], "e2e_ms": res["fp64"]["e2e_ms"], "E_x": res["fp64"]["E_x"],
                          "stage_ms": {k: round(v, 4) for k, v in res["fp64"]["stage_ms"].items()},
-                         "roofline": roofline(args, "fp64", res["fp64"])[0]}
+                         "roofline": roofline(args, "fp64", res["fp64"])[0],
+                         "stage_roofline": stage_roofline("fp64", res["fp64"])}
         extra["mixed_vs_fp64"] = {"dE_x_Ha": res["mixed"]["E_x"] - res["fp64"]["E_x"],
                                   "K_rel_fro": float(torch.linalg.norm(Km - K64) / torch.linalg.norm(K64)),
                                   "speedup": res["fp64"]["ms"] / res["mixed"]["ms"]}
@@ -299,7 +354,9 @@ def run_rix(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD_NAMES[args.config], "precision": head,
                        "n_slices": 6 if head == "mixed" else None,
-                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
+                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}",
+                       "timing": "CUDA graph replay" if args.graph else "eager launches",
+                       "autotuned_tiles_x12_z_x34": r["tiles"]},
             "e2e": {"value": r["e2e_ms"] / world, "unit": "ms", "h2d_bytes_per_step": r["h2d"],
                     "d2h_bytes_per_step": r["d2h"]},
             "gpu_launches": r["launches"] * args.steps,
@@ -308,6 +365,7 @@ def run_rix(args):
             "roofline_tensor_stage": roof_tc,
             "cpu_baseline": cpu,
             "stage_ms": {k: round(v, 4) for k, v in r["stage_ms"].items()},
+            "stage_roofline": stage_roofline(head, r),
             "alg_flops": stats["flops_fp64"],
             "alg_tflops": stats["flops_fp64"] / (r["ms"] * 1e-3) / 1e12,
             "E_x": r["E_x"],
@@ -327,6 +385,8 @@ def main():
     ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
     ap.add_argument("--impl", default="rix", choices=["rix", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--graph", type=int, default=1, help="1: time CUDA graph replays of one step (default)")
+    ap.add_argument("--autotune", type=int, default=1, help="1: rix_autotune before the warm-up (default)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

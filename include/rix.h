@@ -98,7 +98,8 @@ typedef struct {
   int32_t n_slices;                /* mixed mode: BF16 slices per operand (0 = default) */
   int64_t max_workspace_bytes;     /* 0 = no limit beyond the device's free memory */
   int32_t verbose;                 /* 0 = silent */
-  int32_t profile;                 /* 1 = record a CUDA event after every stage of rix_build_K */
+  int32_t profile;                 /* 1 = record a CUDA event after every stage of rix_build_K
+                                      (skipped while the stream is being captured into a graph) */
   int32_t backward;                /* 1 = also plan rix_backward (extra product lists) */
 } rix_options;
 
@@ -140,6 +141,19 @@ rix_status rix_layout_sizes(const rix_ctx *ctx, int64_t *c_elems, int64_t *v_ele
  * default stream); synchronises the stream once to read the symmetry
  * verdict. */
 rix_status rix_set_CV(rix_ctx *ctx, const double *C_dev, const double *V_dev, void *stream);
+
+/* Autotuner (no counterpart in the paper's code path beyond its auto-tuned
+ * Fock-matrix block size): picks the shared-memory tile budget of the three
+ * FP64 contraction kernels (terms 1+2, the term-4 intermediate Z, terms 3+4)
+ * by timing four candidates on a slice of this system's own work items with
+ * the density matrix D_dev (device, packed).  Needs rix_set_CV first.
+ * cache_path (may be NULL): a text file of "key x12 z x34" lines; a line
+ * whose key (device name and list sizes) matches is applied without timing,
+ * and a new choice is appended.  chosen (may be NULL) receives the three
+ * budgets in doubles.  Synchronises `stream`; not allowed during graph
+ * capture (RIX_ESTATE).  Results of later builds change only by rounding. */
+rix_status rix_autotune(rix_ctx *ctx, const double *D_dev, const char *cache_path, int32_t *chosen,
+                        void *stream);
 
 /* K = exchange matrix of D (device, packed, FP64) into K_dev (device, packed
  * on the K list, FP64, fully overwritten).  Asynchronous on `stream`; no host

@@ -19,7 +19,9 @@
 // Each kernel is output-stationary: one CTA owns an output block (or a row
 // tile of it), walks its product list and keeps the sums in registers, so no
 // atomics are needed and every run sums in the same order.
+#include <algorithm>
 #include <cstdio>
+#include <string>
 
 #include "rix_internal.h"
 
@@ -30,7 +32,7 @@ namespace {
 constexpr int NT = 256;      // threads per CTA
 constexpr int MAXE = 32;     // output elements per thread in tiled kernels (NT * MAXE = 8192)
 constexpr int XMAXE = 16;    // output elements per thread for K blocks (64 x 64 / 256)
-constexpr int SM_BIG = 12288;  // doubles of dynamic shared memory for stage tiles (96 KB)
+constexpr int SM_MAX = 16384;  // largest shared-memory tile budget in doubles (128 KB)
 
 // ------------------------------------------------------------------ pair list (a1)
 __device__ __forceinline__ double d2_raw(const double *xyz, const double *cell, int periodic, int a, int b,
@@ -228,7 +230,7 @@ __global__ void __launch_bounds__(NT) k_X12(const int32_t *ord, const int64_t *p
                                             const int64_t *offV, const uint8_t *keepC, const uint8_t *keepV,
                                             const double *__restrict__ T, const int64_t *off2,
                                             const double *__restrict__ U, const int64_t *offU,
-                                            const int64_t *offK, double *X, int64_t tbase) {
+                                            const int64_t *offK, double *X, int64_t tbase, int smb) {
   extern __shared__ double sm[];
   const int tid = threadIdx.x;
   const int s = ord[blockIdx.x];
@@ -252,7 +254,7 @@ __global__ void __launch_bounds__(NT) k_X12(const int32_t *ord, const int64_t *p
       const double *Tt = T + (off2[en.t] - tbase);
       const double *Vae = V + offV[pae];
       const int per = nbA * nbG;
-      const int qt = min(naE, max(1, SM_BIG / per));
+      const int qt = min(naE, max(1, smb / per));
       for (int q0 = 0; q0 < naE; q0 += qt) {
         const int qn = min(qt, naE - q0);
         __syncthreads();
@@ -316,7 +318,7 @@ __global__ void __launch_bounds__(NT) k_Z(const int2 *items, const int64_t *ptrZ
                                           const double *__restrict__ V, const int64_t *offV,
                                           const double *__restrict__ D, const int64_t *offD,
                                           const uint8_t *keepC, const uint8_t *keepV, const uint8_t *keepD,
-                                          double *Z, int64_t zbase) {
+                                          double *Z, int64_t zbase, int smb) {
   extern __shared__ double sm[];
   const int tid = threadIdx.x;
   const int2 it = items[blockIdx.x];
@@ -339,7 +341,7 @@ __global__ void __launch_bounds__(NT) k_Z(const int2 *items, const int64_t *ptrZ
     const double *Vbg = V + offV[en.x];
     const double *Cge = C + offC[en.y];
     const int fper = nbG * nbE;
-    const int ft = max(1, min(pe - p0, SM_BIG / fper));
+    const int ft = max(1, min(pe - p0, smb / fper));
     for (int ps = p0; ps < pe; ps += ft) {
       const int fn = min(ft, pe - ps);
       __syncthreads();
@@ -386,7 +388,7 @@ __global__ void __launch_bounds__(NT) k_X34(const int32_t *ord, const int64_t *p
                                             const double *__restrict__ C, const int64_t *offC,
                                             const uint8_t *keepC, const double *__restrict__ Z,
                                             const int64_t *off2, const int64_t *offK, double *X, int64_t zbase,
-                                            int64_t zlo, int64_t zhi) {
+                                            int64_t zlo, int64_t zhi, int smb) {
   extern __shared__ double sm[];
   const int tid = threadIdx.x;
   const int x = ord[blockIdx.x];
@@ -404,7 +406,7 @@ __global__ void __launch_bounds__(NT) k_X34(const int32_t *ord, const int64_t *p
     const double *Cb = C + offC[en.x] + (int64_t)naA * nbA * nbB;
     const double *Zb = Z + (off2[en.y] - zbase);
     const int csz = nbA * nbB, zsz = nbB * nbE;
-    const int pc = max(1, min(naB, SM_BIG / (csz + zsz)));
+    const int pc = max(1, min(naB, smb / (csz + zsz)));
     for (int P0 = 0; P0 < naB; P0 += pc) {
       const int pn = min(pc, naB - P0);
       __syncthreads();
@@ -549,6 +551,56 @@ rix_status rix_launch_symcheck(rix_ctx *ctx, cudaStream_t st) {
   return last(ctx, "k_symcheck");
 }
 
+namespace {
+
+void set_attrs() {
+  if (!g_attr_done) {
+    cudaFuncSetAttribute(k_X12, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_MAX * 8);
+    cudaFuncSetAttribute(k_Z, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_MAX * 8);
+    cudaFuncSetAttribute(k_X34, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_MAX * 8);
+    g_attr_done = true;
+  }
+}
+
+// Z(B;E') for the Z work items [first, first + count) of block b.
+rix_status launch_Z_items(rix_ctx *ctx, const double *D, int b, int64_t first, int64_t count, int smb,
+                          cudaStream_t st) {
+  set_attrs();
+  if (!count) return RIX_OK;
+  k_Z<<<(unsigned)count, NT, smb * 8, st>>>(ctx->d_itZ + ctx->segZ[b] + first, ctx->d_ptrZ, ctx->d_LZ,
+                                            ctx->d_atomA2, ctx->d_atomB2, ctx->d_off2, ctx->d_pB, ctx->d_nb,
+                                            ctx->d_na, ctx->d_C, ctx->d_offC, ctx->d_V, ctx->d_offV, D, ctx->d_offD,
+                                            ctx->d_keepC, ctx->d_keepV, ctx->d_keepD, ctx->d_Z, ctx->blk_base[b],
+                                            smb);
+  return last(ctx, "k_Z");
+}
+
+// terms 1+2 for the output blocks [first, first + count) of block b's launch order.
+rix_status launch_X12_items(rix_ctx *ctx, int b, int64_t first, int64_t count, int smb, cudaStream_t st) {
+  set_attrs();
+  if (!count) return RIX_OK;
+  k_X12<<<(unsigned)count, NT, smb * 8, st>>>(
+      ctx->d_ordX12 + ctx->segX12[b] + first, ctx->d_ptrX12, ctx->d_LX12, ctx->d_atomA2, ctx->d_atomB2,
+      ctx->d_map2to1, ctx->d_map2to3, ctx->d_pA, ctx->d_onsite, ctx->d_nb, ctx->d_na, ctx->d_C, ctx->d_offC,
+      ctx->d_V, ctx->d_offV, ctx->d_keepC, ctx->d_keepV, ctx->d_T, ctx->d_off2, ctx->d_U, ctx->d_offU, ctx->d_offK,
+      ctx->d_X, ctx->blk_base[b], smb);
+  return last(ctx, "k_X12");
+}
+
+// terms 3+4 (FP64) for the K blocks [first, first + count) of the launch order, Z of block b.
+rix_status launch_X34_items(rix_ctx *ctx, int b, int64_t first, int64_t count, int smb, cudaStream_t st) {
+  set_attrs();
+  if (!count) return RIX_OK;
+  const int64_t zlo = ctx->row2[ctx->blk_atom[b]], zhi = ctx->row2[ctx->blk_atom[b + 1]];
+  k_X34<<<(unsigned)count, NT, smb * 8, st>>>(ctx->d_ordX34 + first, ctx->d_ptrX34, ctx->d_LX34, ctx->d_atomA3,
+                                              ctx->d_atomB3, ctx->d_pB, ctx->d_nb, ctx->d_na, ctx->d_C, ctx->d_offC,
+                                              ctx->d_keepC, ctx->d_Z, ctx->d_off2, ctx->d_offK, ctx->d_X,
+                                              ctx->blk_base[b], zlo, zhi, smb);
+  return last(ctx, "k_X34");
+}
+
+}  // namespace
+
 // T(A,G') for the row atoms of block b (T buffer holds that block).
 rix_status rix_launch_T_block(rix_ctx *ctx, const double *D, int b, cudaStream_t st) {
   const int64_t nT = ctx->segT[b + 1] - ctx->segT[b];
@@ -562,28 +614,11 @@ rix_status rix_launch_T_block(rix_ctx *ctx, const double *D, int b, cudaStream_t
 
 // Z(B;E') for the middle atoms of block b (Z buffer holds that block).
 rix_status rix_launch_Z_block(rix_ctx *ctx, const double *D, int b, cudaStream_t st) {
-  if (!g_attr_done) {
-    cudaFuncSetAttribute(k_X12, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_BIG * 8);
-    cudaFuncSetAttribute(k_Z, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_BIG * 8);
-    cudaFuncSetAttribute(k_X34, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_BIG * 8);
-    g_attr_done = true;
-  }
-  const int64_t nZ = ctx->segZ[b + 1] - ctx->segZ[b];
-  if (!nZ) return RIX_OK;
-  k_Z<<<(unsigned)nZ, NT, SM_BIG * 8, st>>>(ctx->d_itZ + ctx->segZ[b], ctx->d_ptrZ, ctx->d_LZ, ctx->d_atomA2,
-                                            ctx->d_atomB2, ctx->d_off2, ctx->d_pB, ctx->d_nb, ctx->d_na, ctx->d_C,
-                                            ctx->d_offC, ctx->d_V, ctx->d_offV, D, ctx->d_offD, ctx->d_keepC,
-                                            ctx->d_keepV, ctx->d_keepD, ctx->d_Z, ctx->blk_base[b]);
-  return last(ctx, "k_Z");
+  return launch_Z_items(ctx, D, b, 0, ctx->segZ[b + 1] - ctx->segZ[b], ctx->tile_Z, st);
 }
 
 rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t st) {
-  if (!g_attr_done) {
-    cudaFuncSetAttribute(k_X12, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_BIG * 8);
-    cudaFuncSetAttribute(k_Z, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_BIG * 8);
-    cudaFuncSetAttribute(k_X34, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_BIG * 8);
-    g_attr_done = true;
-  }
+  set_attrs();
   rix_status s;
   if ((s = rix_prof_mark(ctx, 0, st)) != RIX_OK) return s;
   if ((s = rix_launch_flags(ctx, D, ctx->d_offD, ctx->np, ctx->d_keepD, st)) != RIX_OK) return s;
@@ -602,15 +637,8 @@ rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t
       if ((s = last(ctx, "k_U2")) != RIX_OK) return s;
     }
     if (b == 0 && (s = rix_prof_mark(ctx, 3, st)) != RIX_OK) return s;
-    const int64_t nX = ctx->segX12[b + 1] - ctx->segX12[b];
-    if (nX) {
-      k_X12<<<(unsigned)nX, NT, SM_BIG * 8, st>>>(
-          ctx->d_ordX12 + ctx->segX12[b], ctx->d_ptrX12, ctx->d_LX12, ctx->d_atomA2, ctx->d_atomB2, ctx->d_map2to1,
-          ctx->d_map2to3, ctx->d_pA, ctx->d_onsite, ctx->d_nb, ctx->d_na, ctx->d_C, ctx->d_offC, ctx->d_V,
-          ctx->d_offV, ctx->d_keepC, ctx->d_keepV, ctx->d_T, ctx->d_off2, ctx->d_U, ctx->d_offU, ctx->d_offK,
-          ctx->d_X, tbase);
-      if ((s = last(ctx, "k_X12")) != RIX_OK) return s;
-    }
+    if ((s = launch_X12_items(ctx, b, 0, ctx->segX12[b + 1] - ctx->segX12[b], ctx->tile_X12, st)) != RIX_OK)
+      return s;
     if (b == 0 && (s = rix_prof_mark(ctx, 4, st)) != RIX_OK) return s;
   }
   // terms 3 and 4, one block of middle atoms B at a time (Z resident for the block)
@@ -620,12 +648,8 @@ rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t
     if (b == 0 && (s = rix_prof_mark(ctx, 5, st)) != RIX_OK) return s;
     if (ctx->have_mx) {
       if ((s = rix_mixed_x34(ctx, ctx->blk_atom[b], ctx->blk_atom[b + 1], zbase, st)) != RIX_OK) return s;
-    } else if (ctx->n_ordX34) {
-      const int64_t zlo = ctx->row2[ctx->blk_atom[b]], zhi = ctx->row2[ctx->blk_atom[b + 1]];
-      k_X34<<<(unsigned)ctx->n_ordX34, NT, SM_BIG * 8, st>>>(
-          ctx->d_ordX34, ctx->d_ptrX34, ctx->d_LX34, ctx->d_atomA3, ctx->d_atomB3, ctx->d_pB, ctx->d_nb, ctx->d_na,
-          ctx->d_C, ctx->d_offC, ctx->d_keepC, ctx->d_Z, ctx->d_off2, ctx->d_offK, ctx->d_X, zbase, zlo, zhi);
-      if ((s = last(ctx, "k_X34")) != RIX_OK) return s;
+    } else if ((s = launch_X34_items(ctx, b, 0, ctx->n_ordX34, ctx->tile_X34, st)) != RIX_OK) {
+      return s;
     }
   }
   if ((s = rix_prof_mark(ctx, 6, st)) != RIX_OK) return s;
@@ -633,6 +657,130 @@ rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t
                                            ctx->d_offK, ctx->d_X, K);
   if ((s = last(ctx, "k_sym")) != RIX_OK) return s;
   return rix_prof_mark(ctx, 7, st);
+}
+
+// ------------------------------------------------------------------ autotuner
+// Picks the shared-memory tile budget of k_X12, k_Z and k_X34 (and with it
+// their tile shapes and CTAs per SM) by timing each candidate on a slice of
+// the real work items of the first memory-plan block; the choice is cached
+// per system in a text file.  The analogue of the paper's auto-tuned Fock
+// block size (Sec. "Initialization"), at the level of one GPU's tiles.
+namespace {
+
+constexpr int N_CAND = 4;
+constexpr int CAND[N_CAND] = {4096, 8192, 12288, 16384};
+
+std::string tune_key(const rix_ctx *ctx) {
+  cudaDeviceProp prop;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaGetDeviceProperties(&prop, dev);
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s|nat=%d|np=%lld|n2=%lld|nk=%lld|prec=%d|blk=%d|", prop.name, ctx->nat,
+           (long long)ctx->np, (long long)ctx->n2, (long long)ctx->nk, (int)ctx->opt.precision, ctx->nblk);
+  std::string k(buf);
+  for (char &c : k)
+    if (c == ' ') c = '_';
+  return k;
+}
+
+// time `launch(c)` for every candidate c (one untimed run first); returns the fastest
+template <class F>
+rix_status pick(rix_ctx *ctx, cudaStream_t st, F launch, int *best, float *best_ms) {
+  cudaEvent_t e0, e1;
+  RIX_CUDA_TRY(ctx, cudaEventCreate(&e0));
+  RIX_CUDA_TRY(ctx, cudaEventCreate(&e1));
+  *best_ms = 3.0e38f;
+  rix_status s = RIX_OK;
+  for (int c = 0; c < N_CAND && s == RIX_OK; c++) {
+    if ((s = launch(CAND[c])) != RIX_OK) break;
+    cudaEventRecord(e0, st);
+    if ((s = launch(CAND[c])) != RIX_OK) break;
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { s = RIX_ECUDA; break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < *best_ms) { *best_ms = ms; *best = CAND[c]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return s;
+}
+
+}  // namespace
+
+extern "C" rix_status rix_autotune(rix_ctx *ctx, const double *D, const char *cache_path, int32_t *chosen,
+                                   void *stream) {
+  if (!ctx || !D) return RIX_EINVAL;
+  if (!ctx->have_cv) return RIX_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (st && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+    ctx->last_error = "rix_autotune times kernels and cannot run inside a graph capture";
+    return RIX_ESTATE;
+  }
+  const std::string key = tune_key(ctx);
+  if (cache_path && *cache_path) {
+    if (FILE *f = fopen(cache_path, "r")) {
+      char line[1024];
+      while (fgets(line, sizeof line, f)) {
+        char k[600];
+        int a = 0, b = 0, c = 0;
+        if (sscanf(line, "%599s %d %d %d", k, &a, &b, &c) == 4 && key == k && a > 0 && b > 0 && c > 0 &&
+            a <= SM_MAX && b <= SM_MAX && c <= SM_MAX) {
+          ctx->tile_X12 = a, ctx->tile_Z = b, ctx->tile_X34 = c;
+          fclose(f);
+          if (chosen) chosen[0] = a, chosen[1] = b, chosen[2] = c;
+          return RIX_OK;
+        }
+      }
+      fclose(f);
+    }
+  }
+  rix_status s;
+  set_attrs();
+  if ((s = rix_launch_flags(ctx, D, ctx->d_offD, ctx->np, ctx->d_keepD, st)) != RIX_OK) return s;
+  RIX_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_X, 0, sizeof(double) * ctx->offK[ctx->nk], st));
+  const int b = 0;
+  const int64_t SAMPLE = 4096;
+  // block 0's T and U2 feed the term 1+2 sample
+  if ((s = rix_launch_T_block(ctx, D, b, st)) != RIX_OK) return s;
+  const int64_t nU = ctx->segU[b + 1] - ctx->segU[b];
+  if (nU) {
+    k_U2<<<(unsigned)nU, NT, 0, st>>>(ctx->d_itU + ctx->segU[b], ctx->d_pA, ctx->d_pB, ctx->d_nb, ctx->d_na,
+                                      ctx->d_V, ctx->d_offV, ctx->d_keepV, ctx->d_map1to2, ctx->d_T, ctx->d_off2,
+                                      ctx->d_offU, ctx->d_U, ctx->blk_base[b]);
+    if ((s = last(ctx, "k_U2")) != RIX_OK) return s;
+  }
+  float ms = 0.f;
+  {
+    const int64_t n = ctx->segX12[b + 1] - ctx->segX12[b], cnt = std::min(n, SAMPLE), first = (n - cnt) / 2;
+    if (cnt && (s = pick(ctx, st, [&](int c) { return launch_X12_items(ctx, b, first, cnt, c, st); },
+                         &ctx->tile_X12, &ms)) != RIX_OK)
+      return s;
+  }
+  {
+    const int64_t n = ctx->segZ[b + 1] - ctx->segZ[b], cnt = std::min(n, SAMPLE), first = (n - cnt) / 2;
+    if (cnt && (s = pick(ctx, st, [&](int c) { return launch_Z_items(ctx, D, b, first, cnt, c, st); },
+                         &ctx->tile_Z, &ms)) != RIX_OK)
+      return s;
+  }
+  if (!ctx->have_mx && ctx->n_ordX34) {
+    if ((s = rix_launch_Z_block(ctx, D, b, st)) != RIX_OK) return s;
+    const int64_t n = ctx->n_ordX34, cnt = std::min(n, SAMPLE), first = (n - cnt) / 2;
+    if ((s = pick(ctx, st, [&](int c) { return launch_X34_items(ctx, b, first, cnt, c, st); }, &ctx->tile_X34,
+                  &ms)) != RIX_OK)
+      return s;
+  }
+  RIX_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  if (cache_path && *cache_path) {
+    if (FILE *f = fopen(cache_path, "a")) {
+      fprintf(f, "%s %d %d %d\n", key.c_str(), ctx->tile_X12, ctx->tile_Z, ctx->tile_X34);
+      fclose(f);
+    }
+  }
+  if (chosen) chosen[0] = ctx->tile_X12, chosen[1] = ctx->tile_Z, chosen[2] = ctx->tile_X34;
+  return RIX_OK;
 }
 
 rix_status rix_launch_energy(rix_ctx *ctx, const double *D, const double *K, double *Ex, cudaStream_t st) {

@@ -155,6 +155,9 @@ struct rix_ctx {
 
   rix_stats_t stats{};
 
+  // shared-memory tile budgets (doubles) of k_X12, k_Z and k_X34; rix_autotune picks them
+  int32_t tile_X12 = 12288, tile_Z = 12288, tile_X34 = 12288;
+
   // stage timing (rix_options.profile): 8 events per build, pooled
   static constexpr int NSTAGE = 7;
   std::vector<cudaEvent_t> ev_pool;

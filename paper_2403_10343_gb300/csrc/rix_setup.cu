@@ -978,6 +978,10 @@ extern "C" const char *rix_last_error(const rix_ctx *ctx) { return ctx ? ctx->la
 
 rix_status rix_prof_mark(rix_ctx *ctx, int i, cudaStream_t st) {
   if (!ctx->opt.profile) return RIX_OK;
+  // no stage events inside a CUDA graph capture (replays would not refresh them)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (st != nullptr && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+    return RIX_OK;
   // at most 4096 builds are kept between two reads
   if (i == 0 && ctx->ev_pending.size() >= (size_t)4096 * (rix_ctx::NSTAGE + 1)) return RIX_OK;
   if (i != 0 && ctx->ev_pending.size() % (rix_ctx::NSTAGE + 1) == 0) return RIX_OK;

@@ -76,6 +76,7 @@ def load():
                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P]
     lib.rix_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
                                     ctypes.POINTER(ctypes.c_int32)]
+    lib.rix_autotune.argtypes = [P, P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32), P]
     lib.rix_strerror.restype = ctypes.c_char_p
     lib.rix_strerror.argtypes = [I]
     lib.rix_last_error.restype = ctypes.c_char_p
@@ -187,6 +188,14 @@ def backward(ctx, D, gEx, dD=None, dC=None, dV=None, stream=None):
                                _dptr(dV, "dV"), _stream(stream)), ctx)
 
 
+def autotune(ctx, D, cache_path=None, stream=None):
+    """rix_autotune: returns the chosen tile budgets (doubles) of k_X12, k_Z, k_X34."""
+    out = (ctypes.c_int32 * 3)()
+    path = None if cache_path is None else os.fsencode(cache_path)
+    _check(load().rix_autotune(ctx, _dptr(D, "D"), path, out, _stream(stream)), ctx)
+    return tuple(out)
+
+
 def fold_gamma(ctx, K, Kdense, stream=None):
     _check(load().rix_fold_gamma(ctx, _dptr(K, "K"), _dptr(Kdense, "Kdense"), _stream(stream)), ctx)
 
@@ -250,6 +259,9 @@ class Exchange:
 
     def set_CV(self, C, V, stream=None):
         set_CV(self.ctx, C, V, stream)
+
+    def autotune(self, D, cache_path=None, stream=None):
+        return autotune(self.ctx, D, cache_path, stream)
 
     def build_K(self, D, K=None, stream=None):
         import torch

@@ -258,3 +258,29 @@ def test_set_CV_from_host_arrays():
     assert np.array_equal(K1, K2)
     ex.close()
     ex2.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotune_choice_and_cache(tmp_path, precision):
+    """rix_autotune picks one of its candidate tile budgets per kernel, the build still
+    matches the oracle, and a second context reads the choice back from the cache file."""
+    s = _mini_perovskite()
+    pk = ri.generate(s)
+    kk, K_ref, E_ref, _ = exchange(s, pk)
+    cache = str(tmp_path / "tiles.txt")
+    ex = Exchange.from_system(s, precision=precision)
+    D = _dev(pk.D)
+    ex.set_CV(_dev(pk.C), _dev(pk.V))
+    chosen = ex.autotune(D, cache)
+    assert all(c in (4096, 8192, 12288, 16384) for c in chosen)
+    K = ex.build_K(D).cpu().numpy()
+    tol = K_TOL if precision == "fp64" else 1e-8
+    assert rel(K, K_ref) < tol
+    lines = open(cache).read().splitlines()
+    assert len(lines) == 1
+    ex2 = Exchange.from_system(s, precision=precision)
+    ex2.set_CV(_dev(pk.C), _dev(pk.V))
+    assert ex2.autotune(D, cache) == chosen
+    assert open(cache).read().splitlines() == lines
+    ex.close()
+    ex2.close()
