@@ -710,7 +710,12 @@ static rix_status build_lists(rix_ctx *ctx) {
     avail = (int64_t)fr - ((int64_t)4 << 30);
     if (ctx->opt.max_workspace_bytes > 0)
       avail = std::min<int64_t>(avail, ctx->opt.max_workspace_bytes - (int64_t)ctx->dev_bytes);
-    if (ctx->opt.precision == RIX_MIXED_BF16) avail -= rix_mixed_bytes(ctx, ptrZ);
+    // still to come besides T and Z: the work-item arrays, the mixed-precision
+    // plan (estimate plus 5 %) and a little slack for allocation granularity
+    const int64_t items = (int64_t)(itT.size() + itZ.size() + itU.size()) * (int64_t)sizeof(int2) +
+                          (int64_t)(ordX12.size() + ordX34.size()) * (int64_t)sizeof(int32_t);
+    avail -= items + ((int64_t)256 << 20);
+    if (ctx->opt.precision == RIX_MIXED_BF16) avail -= rix_mixed_bytes(ctx, ptrZ) / 20 * 21;
   }
   const int64_t per_buf = std::max<int64_t>(0, avail / 2 / (int64_t)sizeof(double));
   ctx->blk_atom.assign(1, 0);

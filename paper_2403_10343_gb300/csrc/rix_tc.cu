@@ -10,19 +10,24 @@
 //   A B = 2^(eA + eB) sum_{s+t <= S+1} 2^{-7(s+t)} (A_s B_t)
 //
 // and every slice product A_s B_t is a sum of integers below 2^14 per term.
-// All products with the same s+t share one FP32 accumulator in tensor memory;
-// over a group of 128 K values and at most S slice pairs such a sum stays
-// below 2^24, so the tensor cores accumulate it exactly.  After each group the
-// accumulators are folded into a 64-bit fixed-point sum per output element
-// (integer arithmetic), and the FP64 result is formed once at the end.  The
-// error is the truncation of the operands after S digits (about 2^-7S of the
-// row/column scale) plus the dropped terms s+t > S+1.
+// Slice s is stored pre-scaled by 2^-7(s-1) (exact in BF16), so a product
+// carries its own power of two.  Four FP32 accumulators in tensor memory
+// take the products with s+t = 2, 3, 4 and s+t >= 5: the first three hold
+// integers (times 2^-7(s+t-2)) whose sums over a group of 320 K values stay
+// below 2^24, so the tensor cores accumulate them exactly; the fourth holds
+// terms at least 2^-21 below the leading one, where FP32 rounding costs about
+// 2^-43 of the row/column scale.  After each group the accumulators are
+// folded into a 64-bit fixed-point sum per output element, and the FP64
+// result is formed once at the end.  The error is the truncation of the
+// operands after S digits (about 2^-7S of the row/column scale), the dropped
+// terms s+t > S+1 and the rounding of the fourth accumulator.
 //
-// Kernel layout: one CTA per 128 x 64 output tile; warp 0 issues the bulk
+// Kernel layout: one CTA per 128 x 128 output tile; warp 0 issues the bulk
 // copies (cp.async.bulk, mbarrier completion), one thread of warp 1 issues
 // tcgen05.mma (A and B from shared memory, accumulators in tensor memory),
-// warps 4-7 drain tensor memory (tcgen05.ld) into the fixed-point sums.  Every
-// wait is bounded; on a timeout the kernel records an error and returns.
+// warps 4-11 drain tensor memory (tcgen05.ld, two warps per 32-lane quadrant,
+// 64 columns each) into the fixed-point sums.  Every wait is bounded; on a
+// timeout the kernel records an error and returns.
 #include <cuda_bf16.h>
 
 #include <cstdint>
@@ -33,15 +38,17 @@
 namespace rixtc {
 
 constexpr int TM = 128;         // output rows per tile (one TMEM lane each)
-constexpr int TN = 64;          // output columns per tile
+constexpr int TN = 128;         // output columns per tile
 constexpr int KC = 32;          // K per pipeline stage
-constexpr int GROUP = 4;        // stages per exact accumulation group (128 K)
+constexpr int GROUP = 10;       // stages per exact accumulation group (320 K: 3 x 320 x 127^2 < 2^24)
+constexpr int NACC = 4;         // accumulators: s+t = 2, 3, 4 and s+t >= 5 (all 512 TMEM columns)
+constexpr int NTHR = 384;       // warps 0-3: copies, MMA, TMEM allocation; warps 4-11: drain
 constexpr int MAXS = 8;         // slices supported
 constexpr uint64_t WAIT_NS = 2000000000ull;  // a wait gives up after 2 s
 
 // bytes of one packed tile (no-swizzle K-major core matrices, 8 rows x 16 B)
 constexpr int A_TILE = TM * KC * 2;  // 8 KB
-constexpr int B_TILE = TN * KC * 2;  // 4 KB
+constexpr int B_TILE = TN * KC * 2;  // 8 KB
 
 constexpr int NSTAGE = 3;            // pipeline stages when they fit in shared memory
 constexpr int SMEM_LIMIT = 227 * 1024;
@@ -171,6 +178,9 @@ __device__ __forceinline__ void digits_of(double x, int e, int S, float *d) {
   for (int s = 0; s < S; s++) d[s] = sg * (float)((frac >> (64 - 7 * (s + 1))) & 127u);
 }
 
+// 2^-7s as a float (exact): slice s (0-based) is stored pre-scaled by it
+__device__ __forceinline__ float slice_scale(int s) { return __int_as_float((127 - 7 * s) << 23); }
+
 // Row exponents of a row-major matrix X [R x Kd] (ld = row stride); zero and padded rows get -2000.
 __global__ void k_row_exp(const double *X, int64_t ld, int R, int Kd, int Rpad, int *e) {
   const int r = blockIdx.x * blockDim.y + threadIdx.y;
@@ -209,7 +219,7 @@ __global__ void k_pack(const double *X, int64_t sr, int64_t sk, int R, int Kd, i
   const int64_t tbase = ((int64_t)rt * (Kpad / KC) + kt) * tile_bytes + tile_off(r % rows_per_tile, k % KC);
   char *base = (char *)planes;
   for (int s = 0; s < S; s++)
-    *(__nv_bfloat16 *)(base + (int64_t)s * ntile * tile_bytes + tbase) = __float2bfloat16_rn(d[s]);
+    *(__nv_bfloat16 *)(base + (int64_t)s * ntile * tile_bytes + tbase) = __float2bfloat16_rn(d[s] * slice_scale(s));
 }
 
 // ------------------------------------------------------------------ the GEMM
@@ -243,8 +253,9 @@ struct GemmArgs {
   double *X;               // X[offK[x] + i * nbE + l] += value (atomic)
 };
 
-// Bits the fixed-point sum needs: products below 2^14, at most Kpad of them per
-// diagonal sum, the top diagonal shifted by 7(S-1), plus sign; keep <= 62.
+// Bits the fixed-point sum needs: products below 2^14, at most Kpad of them in
+// the leading diagonal, scaled up by 7(S-1), plus sign and the lower
+// diagonals (< 2 %); keep <= 62.
 __host__ __device__ inline int fixed_point_drop(int Kpad, int S) {
   int lk = 0;
   while ((1 << lk) < Kpad) lk++;
@@ -252,7 +263,7 @@ __host__ __device__ inline int fixed_point_drop(int Kpad, int S) {
   return bits > 62 ? bits - 62 : 0;
 }
 
-__global__ void __launch_bounds__(256, 1) k_gemm_sliced(GemmArgs g) {
+__global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
   extern __shared__ __align__(1024) uint8_t smem[];
   // layout: [stage][A tiles S][B tiles S], then barriers, then TMEM address
   const int S = g.S;
@@ -293,13 +304,14 @@ __global__ void __launch_bounds__(256, 1) k_gemm_sliced(GemmArgs g) {
       mbar_init(&empty[i], 1);
     }
     mbar_init(accfull, 1);
-    mbar_init(accempty, 128);
+    mbar_init(accempty, NTHR - 128);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 2) {  // TMEM: S diagonals x TN columns, rounded to a power of two >= 32
+  const int nacc = S < NACC ? S : NACC;
+  if (warp == 2) {  // TMEM: nacc accumulators x TN columns, rounded to a power of two >= 32
     uint32_t ncols = 32;
-    while (ncols < (uint32_t)(S * TN)) ncols <<= 1;
+    while (ncols < (uint32_t)(nacc * TN)) ncols <<= 1;
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(ncols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -346,31 +358,35 @@ __global__ void __launch_bounds__(256, 1) k_gemm_sliced(GemmArgs g) {
       tc_fence_after();
       const uint32_t sa = smem_u32(smem + st * stage_bytes);
       const uint32_t sb = sa + S * A_TILE;
-      for (int d = 2; d <= S + 1; d++) {
-        const uint32_t tcol = tmem + (uint32_t)((d - 2) * TN);
-        bool first = (c % GROUP == 0);
-        for (int s = 1; s <= S; s++) {
-          const int t = d - s;
-          if (t < 1 || t > S) continue;
+      bool fresh[NACC];
+#pragma unroll
+      for (int a = 0; a < NACC; a++) fresh[a] = (c % GROUP == 0);
+      for (int s = 0; s < S; s++)
+        for (int t = 0; s + t < S; t++) {
+          const int a = s + t < NACC - 1 ? s + t : NACC - 1;
+          const uint32_t tcol = tmem + (uint32_t)(a * TN);
           for (int kk = 0; kk < KC / 16; kk++) {
             // K step kk covers core-matrix columns 2kk, 2kk+1 (LBO = 128 B apart)
-            const uint64_t ad = sdesc(sa + (s - 1) * A_TILE + kk * 256, 128, (KC / 8) * 128);
-            const uint64_t bd = sdesc(sb + (t - 1) * B_TILE + kk * 256, 128, (KC / 8) * 128);
-            mma_bf16(tcol, ad, bd, idesc, first ? 0u : 1u);
-            first = false;
+            const uint64_t ad = sdesc(sa + s * A_TILE + kk * 256, 128, (KC / 8) * 128);
+            const uint64_t bd = sdesc(sb + t * B_TILE + kk * 256, 128, (KC / 8) * 128);
+            mma_bf16(tcol, ad, bd, idesc, fresh[a] ? 0u : 1u);
+            fresh[a] = false;
           }
         }
-      }
       mma_commit(&empty[st]);
       if (c % GROUP == GROUP - 1 || c == nk - 1) mma_commit(accfull);
     }
   } else if (warp >= 4) {
     // ------------------------------------------------------------ drain and fold
-    const int q = warp - 4;              // TMEM lane quadrant
+    constexpr int HN = TN / 2;           // columns per drain warp
+    const int q = warp & 3;              // TMEM lane quadrant (a warp reaches lanes 32 (warp % 4) ..)
+    const int h = (warp - 4) >> 2;       // column half
     const int row = q * 32 + lane;       // output row inside the tile
-    int64_t acc[TN];
+    // accumulator units -> fixed point: 2^(7(S-1) - drop), exact in FP32
+    const float fscale = __int_as_float((127 + 7 * (S - 1) - drop) << 23);
+    int64_t acc[HN];
 #pragma unroll
-    for (int n = 0; n < TN; n++) acc[n] = 0;
+    for (int n = 0; n < HN; n++) acc[n] = 0;
     bool ok = true;
     for (int grp = 0; grp < ngroups; grp++) {
       if (!mbar_wait(accfull, grp & 1)) {
@@ -379,18 +395,15 @@ __global__ void __launch_bounds__(256, 1) k_gemm_sliced(GemmArgs g) {
         break;
       }
       tc_fence_after();
-      for (int d = 2; d <= S + 1; d++) {
-        const int sh = 7 * (S + 1 - d) - drop;
+      for (int a = 0; a < nacc; a++) {
 #pragma unroll
-        for (int n0 = 0; n0 < TN; n0 += 16) {
+        for (int n0 = 0; n0 < HN; n0 += 16) {
           uint32_t r[16];
-          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((d - 2) * TN + n0), r);
+          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * TN + h * HN + n0), r);
           tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 16; j++) {
-            const int64_t v = (int64_t)__float2ll_rn(__uint_as_float(r[j]));
-            acc[n0 + j] += sh >= 0 ? (v << sh) : (v >> (-sh));
-          }
+          for (int j = 0; j < 16; j++)
+            acc[n0 + j] += (int64_t)__float2ll_rn(__fmul_rn(__uint_as_float(r[j]), fscale));
         }
       }
       tc_fence_before();
@@ -403,8 +416,8 @@ __global__ void __launch_bounds__(256, 1) k_gemm_sliced(GemmArgs g) {
         // fully unrolled with predicates so acc[] stays in registers
         if (!pr) {
 #pragma unroll
-          for (int n = 0; n < TN; n++) {
-            const int gc = nt * TN + n;
+          for (int n = 0; n < HN; n++) {
+            const int gc = nt * TN + h * HN + n;
             if (gc < Ncols) {
               const int sc = er + geB[gc] - 7 * (S + 1) + drop;
               const double v = ldexp((double)acc[n], sc);
@@ -418,8 +431,8 @@ __global__ void __launch_bounds__(256, 1) k_gemm_sliced(GemmArgs g) {
           if (ri.x >= 0) {
             const int32_t *xrow = g.xmap + pr->xoff + (int64_t)ri.x * pr->nz;
 #pragma unroll
-            for (int n = 0; n < TN; n++) {
-              const int gc = nt * TN + n;
+            for (int n = 0; n < HN; n++) {
+              const int gc = nt * TN + h * HN + n;
               if (gc < Ncols) {
                 const int4 ci = g.colinfo[pr->coloff + gc];
                 if (ci.x >= 0) {
@@ -439,7 +452,7 @@ __global__ void __launch_bounds__(256, 1) k_gemm_sliced(GemmArgs g) {
   if (*(volatile int *)abort_flag && threadIdx.x == 0) atomicExch(g.err, 1);
   if (warp == 2) {
     uint32_t ncols = 32;
-    while (ncols < (uint32_t)(S * TN)) ncols <<= 1;
+    while (ncols < (uint32_t)(nacc * TN)) ncols <<= 1;
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
   }
@@ -484,7 +497,7 @@ extern "C" rix_status rix_gemm_sliced(const double *A, int64_t lda, const double
              nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   const int smem = smem_bytes(S);
   cudaFuncSetAttribute(k_gemm_sliced, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_gemm_sliced<<<dim3(Mpad / TM, Npad / TN), 256, smem, st>>>(g);
+  k_gemm_sliced<<<dim3(Mpad / TM, Npad / TN), NTHR, smem, st>>>(g);
   cudaError_t e = cudaGetLastError();
   int herr = 0;
   cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st);
@@ -540,7 +553,8 @@ __global__ void k_pack_C34(int64_t nrows, const int64_t *rowprob, const Prob *pr
     float d[MAXS];
     digits_of(row[(int64_t)P * nbA * nbB + j], m, S, d);
     const int64_t off = ((int64_t)(r / TM) * nkt + k / KC) * A_TILE + tile_off(r % TM, k % KC);
-    for (int s = 0; s < S; s++) *(__nv_bfloat16 *)(base + s * ptile + off) = __float2bfloat16_rn(d[s]);
+    for (int s = 0; s < S; s++)
+      *(__nv_bfloat16 *)(base + s * ptile + off) = __float2bfloat16_rn(d[s] * slice_scale(s));
   }
 }
 
@@ -573,7 +587,8 @@ __global__ void k_pack_Z34(int64_t c0, int64_t ncols, const int64_t *colprob, co
     float d[MAXS];
     digits_of(zc[(int64_t)k * nbE], m, S, d);
     const int64_t off = ((int64_t)(c / TN) * nkt + k / KC) * B_TILE + tile_off(c % TN, k % KC);
-    for (int s = 0; s < S; s++) *(__nv_bfloat16 *)(base + s * ptile + off) = __float2bfloat16_rn(d[s]);
+    for (int s = 0; s < S; s++)
+      *(__nv_bfloat16 *)(base + s * ptile + off) = __float2bfloat16_rn(d[s] * slice_scale(s));
   }
 }
 
@@ -816,7 +831,7 @@ rix_status rix_mixed_x34(rix_ctx *ctx, int b0, int b1, int64_t zbase, cudaStream
                  ctx->d_mx_eB, nullptr, 0, 0, 0, 0, 0, 0, S, 1, 0, ctx->d_mx_err,
                  ctx->d_mx_tiles + t0, probs, ctx->d_mx_rowinfo, ctx->d_mx_colinfo, ctx->d_mx_xmap, ctx->d_offK,
                  ctx->d_X};
-      k_gemm_sliced<<<(unsigned)(t1 - t0), 256, smem, st>>>(g);
+      k_gemm_sliced<<<(unsigned)(t1 - t0), NTHR, smem, st>>>(g);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

@@ -1,10 +1,12 @@
 """Sliced BF16 tensor-core GEMM (rix_gemm_sliced) against exact and FP64 references.
 
-* Integer operands that fit in the digits and with every digit pair kept
-  (n_slices >= 2 * digits - 1) give the exact product: a bit-exact check of
-  the tensor-core accumulation, the operand layouts and the fixed-point fold.
+* Integer operands of two digits (14 bits) with n_slices = 3 keep every
+  digit pair, and every pair lands in one of the exactly accumulated
+  diagonals, so the product is exact: a bit-exact check of the tensor-core
+  accumulation, the operand layouts and the fixed-point fold.
 * Random FP64 operands: error within a small multiple of 2^(-7 S) of
-  (row scale x column scale x K).
+  (row scale x column scale x K), plus 2^-42 of it for the FP32 rounding of
+  the accumulator that takes the terms 2^-21 and more below the leading one.
 """
 import numpy as np
 import pytest
@@ -15,15 +17,15 @@ pytestmark = pytest.mark.gpu
 from paper_2403_10343_gb300 import rix  # noqa: E402
 
 
-@pytest.mark.parametrize("M,N,K", [(128, 64, 32), (200, 100, 300), (129, 65, 33), (300, 200, 784)])
+@pytest.mark.parametrize("M,N,K", [(128, 64, 32), (200, 100, 300), (129, 65, 33), (300, 200, 784), (130, 300, 1700)])
 def test_exact_integers(M, N, K):
     r = np.random.default_rng(M * 7 + N + K)
-    A = r.integers(-(1 << 20), 1 << 20, size=(M, K)).astype(np.int64)
-    B = r.integers(-(1 << 20), 1 << 20, size=(K, N)).astype(np.int64)
+    A = r.integers(-(1 << 13), 1 << 13, size=(M, K)).astype(np.int64)
+    B = r.integers(-(1 << 13), 1 << 13, size=(K, N)).astype(np.int64)
     ref = A @ B                                   # exact in int64 (< 2^53)
     At = torch.from_numpy(A.astype(np.float64)).cuda()
     Bt = torch.from_numpy(B.astype(np.float64)).cuda()
-    C = rix.gemm_sliced(At, Bt, 5).cpu().numpy()  # 21-bit integers: 3 digits, all pairs kept
+    C = rix.gemm_sliced(At, Bt, 3).cpu().numpy()  # 14-bit integers: 2 digits, all pairs kept
     assert np.array_equal(C, ref.astype(np.float64))
 
 
@@ -37,4 +39,4 @@ def test_random_fp64_accuracy(S):
     C = rix.gemm_sliced(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), S).cpu().numpy()
     scale = np.abs(A).max(axis=1)[:, None] * np.abs(B).max(axis=0)[None, :] * K
     err = np.abs(C - ref) / scale
-    assert err.max() < 8 * 2.0 ** (-7 * S), err.max()
+    assert err.max() < 8 * 2.0 ** (-7 * S) + 2.0 ** (-42), err.max()
