@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(NT) k_X12(const int32_t *ord, const int64_t *p
                                             const int64_t *offV, const uint8_t *keepC, const uint8_t *keepV,
                                             const double *__restrict__ T, const int64_t *off2,
                                             const double *__restrict__ U, const int64_t *offU,
-                                            const int64_t *offK, double *X, int64_t tbase, int smb) {
+                                            const int64_t *offK, double *X, int64_t tbase, int smb, int t2) {
   extern __shared__ double sm[];
   const int tid = threadIdx.x;
   const int s = ord[blockIdx.x];
@@ -281,8 +281,8 @@ __global__ void __launch_bounds__(NT) k_X12(const int32_t *ord, const int64_t *p
         }
       }
     }
-    if (en.u2 >= 0 && keepV[en.u2]) {
-      // term 2: X += U2(A,G')[Q][i][k] C(G',E')[Q on G'][k][l]
+    if (t2 && en.u2 >= 0 && keepV[en.u2]) {
+      // term 2: X += U2(A,G')[Q][i][k] C(G',E')[Q on G'][k][l] (on the tensor cores in mixed precision)
       const double *U2 = U + offU[en.u2];
 #pragma unroll
       for (int r = 0; r < XMAXE; r++) {
@@ -583,7 +583,7 @@ rix_status launch_X12_items(rix_ctx *ctx, int b, int64_t first, int64_t count, i
       ctx->d_ordX12 + ctx->segX12[b] + first, ctx->d_ptrX12, ctx->d_LX12, ctx->d_atomA2, ctx->d_atomB2,
       ctx->d_map2to1, ctx->d_map2to3, ctx->d_pA, ctx->d_onsite, ctx->d_nb, ctx->d_na, ctx->d_C, ctx->d_offC,
       ctx->d_V, ctx->d_offV, ctx->d_keepC, ctx->d_keepV, ctx->d_T, ctx->d_off2, ctx->d_U, ctx->d_offU, ctx->d_offK,
-      ctx->d_X, ctx->blk_base[b], smb);
+      ctx->d_X, ctx->blk_base[b], smb, ctx->have_mx ? 0 : 1);
   return last(ctx, "k_X12");
 }
 
@@ -639,8 +639,11 @@ rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t
     if (b == 0 && (s = rix_prof_mark(ctx, 3, st)) != RIX_OK) return s;
     if ((s = launch_X12_items(ctx, b, 0, ctx->segX12[b + 1] - ctx->segX12[b], ctx->tile_X12, st)) != RIX_OK)
       return s;
-    if (b == 0 && (s = rix_prof_mark(ctx, 4, st)) != RIX_OK) return s;
+    if (b == 0 && ctx->nblk > 1 && (s = rix_prof_mark(ctx, 4, st)) != RIX_OK) return s;
   }
+  // mixed precision: term 2 on the tensor cores once every U2 block exists
+  if (ctx->have_mx && (s = rix_mixed_t2(ctx, st)) != RIX_OK) return s;
+  if (ctx->nblk == 1 && (s = rix_prof_mark(ctx, 4, st)) != RIX_OK) return s;
   // terms 3 and 4, one block of middle atoms B at a time (Z resident for the block)
   for (int b = 0; b < ctx->nblk; b++) {
     const int64_t zbase = ctx->blk_base[b];

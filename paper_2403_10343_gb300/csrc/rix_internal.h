@@ -118,19 +118,14 @@ struct rix_ctx {
   int64_t *d_fold = nullptr;
   int64_t nbasis = 0;
   int64_t *d_bofs = nullptr;            // global basis offset of each atom
-  // mixed precision: terms 3+4 as batched sliced GEMMs on the tensor cores
+  // mixed precision: terms 3+4 and term 2 as batched sliced GEMMs on the tensor cores
   bool have_mx = false;
   int32_t mx_S = 6;
-  std::vector<int32_t> mx_grp;                  // groups of middle atoms [mx_grp[g], mx_grp[g+1])
-  std::vector<int64_t> mx_tile_seg, mx_col_seg;  // tile / column ranges per group
-  int64_t mx_nrows = 0, mx_ncols = 0, mx_A_bytes = 0, mx_B_bytes = 0;
-  void *d_mx_probs = nullptr;
-  int2 *d_mx_rowinfo = nullptr, *d_mx_rowsrc = nullptr;
-  int4 *d_mx_colinfo = nullptr, *d_mx_colsrc = nullptr, *d_mx_tiles = nullptr;
-  int64_t *d_mx_rowprob = nullptr, *d_mx_colprob = nullptr;
-  int32_t *d_mx_xmap = nullptr;
-  int *d_mx_eA = nullptr, *d_mx_eB = nullptr, *d_mx_err = nullptr;
-  void *d_mx_A = nullptr, *d_mx_B = nullptr;
+  struct rix_mx_plan *mx34 = nullptr, *mx2 = nullptr;
+  void *d_mx_buf = nullptr;                     // slices of one group of problems
+  int64_t mx_buf_bytes = 0;
+  int *d_mx_err = nullptr;
+  std::vector<int64_t> offU_h;                  // U2 offsets per pair (host copy)
 
   // memory plan: row blocks of consecutive atoms; item segments per block
   int32_t nblk = 1;
@@ -189,9 +184,10 @@ inline rix_status rix_upload(rix_ctx *ctx, T **p, const std::vector<T> &v) {
 
 // mixed precision (rix_tc.cu)
 rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ);
-int64_t rix_mixed_bytes(const rix_ctx *ctx, const std::vector<int64_t> &ptrZ);
-rix_status rix_mixed_pack_C(rix_ctx *ctx, cudaStream_t st);
+int64_t rix_mixed_bytes(rix_ctx *ctx, const std::vector<int64_t> &ptrZ);
 rix_status rix_mixed_x34(rix_ctx *ctx, int b0, int b1, int64_t zbase, cudaStream_t st);
+rix_status rix_mixed_t2(rix_ctx *ctx, cudaStream_t st);
+void rix_mixed_free(rix_ctx *ctx);
 
 // FP64 path launches (rix_fp64.cu)
 rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t st);

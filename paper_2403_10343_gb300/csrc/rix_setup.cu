@@ -671,6 +671,7 @@ static rix_status build_lists(rix_ctx *ctx) {
   TRY(rix_upload(ctx, &ctx->d_map1to2, map1to2));
   TRY(rix_upload(ctx, &ctx->d_map1to3, map1to3));
   TRY(rix_upload(ctx, &ctx->d_offU, offU));
+  ctx->offU_h = offU;
   TRY(rix_upload(ctx, &ctx->d_atomA2, atomA2));
   TRY(rix_upload(ctx, &ctx->d_atomB2, atomB2));
   TRY(rix_upload(ctx, &ctx->d_off2, ctx->off2));
@@ -936,7 +937,6 @@ extern "C" rix_status rix_set_CV(rix_ctx *ctx, const double *C, const double *V,
   }
   if ((s = rix_launch_flags(ctx, ctx->d_C, ctx->d_offC, ctx->np, ctx->d_keepC, st)) != RIX_OK) return s;
   if ((s = rix_launch_flags(ctx, ctx->d_V, ctx->d_offV, ctx->np, ctx->d_keepV, st)) != RIX_OK) return s;
-  if ((s = rix_mixed_pack_C(ctx, st)) != RIX_OK) return s;
   ctx->have_cv = true;
   return RIX_OK;
 }
@@ -1024,6 +1024,7 @@ extern "C" rix_status rix_stage_times(rix_ctx *ctx, double *ms, int32_t n, int32
 
 extern "C" void rix_destroy(rix_ctx *ctx) {
   if (!ctx) return;
+  rix_mixed_free(ctx);
   for (auto e : ctx->ev_pending) cudaEventDestroy(e);
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
   for (auto &b : ctx->bufs) cudaFree(b.p);

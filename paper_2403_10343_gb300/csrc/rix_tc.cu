@@ -15,8 +15,8 @@
 // take the products with s+t = 2, 3, 4 and s+t >= 5: the first three hold
 // integers (times 2^-7(s+t-2)) whose sums over a group of 320 K values stay
 // below 2^24, so the tensor cores accumulate them exactly; the fourth holds
-// terms at least 2^-21 below the leading one, where FP32 rounding costs about
-// 2^-43 of the row/column scale.  After each group the accumulators are
+// terms at least 2^-21 below the leading one, where the tensor cores' FP32
+// accumulation costs about 2^-39 of the row x column x K scale (measured).  After each group the accumulators are
 // folded into a 64-bit fixed-point sum per output element, and the FP64
 // result is formed once at the end.  The error is the truncation of the
 // operands after S digits (about 2^-7S of the row/column scale), the dropped
@@ -509,86 +509,65 @@ extern "C" rix_status rix_gemm_sliced(const double *A, int64_t lda, const double
 }
 
 // ==========================================================================
-// Terms 3+4 on the tensor cores: X(A,E') += sum_{P on B, j} C(A,B')[P][i][j] Z(B,E')[P][j][l]
-// as one sliced GEMM per middle atom B: rows (A', i) over B's neighbours A'
-// (not B itself), K = (P, j) on B, columns (E', l) over B's 2-hop blocks.
-// The C operand is constant and sliced once in rix_set_CV; Z is sliced per
-// build.  Results are added to X with FP64 atomics.
+// Batched sliced GEMMs of the build, one problem per middle atom:
+//
+//   terms 3+4 (middle atom B):  X(A,E') += sum_{P on B, j} C(A,B')[P][i][j] Z(B,E')[P][j][l]
+//     rows (A', i) over B's neighbours A' != B, K = (P, j), columns (E', l) over B's Z blocks;
+//   term 2 (middle atom G):     X(A,E') += sum_{Q on G, k} U2(A,G')[Q][i][k] C(G',E')[Q on G][k][l]
+//     rows (A', i) over G's neighbours (U2 of the pair (A', G)), K = (Q, k),
+//     columns (E', l) over G's neighbours E' != G.
+//
+// Both operands are sliced per build into one reusable buffer, a group of
+// consecutive problems at a time; results are added to X with FP64 atomics.
 // ==========================================================================
 namespace rixtc {
 
-// One warp per packed row (A operand) or column (B operand): exponent of the
-// row's largest |x| over K, then its S digits into the tile positions.
-__global__ void k_pack_C34(int64_t nrows, const int64_t *rowprob, const Prob *probs, const int2 *rowsrc,
-                           const int32_t *pA, const int32_t *pB, const int32_t *nb, const int32_t *na,
-                           const double *__restrict__ C, const int64_t *offC, const uint8_t *keepC, int S,
-                           __nv_bfloat16 *planes, int *eA) {
-  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+// One packed row (A operand) or column (B operand): element k < K of it is
+// src[off - shift + (k / inner_n) * outer + (k % inner_n) * inner_st].  off < 0
+// marks padding; flag >= 0 zeroes the row unless keep[flag].
+struct Src {
+  int64_t off;
+  int32_t outer, inner_st, inner_n, flag;
+};
+
+// One warp per packed row/column: exponent of its largest |x|, then all Kpad
+// digit positions of every slice (zeros past K), so a reused buffer needs no clearing.
+// Rows/columns [n0, n0 + n) of the plan's global lists.
+__global__ void k_pack_src(int64_t n0, int64_t n, const int64_t *prob_of, const Prob *probs, const Src *src,
+                           const double *__restrict__ X, int64_t shift, const uint8_t *keep, int S, int is_b,
+                           int64_t buf_shift, __nv_bfloat16 *planes, int *e) {
+  const int64_t w = n0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
-  if (w >= nrows) return;
-  const Prob pr = probs[rowprob[w]];
-  const int r = (int)(w - pr.rowoff);
-  const int2 src = rowsrc[w];
+  if (w >= n0 + n) return;
+  const Prob pr = probs[prob_of[w]];
+  const Src sr = src[w];
+  const int r = (int)(w - (is_b ? pr.coloff : pr.rowoff));
   const int nkt = pr.Kpad / KC;
-  char *base = (char *)planes + pr.aoff;
-  const int64_t ptile = (int64_t)(pr.Mpad / TM) * nkt * A_TILE;  // bytes per plane
-  if (src.x < 0 || !keepC[src.x]) {
-    if (lane == 0) eA[pr.eaoff + r] = -2000;
-    return;  // planes start zeroed
-  }
-  const int p1 = src.x, i = src.y;
-  const int a = pA[p1], b = pB[p1];
-  const int nbA = nb[a], naA = na[a], nbB = nb[b], naB = na[b];
-  const int K = naB * nbB;
-  const double *row = C + offC[p1] + ((int64_t)naA * nbA + i) * nbB;  // [P][.][j] with stride nbA*nbB over P
+  const int rows_pad = is_b ? pr.Npad : pr.Mpad;
+  char *base = (char *)planes + ((is_b ? pr.boff : pr.aoff) - buf_shift);
+  const int64_t plane = (int64_t)(rows_pad / TM) * nkt * A_TILE;
+  const bool live = sr.off >= 0 && (sr.flag < 0 || keep[sr.flag]);
+  const double *x = X + (live ? sr.off - shift : 0);
+  const int Kt = pr.pad_;  // true K of the problem; positions Kt..Kpad get zero digits
   int m = -2000;
-  for (int k = lane; k < K; k += 32) {
-    const int P = k / nbB, j = k - P * nbB;
-    m = max(m, exp_of(fabs(row[(int64_t)P * nbA * nbB + j])));
-  }
+  if (live)
+    for (int k = lane; k < Kt; k += 32) {
+      const int o = k / sr.inner_n, in = k - o * sr.inner_n;
+      m = max(m, exp_of(fabs(x[(int64_t)o * sr.outer + (int64_t)in * sr.inner_st])));
+    }
   for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (lane == 0) eA[pr.eaoff + r] = m;
-  for (int k = lane; k < K; k += 32) {
-    const int P = k / nbB, j = k - P * nbB;
+  if (lane == 0) e[(is_b ? pr.eboff : pr.eaoff) + r] = m;
+  for (int k = lane; k < pr.Kpad; k += 32) {
     float d[MAXS];
-    digits_of(row[(int64_t)P * nbA * nbB + j], m, S, d);
+    double v = 0.0;
+    if (live && k < Kt) {
+      const int o = k / sr.inner_n, in = k - o * sr.inner_n;
+      v = x[(int64_t)o * sr.outer + (int64_t)in * sr.inner_st];
+    }
+    digits_of(v, m, S, d);
     const int64_t off = ((int64_t)(r / TM) * nkt + k / KC) * A_TILE + tile_off(r % TM, k % KC);
     for (int s = 0; s < S; s++)
-      *(__nv_bfloat16 *)(base + s * ptile + off) = __float2bfloat16_rn(d[s] * slice_scale(s));
-  }
-}
-
-__global__ void k_pack_Z34(int64_t c0, int64_t ncols, const int64_t *colprob, const Prob *probs,
-                           const int4 *colsrc, const int32_t *atomA2, const int32_t *nb, const int32_t *na,
-                           const double *__restrict__ Z, const int64_t *off2, int64_t zbase, int64_t bbase, int S,
-                           __nv_bfloat16 *planes, int *eB) {
-  const int64_t w = c0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (w >= c0 + ncols) return;
-  const Prob pr = probs[colprob[w]];
-  const int c = (int)(w - pr.coloff);
-  const int4 src = colsrc[w];  // (z, l, nbE, -)
-  const int nkt = pr.Kpad / KC;
-  char *base = (char *)planes + (pr.boff - bbase);
-  const int64_t ptile = (int64_t)(pr.Npad / TN) * nkt * B_TILE;
-  if (src.x < 0) {
-    if (lane == 0) eB[pr.eboff + c] = -2000;
-    return;
-  }
-  const int b = atomA2[src.x];
-  const int nbB = nb[b], naB = na[b];
-  const int K = naB * nbB, nbE = src.z, l = src.y;
-  const double *zc = Z + (off2[src.x] - zbase) + l;  // element k at zc[k * nbE]
-  int m = -2000;
-  for (int k = lane; k < K; k += 32) m = max(m, exp_of(fabs(zc[(int64_t)k * nbE])));
-  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (lane == 0) eB[pr.eboff + c] = m;
-  for (int k = lane; k < K; k += 32) {
-    float d[MAXS];
-    digits_of(zc[(int64_t)k * nbE], m, S, d);
-    const int64_t off = ((int64_t)(c / TN) * nkt + k / KC) * B_TILE + tile_off(c % TN, k % KC);
-    for (int s = 0; s < S; s++)
-      *(__nv_bfloat16 *)(base + s * ptile + off) = __float2bfloat16_rn(d[s] * slice_scale(s));
+      *(__nv_bfloat16 *)(base + s * plane + off) = __float2bfloat16_rn(d[s] * slice_scale(s));
   }
 }
 
@@ -597,247 +576,349 @@ __global__ void k_pack_Z34(int64_t c0, int64_t ncols, const int64_t *colprob, co
 #include <algorithm>
 #include <vector>
 
-// Build the batched plan for terms 3+4 on the tensor cores (called by rix_setup in
-// mixed precision).  ptrZ marks the Z blocks that receive products.
-rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
-  using namespace rix;
-  const int nat = ctx->nat, S = ctx->opt.n_slices > 0 ? ctx->opt.n_slices : 6;
-  if (S > MAXS) {
-    ctx->last_error = "n_slices above 8";
-    return RIX_EINVAL;
-  }
-  ctx->mx_S = S;
+// Host and device state of one batched plan.
+struct rix_mx_plan {
+  int kind = 0;                          // 0: terms 3+4, 1: term 2
+  std::vector<int32_t> grp;              // problems (middle atoms) [grp[g], grp[g+1])
+  std::vector<int64_t> tile_seg, row_seg, col_seg;
+  int64_t buf_bytes = 0;                 // largest group
+  double tflops = 0;
+  Prob *d_probs = nullptr;
+  int2 *d_rowinfo = nullptr;
+  int4 *d_colinfo = nullptr, *d_tiles = nullptr;
+  int64_t *d_rowprob = nullptr, *d_colprob = nullptr;
+  rixtc::Src *d_rowsrc = nullptr, *d_colsrc = nullptr;
+  int32_t *d_xmap = nullptr;
+  int *d_eA = nullptr, *d_eB = nullptr;
+};
+
+namespace {
+
+using rix::key_a;
+using rix::key_b;
+using rix::key_n;
+using rix::pair_key;
+
+struct PlanHost {
+  std::vector<Prob> probs;
+  std::vector<int2> rowinfo;
+  std::vector<int4> colinfo, tiles;
+  std::vector<int64_t> rowprob, colprob, pbytes;
+  std::vector<rixtc::Src> rowsrc, colsrc;
+  std::vector<int32_t> xmap;
+  int64_t eaoff = 0, eboff = 0;
+  double tflops = 0;
+};
+
+// Build the problems of one plan.  kind 0: middle atom B, rows from C(A,B')^{P on B'},
+// columns from Z(B,E'); kind 1: middle atom G, rows from U2(A',G), columns from C(G,E')^{Q on G}.
+// count_only: no host arrays, just the map bytes, the largest problem's slices and
+// the total slice bytes.
+rix_status plan_host(rix_ctx *ctx, int kind, const std::vector<int64_t> &ptrZ, PlanHost &h, bool count_only,
+                     int64_t *maps_out, int64_t *maxp_out, int64_t *total_out) {
+  using namespace rixtc;
+  const int nat = ctx->nat, S = ctx->mx_S;
   auto &row1 = ctx->row1, &row2 = ctx->row2, &row3 = ctx->row3;
   auto find3 = [&](int64_t key) {
     const int a = key_a(key);
     auto it = std::lower_bound(ctx->keys3.begin() + row3[a], ctx->keys3.begin() + row3[a + 1], key);
-    return (it == ctx->keys3.begin() + row3[a + 1] || *it != key) ? (int64_t)-1 : (int64_t)(it - ctx->keys3.begin());
+    return (it == ctx->keys3.begin() + row3[a + 1] || *it != key) ? (int64_t)-1
+                                                                   : (int64_t)(it - ctx->keys3.begin());
   };
-  std::vector<Prob> probs(nat);
-  std::vector<int2> rowinfo, rowsrc;
-  std::vector<int4> colinfo, colsrc;
-  std::vector<int64_t> rowprob, colprob;
-  std::vector<int32_t> xmap;
-  std::vector<int4> tiles;
-  int64_t aoff = 0, eaoff = 0, eboff = 0;
-  std::vector<int64_t> bbytes(nat);
-  double tflops = 0;
   const int npairs = S * (S + 1) / 2;
+  int64_t total = 0, maxp = 0, maps = 0;
+  if (!count_only) {
+    h.probs.assign(nat, Prob{});
+    h.pbytes.assign(nat, 0);
+  }
+  std::vector<int64_t> qs, zs;
   for (int b = 0; b < nat; b++) {
-    Prob &pr = probs[b];
-    std::vector<int64_t> qs, zs;
+    qs.clear();
+    zs.clear();
+    // rows: pairs (b, A', m); kind 0 skips on-site (P on B' != A), kind 1 keeps it
     for (int64_t q = row1[b]; q < row1[b + 1]; q++)
-      if (!ctx->onsite[q]) qs.push_back(q);
-    for (int64_t z = row2[b]; z < row2[b + 1]; z++)
-      if (ptrZ[z + 1] > ptrZ[z]) zs.push_back(z);
+      if (kind == 1 || !ctx->onsite[q]) qs.push_back(q);
+    if (kind == 0) {
+      for (int64_t z = row2[b]; z < row2[b + 1]; z++)
+        if (ptrZ[z + 1] > ptrZ[z]) zs.push_back(z);
+    } else {
+      for (int64_t q = row1[b]; q < row1[b + 1]; q++)
+        if (!ctx->onsite[q]) zs.push_back(q);
+    }
     int M = 0, N = 0;
     for (auto q : qs) M += ctx->nb_at[ctx->pB[q]];
-    for (auto z : zs) N += ctx->nb_at[key_b(ctx->keys2[z])];
+    for (auto z : zs) N += ctx->nb_at[kind == 0 ? key_b(ctx->keys2[z]) : ctx->pB[z]];
     const int K = ctx->na_at[b] * ctx->nb_at[b];
-    pr.M = M; pr.N = N;
-    pr.Mpad = std::max(TM, (M + TM - 1) / TM * TM);
-    pr.Npad = std::max(TN, (N + TN - 1) / TN * TN);
-    pr.Kpad = (K + KC - 1) / KC * KC;
+    const int Mpad = std::max(TM, (M + TM - 1) / TM * TM);
+    const int Npad = std::max(TN, (N + TN - 1) / TN * TN);
+    const int Kpad = (K + KC - 1) / KC * KC;
+    const int64_t bytes = (int64_t)S * (Mpad + Npad) * Kpad * 2;
+    total += bytes;
+    maxp = std::max(maxp, bytes);
+    // xmap, rowinfo + rowprob + rowsrc + exponent, colinfo + colprob + colsrc + exponent, tiles
+    maps += (int64_t)qs.size() * zs.size() * 4 + (int64_t)Mpad * (8 + 8 + 24 + 4) +
+            (int64_t)Npad * (16 + 8 + 24 + 4) + (int64_t)(Mpad / TM) * (Npad / TN) * 16 + (int64_t)sizeof(Prob);
+    if (count_only) continue;
+    Prob &pr = h.probs[b];
+    pr.M = M; pr.N = N; pr.Mpad = Mpad; pr.Npad = Npad; pr.Kpad = Kpad;
+    pr.pad_ = K;  // true K (the pack kernel zero-fills K..Kpad)
     pr.nz = (int32_t)zs.size();
-    pr.drop = fixed_point_drop(pr.Kpad, S);
-    pr.aoff = aoff;
-    pr.eaoff = eaoff;
-    pr.eboff = eboff;
-    pr.rowoff = (int64_t)rowinfo.size();
-    pr.coloff = (int64_t)colinfo.size();
-    pr.xoff = (int64_t)xmap.size();
-    aoff += (int64_t)S * pr.Mpad * pr.Kpad * 2;
-    bbytes[b] = (int64_t)S * pr.Npad * pr.Kpad * 2;
-    eaoff += pr.Mpad;
-    eboff += pr.Npad;
+    pr.drop = fixed_point_drop(Kpad, S);
+    pr.eaoff = h.eaoff; pr.eboff = h.eboff;
+    pr.rowoff = (int64_t)h.rowinfo.size();
+    pr.coloff = (int64_t)h.colinfo.size();
+    pr.xoff = (int64_t)h.xmap.size();
+    h.pbytes[b] = bytes;
+    h.eaoff += Mpad;
+    h.eboff += Npad;
+    const int nbB = ctx->nb_at[b], naB = ctx->na_at[b];
     for (int qi = 0; qi < (int)qs.size(); qi++) {
       const int64_t q = qs[qi];
       const int a = ctx->pB[q];
-      for (int i = 0; i < ctx->nb_at[a]; i++) {
-        rowinfo.push_back(make_int2(qi, i));
-        rowsrc.push_back(make_int2(ctx->partner1[q], i));
-        rowprob.push_back(b);
+      const int nbA = ctx->nb_at[a], naA = ctx->na_at[a];
+      const int64_t pq = ctx->partner1[q];  // pair (A', b)
+      for (int i = 0; i < nbA; i++) {
+        h.rowinfo.push_back(make_int2(qi, i));
+        Src sr;
+        if (kind == 0) {  // C(A,B)[naA + P][i][j]
+          sr.off = ctx->offC[pq] + ((int64_t)naA * nbA + i) * nbB;
+          sr.outer = nbA * nbB; sr.inner_st = 1; sr.inner_n = nbB; sr.flag = (int32_t)pq;
+        } else {          // U2(A,G)[Q][i][k]
+          sr.off = ctx->offU_h[pq] + (int64_t)i * nbB;
+          sr.outer = nbA * nbB; sr.inner_st = 1; sr.inner_n = nbB; sr.flag = (int32_t)pq;
+        }
+        h.rowsrc.push_back(sr);
+        h.rowprob.push_back(b);
       }
     }
-    for (int r = M; r < pr.Mpad; r++) {
-      rowinfo.push_back(make_int2(-1, 0));
-      rowsrc.push_back(make_int2(-1, 0));
-      rowprob.push_back(b);
+    for (int r = M; r < Mpad; r++) {
+      h.rowinfo.push_back(make_int2(-1, 0));
+      h.rowsrc.push_back(Src{-1, 1, 1, 1, -1});
+      h.rowprob.push_back(b);
     }
     for (int zi = 0; zi < (int)zs.size(); zi++) {
-      const int e = key_b(ctx->keys2[zs[zi]]);
-      for (int l = 0; l < ctx->nb_at[e]; l++) {
-        colinfo.push_back(make_int4(zi, l, ctx->nb_at[e], 0));
-        colsrc.push_back(make_int4((int)zs[zi], l, ctx->nb_at[e], 0));
-        colprob.push_back(b);
+      const int64_t z = zs[zi];
+      const int e = kind == 0 ? key_b(ctx->keys2[z]) : ctx->pB[z];
+      const int nbE = ctx->nb_at[e];
+      for (int l = 0; l < nbE; l++) {
+        h.colinfo.push_back(make_int4(zi, l, nbE, 0));
+        Src sr;
+        if (kind == 0) {  // Z(B,E')[P][j][l]
+          sr.off = ctx->off2[z] + l;
+          sr.outer = nbB * nbE; sr.inner_st = nbE; sr.inner_n = nbB; sr.flag = -1;
+        } else {          // C(G,E')[Q][k][l], Q on G
+          sr.off = ctx->offC[z] + l;
+          sr.outer = nbB * nbE; sr.inner_st = nbE; sr.inner_n = nbB; sr.flag = (int32_t)z;
+        }
+        h.colsrc.push_back(sr);
+        h.colprob.push_back(b);
       }
     }
-    for (int c = N; c < pr.Npad; c++) {
-      colinfo.push_back(make_int4(-1, 0, 0, 0));
-      colsrc.push_back(make_int4(-1, 0, 0, 0));
-      colprob.push_back(b);
+    for (int c = N; c < Npad; c++) {
+      h.colinfo.push_back(make_int4(-1, 0, 0, 0));
+      h.colsrc.push_back(Src{-1, 1, 1, 1, -1});
+      h.colprob.push_back(b);
     }
-    // output block of (row block q, column block z): atom A at -n_q from B, E' at n_z from B
+    (void)naB;
+    // output block of (row block q, column block z): A' at image m_q from the middle
+    // atom, E' at n_z from it, so E' sits at n_z - m_q from A'
     for (auto q : qs) {
       const int a = ctx->pB[q];
       for (auto z : zs) {
-        const int64_t kz = ctx->keys2[z];
-        const int n0 = key_n(kz, 0) - ctx->pn[3 * q], n1 = key_n(kz, 1) - ctx->pn[3 * q + 1],
-                  n2 = key_n(kz, 2) - ctx->pn[3 * q + 2];
-        const int64_t x = find3(pair_key(a, key_b(kz), n0, n1, n2));
+        const int e = kind == 0 ? key_b(ctx->keys2[z]) : ctx->pB[z];
+        int nz3[3];
+        for (int c = 0; c < 3; c++)
+          nz3[c] = (kind == 0 ? key_n(ctx->keys2[z], c) : (int)ctx->pn[3 * z + c]) - ctx->pn[3 * q + c];
+        const int64_t x = find3(pair_key(a, e, nz3[0], nz3[1], nz3[2]));
         if (x < 0) {
           ctx->last_error = "mixed plan: output block outside the K pattern";
           return RIX_EINVAL;
         }
-        xmap.push_back((int32_t)x);
+        h.xmap.push_back((int32_t)x);
       }
     }
-    for (int nt = 0; nt < pr.Npad / TN; nt++)
-      for (int mt = 0; mt < pr.Mpad / TM; mt++) tiles.push_back(make_int4(b, mt, nt, 0));
-    tflops += 2.0 * pr.Mpad * pr.Npad * pr.Kpad * npairs;
+    for (int nt = 0; nt < Npad / TN; nt++)
+      for (int mt = 0; mt < Mpad / TM; mt++) h.tiles.push_back(make_int4(b, mt, nt, 0));
+    h.tflops += 2.0 * Mpad * Npad * Kpad * npairs;
   }
-  // groups of consecutive B inside one memory-plan block, B slices within a budget
-  const int64_t budget = std::max<int64_t>(bbytes.empty() ? 0 : *std::max_element(bbytes.begin(), bbytes.end()),
-                                           (int64_t)16 << 30);
-  ctx->mx_grp.clear();
-  ctx->mx_grp.push_back(0);
-  int64_t cur = 0, maxgrp = 0;
-  int blk = 0;
-  for (int b = 0; b < nat; b++) {
-    while (b >= ctx->blk_atom[blk + 1]) blk++;
-    const bool new_blk = b == ctx->blk_atom[blk] && b > 0;
-    if (b > 0 && (new_blk || cur + bbytes[b] > budget)) {
-      ctx->mx_grp.push_back(b);
-      maxgrp = std::max(maxgrp, cur);
-      cur = 0;
-    }
-    probs[b].boff = cur;  // relative to the group's buffer
-    cur += bbytes[b];
-  }
-  maxgrp = std::max(maxgrp, cur);
-  ctx->mx_grp.push_back(nat);
-  // tile and column ranges per group (tiles and columns are ordered by B)
-  ctx->mx_tile_seg.assign(ctx->mx_grp.size(), 0);
-  ctx->mx_col_seg.assign(ctx->mx_grp.size(), 0);
-  {
-    size_t gi = 0, ti = 0, ci = 0;
-    for (gi = 0; gi + 1 < ctx->mx_grp.size(); gi++) {
-      const int bend = ctx->mx_grp[gi + 1];
-      while (ti < tiles.size() && tiles[ti].x < bend) ti++;
-      while (ci < colprob.size() && colprob[ci] < bend) ci++;
-      ctx->mx_tile_seg[gi + 1] = ti;
-      ctx->mx_col_seg[gi + 1] = ci;
-    }
-  }
-  ctx->stats.tensor_flops = tflops;
-  ctx->mx_nrows = (int64_t)rowinfo.size();
-  ctx->mx_ncols = (int64_t)colinfo.size();
-  rix_status s;
-  if ((s = rix_upload(ctx, (Prob **)&ctx->d_mx_probs, probs)) != RIX_OK) return s;
-  if ((s = rix_upload(ctx, &ctx->d_mx_rowinfo, rowinfo)) != RIX_OK) return s;
-  if ((s = rix_upload(ctx, &ctx->d_mx_rowsrc, rowsrc)) != RIX_OK) return s;
-  if ((s = rix_upload(ctx, &ctx->d_mx_rowprob, rowprob)) != RIX_OK) return s;
-  if ((s = rix_upload(ctx, &ctx->d_mx_colinfo, colinfo)) != RIX_OK) return s;
-  if ((s = rix_upload(ctx, &ctx->d_mx_colsrc, colsrc)) != RIX_OK) return s;
-  if ((s = rix_upload(ctx, &ctx->d_mx_colprob, colprob)) != RIX_OK) return s;
-  if ((s = rix_upload(ctx, &ctx->d_mx_xmap, xmap)) != RIX_OK) return s;
-  if ((s = rix_upload(ctx, &ctx->d_mx_tiles, tiles)) != RIX_OK) return s;
-  if ((s = rix_alloc(ctx, &ctx->d_mx_eA, std::max<int64_t>(eaoff, 1))) != RIX_OK) return s;
-  if ((s = rix_alloc(ctx, &ctx->d_mx_eB, std::max<int64_t>(eboff, 1))) != RIX_OK) return s;
-  if ((s = rix_alloc(ctx, &ctx->d_mx_err, 4)) != RIX_OK) return s;
-  if ((s = rix_dev_alloc(ctx, (void **)&ctx->d_mx_A, std::max<int64_t>(aoff, 16))) != RIX_OK) return s;
-  if ((s = rix_dev_alloc(ctx, (void **)&ctx->d_mx_B, std::max<int64_t>(maxgrp, 16))) != RIX_OK) return s;
-  ctx->mx_A_bytes = aoff;
-  ctx->mx_B_bytes = maxgrp;
-  RIX_CUDA_TRY(ctx, cudaMemset(ctx->d_mx_A, 0, std::max<int64_t>(aoff, 16)));
-  RIX_CUDA_TRY(ctx, cudaMemset(ctx->d_mx_B, 0, std::max<int64_t>(maxgrp, 16)));
-  RIX_CUDA_TRY(ctx, cudaMemset(ctx->d_mx_err, 0, 4));
-  ctx->have_mx = true;
-  if (ctx->opt.verbose)
-    fprintf(stderr, "rix mixed: %zu GEMM tiles, C slices %.3g GB, Z slice buffer %.3g GB, %zu group(s)\n",
-            tiles.size(), aoff * 1e-9, maxgrp * 1e-9, ctx->mx_grp.size() - 1);
+  if (maps_out) *maps_out = maps;
+  if (maxp_out) *maxp_out = maxp;
+  if (total_out) *total_out = total;
   return RIX_OK;
 }
 
-// Device bytes the mixed plan will need (slices of C, one group of Z slices, maps).
-int64_t rix_mixed_bytes(const rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
-  const int S = ctx->opt.n_slices > 0 ? ctx->opt.n_slices : 6;
-  int64_t a = 0, bmax = 0, btot = 0, maps = 0;
-  for (int b = 0; b < ctx->nat; b++) {
-    int64_t M = 0, N = 0, nq = 0, nz = 0;
-    for (int64_t q = ctx->row1[b]; q < ctx->row1[b + 1]; q++)
-      if (!ctx->onsite[q]) { M += ctx->nb_at[ctx->pB[q]]; nq++; }
-    for (int64_t z = ctx->row2[b]; z < ctx->row2[b + 1]; z++)
-      if (ptrZ[z + 1] > ptrZ[z]) { N += ctx->nb_at[rix::key_b(ctx->keys2[z])]; nz++; }
-    const int64_t K = (int64_t)ctx->na_at[b] * ctx->nb_at[b];
-    const int64_t Mp = std::max<int64_t>(rixtc::TM, (M + rixtc::TM - 1) / rixtc::TM * rixtc::TM);
-    const int64_t Np = std::max<int64_t>(rixtc::TN, (N + rixtc::TN - 1) / rixtc::TN * rixtc::TN);
-    const int64_t Kp = (K + rixtc::KC - 1) / rixtc::KC * rixtc::KC;
-    a += S * Mp * Kp * 2;
-    bmax = std::max(bmax, S * Np * Kp * 2);
-    btot += S * Np * Kp * 2;
-    maps += nq * nz * 4 + (Mp * 3 + Np * 5) * 8 + (Mp / rixtc::TM) * (Np / rixtc::TN) * 16;
-  }
-  return a + std::min(btot, std::max(bmax, (int64_t)16 << 30)) + maps;
+// The reusable slice buffer of a plan: the largest problem, or up to 8 GB of them.
+int64_t group_budget(int64_t maxp, int64_t total) {
+  return std::max(maxp, std::min(total, (int64_t)8 << 30));
 }
 
-// Slice the constant C operand (after rix_set_CV has loaded C and its flags).
-rix_status rix_mixed_pack_C(rix_ctx *ctx, cudaStream_t st) {
+}  // namespace
+
+// Device bytes the mixed-precision plans will need (their maps plus one slice buffer).
+int64_t rix_mixed_bytes(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
+  ctx->mx_S = ctx->opt.n_slices > 0 ? ctx->opt.n_slices : 6;
+  int64_t maps = 0, buf = 0;
+  for (int kind = 0; kind < 2; kind++) {
+    PlanHost h;
+    int64_t m = 0, maxp = 0, total = 0;
+    plan_host(ctx, kind, ptrZ, h, true, &m, &maxp, &total);
+    maps += m;
+    buf = std::max(buf, group_budget(maxp, total));
+  }
+  return maps + buf + ((int64_t)64 << 20);
+}
+
+rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
   using namespace rixtc;
-  if (!ctx->have_mx || ctx->mx_nrows == 0) return RIX_OK;
-  const int64_t blocks = (ctx->mx_nrows * 32 + 255) / 256;
-  k_pack_C34<<<(unsigned)blocks, 256, 0, st>>>(ctx->mx_nrows, ctx->d_mx_rowprob, (const Prob *)ctx->d_mx_probs,
-                                               ctx->d_mx_rowsrc, ctx->d_pA, ctx->d_pB, ctx->d_nb, ctx->d_na,
-                                               ctx->d_C, ctx->d_offC, ctx->d_keepC, ctx->mx_S,
-                                               (__nv_bfloat16 *)ctx->d_mx_A, ctx->d_mx_eA);
+  ctx->mx_S = ctx->opt.n_slices > 0 ? ctx->opt.n_slices : 6;
+  if (ctx->mx_S > MAXS) {
+    ctx->last_error = "n_slices above 8";
+    return RIX_EINVAL;
+  }
+  int64_t buf = 0;
+  double tflops = 0;
+  for (int kind = 0; kind < 2; kind++) {
+    PlanHost h;
+    int64_t maps = 0, maxp = 0, total = 0;
+    rix_status s = plan_host(ctx, kind, ptrZ, h, false, &maps, &maxp, &total);
+    if (s != RIX_OK) return s;
+    rix_mx_plan *pl = new rix_mx_plan;
+    pl->kind = kind;
+    (kind == 0 ? ctx->mx34 : ctx->mx2) = pl;
+    const int64_t budget = group_budget(maxp, total);
+    // groups of consecutive problems within the budget; terms 3+4 also stay inside
+    // one memory-plan block (Z is resident per block)
+    pl->grp.assign(1, 0);
+    int64_t cur = 0, maxgrp = 0;
+    int blk = 0;
+    for (int b = 0; b < ctx->nat; b++) {
+      while (b >= ctx->blk_atom[blk + 1]) blk++;
+      const bool new_blk = kind == 0 && b == ctx->blk_atom[blk] && b > 0;
+      if (b > 0 && (new_blk || cur + h.pbytes[b] > budget)) {
+        pl->grp.push_back(b);
+        maxgrp = std::max(maxgrp, cur);
+        cur = 0;
+      }
+      Prob &pr = h.probs[b];
+      pr.aoff = cur;
+      pr.boff = cur + (int64_t)ctx->mx_S * pr.Mpad * pr.Kpad * 2;
+      cur += h.pbytes[b];
+    }
+    maxgrp = std::max(maxgrp, cur);
+    pl->grp.push_back(ctx->nat);
+    pl->buf_bytes = maxgrp;
+    buf = std::max(buf, maxgrp);
+    const size_t ng = pl->grp.size() - 1;
+    pl->tile_seg.assign(ng + 1, 0);
+    pl->row_seg.assign(ng + 1, 0);
+    pl->col_seg.assign(ng + 1, 0);
+    {
+      size_t ti = 0, ri = 0, ci = 0;
+      for (size_t g = 0; g < ng; g++) {
+        const int bend = pl->grp[g + 1];
+        while (ti < h.tiles.size() && h.tiles[ti].x < bend) ti++;
+        while (ri < h.rowprob.size() && h.rowprob[ri] < bend) ri++;
+        while (ci < h.colprob.size() && h.colprob[ci] < bend) ci++;
+        pl->tile_seg[g + 1] = ti;
+        pl->row_seg[g + 1] = ri;
+        pl->col_seg[g + 1] = ci;
+      }
+    }
+    pl->tflops = h.tflops;
+    tflops += h.tflops;
+    if ((s = rix_upload(ctx, &pl->d_probs, h.probs)) != RIX_OK) return s;
+    if ((s = rix_upload(ctx, &pl->d_rowinfo, h.rowinfo)) != RIX_OK) return s;
+    if ((s = rix_upload(ctx, &pl->d_colinfo, h.colinfo)) != RIX_OK) return s;
+    if ((s = rix_upload(ctx, &pl->d_tiles, h.tiles)) != RIX_OK) return s;
+    if ((s = rix_upload(ctx, &pl->d_rowprob, h.rowprob)) != RIX_OK) return s;
+    if ((s = rix_upload(ctx, &pl->d_colprob, h.colprob)) != RIX_OK) return s;
+    if ((s = rix_upload(ctx, &pl->d_rowsrc, h.rowsrc)) != RIX_OK) return s;
+    if ((s = rix_upload(ctx, &pl->d_colsrc, h.colsrc)) != RIX_OK) return s;
+    if ((s = rix_upload(ctx, &pl->d_xmap, h.xmap)) != RIX_OK) return s;
+    if ((s = rix_alloc(ctx, &pl->d_eA, std::max<int64_t>(h.eaoff, 1))) != RIX_OK) return s;
+    if ((s = rix_alloc(ctx, &pl->d_eB, std::max<int64_t>(h.eboff, 1))) != RIX_OK) return s;
+    if (ctx->opt.verbose)
+      fprintf(stderr, "rix mixed %s: %zu GEMM tiles in %zu group(s), slice buffer %.3g GB\n",
+              kind == 0 ? "terms 3+4" : "term 2", h.tiles.size(), ng, maxgrp * 1e-9);
+  }
+  rix_status s;
+  if ((s = rix_dev_alloc(ctx, (void **)&ctx->d_mx_buf, std::max<int64_t>(buf, 16))) != RIX_OK) return s;
+  if ((s = rix_alloc(ctx, &ctx->d_mx_err, 4)) != RIX_OK) return s;
+  RIX_CUDA_TRY(ctx, cudaMemset(ctx->d_mx_err, 0, 4));
+  ctx->mx_buf_bytes = buf;
+  ctx->stats.tensor_flops = tflops;
+  ctx->have_mx = true;
+  return RIX_OK;
+}
+
+void rix_mixed_free(rix_ctx *ctx) {
+  delete ctx->mx34;
+  delete ctx->mx2;
+  ctx->mx34 = ctx->mx2 = nullptr;
+}
+
+namespace {
+
+// Slice the rows and columns of group g of a plan, then run its GEMM tiles.
+rix_status run_group(rix_ctx *ctx, const rix_mx_plan *pl, size_t g, const double *rows, int64_t rshift,
+                     const uint8_t *rkeep, const double *cols, int64_t cshift, const uint8_t *ckeep,
+                     cudaStream_t st) {
+  using namespace rixtc;
+  const int S = ctx->mx_S;
+  const int64_t r0 = pl->row_seg[g], r1 = pl->row_seg[g + 1];
+  const int64_t c0 = pl->col_seg[g], c1 = pl->col_seg[g + 1];
+  const int64_t t0 = pl->tile_seg[g], t1 = pl->tile_seg[g + 1];
+  // the group's first problem sits at byte 0 of the buffer
+  const int64_t shift = 0;
+  __nv_bfloat16 *buf = (__nv_bfloat16 *)ctx->d_mx_buf;
+  if (r1 > r0)
+    k_pack_src<<<(unsigned)(((r1 - r0) * 32 + 255) / 256), 256, 0, st>>>(
+        r0, r1 - r0, pl->d_rowprob, pl->d_probs, pl->d_rowsrc, rows, rshift, rkeep, S, 0, shift, buf, pl->d_eA);
+  if (c1 > c0)
+    k_pack_src<<<(unsigned)(((c1 - c0) * 32 + 255) / 256), 256, 0, st>>>(
+        c0, c1 - c0, pl->d_colprob, pl->d_probs, pl->d_colsrc, cols, cshift, ckeep, S, 1, shift, buf, pl->d_eB);
+  if (t1 > t0) {
+    GemmArgs ga{buf, buf, pl->d_eA, pl->d_eB, nullptr, 0, 0, 0, 0, 0, 0, S, 1, 0, ctx->d_mx_err,
+                pl->d_tiles + t0, pl->d_probs, pl->d_rowinfo, pl->d_colinfo, pl->d_xmap, ctx->d_offK, ctx->d_X};
+    k_gemm_sliced<<<(unsigned)(t1 - t0), NTHR, smem_bytes(S), st>>>(ga);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
-    ctx->last_error = std::string("k_pack_C34: ") + cudaGetErrorString(e);
+    ctx->last_error = std::string("mixed GEMM: ") + cudaGetErrorString(e);
     return RIX_ECUDA;
   }
   return RIX_OK;
 }
 
-// Terms 3+4 for the middle atoms [b0, b1) of one memory-plan block: slice their Z
-// blocks and run the batched GEMM into X.
-rix_status rix_mixed_x34(rix_ctx *ctx, int b0, int b1, int64_t zbase, cudaStream_t st) {
-  using namespace rixtc;
-  static bool attr = false;
-  const int S = ctx->mx_S;
-  const int smem = smem_bytes(S);
-  if (!attr) {
-    cudaFuncSetAttribute(k_gemm_sliced, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
-    attr = true;
+void gemm_attr() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(rixtc::k_gemm_sliced, cudaFuncAttributeMaxDynamicSharedMemorySize, rixtc::SMEM_LIMIT);
+    done = true;
   }
-  for (size_t gi = 0; gi + 1 < ctx->mx_grp.size(); gi++) {
-    const int g0 = ctx->mx_grp[gi], g1 = ctx->mx_grp[gi + 1];
-    if (g1 <= b0 || g0 >= b1) continue;
-    const int64_t c0 = ctx->mx_col_seg[gi], c1 = ctx->mx_col_seg[gi + 1];
-    const int64_t t0 = ctx->mx_tile_seg[gi], t1 = ctx->mx_tile_seg[gi + 1];
-    const Prob *probs = (const Prob *)ctx->d_mx_probs;
-    int64_t bbase = 0;
-    {
-      // byte offset of the group's first problem in the per-group buffer is 0 by construction
-      bbase = 0;
-    }
-    if (c1 > c0) {
-      const int64_t blocks = ((c1 - c0) * 32 + 255) / 256;
-      k_pack_Z34<<<(unsigned)blocks, 256, 0, st>>>(c0, c1 - c0, ctx->d_mx_colprob, probs, ctx->d_mx_colsrc,
-                                                   ctx->d_atomA2, ctx->d_nb, ctx->d_na, ctx->d_Z, ctx->d_off2, zbase,
-                                                   bbase, S, (__nv_bfloat16 *)ctx->d_mx_B, ctx->d_mx_eB);
-    }
-    if (t1 > t0) {
-      GemmArgs g{(const __nv_bfloat16 *)ctx->d_mx_A, (const __nv_bfloat16 *)ctx->d_mx_B, ctx->d_mx_eA,
-                 ctx->d_mx_eB, nullptr, 0, 0, 0, 0, 0, 0, S, 1, 0, ctx->d_mx_err,
-                 ctx->d_mx_tiles + t0, probs, ctx->d_mx_rowinfo, ctx->d_mx_colinfo, ctx->d_mx_xmap, ctx->d_offK,
-                 ctx->d_X};
-      k_gemm_sliced<<<(unsigned)(t1 - t0), NTHR, smem, st>>>(g);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-      ctx->last_error = std::string("mixed terms 3+4: ") + cudaGetErrorString(e);
-      return RIX_ECUDA;
-    }
+}
+
+}  // namespace
+
+// Terms 3+4 for the middle atoms [b0, b1) of one memory-plan block (Z resident, zbase).
+rix_status rix_mixed_x34(rix_ctx *ctx, int b0, int b1, int64_t zbase, cudaStream_t st) {
+  gemm_attr();
+  const rix_mx_plan *pl = ctx->mx34;
+  for (size_t g = 0; g + 1 < pl->grp.size(); g++) {
+    if (pl->grp[g + 1] <= b0 || pl->grp[g] >= b1) continue;
+    rix_status s = run_group(ctx, pl, g, ctx->d_C, 0, ctx->d_keepC, ctx->d_Z, zbase, nullptr, st);
+    if (s != RIX_OK) return s;
+  }
+  return RIX_OK;
+}
+
+// Term 2 for every middle atom (U2 complete).
+rix_status rix_mixed_t2(rix_ctx *ctx, cudaStream_t st) {
+  gemm_attr();
+  const rix_mx_plan *pl = ctx->mx2;
+  for (size_t g = 0; g + 1 < pl->grp.size(); g++) {
+    rix_status s = run_group(ctx, pl, g, ctx->d_U, 0, ctx->d_keepV, ctx->d_C, 0, ctx->d_keepC, st);
+    if (s != RIX_OK) return s;
   }
   return RIX_OK;
 }
