@@ -639,27 +639,27 @@ rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t
     if (b == 0 && (s = rix_prof_mark(ctx, 3, st)) != RIX_OK) return s;
     if ((s = launch_X12_items(ctx, b, 0, ctx->segX12[b + 1] - ctx->segX12[b], ctx->tile_X12, st)) != RIX_OK)
       return s;
-    if (b == 0 && ctx->nblk > 1 && (s = rix_prof_mark(ctx, 4, st)) != RIX_OK) return s;
   }
+  if ((s = rix_prof_mark(ctx, 4, st)) != RIX_OK) return s;
   // mixed precision: term 2 on the tensor cores once every U2 block exists
   if (ctx->have_mx && (s = rix_mixed_t2(ctx, st)) != RIX_OK) return s;
-  if (ctx->nblk == 1 && (s = rix_prof_mark(ctx, 4, st)) != RIX_OK) return s;
+  if ((s = rix_prof_mark(ctx, 5, st)) != RIX_OK) return s;
   // terms 3 and 4, one block of middle atoms B at a time (Z resident for the block)
   for (int b = 0; b < ctx->nblk; b++) {
     const int64_t zbase = ctx->blk_base[b];
     if ((s = rix_launch_Z_block(ctx, D, b, st)) != RIX_OK) return s;
-    if (b == 0 && (s = rix_prof_mark(ctx, 5, st)) != RIX_OK) return s;
+    if (b == 0 && (s = rix_prof_mark(ctx, 6, st)) != RIX_OK) return s;
     if (ctx->have_mx) {
       if ((s = rix_mixed_x34(ctx, ctx->blk_atom[b], ctx->blk_atom[b + 1], zbase, st)) != RIX_OK) return s;
     } else if ((s = launch_X34_items(ctx, b, 0, ctx->n_ordX34, ctx->tile_X34, st)) != RIX_OK) {
       return s;
     }
   }
-  if ((s = rix_prof_mark(ctx, 6, st)) != RIX_OK) return s;
+  if ((s = rix_prof_mark(ctx, 7, st)) != RIX_OK) return s;
   k_sym<<<(unsigned)ctx->nk, 128, 0, st>>>(ctx->nk, ctx->d_atomA3, ctx->d_atomB3, ctx->d_partner3, ctx->d_nb,
                                            ctx->d_offK, ctx->d_X, K);
   if ((s = last(ctx, "k_sym")) != RIX_OK) return s;
-  return rix_prof_mark(ctx, 7, st);
+  return rix_prof_mark(ctx, 8, st);
 }
 
 // ------------------------------------------------------------------ autotuner

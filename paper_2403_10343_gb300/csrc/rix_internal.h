@@ -154,7 +154,7 @@ struct rix_ctx {
   int32_t tile_X12 = 12288, tile_Z = 12288, tile_X34 = 12288;
 
   // stage timing (rix_options.profile): 8 events per build, pooled
-  static constexpr int NSTAGE = 7;
+  static constexpr int NSTAGE = 8;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<cudaEvent_t> ev_pending;  // NSTAGE + 1 per recorded build
 };
@@ -188,6 +188,7 @@ int64_t rix_mixed_bytes(rix_ctx *ctx, const std::vector<int64_t> &ptrZ);
 rix_status rix_mixed_x34(rix_ctx *ctx, int b0, int b1, int64_t zbase, cudaStream_t st);
 rix_status rix_mixed_t2(rix_ctx *ctx, cudaStream_t st);
 void rix_mixed_free(rix_ctx *ctx);
+int32_t rix_launch_count(const rix_ctx *ctx);
 
 // FP64 path launches (rix_fp64.cu)
 rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t st);

@@ -414,8 +414,8 @@ static rix_status build_lists(rix_ctx *ctx) {
   // ---------------------------------------------------------------- X12 list (terms 1 and 2)
   std::vector<std::vector<X12Entry>> lx(nat);
   std::vector<std::vector<int64_t>> lxk(nat);
-  double flX12 = 0, flU2 = 0;
-#pragma omp parallel for schedule(dynamic, 1) reduction(+ : flX12)
+  double flX12 = 0, flU2 = 0, flT2 = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : flX12, flT2)
   for (int a = 0; a < nat; a++) {
     struct Rec { int64_t s; int32_t t, p3, u2, t1; };
     std::vector<Rec> r;
@@ -457,7 +457,10 @@ static rix_status build_lists(rix_ctx *ctx) {
       }
       int e = pB[en.p3], g = pA[en.p3];
       if (en.t1) flX12 += 2.0 * NA(e) * NA(a) * NB(a) * NB(g) + 2.0 * NA(e) * NB(a) * NB(g) * NB(e);
-      if (en.u2 >= 0) flX12 += 2.0 * NA(g) * NB(a) * NB(g) * NB(e);
+      if (en.u2 >= 0) {
+        flX12 += 2.0 * NA(g) * NB(a) * NB(g) * NB(e);
+        flT2 += 2.0 * NA(g) * NB(a) * NB(g) * NB(e);
+      }
       out.push_back(en);
       outk.push_back(r[i].s);
       i = j;
@@ -661,6 +664,7 @@ static rix_status build_lists(rix_ctx *ctx) {
   st.flops_stage[0] = flT; st.flops_stage[1] = flU2; st.flops_stage[2] = flX12;
   st.flops_stage[3] = flZ; st.flops_stage[4] = flX34; st.flops_stage[5] = (double)ctx->offK[nk];
   st.flops_fp64 = flT + flU2 + flX12 + flZ + flX34 + st.flops_stage[5];
+  st.flops_term2 = flT2;
   st.min_bytes = 8.0 * (st.c_elems + st.v_elems + st.d_elems) + 8.0 * st.k_elems;
   if (ctx->opt.verbose)
     fprintf(stderr, "rix: %lld pairs, %lld 2-hop, %lld K blocks; lists T %zu X12 %zu Z %zu X34 %zu; %.3g FLOP\n",
@@ -715,7 +719,7 @@ static rix_status build_lists(rix_ctx *ctx) {
     // plan (estimate plus 5 %) and a little slack for allocation granularity
     const int64_t items = (int64_t)(itT.size() + itZ.size() + itU.size()) * (int64_t)sizeof(int2) +
                           (int64_t)(ordX12.size() + ordX34.size()) * (int64_t)sizeof(int32_t);
-    avail -= items + ((int64_t)256 << 20);
+    avail -= items + ((int64_t)1 << 20);
     if (ctx->opt.precision == RIX_MIXED_BF16) avail -= rix_mixed_bytes(ctx, ptrZ) / 20 * 21;
   }
   const int64_t per_buf = std::max<int64_t>(0, avail / 2 / (int64_t)sizeof(double));
@@ -962,6 +966,7 @@ extern "C" rix_status rix_stats(const rix_ctx *ctx, rix_stats_t *out) {
   *out = ctx->stats;
   out->workspace_bytes = (int64_t)ctx->dev_bytes;
   out->n_row_blocks = ctx->nblk;
+  out->launches_build = rix_launch_count(ctx);
   return RIX_OK;
 }
 

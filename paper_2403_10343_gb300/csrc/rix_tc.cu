@@ -826,6 +826,7 @@ rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
     }
     pl->tflops = h.tflops;
     tflops += h.tflops;
+    ctx->stats.tensor_flops_stage[kind] = h.tflops;
     if ((s = rix_upload(ctx, &pl->d_probs, h.probs)) != RIX_OK) return s;
     if ((s = rix_upload(ctx, &pl->d_rowinfo, h.rowinfo)) != RIX_OK) return s;
     if ((s = rix_upload(ctx, &pl->d_colinfo, h.colinfo)) != RIX_OK) return s;
@@ -849,6 +850,18 @@ rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
   ctx->stats.tensor_flops = tflops;
   ctx->have_mx = true;
   return RIX_OK;
+}
+
+// Kernel launches of one rix_build_K: flags, per block T, U2, terms 1+2, Z and
+// terms 3+4 (FP64) or per group two packs and a GEMM (mixed), term 2, symmetrise.
+int32_t rix_launch_count(const rix_ctx *ctx) {
+  int32_t n = 2 + 4 * ctx->nblk;
+  if (ctx->have_mx) {
+    n += 3 * (int32_t)(ctx->mx34->grp.size() - 1) + 3 * (int32_t)(ctx->mx2->grp.size() - 1);
+  } else {
+    n += ctx->nblk;
+  }
+  return n;
 }
 
 void rix_mixed_free(rix_ctx *ctx) {

@@ -44,7 +44,8 @@ class _Stats(ctypes.Structure):
                 ("d_elems", ctypes.c_int64), ("k_elems", ctypes.c_int64), ("flops_fp64", ctypes.c_double),
                 ("flops_stage", ctypes.c_double * 6), ("min_bytes", ctypes.c_double),
                 ("tensor_flops", ctypes.c_double), ("workspace_bytes", ctypes.c_int64),
-                ("n_row_blocks", ctypes.c_int32)]
+                ("n_row_blocks", ctypes.c_int32), ("flops_term2", ctypes.c_double),
+                ("tensor_flops_stage", ctypes.c_double * 2), ("launches_build", ctypes.c_int32)]
 
 
 _lib = None
@@ -203,8 +204,9 @@ def fold_gamma(ctx, K, Kdense, stream=None):
 def stats(ctx):
     s = _Stats()
     _check(load().rix_stats(ctx, ctypes.byref(s)), ctx)
-    d = {f: getattr(s, f) for f, _ in _Stats._fields_ if f != "flops_stage"}
+    d = {f: getattr(s, f) for f, _ in _Stats._fields_ if f not in ("flops_stage", "tensor_flops_stage")}
     d["flops_stage"] = list(s.flops_stage)
+    d["tensor_flops_stage"] = list(s.tensor_flops_stage)
     return d
 
 
@@ -221,7 +223,7 @@ def gemm_sliced(A, B, n_slices, C=None, stream=None):
     return C
 
 
-STAGES = ("flags", "T", "U2", "X12", "Z", "X34", "sym")
+STAGES = ("flags", "T", "U2", "X12", "T2", "Z", "X34", "sym")
 
 
 def stage_times(ctx):
