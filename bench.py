@@ -40,18 +40,18 @@ WORKLOAD_NAMES = {
     3: "perovskite-like periodic, 1536 atoms, nbasis 24911, 8 A images",
     4: "ice-like periodic, 3072 atoms (1024 H2O), nbasis 24576, 8 A images",
 }
-STAGE_KERNEL = {"flags": "k_flags", "T": "k_T", "U2": "k_U2", "X12": "k_X12", "T2": "k_gemm_sliced (term 2)",
-                "Z": "k_Z", "X34": "k_X34", "sym": "k_sym"}
-# in mixed precision the T2 and X34 stages are k_pack_src + k_gemm_sliced; T2 is empty in FP64
-TENSOR_STAGE = {"X34": 0, "T2": 1}
+STAGE_KERNEL = {"flags": "k_flags", "T": "k_T", "U2": "k_U2", "X12": "k_X12",
+                "TC12": "k_gemm_sliced (terms 1 and 2)", "Z": "k_Z", "X34": "k_X34", "sym": "k_sym"}
+# in mixed precision the TC12 and X34 stages are packing kernels + k_gemm_sliced; TC12 is empty in FP64
+TENSOR_STAGE = {"X34": (0,), "TC12": (1, 2)}
 
 
 def stage_flops(stats, st, precision):
     """Algorithmic FP64-equivalent FLOPs of one stage as the path runs it."""
     fs = stats["flops_stage"]
-    t2 = stats["flops_term2"]
+    tc12 = stats["flops_term2"] + stats["flops_term1_tc"]
     mixed = precision == "mixed"
-    return {"T": fs[0], "U2": fs[1], "X12": fs[2] - t2 if mixed else fs[2], "T2": t2 if mixed else 0.0,
+    return {"T": fs[0], "U2": fs[1], "X12": fs[2] - tc12 if mixed else fs[2], "TC12": tc12 if mixed else 0.0,
             "Z": fs[3], "X34": fs[4]}.get(st, 0.0)
 # FP64 peak of GB300 (recipe table: FP64 1.25 TFLOP/s), used when no measured FP64 peak exists.
 FP64_PEAK_TFLOPS_NOMINAL = 1.25
@@ -279,16 +279,16 @@ def roofline(args, precision, r):
     achieved = flops / (stage_ms[dom] * 1e-3) / 1e12
     roof_tc = None
     if precision == "mixed":
-        # terms 3+4 and term 2 on the tensor cores: issued BF16 FLOPs (all slice pairs, padded tiles)
-        ms = stage_ms.get("X34", 0.0) + stage_ms.get("T2", 0.0)
+        # terms 3+4, term 2 and term 1 on the tensor cores: issued BF16 FLOPs (all slice pairs, padded tiles)
+        ms = stage_ms.get("X34", 0.0) + stage_ms.get("TC12", 0.0)
         if ms > 0:
             tc = stats["tensor_flops"] / (ms * 1e-3) / 1e12
             peak_tc = pk_peaks["bf16_tflops_sustained"]
-            roof_tc = {"bound": "tensor", "kernel": "k_gemm_sliced (+ k_pack_src), terms 3+4 and term 2",
+            roof_tc = {"bound": "tensor", "kernel": "k_gemm_sliced (+ packing), terms 1-4",
                        "achieved": tc, "peak": peak_tc, "unit": "TFLOP/s", "frac": tc / peak_tc, "traffic": None,
                        "peak_source": f"bf16 sustained, {src}",
                        "fp64_equivalent_tflops": (stage_flops(stats, "X34", precision) +
-                                                  stage_flops(stats, "T2", precision)) / (ms * 1e-3) / 1e12}
+                                                  stage_flops(stats, "TC12", precision)) / (ms * 1e-3) / 1e12}
     peak = pk_peaks.get("fp64_tflops", FP64_PEAK_TFLOPS_NOMINAL)
     roof = {"bound": "alu", "kernel": STAGE_KERNEL[dom], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": None,
@@ -301,14 +301,14 @@ def stage_roofline(precision, r):
     stats, stage_ms = r["stats"], r["stage_ms"]
     pk_peaks, src = peaks()
     out = {}
-    for st in ("T", "U2", "X12", "T2", "Z", "X34"):
+    for st in ("T", "U2", "X12", "TC12", "Z", "X34"):
         ms = stage_ms.get(st, 0.0)
         fl = stage_flops(stats, st, precision)
         if ms <= 0 or fl <= 0:
             continue
         ach = fl / (ms * 1e-3) / 1e12
         if precision == "mixed" and st in TENSOR_STAGE:
-            tc = stats["tensor_flops_stage"][TENSOR_STAGE[st]] / (ms * 1e-3) / 1e12
+            tc = sum(stats["tensor_flops_stage"][i] for i in TENSOR_STAGE[st]) / (ms * 1e-3) / 1e12
             peak = pk_peaks["bf16_tflops_sustained"]
             out[st] = {"ms": round(ms, 4), "pipe": "tensor (bf16 slices)", "issued_tflops": round(tc, 2),
                        "peak": peak, "frac": round(tc / peak, 4), "fp64_equivalent_tflops": round(ach, 3)}

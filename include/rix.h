@@ -113,8 +113,9 @@ typedef struct {
   int64_t workspace_bytes;         /* library-owned device memory */
   int32_t n_row_blocks;            /* row blocks of the memory plan (1 = all intermediates resident) */
   double flops_term2;              /* the term-2 part of flops_stage[2] (on the tensor cores when mixed) */
-  double tensor_flops_stage[2];    /* mixed mode: tensor FLOPs issued per build for terms 3+4, term 2 */
+  double tensor_flops_stage[3];    /* mixed mode: tensor FLOPs issued per build for terms 3+4, term 2, term 1 */
   int32_t launches_build;          /* kernel launches of one rix_build_K (rix_energy adds 3) */
+  double flops_term1_tc;           /* mixed mode: the term-1 FLOPs (FP64 grouping) moved to the tensor cores */
 } rix_stats_t;
 
 /* Set up a system: copies the host arrays, builds the pair list on the device
@@ -211,10 +212,11 @@ rix_status rix_stats(const rix_ctx *ctx, rix_stats_t *out);
 
 /* Device time of each stage of rix_build_K (ms), summed over the builds since
  * the previous call, and the number of builds: ms[0..7] = screening flags,
- * T, U2, terms 1+2 (FP64 kernel), term 2 on the tensor cores (mixed only),
- * Z, terms 3+4, symmetrise.  With several row blocks the T and U2 entries
- * cover the first block and the terms 1+2 entry the rest of that loop; the Z
- * entry likewise covers the first block.  Needs rix_options.profile = 1
+ * T, U2, terms 1+2 (FP64 kernel), terms 1 and 2 on the tensor cores (mixed
+ * only), Z, terms 3+4, symmetrise.  With several row blocks the T and U2
+ * entries cover the first block and the terms 1+2 entry the rest of that
+ * loop (including the tensor-core term 1 of those blocks); the Z entry
+ * likewise covers the first block.  Needs rix_options.profile = 1
  * (the events are recorded on the build's stream); synchronises on the last
  * recorded event.  EUNSUPPORTED without profiling. */
 rix_status rix_stage_times(rix_ctx *ctx, double *ms, int32_t n, int32_t *n_builds);

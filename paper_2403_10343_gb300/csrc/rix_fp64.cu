@@ -230,7 +230,8 @@ __global__ void __launch_bounds__(NT) k_X12(const int32_t *ord, const int64_t *p
                                             const int64_t *offV, const uint8_t *keepC, const uint8_t *keepV,
                                             const double *__restrict__ T, const int64_t *off2,
                                             const double *__restrict__ U, const int64_t *offU,
-                                            const int64_t *offK, double *X, int64_t tbase, int smb, int t2) {
+                                            const int64_t *offK, double *X, int64_t tbase, int smb, int t2,
+                                            const uint8_t *t1tc) {
   extern __shared__ double sm[];
   const int tid = threadIdx.x;
   const int s = ord[blockIdx.x];
@@ -238,7 +239,8 @@ __global__ void __launch_bounds__(NT) k_X12(const int32_t *ord, const int64_t *p
   const int nbA = nb[a], naA = na[a], nbE = nb[e], naE = na[e];
   const int nel = nbA * nbE;
   const int pae = map2to1[s];
-  const bool has1 = pae >= 0 && keepV[pae];
+  const bool has1 = pae >= 0 && keepV[pae] && !(t1tc && t1tc[e]);  // else term 1 runs on the tensor cores
+  if (!has1 && !t2) return;
   double acc[XMAXE];
 #pragma unroll
   for (int r = 0; r < XMAXE; r++) acc[r] = 0.0;
@@ -583,7 +585,7 @@ rix_status launch_X12_items(rix_ctx *ctx, int b, int64_t first, int64_t count, i
       ctx->d_ordX12 + ctx->segX12[b] + first, ctx->d_ptrX12, ctx->d_LX12, ctx->d_atomA2, ctx->d_atomB2,
       ctx->d_map2to1, ctx->d_map2to3, ctx->d_pA, ctx->d_onsite, ctx->d_nb, ctx->d_na, ctx->d_C, ctx->d_offC,
       ctx->d_V, ctx->d_offV, ctx->d_keepC, ctx->d_keepV, ctx->d_T, ctx->d_off2, ctx->d_U, ctx->d_offU, ctx->d_offK,
-      ctx->d_X, ctx->blk_base[b], smb, ctx->have_mx ? 0 : 1);
+      ctx->d_X, ctx->blk_base[b], smb, ctx->have_mx ? 0 : 1, ctx->have_mx ? ctx->d_t1tc : nullptr);
   return last(ctx, "k_X12");
 }
 
@@ -637,11 +639,15 @@ rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t
       if ((s = last(ctx, "k_U2")) != RIX_OK) return s;
     }
     if (b == 0 && (s = rix_prof_mark(ctx, 3, st)) != RIX_OK) return s;
-    if ((s = launch_X12_items(ctx, b, 0, ctx->segX12[b + 1] - ctx->segX12[b], ctx->tile_X12, st)) != RIX_OK)
+    if ((!ctx->have_mx || ctx->n_t1tc < ctx->nat) &&
+        (s = launch_X12_items(ctx, b, 0, ctx->segX12[b + 1] - ctx->segX12[b], ctx->tile_X12, st)) != RIX_OK)
       return s;
+    // mixed precision, several row blocks: term 1 on the tensor cores while T of the block is resident
+    if (ctx->have_mx && ctx->nblk > 1 && (s = rix_mixed_t1(ctx, b, tbase, st)) != RIX_OK) return s;
   }
   if ((s = rix_prof_mark(ctx, 4, st)) != RIX_OK) return s;
-  // mixed precision: term 2 on the tensor cores once every U2 block exists
+  // mixed precision: term 1 (single block) and term 2 on the tensor cores
+  if (ctx->have_mx && ctx->nblk == 1 && (s = rix_mixed_t1(ctx, 0, ctx->blk_base[0], st)) != RIX_OK) return s;
   if (ctx->have_mx && (s = rix_mixed_t2(ctx, st)) != RIX_OK) return s;
   if ((s = rix_prof_mark(ctx, 5, st)) != RIX_OK) return s;
   // terms 3 and 4, one block of middle atoms B at a time (Z resident for the block)

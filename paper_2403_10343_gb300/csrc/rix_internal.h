@@ -122,6 +122,9 @@ struct rix_ctx {
   bool have_mx = false;
   int32_t mx_S = 6;
   struct rix_mx_plan *mx34 = nullptr, *mx2 = nullptr;
+  struct rix_t1_plan *mx1 = nullptr;           // term 1 for the column atoms where it pays
+  uint8_t *d_t1tc = nullptr;                    // per atom: 1 if its term 1 runs on the tensor cores
+  int n_t1tc = 0;
   void *d_mx_buf = nullptr;                     // slices of one group of problems
   int64_t mx_buf_bytes = 0;
   int *d_mx_err = nullptr;
@@ -189,6 +192,10 @@ rix_status rix_mixed_x34(rix_ctx *ctx, int b0, int b1, int64_t zbase, cudaStream
 rix_status rix_mixed_t2(rix_ctx *ctx, cudaStream_t st);
 void rix_mixed_free(rix_ctx *ctx);
 int32_t rix_launch_count(const rix_ctx *ctx);
+rix_status rix_t1_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out);
+void rix_t1_plan_free(rix_ctx *ctx);
+rix_status rix_mixed_t1(rix_ctx *ctx, int b, int64_t tbase, cudaStream_t st);
+int32_t rix_t1_launches(const rix_ctx *ctx);
 
 // FP64 path launches (rix_fp64.cu)
 rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t st);

@@ -233,6 +233,13 @@ struct Prob {
   int32_t Mpad, Npad, Kpad, M, N, nz, drop, pad_;
 };
 
+// Output row block of a term-1 problem: the K block X(A',E'), the pair (A',E')
+// carrying V(A',E') (offset voff), and nb of A'.
+struct QInfo {
+  int64_t voff;
+  int32_t x, vpair, nbA, pad_;
+};
+
 struct GemmArgs {
   const __nv_bfloat16 *A;  // planes [S][Mpad/128][Kpad/32] tiles
   const __nv_bfloat16 *B;  // planes [S][Npad/64][Kpad/32] tiles
@@ -251,6 +258,13 @@ struct GemmArgs {
   const int32_t *xmap;     // output block index per (q, z)
   const int64_t *offK;
   double *X;               // X[offK[x] + i * nbE + l] += value (atomic)
+  // mode 1 (term 1): rows (q, P nbA + i), columns (l, Q, nbE, naE) l-major;
+  // X(A',E')[i][l] += oscale * sum_Q V(A',E')[P][Q] R[row][col], one atomic per l
+  int mode;
+  const QInfo *qinfo;      // per row block, indexed from Prob::xoff
+  const double *V;
+  const uint8_t *keepV;
+  double oscale;
 };
 
 // Bits the fixed-point sum needs: products below 2^14, at most Kpad of them in
@@ -424,6 +438,35 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
               double *dst = g.C + (int64_t)gr * g.ldc + gc;
               if (g.accumulate) *dst += v;
               else *dst = v;
+            }
+          }
+        } else if (g.mode == 1) {
+          const int2 ri = g.rowinfo[pr->rowoff + gr];
+          if (ri.x >= 0) {
+            const QInfo qi = g.qinfo[pr->xoff + ri.x];
+            if (g.keepV[qi.vpair]) {
+              const int P = ri.y / qi.nbA, i = ri.y - P * qi.nbA;
+              double *xb = g.X + g.offK[qi.x];
+              int lcur = -1, nbE = 0;
+              double part = 0.0;
+#pragma unroll
+              for (int n = 0; n < HN; n++) {
+                const int gc = nt * TN + h * HN + n;
+                if (gc < Ncols) {
+                  const int4 ci = g.colinfo[pr->coloff + gc];  // (l, Q, nbE, naE)
+                  if (ci.x >= 0) {
+                    if (ci.x != lcur) {
+                      if (lcur >= 0) atomicAdd(xb + (int64_t)i * nbE + lcur, g.oscale * part);
+                      lcur = ci.x;
+                      nbE = ci.z;
+                      part = 0.0;
+                    }
+                    const int sc = er + geB[gc] - 7 * (S + 1) + drop;
+                    part = fma(g.V[qi.voff + (int64_t)P * ci.w + ci.y], ldexp((double)acc[n], sc), part);
+                  }
+                }
+              }
+              if (lcur >= 0) atomicAdd(xb + (int64_t)i * nbE + lcur, g.oscale * part);
             }
           }
         } else {
@@ -758,6 +801,11 @@ int64_t group_budget(int64_t maxp, int64_t total) {
 int64_t rix_mixed_bytes(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
   ctx->mx_S = ctx->opt.n_slices > 0 ? ctx->opt.n_slices : 6;
   int64_t maps = 0, buf = 0;
+  {
+    int64_t t1 = 0;
+    rix_t1_plan_build(ctx, true, &t1);  // maps plus its slice buffer
+    maps += t1;
+  }
   for (int kind = 0; kind < 2; kind++) {
     PlanHost h;
     int64_t m = 0, maxp = 0, total = 0;
@@ -843,6 +891,12 @@ rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
               kind == 0 ? "terms 3+4" : "term 2", h.tiles.size(), ng, maxgrp * 1e-9);
   }
   rix_status s;
+  {
+    int64_t t1buf = 0;
+    if ((s = rix_t1_plan_build(ctx, false, &t1buf)) != RIX_OK) return s;
+    buf = std::max(buf, t1buf);
+    tflops += ctx->stats.tensor_flops_stage[2];
+  }
   if ((s = rix_dev_alloc(ctx, (void **)&ctx->d_mx_buf, std::max<int64_t>(buf, 16))) != RIX_OK) return s;
   if ((s = rix_alloc(ctx, &ctx->d_mx_err, 4)) != RIX_OK) return s;
   RIX_CUDA_TRY(ctx, cudaMemset(ctx->d_mx_err, 0, 4));
@@ -855,16 +909,19 @@ rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
 // Kernel launches of one rix_build_K: flags, per block T, U2, terms 1+2, Z and
 // terms 3+4 (FP64) or per group two packs and a GEMM (mixed), term 2, symmetrise.
 int32_t rix_launch_count(const rix_ctx *ctx) {
-  int32_t n = 2 + 4 * ctx->nblk;
+  int32_t n = 2 + 3 * ctx->nblk;  // flags, symmetrise; T, U2, Z per block
   if (ctx->have_mx) {
-    n += 3 * (int32_t)(ctx->mx34->grp.size() - 1) + 3 * (int32_t)(ctx->mx2->grp.size() - 1);
+    n += 3 * (int32_t)(ctx->mx34->grp.size() - 1) + 3 * (int32_t)(ctx->mx2->grp.size() - 1) +
+         rix_t1_launches(ctx);
+    if (ctx->n_t1tc < ctx->nat) n += ctx->nblk;  // k_X12 for the other column atoms
   } else {
-    n += ctx->nblk;
+    n += 2 * ctx->nblk;  // k_X12, k_X34
   }
   return n;
 }
 
 void rix_mixed_free(rix_ctx *ctx) {
+  rix_t1_plan_free(ctx);
   delete ctx->mx34;
   delete ctx->mx2;
   ctx->mx34 = ctx->mx2 = nullptr;
@@ -934,4 +991,407 @@ rix_status rix_mixed_t2(rix_ctx *ctx, cudaStream_t st) {
     if (s != RIX_OK) return s;
   }
   return RIX_OK;
+}
+
+// ==========================================================================
+// Term 1 on the tensor cores, one problem per column atom E (and memory-plan
+// block of row atoms):
+//
+//   R(A',E')[(P,i)][(l,Q)] = sum_{G' near E'} sum_k T(A',G')[P][i][k] C(G',E')[Q on E'][k][l]
+//   X(A',E')[i][l]        += 1/2 sum_{P,Q} V(A',E')[P][Q] R[(P,i)][(l,Q)]
+//
+// rows (A', P, i) over the row atoms A' near E', K = (G', k) over E's
+// neighbours G', columns (l, Q).  The V contraction (a few FLOPs per R
+// element) runs in the GEMM epilogue in FP64.  This costs about nb_E times
+// the FLOPs of the FP64 grouping (which applies V per (A', G', E') triple),
+// so a column atom runs here only when its tensor time is estimated lower.
+// ==========================================================================
+namespace rixtc {
+
+// per-problem segment tables of a term-1 problem
+struct T1Ext {
+  int64_t koff;    // kmap offset (Kpad entries: (g, k, nbG, -), g < 0 past K)
+  int64_t segoff;  // segT offset ([nq][ng]: off2 of T(A'_q, G'_g), -1 if absent)
+  int64_t goff;    // segC / gpair offset ([ng])
+  int32_t nq, ng;
+};
+
+// rows: element (q, P, i ; g, k) = T(A'_q, G'_g)[P][i][k]
+__global__ void k_pack_t1_rows(int64_t n0, int64_t n, const int64_t *prob_of, const Prob *probs,
+                               const T1Ext *ext, const int2 *rowinfo, const QInfo *qinfo, const int4 *kmap,
+                               const int64_t *segT, const double *__restrict__ T, int64_t tbase, int S,
+                               __nv_bfloat16 *planes, int *e) {
+  const int64_t w = n0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= n0 + n) return;
+  const int64_t pi = prob_of[w];
+  const Prob pr = probs[pi];
+  const T1Ext ex = ext[pi];
+  const int r = (int)(w - pr.rowoff);
+  const int2 ri = rowinfo[w];
+  const int nkt = pr.Kpad / KC;
+  char *base = (char *)planes + pr.aoff;
+  const int64_t plane = (int64_t)(pr.Mpad / TM) * nkt * A_TILE;
+  int P = 0, i = 0, nbA = 1;
+  const int64_t *seg = nullptr;
+  if (ri.x >= 0) {
+    nbA = qinfo[pr.xoff + ri.x].nbA;
+    P = ri.y / nbA;
+    i = ri.y - P * nbA;
+    seg = segT + ex.segoff + (int64_t)ri.x * ex.ng;
+  }
+  auto elem = [&](int kk) -> double {
+    if (!seg) return 0.0;
+    const int4 km = kmap[ex.koff + kk];
+    if (km.x < 0) return 0.0;
+    const int64_t so = seg[km.x];
+    if (so < 0) return 0.0;
+    return T[so - tbase + ((int64_t)P * nbA + i) * km.z + km.y];
+  };
+  int m = -2000;
+  for (int k = lane; k < pr.Kpad; k += 32) m = max(m, exp_of(fabs(elem(k))));
+  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) e[pr.eaoff + r] = m;
+  for (int k = lane; k < pr.Kpad; k += 32) {
+    float d[MAXS];
+    digits_of(elem(k), m, S, d);
+    const int64_t off = ((int64_t)(r / TM) * nkt + k / KC) * A_TILE + tile_off(r % TM, k % KC);
+    for (int s = 0; s < S; s++)
+      *(__nv_bfloat16 *)(base + s * plane + off) = __float2bfloat16_rn(d[s] * slice_scale(s));
+  }
+}
+
+// columns: element (l, Q ; g, k) = C(G'_g, E')[Q on E'][k][l]
+__global__ void k_pack_t1_cols(int64_t n0, int64_t n, const int64_t *prob_of, const Prob *probs,
+                               const T1Ext *ext, const int4 *colinfo, const int4 *kmap, const int64_t *segC,
+                               const int32_t *gpair, const uint8_t *keepC, const double *__restrict__ C, int S,
+                               __nv_bfloat16 *planes, int *e) {
+  const int64_t w = n0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= n0 + n) return;
+  const int64_t pi = prob_of[w];
+  const Prob pr = probs[pi];
+  const T1Ext ex = ext[pi];
+  const int c = (int)(w - pr.coloff);
+  const int4 ci = colinfo[w];  // (l, Q, nbE, naE)
+  const int nkt = pr.Kpad / KC;
+  char *base = (char *)planes + pr.boff;
+  const int64_t plane = (int64_t)(pr.Npad / TN) * nkt * B_TILE;
+  auto elem = [&](int kk) -> double {
+    if (ci.x < 0) return 0.0;
+    const int4 km = kmap[ex.koff + kk];
+    if (km.x < 0 || !keepC[gpair[ex.goff + km.x]]) return 0.0;
+    return C[segC[ex.goff + km.x] + ((int64_t)ci.y * km.z + km.y) * ci.z + ci.x];
+  };
+  int m = -2000;
+  for (int k = lane; k < pr.Kpad; k += 32) m = max(m, exp_of(fabs(elem(k))));
+  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) e[pr.eboff + c] = m;
+  for (int k = lane; k < pr.Kpad; k += 32) {
+    float d[MAXS];
+    digits_of(elem(k), m, S, d);
+    const int64_t off = ((int64_t)(c / TN) * nkt + k / KC) * B_TILE + tile_off(c % TN, k % KC);
+    for (int s = 0; s < S; s++)
+      *(__nv_bfloat16 *)(base + s * plane + off) = __float2bfloat16_rn(d[s] * slice_scale(s));
+  }
+}
+
+__global__ void k_flag_set(int n, const int32_t *idx, uint8_t *flags) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) flags[idx[t]] = 1;
+}
+
+}  // namespace rixtc
+
+struct rix_t1_plan {
+  std::vector<int32_t> grp_prob;          // groups of problems [grp_prob[g], grp_prob[g+1])
+  std::vector<int32_t> grp_blk;           // memory-plan block of each group
+  std::vector<int64_t> tile_seg, row_seg, col_seg;
+  int64_t buf_bytes = 0;
+  double tflops = 0, fl64 = 0;            // issued tensor FLOPs, FP64 FLOPs of the same work
+  Prob *d_probs = nullptr;
+  rixtc::T1Ext *d_ext = nullptr;
+  int2 *d_rowinfo = nullptr;
+  int4 *d_colinfo = nullptr, *d_tiles = nullptr, *d_kmap = nullptr;
+  int64_t *d_rowprob = nullptr, *d_colprob = nullptr, *d_segT = nullptr, *d_segC = nullptr;
+  int32_t *d_gpair = nullptr;
+  QInfo *d_qinfo = nullptr;
+  int *d_eA = nullptr, *d_eB = nullptr;
+};
+
+namespace {
+
+// Estimated seconds of a column atom's term 1 on each path (rates seen on GB300:
+// about 1 TFLOP/s for the FP64 kernels, 0.5 PFLOP/s issued for the sliced GEMM).
+constexpr double T1_FP64_RATE = 1.0e12, T1_TC_RATE = 5.0e11;
+
+}  // namespace
+
+// Term-1 plan: decide per column atom, build problems (E, block) for the tensor ones.
+rix_status rix_t1_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) {
+  using namespace rixtc;
+  using rix::key_a;
+  using rix::key_b;
+  using rix::pair_key;
+  const int nat = ctx->nat, S = ctx->mx_S;
+  const int npairs = S * (S + 1) / 2;
+  auto &row1 = ctx->row1, &row2 = ctx->row2, &row3 = ctx->row3;
+  auto find_sorted = [&](const std::vector<int64_t> &keys, int64_t lo, int64_t hi, int64_t key) {
+    auto it = std::lower_bound(keys.begin() + lo, keys.begin() + hi, key);
+    return (it == keys.begin() + hi || *it != key) ? (int64_t)-1 : (int64_t)(it - keys.begin());
+  };
+  // per column atom: FP64 FLOPs of its term 1 and tensor FLOPs of the R form
+  std::vector<uint8_t> use(nat, 0);
+  double fl64_tc = 0;
+  for (int e = 0; e < nat; e++) {
+    const int nbE = ctx->nb_at[e], naE = ctx->na_at[e];
+    int64_t M = 0, K = 0;
+    double f64 = 0;
+    for (int64_t q = row1[e]; q < row1[e + 1]; q++) {
+      const int a = ctx->pB[q];
+      M += (int64_t)ctx->na_at[a] * ctx->nb_at[a];
+      for (int64_t g = row1[e]; g < row1[e + 1]; g++) {
+        const int gg = ctx->pB[g];
+        f64 += 2.0 * naE * ctx->na_at[a] * ctx->nb_at[a] * ctx->nb_at[gg] +
+               2.0 * naE * ctx->nb_at[a] * ctx->nb_at[gg] * nbE;
+      }
+    }
+    for (int64_t g = row1[e]; g < row1[e + 1]; g++) K += ctx->nb_at[ctx->pB[g]];
+    const double Mp = (double)((M + TM - 1) / TM * TM), Np = (double)((naE * nbE + TN - 1) / TN * TN),
+                 Kp = (double)((K + KC - 1) / KC * KC);
+    const double tc = 2.0 * Mp * Np * Kp * npairs;
+    if (tc / T1_TC_RATE < f64 / T1_FP64_RATE) {
+      use[e] = 1;
+      fl64_tc += f64;
+    }
+  }
+  // the memory plan is not known yet when only counting: treat all rows as one block
+  const int nblk = count_only ? 1 : ctx->nblk;
+  std::vector<int32_t> blk_of(nat, 0);
+  if (!count_only)
+    for (int b = 0; b < nblk; b++)
+      for (int a = ctx->blk_atom[b]; a < ctx->blk_atom[b + 1]; a++) blk_of[a] = b;
+  std::vector<Prob> probs;
+  std::vector<T1Ext> ext;
+  std::vector<int2> rowinfo;
+  std::vector<int4> colinfo, tiles, kmap;
+  std::vector<int64_t> rowprob, colprob, segT, segC, pbytes;
+  std::vector<int32_t> gpair, pblk;
+  std::vector<QInfo> qinfo;
+  int64_t eaoff = 0, eboff = 0, maps = 0, maxp = 0, total = 0;
+  double tflops = 0;
+  std::vector<int64_t> qs;
+  for (int b = 0; b < nblk; b++)
+    for (int e = 0; e < nat; e++) {
+      if (!use[e]) continue;
+      qs.clear();
+      for (int64_t q = row1[e]; q < row1[e + 1]; q++)
+        if (blk_of[ctx->pB[q]] == b) qs.push_back(q);
+      if (qs.empty()) continue;
+      const int nbE = ctx->nb_at[e], naE = ctx->na_at[e];
+      const int ng = (int)(row1[e + 1] - row1[e]);
+      int M = 0, K = 0;
+      for (auto q : qs) M += ctx->na_at[ctx->pB[q]] * ctx->nb_at[ctx->pB[q]];
+      for (int64_t g = row1[e]; g < row1[e + 1]; g++) K += ctx->nb_at[ctx->pB[g]];
+      const int N = naE * nbE;
+      const int Mpad = std::max(TM, (M + TM - 1) / TM * TM), Npad = std::max(TN, (N + TN - 1) / TN * TN);
+      const int Kpad = std::max(KC, (K + KC - 1) / KC * KC);
+      const int64_t bytes = (int64_t)S * (Mpad + Npad) * Kpad * 2;
+      total += bytes;
+      maxp = std::max(maxp, bytes);
+      maps += (int64_t)Mpad * (8 + 8 + 4) + (int64_t)Npad * (16 + 8 + 4) + (int64_t)Kpad * 16 +
+              (int64_t)qs.size() * ng * 8 + (int64_t)ng * 12 + (int64_t)qs.size() * 24 +
+              (int64_t)(Mpad / TM) * (Npad / TN) * 16 + (int64_t)(sizeof(Prob) + sizeof(T1Ext));
+      tflops += 2.0 * Mpad * Npad * Kpad * npairs;
+      if (count_only) continue;
+      const int pidx = (int)probs.size();
+      Prob pr{};
+      pr.M = M; pr.N = N; pr.Mpad = Mpad; pr.Npad = Npad; pr.Kpad = Kpad; pr.pad_ = K;
+      pr.nz = ng;
+      pr.drop = fixed_point_drop(Kpad, S);
+      pr.eaoff = eaoff; pr.eboff = eboff;
+      pr.rowoff = (int64_t)rowinfo.size();
+      pr.coloff = (int64_t)colinfo.size();
+      pr.xoff = (int64_t)qinfo.size();
+      eaoff += Mpad;
+      eboff += Npad;
+      T1Ext ex{(int64_t)kmap.size(), (int64_t)segT.size(), (int64_t)segC.size(), (int32_t)qs.size(), ng};
+      // K map and the C segments (G' at image n from E'; C(G',E') is the partner of (E',G',n))
+      for (int64_t g = row1[e]; g < row1[e + 1]; g++) {
+        const int gg = ctx->pB[g];
+        const int64_t p3 = ctx->partner1[g];
+        const int nbG = ctx->nb_at[gg];
+        const int qE0 = ctx->onsite[p3] ? 0 : ctx->na_at[gg];
+        for (int k = 0; k < nbG; k++) kmap.push_back(make_int4((int)(g - row1[e]), k, nbG, 0));
+        segC.push_back(ctx->offC[p3] + (int64_t)qE0 * nbG * nbE);
+        gpair.push_back((int32_t)p3);
+      }
+      for (int k = K; k < Kpad; k++) kmap.push_back(make_int4(-1, 0, 1, 0));
+      for (int qi = 0; qi < (int)qs.size(); qi++) {
+        const int64_t q = qs[qi];
+        const int a = ctx->pB[q];
+        const int nbA = ctx->nb_at[a], naA = ctx->na_at[a];
+        const int64_t vp = ctx->partner1[q];  // pair (A', E', -m)
+        int nm[3];
+        for (int c = 0; c < 3; c++) nm[c] = -(int)ctx->pn[3 * q + c];
+        const int64_t x = find_sorted(ctx->keys3, row3[a], row3[a + 1], pair_key(a, e, nm[0], nm[1], nm[2]));
+        if (x < 0) {
+          ctx->last_error = "term-1 plan: output block outside the K pattern";
+          return RIX_EINVAL;
+        }
+        qinfo.push_back(QInfo{ctx->offV[vp], (int32_t)x, (int32_t)vp, nbA, 0});
+        for (int64_t g = row1[e]; g < row1[e + 1]; g++) {
+          int d[3];
+          for (int c = 0; c < 3; c++) d[c] = (int)ctx->pn[3 * g + c] - (int)ctx->pn[3 * q + c];
+          const int64_t t =
+              find_sorted(ctx->keys2, row2[a], row2[a + 1], pair_key(a, ctx->pB[g], d[0], d[1], d[2]));
+          segT.push_back(t < 0 ? -1 : ctx->off2[t]);
+        }
+        for (int r = 0; r < naA * nbA; r++) {
+          rowinfo.push_back(make_int2(qi, r));
+          rowprob.push_back(pidx);
+        }
+      }
+      for (int r = M; r < Mpad; r++) {
+        rowinfo.push_back(make_int2(-1, 0));
+        rowprob.push_back(pidx);
+      }
+      for (int l = 0; l < nbE; l++)
+        for (int Q = 0; Q < naE; Q++) {
+          colinfo.push_back(make_int4(l, Q, nbE, naE));
+          colprob.push_back(pidx);
+        }
+      for (int c = N; c < Npad; c++) {
+        colinfo.push_back(make_int4(-1, 0, 1, 1));
+        colprob.push_back(pidx);
+      }
+      for (int mt = 0; mt < Mpad / TM; mt++)
+        for (int nt = 0; nt < Npad / TN; nt++) tiles.push_back(make_int4(pidx, mt, nt, 0));
+      probs.push_back(pr);
+      ext.push_back(ex);
+      pbytes.push_back(bytes);
+      pblk.push_back(b);
+    }
+  if (count_only) {
+    if (bytes_out) *bytes_out = maps + (total ? std::max(maxp, std::min(total, (int64_t)8 << 30)) : 0);
+    return RIX_OK;
+  }
+  rix_t1_plan *pl = new rix_t1_plan;
+  ctx->mx1 = pl;
+  pl->fl64 = fl64_tc;
+  pl->tflops = tflops;
+  const int64_t budget = std::max(maxp, std::min(total, (int64_t)8 << 30));
+  pl->grp_prob.assign(1, 0);
+  int64_t cur = 0, maxgrp = 0;
+  for (int p = 0; p < (int)probs.size(); p++) {
+    if (p > 0 && (pblk[p] != pblk[p - 1] || cur + pbytes[p] > budget)) {
+      pl->grp_prob.push_back(p);
+      maxgrp = std::max(maxgrp, cur);
+      cur = 0;
+    }
+    probs[p].aoff = cur;
+    probs[p].boff = cur + (int64_t)S * probs[p].Mpad * probs[p].Kpad * 2;
+    cur += pbytes[p];
+  }
+  maxgrp = std::max(maxgrp, cur);
+  pl->grp_prob.push_back((int)probs.size());
+  pl->buf_bytes = probs.empty() ? 0 : maxgrp;
+  const size_t ng = pl->grp_prob.size() - 1;
+  pl->grp_blk.assign(ng, 0);
+  pl->tile_seg.assign(ng + 1, 0);
+  pl->row_seg.assign(ng + 1, 0);
+  pl->col_seg.assign(ng + 1, 0);
+  {
+    size_t ti = 0, ri = 0, ci = 0;
+    for (size_t g = 0; g < ng; g++) {
+      const int pend = pl->grp_prob[g + 1];
+      if (pl->grp_prob[g] < (int)pblk.size()) pl->grp_blk[g] = pblk[pl->grp_prob[g]];
+      while (ti < tiles.size() && tiles[ti].x < pend) ti++;
+      while (ri < rowprob.size() && rowprob[ri] < pend) ri++;
+      while (ci < colprob.size() && colprob[ci] < pend) ci++;
+      pl->tile_seg[g + 1] = ti;
+      pl->row_seg[g + 1] = ri;
+      pl->col_seg[g + 1] = ci;
+    }
+  }
+  rix_status s;
+  if ((s = rix_upload(ctx, &pl->d_probs, probs)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &pl->d_ext, ext)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &pl->d_rowinfo, rowinfo)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &pl->d_colinfo, colinfo)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &pl->d_tiles, tiles)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &pl->d_kmap, kmap)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &pl->d_rowprob, rowprob)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &pl->d_colprob, colprob)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &pl->d_segT, segT)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &pl->d_segC, segC)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &pl->d_gpair, gpair)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &pl->d_qinfo, qinfo)) != RIX_OK) return s;
+  if ((s = rix_alloc(ctx, &pl->d_eA, std::max<int64_t>(eaoff, 1))) != RIX_OK) return s;
+  if ((s = rix_alloc(ctx, &pl->d_eB, std::max<int64_t>(eboff, 1))) != RIX_OK) return s;
+  // column atoms whose term 1 runs here: k_X12 skips them
+  std::vector<int32_t> on;
+  for (int e = 0; e < nat; e++)
+    if (use[e]) on.push_back(e);
+  if ((s = rix_alloc(ctx, &ctx->d_t1tc, nat)) != RIX_OK) return s;
+  RIX_CUDA_TRY(ctx, cudaMemset(ctx->d_t1tc, 0, nat));
+  if (!on.empty()) {
+    int32_t *d_on = nullptr;
+    if ((s = rix_upload(ctx, &d_on, on)) != RIX_OK) return s;
+    rixtc::k_flag_set<<<(unsigned)((on.size() + 255) / 256), 256>>>((int)on.size(), d_on, ctx->d_t1tc);
+    RIX_CUDA_TRY(ctx, cudaDeviceSynchronize());
+  }
+  ctx->n_t1tc = (int)on.size();
+  ctx->stats.tensor_flops_stage[2] = tflops;
+  ctx->stats.flops_term1_tc = fl64_tc;
+  if (ctx->opt.verbose)
+    fprintf(stderr, "rix mixed term 1: %zu of %d column atoms on the tensor cores, %zu GEMM tiles, %zu group(s), "
+                    "slice buffer %.3g GB\n", on.size(), nat, tiles.size(), ng, maxgrp * 1e-9);
+  if (bytes_out) *bytes_out = maxgrp;
+  return RIX_OK;
+}
+
+void rix_t1_plan_free(rix_ctx *ctx) {
+  delete ctx->mx1;
+  ctx->mx1 = nullptr;
+}
+
+// Term 1 for the problems of memory-plan block b (T of block b resident at tbase).
+rix_status rix_mixed_t1(rix_ctx *ctx, int b, int64_t tbase, cudaStream_t st) {
+  using namespace rixtc;
+  const rix_t1_plan *pl = ctx->mx1;
+  if (!pl) return RIX_OK;
+  gemm_attr();
+  const int S = ctx->mx_S;
+  __nv_bfloat16 *buf = (__nv_bfloat16 *)ctx->d_mx_buf;
+  for (size_t g = 0; g + 1 < pl->grp_prob.size(); g++) {
+    if (pl->grp_blk[g] != b || pl->grp_prob[g + 1] == pl->grp_prob[g]) continue;
+    const int64_t r0 = pl->row_seg[g], r1 = pl->row_seg[g + 1];
+    const int64_t c0 = pl->col_seg[g], c1 = pl->col_seg[g + 1];
+    const int64_t t0 = pl->tile_seg[g], t1 = pl->tile_seg[g + 1];
+    if (r1 > r0)
+      k_pack_t1_rows<<<(unsigned)(((r1 - r0) * 32 + 255) / 256), 256, 0, st>>>(
+          r0, r1 - r0, pl->d_rowprob, pl->d_probs, pl->d_ext, pl->d_rowinfo, pl->d_qinfo, pl->d_kmap, pl->d_segT,
+          ctx->d_T, tbase, S, buf, pl->d_eA);
+    if (c1 > c0)
+      k_pack_t1_cols<<<(unsigned)(((c1 - c0) * 32 + 255) / 256), 256, 0, st>>>(
+          c0, c1 - c0, pl->d_colprob, pl->d_probs, pl->d_ext, pl->d_colinfo, pl->d_kmap, pl->d_segC,
+          pl->d_gpair, ctx->d_keepC, ctx->d_C, S, buf, pl->d_eB);
+    if (t1 > t0) {
+      GemmArgs ga{buf, buf, pl->d_eA, pl->d_eB, nullptr, 0, 0, 0, 0, 0, 0, S, 1, 0, ctx->d_mx_err,
+                  pl->d_tiles + t0, pl->d_probs, pl->d_rowinfo, pl->d_colinfo, nullptr, ctx->d_offK, ctx->d_X,
+                  1, pl->d_qinfo, ctx->d_V, ctx->d_keepV, 0.5};
+      k_gemm_sliced<<<(unsigned)(t1 - t0), NTHR, smem_bytes(S), st>>>(ga);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      ctx->last_error = std::string("mixed term 1: ") + cudaGetErrorString(e);
+      return RIX_ECUDA;
+    }
+  }
+  return RIX_OK;
+}
+
+int32_t rix_t1_launches(const rix_ctx *ctx) {
+  return ctx->mx1 ? 3 * (int32_t)(ctx->mx1->grp_prob.size() - 1) : 0;
 }

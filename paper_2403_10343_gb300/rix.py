@@ -45,7 +45,8 @@ class _Stats(ctypes.Structure):
                 ("flops_stage", ctypes.c_double * 6), ("min_bytes", ctypes.c_double),
                 ("tensor_flops", ctypes.c_double), ("workspace_bytes", ctypes.c_int64),
                 ("n_row_blocks", ctypes.c_int32), ("flops_term2", ctypes.c_double),
-                ("tensor_flops_stage", ctypes.c_double * 2), ("launches_build", ctypes.c_int32)]
+                ("tensor_flops_stage", ctypes.c_double * 3), ("launches_build", ctypes.c_int32),
+                ("flops_term1_tc", ctypes.c_double)]
 
 
 _lib = None
@@ -223,7 +224,7 @@ def gemm_sliced(A, B, n_slices, C=None, stream=None):
     return C
 
 
-STAGES = ("flags", "T", "U2", "X12", "T2", "Z", "X34", "sym")
+STAGES = ("flags", "T", "U2", "X12", "TC12", "Z", "X34", "sym")
 
 
 def stage_times(ctx):
