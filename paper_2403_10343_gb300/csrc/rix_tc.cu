@@ -1123,7 +1123,7 @@ namespace {
 
 // Estimated seconds of a column atom's term 1 on each path (rates seen on GB300:
 // about 1 TFLOP/s for the FP64 kernels, 0.5 PFLOP/s issued for the sliced GEMM).
-constexpr double T1_FP64_RATE = 1.0e12, T1_TC_RATE = 5.0e11;
+constexpr double T1_FP64_RATE = 1.0e12, T1_TC_RATE = 5.0e14;
 
 }  // namespace
 
