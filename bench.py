@@ -42,8 +42,9 @@ WORKLOAD_NAMES = {
 }
 STAGE_KERNEL = {"flags": "k_flags", "T": "k_T", "U2": "k_U2", "X12": "k_X12",
                 "TC12": "k_gemm_sliced (terms 1 and 2)", "Z": "k_Z", "X34": "k_X34", "sym": "k_sym"}
-# in mixed precision the TC12 and X34 stages are packing kernels + k_gemm_sliced; TC12 is empty in FP64
-TENSOR_STAGE = {"X34": (0,), "TC12": (1, 2)}
+# in mixed precision the TC12 and X34 stages are packing kernels + k_gemm_sliced (TC12 is empty in FP64),
+# and the Z stage is k_Z for some middle atoms plus k_gemm_sliced for the others
+TENSOR_STAGE = {"X34": (0,), "TC12": (1, 2), "Z": (3,)}
 
 
 def stage_flops(stats, st, precision):
@@ -53,6 +54,18 @@ def stage_flops(stats, st, precision):
     mixed = precision == "mixed"
     return {"T": fs[0], "U2": fs[1], "X12": fs[2] - tc12 if mixed else fs[2], "TC12": tc12 if mixed else 0.0,
             "Z": fs[3], "X34": fs[4]}.get(st, 0.0)
+
+
+def stage_fp64_share(stats, st, precision):
+    """Fraction of a stage's algorithmic FLOPs left on the FP64 pipe."""
+    if precision != "mixed":
+        return 1.0
+    if st in ("X34", "TC12"):
+        return 0.0
+    if st == "Z":
+        fz = stats["flops_stage"][3]
+        return (fz - stats["flops_z_tc"]) / fz if fz > 0 else 0.0
+    return 1.0
 # FP64 peak of GB300 (recipe table: FP64 1.25 TFLOP/s), used when no measured FP64 peak exists.
 FP64_PEAK_TFLOPS_NOMINAL = 1.25
 
@@ -273,22 +286,26 @@ def measure(args, s, pk, precision, dev, world, rank, local):
 def roofline(args, precision, r):
     stats, stage_ms = r["stats"], r["stage_ms"]
     pk_peaks, src = peaks()
-    fp64_stages = [k for k in ("T", "U2", "X12", "Z", "X34") if not (precision == "mixed" and k in TENSOR_STAGE)]
+    fp64_stages = [k for k in ("T", "U2", "X12", "Z", "X34") if stage_fp64_share(stats, k, precision) >= 0.5]
     dom = max(fp64_stages, key=lambda k: stage_ms.get(k, 0.0))
-    flops = stage_flops(stats, dom, precision)
+    flops = stage_flops(stats, dom, precision) * stage_fp64_share(stats, dom, precision)
     achieved = flops / (stage_ms[dom] * 1e-3) / 1e12
     roof_tc = None
     if precision == "mixed":
-        # terms 3+4, term 2 and term 1 on the tensor cores: issued BF16 FLOPs (all slice pairs, padded tiles)
-        ms = stage_ms.get("X34", 0.0) + stage_ms.get("TC12", 0.0)
+        # terms 1-4 and Z on the tensor cores: issued BF16 FLOPs (all slice pairs, padded tiles)
+        ms = sum(stage_ms.get(k, 0.0) for k in TENSOR_STAGE if stage_fp64_share(stats, k, precision) < 0.5)
         if ms > 0:
             tc = stats["tensor_flops"] / (ms * 1e-3) / 1e12
             peak_tc = pk_peaks["bf16_tflops_sustained"]
-            roof_tc = {"bound": "tensor", "kernel": "k_gemm_sliced (+ packing), terms 1-4",
+            roof_tc = {"bound": "tensor", "kernel": "k_gemm_sliced (+ packing): terms 1-4 and Z",
                        "achieved": tc, "peak": peak_tc, "unit": "TFLOP/s", "frac": tc / peak_tc, "traffic": None,
                        "peak_source": f"bf16 sustained, {src}",
                        "fp64_equivalent_tflops": (stage_flops(stats, "X34", precision) +
-                                                  stage_flops(stats, "TC12", precision)) / (ms * 1e-3) / 1e12}
+                                                  stage_flops(stats, "TC12", precision) +
+                                                  stats["flops_z_tc"]) / (ms * 1e-3) / 1e12}
+            # the headline bound is the stage that takes longest: FP64 kernel or tensor-core stages
+            if ms > stage_ms.get(dom, 0.0):
+                return roof_tc, roof_tc
     peak = pk_peaks.get("fp64_tflops", FP64_PEAK_TFLOPS_NOMINAL)
     roof = {"bound": "alu", "kernel": STAGE_KERNEL[dom], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": None,
@@ -307,7 +324,7 @@ def stage_roofline(precision, r):
         if ms <= 0 or fl <= 0:
             continue
         ach = fl / (ms * 1e-3) / 1e12
-        if precision == "mixed" and st in TENSOR_STAGE:
+        if precision == "mixed" and st in TENSOR_STAGE and stage_fp64_share(stats, st, precision) < 0.5:
             tc = sum(stats["tensor_flops_stage"][i] for i in TENSOR_STAGE[st]) / (ms * 1e-3) / 1e12
             peak = pk_peaks["bf16_tflops_sustained"]
             out[st] = {"ms": round(ms, 4), "pipe": "tensor (bf16 slices)", "issued_tflops": round(tc, 2),

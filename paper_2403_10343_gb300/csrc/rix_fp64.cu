@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(NT) k_Z(const int2 *items, const int64_t *ptrZ
                                           const double *__restrict__ V, const int64_t *offV,
                                           const double *__restrict__ D, const int64_t *offD,
                                           const uint8_t *keepC, const uint8_t *keepV, const uint8_t *keepD,
-                                          double *Z, int64_t zbase, int smb) {
+                                          double *Z, int64_t zbase, int smb, const uint8_t *ztc) {
   extern __shared__ double sm[];
   const int tid = threadIdx.x;
   const int2 it = items[blockIdx.x];
@@ -338,6 +338,7 @@ __global__ void __launch_bounds__(NT) k_Z(const int2 *items, const int64_t *ptrZ
     const int2 en = LZ[x];
     if (!keepD[en.x] || !keepV[en.x] || !keepC[en.y]) continue;
     const int g = pB[en.x];
+    if (ztc && ztc[g]) continue;  // this middle atom's part runs on the tensor cores
     const int nbG = nb[g], naG = na[g];
     const double *Dbg = D + offD[en.x];
     const double *Vbg = V + offV[en.x];
@@ -573,7 +574,7 @@ rix_status launch_Z_items(rix_ctx *ctx, const double *D, int b, int64_t first, i
                                             ctx->d_atomA2, ctx->d_atomB2, ctx->d_off2, ctx->d_pB, ctx->d_nb,
                                             ctx->d_na, ctx->d_C, ctx->d_offC, ctx->d_V, ctx->d_offV, D, ctx->d_offD,
                                             ctx->d_keepC, ctx->d_keepV, ctx->d_keepD, ctx->d_Z, ctx->blk_base[b],
-                                            smb);
+                                            smb, ctx->have_mx ? ctx->d_ztc : nullptr);
   return last(ctx, "k_Z");
 }
 
@@ -614,9 +615,12 @@ rix_status rix_launch_T_block(rix_ctx *ctx, const double *D, int b, cudaStream_t
   return last(ctx, "k_T");
 }
 
-// Z(B;E') for the middle atoms of block b (Z buffer holds that block).
+// Z(B;E') for the middle atoms of block b (Z buffer holds that block): the FP64
+// kernel stores its part, then in mixed precision the tensor cores add theirs.
 rix_status rix_launch_Z_block(rix_ctx *ctx, const double *D, int b, cudaStream_t st) {
-  return launch_Z_items(ctx, D, b, 0, ctx->segZ[b + 1] - ctx->segZ[b], ctx->tile_Z, st);
+  rix_status s = launch_Z_items(ctx, D, b, 0, ctx->segZ[b + 1] - ctx->segZ[b], ctx->tile_Z, st);
+  if (s == RIX_OK && ctx->have_mx) s = rix_mixed_z(ctx, b, ctx->blk_base[b], D, st);
+  return s;
 }
 
 rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t st) {
@@ -656,7 +660,7 @@ rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t
     if ((s = rix_launch_Z_block(ctx, D, b, st)) != RIX_OK) return s;
     if (b == 0 && (s = rix_prof_mark(ctx, 6, st)) != RIX_OK) return s;
     if (ctx->have_mx) {
-      if ((s = rix_mixed_x34(ctx, ctx->blk_atom[b], ctx->blk_atom[b + 1], zbase, st)) != RIX_OK) return s;
+      if ((s = rix_mixed_x34(ctx, b, zbase, st)) != RIX_OK) return s;
     } else if ((s = launch_X34_items(ctx, b, 0, ctx->n_ordX34, ctx->tile_X34, st)) != RIX_OK) {
       return s;
     }

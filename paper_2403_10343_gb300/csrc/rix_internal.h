@@ -123,6 +123,9 @@ struct rix_ctx {
   int32_t mx_S = 6;
   struct rix_mx_plan *mx34 = nullptr, *mx2 = nullptr;
   struct rix_t1_plan *mx1 = nullptr;           // term 1 for the column atoms where it pays
+  struct rix_mx_plan *mxz = nullptr;            // term-4 intermediate for the middle atoms where it pays
+  uint8_t *d_ztc = nullptr;                     // per atom: 1 if Z's terms through it run on the tensor cores
+  int n_ztc = 0;
   uint8_t *d_t1tc = nullptr;                    // per atom: 1 if its term 1 runs on the tensor cores
   int n_t1tc = 0;
   void *d_mx_buf = nullptr;                     // slices of one group of problems
@@ -188,7 +191,8 @@ inline rix_status rix_upload(rix_ctx *ctx, T **p, const std::vector<T> &v) {
 // mixed precision (rix_tc.cu)
 rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ);
 int64_t rix_mixed_bytes(rix_ctx *ctx, const std::vector<int64_t> &ptrZ);
-rix_status rix_mixed_x34(rix_ctx *ctx, int b0, int b1, int64_t zbase, cudaStream_t st);
+rix_status rix_mixed_x34(rix_ctx *ctx, int blk, int64_t zbase, cudaStream_t st);
+rix_status rix_mixed_z(rix_ctx *ctx, int blk, int64_t zbase, const double *D, cudaStream_t st);
 rix_status rix_mixed_t2(rix_ctx *ctx, cudaStream_t st);
 void rix_mixed_free(rix_ctx *ctx);
 int32_t rix_launch_count(const rix_ctx *ctx);

@@ -264,7 +264,8 @@ struct GemmArgs {
   const QInfo *qinfo;      // per row block, indexed from Prob::xoff
   const double *V;
   const uint8_t *keepV;
-  double oscale;
+  double oscale;           // scale of the added values (modes 0 and 1)
+  int64_t xshift;          // mode 0: X + offK[x] - xshift is the output block
 };
 
 // Bits the fixed-point sum needs: products below 2^14, at most Kpad of them in
@@ -481,7 +482,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
                 if (ci.x >= 0) {
                   const int sc = er + geB[gc] - 7 * (S + 1) + drop;
                   const double v = ldexp((double)acc[n], sc);
-                  atomicAdd(g.X + g.offK[xrow[ci.x]] + (int64_t)ri.y * ci.z + ci.y, v);
+                  atomicAdd(g.X + (g.offK[xrow[ci.x]] - g.xshift) + (int64_t)ri.y * ci.z + ci.y, g.oscale * v);
                 }
               }
             }
@@ -552,33 +553,42 @@ extern "C" rix_status rix_gemm_sliced(const double *A, int64_t lda, const double
 }
 
 // ==========================================================================
-// Batched sliced GEMMs of the build, one problem per middle atom:
+// Batched sliced GEMMs of the build, one problem per middle atom (and, where
+// the intermediate is resident per memory-plan block, per block of rows):
 //
 //   terms 3+4 (middle atom B):  X(A,E') += sum_{P on B, j} C(A,B')[P][i][j] Z(B,E')[P][j][l]
 //     rows (A', i) over B's neighbours A' != B, K = (P, j), columns (E', l) over B's Z blocks;
 //   term 2 (middle atom G):     X(A,E') += sum_{Q on G, k} U2(A,G')[Q][i][k] C(G',E')[Q on G][k][l]
 //     rows (A', i) over G's neighbours (U2 of the pair (A', G)), K = (Q, k),
-//     columns (E', l) over G's neighbours E' != G.
+//     columns (E', l) over G's neighbours E' != G;
+//   term 4 intermediate (middle atom G, rows of one block):
+//     Z(B,E')[P][j][l] += 1/2 sum_{Q on G, k} V(B,G')[P][Q] D(B,G')[j][k] C(G',E')[Q on G][k][l]
+//     rows (B, P, j), K = (Q, k), columns (E', l) as for term 2.  The row
+//     operand is the Kronecker product of the V and D blocks, formed while
+//     slicing; this costs about nb_B times the FLOPs of the FP64 grouping, so a
+//     middle atom runs here only where its estimated tensor time is lower.
 //
 // Both operands are sliced per build into one reusable buffer, a group of
-// consecutive problems at a time; results are added to X with FP64 atomics.
+// consecutive problems at a time; results are added with FP64 atomics.
 // ==========================================================================
 namespace rixtc {
 
 // One packed row (A operand) or column (B operand): element k < K of it is
-// src[off - shift + (k / inner_n) * outer + (k % inner_n) * inner_st].  off < 0
-// marks padding; flag >= 0 zeroes the row unless keep[flag].
+//   X[off - shift + o * outer + in * inner_st] * (off2 < 0 ? 1 : X2[off2 + in]),
+// o = k / inner_n, in = k % inner_n.  off < 0 marks padding; flag >= 0 zeroes
+// the row unless keep[flag] (and keep2[flag] when given).
 struct Src {
-  int64_t off;
+  int64_t off, off2;
   int32_t outer, inner_st, inner_n, flag;
 };
 
-// One warp per packed row/column: exponent of its largest |x|, then all Kpad
-// digit positions of every slice (zeros past K), so a reused buffer needs no clearing.
-// Rows/columns [n0, n0 + n) of the plan's global lists.
+// One warp per packed row/column (rows/columns [n0, n0 + n) of the plan's
+// lists): exponent of its largest |x|, then all Kpad digit positions of every
+// slice (zeros past K), so a reused buffer needs no clearing.
 __global__ void k_pack_src(int64_t n0, int64_t n, const int64_t *prob_of, const Prob *probs, const Src *src,
-                           const double *__restrict__ X, int64_t shift, const uint8_t *keep, int S, int is_b,
-                           int64_t buf_shift, __nv_bfloat16 *planes, int *e) {
+                           const double *__restrict__ X, int64_t shift, const double *__restrict__ X2,
+                           const uint8_t *keep, const uint8_t *keep2, int S, int is_b, __nv_bfloat16 *planes,
+                           int *e) {
   const int64_t w = n0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (w >= n0 + n) return;
@@ -587,31 +597,34 @@ __global__ void k_pack_src(int64_t n0, int64_t n, const int64_t *prob_of, const 
   const int r = (int)(w - (is_b ? pr.coloff : pr.rowoff));
   const int nkt = pr.Kpad / KC;
   const int rows_pad = is_b ? pr.Npad : pr.Mpad;
-  char *base = (char *)planes + ((is_b ? pr.boff : pr.aoff) - buf_shift);
+  char *base = (char *)planes + (is_b ? pr.boff : pr.aoff);
   const int64_t plane = (int64_t)(rows_pad / TM) * nkt * A_TILE;
-  const bool live = sr.off >= 0 && (sr.flag < 0 || keep[sr.flag]);
+  const bool live = sr.off >= 0 && (sr.flag < 0 || (keep[sr.flag] && (!keep2 || keep2[sr.flag])));
   const double *x = X + (live ? sr.off - shift : 0);
+  const double *x2 = (live && sr.off2 >= 0) ? X2 + sr.off2 : nullptr;
   const int Kt = pr.pad_;  // true K of the problem; positions Kt..Kpad get zero digits
+  auto elem = [&](int k) -> double {
+    if (!live || k >= Kt) return 0.0;
+    const int o = k / sr.inner_n, in = k - o * sr.inner_n;
+    const double v = x[(int64_t)o * sr.outer + (int64_t)in * sr.inner_st];
+    return x2 ? v * x2[in] : v;
+  };
   int m = -2000;
-  if (live)
-    for (int k = lane; k < Kt; k += 32) {
-      const int o = k / sr.inner_n, in = k - o * sr.inner_n;
-      m = max(m, exp_of(fabs(x[(int64_t)o * sr.outer + (int64_t)in * sr.inner_st])));
-    }
+  for (int k = lane; k < Kt; k += 32) m = max(m, exp_of(fabs(elem(k))));
   for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if (lane == 0) e[(is_b ? pr.eboff : pr.eaoff) + r] = m;
   for (int k = lane; k < pr.Kpad; k += 32) {
     float d[MAXS];
-    double v = 0.0;
-    if (live && k < Kt) {
-      const int o = k / sr.inner_n, in = k - o * sr.inner_n;
-      v = x[(int64_t)o * sr.outer + (int64_t)in * sr.inner_st];
-    }
-    digits_of(v, m, S, d);
+    digits_of(elem(k), m, S, d);
     const int64_t off = ((int64_t)(r / TM) * nkt + k / KC) * A_TILE + tile_off(r % TM, k % KC);
     for (int s = 0; s < S; s++)
       *(__nv_bfloat16 *)(base + s * plane + off) = __float2bfloat16_rn(d[s] * slice_scale(s));
   }
+}
+
+__global__ void k_flag_set(int n, const int32_t *idx, uint8_t *flags) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) flags[idx[t]] = 1;
 }
 
 }  // namespace rixtc
@@ -621,11 +634,12 @@ __global__ void k_pack_src(int64_t n0, int64_t n, const int64_t *prob_of, const 
 
 // Host and device state of one batched plan.
 struct rix_mx_plan {
-  int kind = 0;                          // 0: terms 3+4, 1: term 2
-  std::vector<int32_t> grp;              // problems (middle atoms) [grp[g], grp[g+1])
+  int kind = 0;                          // 0: terms 3+4, 1: term 2, 2: term-4 intermediate Z
+  std::vector<int32_t> grp;              // problems [grp[g], grp[g+1])
+  std::vector<int32_t> grp_blk;          // memory-plan block of each group (-1: any)
   std::vector<int64_t> tile_seg, row_seg, col_seg;
   int64_t buf_bytes = 0;                 // largest group
-  double tflops = 0;
+  double tflops = 0, fl64 = 0;           // issued tensor FLOPs, FP64 FLOPs of the same work
   Prob *d_probs = nullptr;
   int2 *d_rowinfo = nullptr;
   int4 *d_colinfo = nullptr, *d_tiles = nullptr;
@@ -644,146 +658,206 @@ using rix::pair_key;
 
 struct PlanHost {
   std::vector<Prob> probs;
+  std::vector<int32_t> pblk;
   std::vector<int2> rowinfo;
   std::vector<int4> colinfo, tiles;
   std::vector<int64_t> rowprob, colprob, pbytes;
   std::vector<rixtc::Src> rowsrc, colsrc;
   std::vector<int32_t> xmap;
+  std::vector<uint8_t> use;                // kind 2: middle atoms that run here
   int64_t eaoff = 0, eboff = 0;
-  double tflops = 0;
+  double tflops = 0, fl64 = 0;
 };
 
-// Build the problems of one plan.  kind 0: middle atom B, rows from C(A,B')^{P on B'},
-// columns from Z(B,E'); kind 1: middle atom G, rows from U2(A',G), columns from C(G,E')^{Q on G}.
-// count_only: no host arrays, just the map bytes, the largest problem's slices and
-// the total slice bytes.
+// Estimated rates on GB300 for the choice between the FP64 kernels and the
+// tensor-core regroupings: about 1 TFLOP/s for the FP64 kernels, about
+// 0.5 PFLOP/s issued for the sliced GEMM.
+constexpr double FP64_RATE = 1.0e12, TC_RATE = 5.0e14;
+
+// Build the problems of one plan (see the section comment for the three kinds).
+// count_only: no host arrays, just the map bytes, the largest problem's slices
+// and the total slice bytes (the memory plan is not known yet: one block).
 rix_status plan_host(rix_ctx *ctx, int kind, const std::vector<int64_t> &ptrZ, PlanHost &h, bool count_only,
                      int64_t *maps_out, int64_t *maxp_out, int64_t *total_out) {
   using namespace rixtc;
   const int nat = ctx->nat, S = ctx->mx_S;
   auto &row1 = ctx->row1, &row2 = ctx->row2, &row3 = ctx->row3;
-  auto find3 = [&](int64_t key) {
-    const int a = key_a(key);
-    auto it = std::lower_bound(ctx->keys3.begin() + row3[a], ctx->keys3.begin() + row3[a + 1], key);
-    return (it == ctx->keys3.begin() + row3[a + 1] || *it != key) ? (int64_t)-1
-                                                                   : (int64_t)(it - ctx->keys3.begin());
+  auto find_sorted = [&](const std::vector<int64_t> &keys, int64_t lo, int64_t hi, int64_t key) {
+    auto it = std::lower_bound(keys.begin() + lo, keys.begin() + hi, key);
+    return (it == keys.begin() + hi || *it != key) ? (int64_t)-1 : (int64_t)(it - keys.begin());
   };
   const int npairs = S * (S + 1) / 2;
   int64_t total = 0, maxp = 0, maps = 0;
-  if (!count_only) {
-    h.probs.assign(nat, Prob{});
-    h.pbytes.assign(nat, 0);
+  // kind 2: which middle atoms G' run on the tensor cores (estimated times)
+  h.use.assign(nat, kind == 2 ? 0 : 1);
+  if (kind == 2) {
+    for (int g = 0; g < nat; g++) {
+      double sB1 = 0, sB2 = 0, sE = 0, M = 0;
+      for (int64_t q = row1[g]; q < row1[g + 1]; q++) {
+        const int b = ctx->pB[q];
+        sB1 += ctx->na_at[b];
+        sB2 += (double)ctx->na_at[b] * ctx->nb_at[b];
+        if (!ctx->onsite[q]) sE += ctx->nb_at[b];
+      }
+      M = sB2;
+      const double naG = ctx->na_at[g], nbG = ctx->nb_at[g];
+      const double f64 = 2.0 * sB1 * naG * nbG * sE + 2.0 * sB2 * nbG * sE;
+      const double Mp = std::ceil(M / TM) * TM, Np = std::ceil(sE / TN) * TN,
+                   Kp = std::ceil(naG * nbG / KC) * KC;
+      const double tc = 2.0 * Mp * Np * Kp * npairs;
+      if (sE > 0 && tc / TC_RATE < f64 / FP64_RATE) {
+        h.use[g] = 1;
+        h.fl64 += f64;
+      }
+    }
   }
+  const int nblk = (kind == 2 && !count_only) ? ctx->nblk : 1;
+  std::vector<int32_t> blk_of(nat, 0);
+  if (kind == 2 && !count_only)
+    for (int b = 0; b < nblk; b++)
+      for (int a = ctx->blk_atom[b]; a < ctx->blk_atom[b + 1]; a++) blk_of[a] = b;
   std::vector<int64_t> qs, zs;
-  for (int b = 0; b < nat; b++) {
-    qs.clear();
-    zs.clear();
-    // rows: pairs (b, A', m); kind 0 skips on-site (P on B' != A), kind 1 keeps it
-    for (int64_t q = row1[b]; q < row1[b + 1]; q++)
-      if (kind == 1 || !ctx->onsite[q]) qs.push_back(q);
-    if (kind == 0) {
-      for (int64_t z = row2[b]; z < row2[b + 1]; z++)
-        if (ptrZ[z + 1] > ptrZ[z]) zs.push_back(z);
-    } else {
-      for (int64_t q = row1[b]; q < row1[b + 1]; q++)
-        if (!ctx->onsite[q]) zs.push_back(q);
-    }
-    int M = 0, N = 0;
-    for (auto q : qs) M += ctx->nb_at[ctx->pB[q]];
-    for (auto z : zs) N += ctx->nb_at[kind == 0 ? key_b(ctx->keys2[z]) : ctx->pB[z]];
-    const int K = ctx->na_at[b] * ctx->nb_at[b];
-    const int Mpad = std::max(TM, (M + TM - 1) / TM * TM);
-    const int Npad = std::max(TN, (N + TN - 1) / TN * TN);
-    const int Kpad = (K + KC - 1) / KC * KC;
-    const int64_t bytes = (int64_t)S * (Mpad + Npad) * Kpad * 2;
-    total += bytes;
-    maxp = std::max(maxp, bytes);
-    // xmap, rowinfo + rowprob + rowsrc + exponent, colinfo + colprob + colsrc + exponent, tiles
-    maps += (int64_t)qs.size() * zs.size() * 4 + (int64_t)Mpad * (8 + 8 + 24 + 4) +
-            (int64_t)Npad * (16 + 8 + 24 + 4) + (int64_t)(Mpad / TM) * (Npad / TN) * 16 + (int64_t)sizeof(Prob);
-    if (count_only) continue;
-    Prob &pr = h.probs[b];
-    pr.M = M; pr.N = N; pr.Mpad = Mpad; pr.Npad = Npad; pr.Kpad = Kpad;
-    pr.pad_ = K;  // true K (the pack kernel zero-fills K..Kpad)
-    pr.nz = (int32_t)zs.size();
-    pr.drop = fixed_point_drop(Kpad, S);
-    pr.eaoff = h.eaoff; pr.eboff = h.eboff;
-    pr.rowoff = (int64_t)h.rowinfo.size();
-    pr.coloff = (int64_t)h.colinfo.size();
-    pr.xoff = (int64_t)h.xmap.size();
-    h.pbytes[b] = bytes;
-    h.eaoff += Mpad;
-    h.eboff += Npad;
-    const int nbB = ctx->nb_at[b], naB = ctx->na_at[b];
-    for (int qi = 0; qi < (int)qs.size(); qi++) {
-      const int64_t q = qs[qi];
-      const int a = ctx->pB[q];
-      const int nbA = ctx->nb_at[a], naA = ctx->na_at[a];
-      const int64_t pq = ctx->partner1[q];  // pair (A', b)
-      for (int i = 0; i < nbA; i++) {
-        h.rowinfo.push_back(make_int2(qi, i));
-        Src sr;
-        if (kind == 0) {  // C(A,B)[naA + P][i][j]
-          sr.off = ctx->offC[pq] + ((int64_t)naA * nbA + i) * nbB;
-          sr.outer = nbA * nbB; sr.inner_st = 1; sr.inner_n = nbB; sr.flag = (int32_t)pq;
-        } else {          // U2(A,G)[Q][i][k]
-          sr.off = ctx->offU_h[pq] + (int64_t)i * nbB;
-          sr.outer = nbA * nbB; sr.inner_st = 1; sr.inner_n = nbB; sr.flag = (int32_t)pq;
-        }
-        h.rowsrc.push_back(sr);
-        h.rowprob.push_back(b);
+  for (int blk = 0; blk < nblk; blk++)
+    for (int b = 0; b < nat; b++) {
+      if (!h.use[b]) continue;
+      qs.clear();
+      zs.clear();
+      // rows: pairs (b, A', m); terms 3+4 skip on-site (P on B' != A)
+      for (int64_t q = row1[b]; q < row1[b + 1]; q++) {
+        if (kind == 0 && ctx->onsite[q]) continue;
+        if (kind == 2 && blk_of[ctx->pB[q]] != blk) continue;
+        qs.push_back(q);
       }
-    }
-    for (int r = M; r < Mpad; r++) {
-      h.rowinfo.push_back(make_int2(-1, 0));
-      h.rowsrc.push_back(Src{-1, 1, 1, 1, -1});
-      h.rowprob.push_back(b);
-    }
-    for (int zi = 0; zi < (int)zs.size(); zi++) {
-      const int64_t z = zs[zi];
-      const int e = kind == 0 ? key_b(ctx->keys2[z]) : ctx->pB[z];
-      const int nbE = ctx->nb_at[e];
-      for (int l = 0; l < nbE; l++) {
-        h.colinfo.push_back(make_int4(zi, l, nbE, 0));
-        Src sr;
-        if (kind == 0) {  // Z(B,E')[P][j][l]
-          sr.off = ctx->off2[z] + l;
-          sr.outer = nbB * nbE; sr.inner_st = nbE; sr.inner_n = nbB; sr.flag = -1;
-        } else {          // C(G,E')[Q][k][l], Q on G
-          sr.off = ctx->offC[z] + l;
-          sr.outer = nbB * nbE; sr.inner_st = nbE; sr.inner_n = nbB; sr.flag = (int32_t)z;
-        }
-        h.colsrc.push_back(sr);
-        h.colprob.push_back(b);
+      if (qs.empty()) continue;
+      if (kind == 0) {
+        for (int64_t z = row2[b]; z < row2[b + 1]; z++)
+          if (ptrZ[z + 1] > ptrZ[z]) zs.push_back(z);
+      } else {
+        for (int64_t q = row1[b]; q < row1[b + 1]; q++)
+          if (!ctx->onsite[q]) zs.push_back(q);
       }
-    }
-    for (int c = N; c < Npad; c++) {
-      h.colinfo.push_back(make_int4(-1, 0, 0, 0));
-      h.colsrc.push_back(Src{-1, 1, 1, 1, -1});
-      h.colprob.push_back(b);
-    }
-    (void)naB;
-    // output block of (row block q, column block z): A' at image m_q from the middle
-    // atom, E' at n_z from it, so E' sits at n_z - m_q from A'
-    for (auto q : qs) {
-      const int a = ctx->pB[q];
-      for (auto z : zs) {
+      int M = 0, N = 0;
+      for (auto q : qs) {
+        const int a = ctx->pB[q];
+        M += kind == 2 ? ctx->na_at[a] * ctx->nb_at[a] : ctx->nb_at[a];
+      }
+      for (auto z : zs) N += ctx->nb_at[kind == 0 ? key_b(ctx->keys2[z]) : ctx->pB[z]];
+      const int K = ctx->na_at[b] * ctx->nb_at[b];
+      const int Mpad = std::max(TM, (M + TM - 1) / TM * TM);
+      const int Npad = std::max(TN, (N + TN - 1) / TN * TN);
+      const int Kpad = std::max(KC, (K + KC - 1) / KC * KC);
+      const int64_t bytes = (int64_t)S * (Mpad + Npad) * Kpad * 2;
+      total += bytes;
+      maxp = std::max(maxp, bytes);
+      // xmap, rowinfo + rowprob + rowsrc + exponent, colinfo + colprob + colsrc + exponent, tiles
+      maps += (int64_t)qs.size() * zs.size() * 4 + (int64_t)Mpad * (8 + 8 + 32 + 4) +
+              (int64_t)Npad * (16 + 8 + 32 + 4) + (int64_t)(Mpad / TM) * (Npad / TN) * 16 + (int64_t)sizeof(Prob);
+      h.tflops += 2.0 * Mpad * Npad * Kpad * npairs;
+      if (count_only) continue;
+      const int pidx = (int)h.probs.size();
+      Prob pr{};
+      pr.M = M; pr.N = N; pr.Mpad = Mpad; pr.Npad = Npad; pr.Kpad = Kpad;
+      pr.pad_ = K;  // true K (the pack kernel zero-fills K..Kpad)
+      pr.nz = (int32_t)zs.size();
+      pr.drop = fixed_point_drop(Kpad, S);
+      pr.eaoff = h.eaoff; pr.eboff = h.eboff;
+      pr.rowoff = (int64_t)h.rowinfo.size();
+      pr.coloff = (int64_t)h.colinfo.size();
+      pr.xoff = (int64_t)h.xmap.size();
+      h.eaoff += Mpad;
+      h.eboff += Npad;
+      const int nbB = ctx->nb_at[b], naB = ctx->na_at[b];
+      for (int qi = 0; qi < (int)qs.size(); qi++) {
+        const int64_t q = qs[qi];
+        const int a = ctx->pB[q];
+        const int nbA = ctx->nb_at[a], naA = ctx->na_at[a];
+        const int64_t pq = ctx->partner1[q];  // pair (A', b)
+        if (kind == 2) {  // rows (P, j) of V(B,G')[P][.] x D(B,G')[j][.]
+          for (int P = 0; P < naA; P++)
+            for (int j = 0; j < nbA; j++) {
+              h.rowinfo.push_back(make_int2(qi, P * nbA + j));
+              h.rowsrc.push_back(Src{ctx->offV[pq] + (int64_t)P * naB, ctx->offD[pq] + (int64_t)j * nbB, 1, 0,
+                                     nbB, (int32_t)pq});
+              h.rowprob.push_back(pidx);
+            }
+          continue;
+        }
+        for (int i = 0; i < nbA; i++) {
+          h.rowinfo.push_back(make_int2(qi, i));
+          Src sr;
+          sr.off2 = -1;
+          if (kind == 0) {  // C(A,B)[naA + P][i][j]
+            sr.off = ctx->offC[pq] + ((int64_t)naA * nbA + i) * nbB;
+            sr.outer = nbA * nbB; sr.inner_st = 1; sr.inner_n = nbB; sr.flag = (int32_t)pq;
+          } else {          // U2(A,G)[Q][i][k]
+            sr.off = ctx->offU_h[pq] + (int64_t)i * nbB;
+            sr.outer = nbA * nbB; sr.inner_st = 1; sr.inner_n = nbB; sr.flag = (int32_t)pq;
+          }
+          h.rowsrc.push_back(sr);
+          h.rowprob.push_back(pidx);
+        }
+      }
+      for (int r = M; r < Mpad; r++) {
+        h.rowinfo.push_back(make_int2(-1, 0));
+        h.rowsrc.push_back(Src{-1, -1, 1, 1, 1, -1});
+        h.rowprob.push_back(pidx);
+      }
+      for (int zi = 0; zi < (int)zs.size(); zi++) {
+        const int64_t z = zs[zi];
         const int e = kind == 0 ? key_b(ctx->keys2[z]) : ctx->pB[z];
-        int nz3[3];
-        for (int c = 0; c < 3; c++)
-          nz3[c] = (kind == 0 ? key_n(ctx->keys2[z], c) : (int)ctx->pn[3 * z + c]) - ctx->pn[3 * q + c];
-        const int64_t x = find3(pair_key(a, e, nz3[0], nz3[1], nz3[2]));
-        if (x < 0) {
-          ctx->last_error = "mixed plan: output block outside the K pattern";
-          return RIX_EINVAL;
+        const int nbE = ctx->nb_at[e];
+        for (int l = 0; l < nbE; l++) {
+          h.colinfo.push_back(make_int4(zi, l, nbE, 0));
+          Src sr;
+          sr.off2 = -1;
+          if (kind == 0) {  // Z(B,E')[P][j][l]
+            sr.off = ctx->off2[z] + l;
+            sr.outer = nbB * nbE; sr.inner_st = nbE; sr.inner_n = nbB; sr.flag = -1;
+          } else {          // C(G,E')[Q][k][l], Q on G
+            sr.off = ctx->offC[z] + l;
+            sr.outer = nbB * nbE; sr.inner_st = nbE; sr.inner_n = nbB; sr.flag = (int32_t)z;
+          }
+          h.colsrc.push_back(sr);
+          h.colprob.push_back(pidx);
         }
-        h.xmap.push_back((int32_t)x);
+      }
+      for (int c = N; c < Npad; c++) {
+        h.colinfo.push_back(make_int4(-1, 0, 0, 0));
+        h.colsrc.push_back(Src{-1, -1, 1, 1, 1, -1});
+        h.colprob.push_back(pidx);
+      }
+      // output block of (row block q, column block z): A' at image m_q from the middle
+      // atom, E' at n_z from it, so E' sits at n_z - m_q from A' (a K block, or for
+      // kind 2 a Z block of the 2-hop list)
+      for (auto q : qs) {
+        const int a = ctx->pB[q];
+        for (auto z : zs) {
+          const int e = kind == 0 ? key_b(ctx->keys2[z]) : ctx->pB[z];
+          int nz3[3];
+          for (int c = 0; c < 3; c++)
+            nz3[c] = (kind == 0 ? key_n(ctx->keys2[z], c) : (int)ctx->pn[3 * z + c]) - ctx->pn[3 * q + c];
+          const int64_t key = pair_key(a, e, nz3[0], nz3[1], nz3[2]);
+          const int64_t x = kind == 2 ? find_sorted(ctx->keys2, row2[a], row2[a + 1], key)
+                                      : find_sorted(ctx->keys3, row3[a], row3[a + 1], key);
+          if (x < 0) {
+            ctx->last_error = "mixed plan: output block outside its list";
+            return RIX_EINVAL;
+          }
+          h.xmap.push_back((int32_t)x);
+        }
+      }
+      for (int nt = 0; nt < Npad / TN; nt++)
+        for (int mt = 0; mt < Mpad / TM; mt++) h.tiles.push_back(make_int4(pidx, mt, nt, 0));
+      h.probs.push_back(pr);
+      h.pbytes.push_back(bytes);
+      // Z of terms 3+4 is resident per block of its middle atom; kind 2 rows per block
+      h.pblk.push_back(kind == 0 ? -1 : (kind == 2 ? blk : -1));
+      if (kind == 0) {
+        int bb = 0;
+        while (b >= ctx->blk_atom[bb + 1]) bb++;
+        h.pblk.back() = bb;
       }
     }
-    for (int nt = 0; nt < Npad / TN; nt++)
-      for (int mt = 0; mt < Mpad / TM; mt++) h.tiles.push_back(make_int4(b, mt, nt, 0));
-    h.tflops += 2.0 * Mpad * Npad * Kpad * npairs;
-  }
   if (maps_out) *maps_out = maps;
   if (maxp_out) *maxp_out = maxp;
   if (total_out) *total_out = total;
@@ -792,7 +866,7 @@ rix_status plan_host(rix_ctx *ctx, int kind, const std::vector<int64_t> &ptrZ, P
 
 // The reusable slice buffer of a plan: the largest problem, or up to 8 GB of them.
 int64_t group_budget(int64_t maxp, int64_t total) {
-  return std::max(maxp, std::min(total, (int64_t)8 << 30));
+  return total ? std::max(maxp, std::min(total, (int64_t)8 << 30)) : 0;
 }
 
 }  // namespace
@@ -806,11 +880,11 @@ int64_t rix_mixed_bytes(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
     rix_t1_plan_build(ctx, true, &t1);  // maps plus its slice buffer
     maps += t1;
   }
-  for (int kind = 0; kind < 2; kind++) {
+  for (int kind = 0; kind < 3; kind++) {
     PlanHost h;
     int64_t m = 0, maxp = 0, total = 0;
     plan_host(ctx, kind, ptrZ, h, true, &m, &maxp, &total);
-    maps += m;
+    maps += m + (kind == 2 ? ctx->nat : 0);
     buf = std::max(buf, group_budget(maxp, total));
   }
   return maps + buf + ((int64_t)64 << 20);
@@ -825,56 +899,56 @@ rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
   }
   int64_t buf = 0;
   double tflops = 0;
-  for (int kind = 0; kind < 2; kind++) {
+  for (int kind = 0; kind < 3; kind++) {
     PlanHost h;
     int64_t maps = 0, maxp = 0, total = 0;
     rix_status s = plan_host(ctx, kind, ptrZ, h, false, &maps, &maxp, &total);
     if (s != RIX_OK) return s;
     rix_mx_plan *pl = new rix_mx_plan;
     pl->kind = kind;
-    (kind == 0 ? ctx->mx34 : ctx->mx2) = pl;
+    (kind == 0 ? ctx->mx34 : kind == 1 ? ctx->mx2 : ctx->mxz) = pl;
     const int64_t budget = group_budget(maxp, total);
-    // groups of consecutive problems within the budget; terms 3+4 also stay inside
-    // one memory-plan block (Z is resident per block)
+    // groups of consecutive problems within the budget and within one memory-plan block
     pl->grp.assign(1, 0);
     int64_t cur = 0, maxgrp = 0;
-    int blk = 0;
-    for (int b = 0; b < ctx->nat; b++) {
-      while (b >= ctx->blk_atom[blk + 1]) blk++;
-      const bool new_blk = kind == 0 && b == ctx->blk_atom[blk] && b > 0;
-      if (b > 0 && (new_blk || cur + h.pbytes[b] > budget)) {
-        pl->grp.push_back(b);
+    const int np = (int)h.probs.size();
+    for (int p = 0; p < np; p++) {
+      if (p > 0 && (h.pblk[p] != h.pblk[p - 1] || cur + h.pbytes[p] > budget)) {
+        pl->grp.push_back(p);
         maxgrp = std::max(maxgrp, cur);
         cur = 0;
       }
-      Prob &pr = h.probs[b];
+      Prob &pr = h.probs[p];
       pr.aoff = cur;
       pr.boff = cur + (int64_t)ctx->mx_S * pr.Mpad * pr.Kpad * 2;
-      cur += h.pbytes[b];
+      cur += h.pbytes[p];
     }
     maxgrp = std::max(maxgrp, cur);
-    pl->grp.push_back(ctx->nat);
-    pl->buf_bytes = maxgrp;
-    buf = std::max(buf, maxgrp);
+    pl->grp.push_back(np);
+    pl->buf_bytes = np ? maxgrp : 0;
+    buf = std::max(buf, pl->buf_bytes);
     const size_t ng = pl->grp.size() - 1;
+    pl->grp_blk.assign(ng, -1);
     pl->tile_seg.assign(ng + 1, 0);
     pl->row_seg.assign(ng + 1, 0);
     pl->col_seg.assign(ng + 1, 0);
     {
       size_t ti = 0, ri = 0, ci = 0;
       for (size_t g = 0; g < ng; g++) {
-        const int bend = pl->grp[g + 1];
-        while (ti < h.tiles.size() && h.tiles[ti].x < bend) ti++;
-        while (ri < h.rowprob.size() && h.rowprob[ri] < bend) ri++;
-        while (ci < h.colprob.size() && h.colprob[ci] < bend) ci++;
+        const int pend = pl->grp[g + 1];
+        if (pl->grp[g] < np) pl->grp_blk[g] = h.pblk[pl->grp[g]];
+        while (ti < h.tiles.size() && h.tiles[ti].x < pend) ti++;
+        while (ri < h.rowprob.size() && h.rowprob[ri] < pend) ri++;
+        while (ci < h.colprob.size() && h.colprob[ci] < pend) ci++;
         pl->tile_seg[g + 1] = ti;
         pl->row_seg[g + 1] = ri;
         pl->col_seg[g + 1] = ci;
       }
     }
     pl->tflops = h.tflops;
+    pl->fl64 = h.fl64;
     tflops += h.tflops;
-    ctx->stats.tensor_flops_stage[kind] = h.tflops;
+    ctx->stats.tensor_flops_stage[kind == 0 ? 0 : kind == 1 ? 1 : 3] = h.tflops;
     if ((s = rix_upload(ctx, &pl->d_probs, h.probs)) != RIX_OK) return s;
     if ((s = rix_upload(ctx, &pl->d_rowinfo, h.rowinfo)) != RIX_OK) return s;
     if ((s = rix_upload(ctx, &pl->d_colinfo, h.colinfo)) != RIX_OK) return s;
@@ -886,9 +960,26 @@ rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
     if ((s = rix_upload(ctx, &pl->d_xmap, h.xmap)) != RIX_OK) return s;
     if ((s = rix_alloc(ctx, &pl->d_eA, std::max<int64_t>(h.eaoff, 1))) != RIX_OK) return s;
     if ((s = rix_alloc(ctx, &pl->d_eB, std::max<int64_t>(h.eboff, 1))) != RIX_OK) return s;
+    if (kind == 2) {
+      // middle atoms whose term-4 intermediate runs here: k_Z skips them
+      std::vector<int32_t> on;
+      for (int g = 0; g < ctx->nat; g++)
+        if (h.use[g]) on.push_back(g);
+      if ((s = rix_alloc(ctx, &ctx->d_ztc, ctx->nat)) != RIX_OK) return s;
+      RIX_CUDA_TRY(ctx, cudaMemset(ctx->d_ztc, 0, ctx->nat));
+      if (!on.empty()) {
+        int32_t *d_on = nullptr;
+        if ((s = rix_upload(ctx, &d_on, on)) != RIX_OK) return s;
+        k_flag_set<<<(unsigned)((on.size() + 255) / 256), 256>>>((int)on.size(), d_on, ctx->d_ztc);
+        RIX_CUDA_TRY(ctx, cudaDeviceSynchronize());
+      }
+      ctx->n_ztc = (int)on.size();
+      ctx->stats.flops_z_tc = h.fl64;
+    }
     if (ctx->opt.verbose)
-      fprintf(stderr, "rix mixed %s: %zu GEMM tiles in %zu group(s), slice buffer %.3g GB\n",
-              kind == 0 ? "terms 3+4" : "term 2", h.tiles.size(), ng, maxgrp * 1e-9);
+      fprintf(stderr, "rix mixed %s: %zu GEMM tiles in %zu group(s), slice buffer %.3g GB%s\n",
+              kind == 0 ? "terms 3+4" : kind == 1 ? "term 2" : "term-4 intermediate", h.tiles.size(), ng,
+              maxgrp * 1e-9, kind == 2 ? (", " + std::to_string(ctx->n_ztc) + " middle atoms").c_str() : "");
   }
   rix_status s;
   {
@@ -906,13 +997,13 @@ rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
   return RIX_OK;
 }
 
-// Kernel launches of one rix_build_K: flags, per block T, U2, terms 1+2, Z and
-// terms 3+4 (FP64) or per group two packs and a GEMM (mixed), term 2, symmetrise.
+// Kernel launches of one rix_build_K: flags, per block T, U2 and Z, terms 1+2 and
+// terms 3+4 (FP64 per block) or per group two packs and a GEMM (mixed), symmetrise.
 int32_t rix_launch_count(const rix_ctx *ctx) {
-  int32_t n = 2 + 3 * ctx->nblk;  // flags, symmetrise; T, U2, Z per block
+  int32_t n = 2 + 3 * ctx->nblk;
   if (ctx->have_mx) {
     n += 3 * (int32_t)(ctx->mx34->grp.size() - 1) + 3 * (int32_t)(ctx->mx2->grp.size() - 1) +
-         rix_t1_launches(ctx);
+         3 * (int32_t)(ctx->mxz->grp.size() - 1) + rix_t1_launches(ctx);
     if (ctx->n_t1tc < ctx->nat) n += ctx->nblk;  // k_X12 for the other column atoms
   } else {
     n += 2 * ctx->nblk;  // k_X12, k_X34
@@ -924,32 +1015,43 @@ void rix_mixed_free(rix_ctx *ctx) {
   rix_t1_plan_free(ctx);
   delete ctx->mx34;
   delete ctx->mx2;
-  ctx->mx34 = ctx->mx2 = nullptr;
+  delete ctx->mxz;
+  ctx->mx34 = ctx->mx2 = ctx->mxz = nullptr;
 }
 
 namespace {
 
-// Slice the rows and columns of group g of a plan, then run its GEMM tiles.
-rix_status run_group(rix_ctx *ctx, const rix_mx_plan *pl, size_t g, const double *rows, int64_t rshift,
-                     const uint8_t *rkeep, const double *cols, int64_t cshift, const uint8_t *ckeep,
-                     cudaStream_t st) {
+struct Operand {
+  const double *x;
+  int64_t shift;
+  const double *x2;
+  const uint8_t *keep, *keep2;
+};
+
+// Slice the rows and columns of group g of a plan, then run its GEMM tiles; the
+// results go to out + offs[xmap] - oshift (scaled by oscale).
+rix_status run_group(rix_ctx *ctx, const rix_mx_plan *pl, size_t g, const Operand &ra, const Operand &cb,
+                     const int64_t *offs, double *out, int64_t oshift, double oscale, cudaStream_t st) {
   using namespace rixtc;
   const int S = ctx->mx_S;
   const int64_t r0 = pl->row_seg[g], r1 = pl->row_seg[g + 1];
   const int64_t c0 = pl->col_seg[g], c1 = pl->col_seg[g + 1];
   const int64_t t0 = pl->tile_seg[g], t1 = pl->tile_seg[g + 1];
-  // the group's first problem sits at byte 0 of the buffer
-  const int64_t shift = 0;
   __nv_bfloat16 *buf = (__nv_bfloat16 *)ctx->d_mx_buf;
   if (r1 > r0)
     k_pack_src<<<(unsigned)(((r1 - r0) * 32 + 255) / 256), 256, 0, st>>>(
-        r0, r1 - r0, pl->d_rowprob, pl->d_probs, pl->d_rowsrc, rows, rshift, rkeep, S, 0, shift, buf, pl->d_eA);
+        r0, r1 - r0, pl->d_rowprob, pl->d_probs, pl->d_rowsrc, ra.x, ra.shift, ra.x2, ra.keep, ra.keep2, S, 0,
+        buf, pl->d_eA);
   if (c1 > c0)
     k_pack_src<<<(unsigned)(((c1 - c0) * 32 + 255) / 256), 256, 0, st>>>(
-        c0, c1 - c0, pl->d_colprob, pl->d_probs, pl->d_colsrc, cols, cshift, ckeep, S, 1, shift, buf, pl->d_eB);
+        c0, c1 - c0, pl->d_colprob, pl->d_probs, pl->d_colsrc, cb.x, cb.shift, cb.x2, cb.keep, cb.keep2, S, 1,
+        buf, pl->d_eB);
   if (t1 > t0) {
     GemmArgs ga{buf, buf, pl->d_eA, pl->d_eB, nullptr, 0, 0, 0, 0, 0, 0, S, 1, 0, ctx->d_mx_err,
-                pl->d_tiles + t0, pl->d_probs, pl->d_rowinfo, pl->d_colinfo, pl->d_xmap, ctx->d_offK, ctx->d_X};
+                pl->d_tiles + t0, pl->d_probs, pl->d_rowinfo, pl->d_colinfo, pl->d_xmap, offs, out};
+    ga.mode = 0;
+    ga.oscale = oscale;
+    ga.xshift = oshift;
     k_gemm_sliced<<<(unsigned)(t1 - t0), NTHR, smem_bytes(S), st>>>(ga);
   }
   cudaError_t e = cudaGetLastError();
@@ -970,13 +1072,15 @@ void gemm_attr() {
 
 }  // namespace
 
-// Terms 3+4 for the middle atoms [b0, b1) of one memory-plan block (Z resident, zbase).
-rix_status rix_mixed_x34(rix_ctx *ctx, int b0, int b1, int64_t zbase, cudaStream_t st) {
+// Terms 3+4 for the middle atoms of memory-plan block blk (Z resident, zbase).
+rix_status rix_mixed_x34(rix_ctx *ctx, int blk, int64_t zbase, cudaStream_t st) {
   gemm_attr();
   const rix_mx_plan *pl = ctx->mx34;
+  const Operand rows{ctx->d_C, 0, nullptr, ctx->d_keepC, nullptr};
+  const Operand cols{ctx->d_Z, zbase, nullptr, nullptr, nullptr};
   for (size_t g = 0; g + 1 < pl->grp.size(); g++) {
-    if (pl->grp[g + 1] <= b0 || pl->grp[g] >= b1) continue;
-    rix_status s = run_group(ctx, pl, g, ctx->d_C, 0, ctx->d_keepC, ctx->d_Z, zbase, nullptr, st);
+    if (pl->grp_blk[g] != blk) continue;
+    rix_status s = run_group(ctx, pl, g, rows, cols, ctx->d_offK, ctx->d_X, 0, 1.0, st);
     if (s != RIX_OK) return s;
   }
   return RIX_OK;
@@ -986,8 +1090,25 @@ rix_status rix_mixed_x34(rix_ctx *ctx, int b0, int b1, int64_t zbase, cudaStream
 rix_status rix_mixed_t2(rix_ctx *ctx, cudaStream_t st) {
   gemm_attr();
   const rix_mx_plan *pl = ctx->mx2;
+  const Operand rows{ctx->d_U, 0, nullptr, ctx->d_keepV, nullptr};
+  const Operand cols{ctx->d_C, 0, nullptr, ctx->d_keepC, nullptr};
   for (size_t g = 0; g + 1 < pl->grp.size(); g++) {
-    rix_status s = run_group(ctx, pl, g, ctx->d_U, 0, ctx->d_keepV, ctx->d_C, 0, ctx->d_keepC, st);
+    rix_status s = run_group(ctx, pl, g, rows, cols, ctx->d_offK, ctx->d_X, 0, 1.0, st);
+    if (s != RIX_OK) return s;
+  }
+  return RIX_OK;
+}
+
+// Term-4 intermediate for the rows B of memory-plan block blk (after k_Z stored the
+// FP64 part of those Z blocks; Z resident at zbase).
+rix_status rix_mixed_z(rix_ctx *ctx, int blk, int64_t zbase, const double *D, cudaStream_t st) {
+  gemm_attr();
+  const rix_mx_plan *pl = ctx->mxz;
+  const Operand rows{ctx->d_V, 0, D, ctx->d_keepV, ctx->d_keepD};
+  const Operand cols{ctx->d_C, 0, nullptr, ctx->d_keepC, nullptr};
+  for (size_t g = 0; g + 1 < pl->grp.size(); g++) {
+    if (pl->grp_blk[g] != blk) continue;
+    rix_status s = run_group(ctx, pl, g, rows, cols, ctx->d_off2, ctx->d_Z, zbase, 0.5, st);
     if (s != RIX_OK) return s;
   }
   return RIX_OK;
@@ -1096,11 +1217,6 @@ __global__ void k_pack_t1_cols(int64_t n0, int64_t n, const int64_t *prob_of, co
   }
 }
 
-__global__ void k_flag_set(int n, const int32_t *idx, uint8_t *flags) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) flags[idx[t]] = 1;
-}
-
 }  // namespace rixtc
 
 struct rix_t1_plan {
@@ -1118,14 +1234,6 @@ struct rix_t1_plan {
   QInfo *d_qinfo = nullptr;
   int *d_eA = nullptr, *d_eB = nullptr;
 };
-
-namespace {
-
-// Estimated seconds of a column atom's term 1 on each path (rates seen on GB300:
-// about 1 TFLOP/s for the FP64 kernels, 0.5 PFLOP/s issued for the sliced GEMM).
-constexpr double T1_FP64_RATE = 1.0e12, T1_TC_RATE = 5.0e14;
-
-}  // namespace
 
 // Term-1 plan: decide per column atom, build problems (E, block) for the tensor ones.
 rix_status rix_t1_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) {
@@ -1160,7 +1268,7 @@ rix_status rix_t1_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
     const double Mp = (double)((M + TM - 1) / TM * TM), Np = (double)((naE * nbE + TN - 1) / TN * TN),
                  Kp = (double)((K + KC - 1) / KC * KC);
     const double tc = 2.0 * Mp * Np * Kp * npairs;
-    if (tc / T1_TC_RATE < f64 / T1_FP64_RATE) {
+    if (tc / TC_RATE < f64 / FP64_RATE) {
       use[e] = 1;
       fl64_tc += f64;
     }
