@@ -719,7 +719,7 @@ static rix_status build_lists(rix_ctx *ctx) {
     // plan (estimate plus 5 %) and a little slack for allocation granularity
     const int64_t items = (int64_t)(itT.size() + itZ.size() + itU.size()) * (int64_t)sizeof(int2) +
                           (int64_t)(ordX12.size() + ordX34.size()) * (int64_t)sizeof(int32_t);
-    avail -= items + ((int64_t)1 << 20);
+    avail -= items + ((int64_t)64 << 10);
     if (ctx->opt.precision == RIX_MIXED_BF16) avail -= rix_mixed_bytes(ctx, ptrZ) / 20 * 21;
   }
   const int64_t per_buf = std::max<int64_t>(0, avail / 2 / (int64_t)sizeof(double));

@@ -219,30 +219,33 @@ def test_pair_lists_of_all_workloads():
         ex.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("case", ["cluster24", "pbc2"])
-def test_row_blocked_memory_plan(case):
-    """A workspace too small for T and Z forces the build into row blocks; results are unchanged."""
+def test_row_blocked_memory_plan(case, precision):
+    """A workspace too small for T and Z forces the build into row blocks; results are unchanged
+    (in mixed precision the tensor-core problems are then split by block as well)."""
     if case == "cluster24":
         s = ri.config(0)
     else:
         s = _small_waters([[1.0, 1.2, 0.8], [3.9, 3.1, 3.3]], 11, side=6.0, cut=4.0)
     pk = ri.generate(s)
     kk, K_ref, E_ref, _ = exchange(s, pk)
-    full = Exchange.from_system(s)
+    full = Exchange.from_system(s, precision=precision)
     w0 = full.stats()["workspace_bytes"]
     assert full.stats()["n_row_blocks"] == 1
     full.close()
+    ktol, etol = (K_TOL, E_TOL * abs(E_ref)) if precision == "fp64" else (1e-8, 1e-6)
     seen = set()
-    for frac in (0.85, 0.7, 0.6):
+    for frac in (0.97, 0.94, 0.9, 0.85, 0.8, 0.7, 0.6):
         try:
-            ex, keys, K, E, _ = run_gpu(s, pk, max_workspace_bytes=int(w0 * frac))
+            ex, keys, K, E, _ = run_gpu(s, pk, max_workspace_bytes=int(w0 * frac), precision=precision)
         except RixError:
             continue
         nb = ex.stats()["n_row_blocks"]
         seen.add(nb)
         assert np.array_equal(keys, kk)
-        assert rel(K, K_ref) < K_TOL
-        assert abs(E - E_ref) < E_TOL * abs(E_ref)
+        assert rel(K, K_ref) < ktol
+        assert abs(E - E_ref) < etol
         ex.close()
     assert max(seen) >= 2, seen
 

@@ -174,7 +174,7 @@ def test_backward_row_blocked_plan(case):
     w0 = full.stats()["workspace_bytes"]
     full.close()
     seen = set()
-    for frac in (0.9, 0.8, 0.7, 0.6):
+    for frac in (0.97, 0.94, 0.9, 0.85, 0.8, 0.7, 0.6):
         try:
             ex = Exchange.from_system(s, backward=1, max_workspace_bytes=int(w0 * frac))
         except RixError:
