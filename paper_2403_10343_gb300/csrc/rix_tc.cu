@@ -11,22 +11,23 @@
 //
 // and every slice product A_s B_t is a sum of integers below 2^14 per term.
 // Slice s is stored pre-scaled by 2^-7(s-1) (exact in BF16), so a product
-// carries its own power of two.  Four FP32 accumulators in tensor memory
-// take the products with s+t = 2, 3, 4 and s+t >= 5: the first three hold
-// integers (times 2^-7(s+t-2)) whose sums over a group of 320 K values stay
-// below 2^24, so the tensor cores accumulate them exactly; the fourth holds
-// terms at least 2^-21 below the leading one, where the tensor cores' FP32
-// accumulation costs about 2^-39 of the row x column x K scale (measured).  After each group the accumulators are
-// folded into a 64-bit fixed-point sum per output element, and the FP64
-// result is formed once at the end.  The error is the truncation of the
-// operands after S digits (about 2^-7S of the row/column scale), the dropped
-// terms s+t > S+1 and the rounding of the fourth accumulator.
+// carries its own power of two.  Five FP32 accumulators in tensor memory
+// take the products with s+t = 2, 3, 4, 5 and s+t >= 6: the first four hold
+// integers (times 2^-7(s+t-2)) whose sums over a group of 256 K values stay
+// below 2^24, so the tensor cores accumulate them exactly; the fifth holds
+// terms at least 2^-28 below the leading one, where the tensor cores' FP32
+// accumulation costs about 2^-46 of the row x column x K scale.  After each
+// group the accumulators are folded into a 64-bit fixed-point sum per output
+// element, and the FP64 result is formed once at the end.  The error is the
+// truncation of the operands after S digits (about 2^-7S of the row/column
+// scale), the dropped terms s+t > S+1 and the rounding of the fifth
+// accumulator.
 //
-// Kernel layout: one CTA per 128 x 128 output tile; warp 0 issues the bulk
+// Kernel layout: one CTA per 128 x 96 output tile; warp 0 issues the bulk
 // copies (cp.async.bulk, mbarrier completion), one thread of warp 1 issues
 // tcgen05.mma (A and B from shared memory, accumulators in tensor memory),
 // warps 4-11 drain tensor memory (tcgen05.ld, two warps per 32-lane quadrant,
-// 64 columns each) into the fixed-point sums.  Every wait is bounded; on a
+// 48 columns each) into the fixed-point sums.  Every wait is bounded; on a
 // timeout the kernel records an error and returns.
 #include <cuda_bf16.h>
 
@@ -38,17 +39,17 @@
 namespace rixtc {
 
 constexpr int TM = 128;         // output rows per tile (one TMEM lane each)
-constexpr int TN = 128;         // output columns per tile
+constexpr int TN = 96;          // output columns per tile
 constexpr int KC = 32;          // K per pipeline stage
-constexpr int GROUP = 10;       // stages per exact accumulation group (320 K: 3 x 320 x 127^2 < 2^24)
-constexpr int NACC = 4;         // accumulators: s+t = 2, 3, 4 and s+t >= 5 (all 512 TMEM columns)
+constexpr int GROUP = 8;        // stages per exact accumulation group (256 K: 4 x 256 x 127^2 < 2^24)
+constexpr int NACC = 5;         // accumulators: s+t = 2, 3, 4, 5 and s+t >= 6 (480 TMEM columns)
 constexpr int NTHR = 384;       // warps 0-3: copies, MMA, TMEM allocation; warps 4-11: drain
 constexpr int MAXS = 8;         // slices supported
 constexpr uint64_t WAIT_NS = 2000000000ull;  // a wait gives up after 2 s
 
 // bytes of one packed tile (no-swizzle K-major core matrices, 8 rows x 16 B)
 constexpr int A_TILE = TM * KC * 2;  // 8 KB
-constexpr int B_TILE = TN * KC * 2;  // 8 KB
+constexpr int B_TILE = TN * KC * 2;  // 6 KB
 
 constexpr int NSTAGE = 3;            // pipeline stages when they fit in shared memory
 constexpr int SMEM_LIMIT = 227 * 1024;
@@ -373,9 +374,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
       tc_fence_after();
       const uint32_t sa = smem_u32(smem + st * stage_bytes);
       const uint32_t sb = sa + S * A_TILE;
-      bool fresh[NACC];
-#pragma unroll
-      for (int a = 0; a < NACC; a++) fresh[a] = (c % GROUP == 0);
+      uint32_t fresh = (c % GROUP == 0) ? (1u << NACC) - 1 : 0u;  // accumulators still to overwrite
       for (int s = 0; s < S; s++)
         for (int t = 0; s + t < S; t++) {
           const int a = s + t < NACC - 1 ? s + t : NACC - 1;
@@ -384,8 +383,8 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
             // K step kk covers core-matrix columns 2kk, 2kk+1 (LBO = 128 B apart)
             const uint64_t ad = sdesc(sa + s * A_TILE + kk * 256, 128, (KC / 8) * 128);
             const uint64_t bd = sdesc(sb + t * B_TILE + kk * 256, 128, (KC / 8) * 128);
-            mma_bf16(tcol, ad, bd, idesc, fresh[a] ? 0u : 1u);
-            fresh[a] = false;
+            mma_bf16(tcol, ad, bd, idesc, ((fresh >> a) & 1u) ? 0u : 1u);
+            fresh &= ~(1u << a);
           }
         }
       mma_commit(&empty[st]);
@@ -597,8 +596,9 @@ __global__ void k_pack_src(int64_t n0, int64_t n, const int64_t *prob_of, const 
   const int r = (int)(w - (is_b ? pr.coloff : pr.rowoff));
   const int nkt = pr.Kpad / KC;
   const int rows_pad = is_b ? pr.Npad : pr.Mpad;
+  const int trows = is_b ? TN : TM, tbytes = is_b ? B_TILE : A_TILE;
   char *base = (char *)planes + (is_b ? pr.boff : pr.aoff);
-  const int64_t plane = (int64_t)(rows_pad / TM) * nkt * A_TILE;
+  const int64_t plane = (int64_t)(rows_pad / trows) * nkt * tbytes;
   const bool live = sr.off >= 0 && (sr.flag < 0 || (keep[sr.flag] && (!keep2 || keep2[sr.flag])));
   const double *x = X + (live ? sr.off - shift : 0);
   const double *x2 = (live && sr.off2 >= 0) ? X2 + sr.off2 : nullptr;
@@ -616,7 +616,7 @@ __global__ void k_pack_src(int64_t n0, int64_t n, const int64_t *prob_of, const 
   for (int k = lane; k < pr.Kpad; k += 32) {
     float d[MAXS];
     digits_of(elem(k), m, S, d);
-    const int64_t off = ((int64_t)(r / TM) * nkt + k / KC) * A_TILE + tile_off(r % TM, k % KC);
+    const int64_t off = ((int64_t)(r / trows) * nkt + k / KC) * tbytes + tile_off(r % trows, k % KC);
     for (int s = 0; s < S; s++)
       *(__nv_bfloat16 *)(base + s * plane + off) = __float2bfloat16_rn(d[s] * slice_scale(s));
   }
@@ -635,6 +635,7 @@ __global__ void k_flag_set(int n, const int32_t *idx, uint8_t *flags) {
 // Host and device state of one batched plan.
 struct rix_mx_plan {
   int kind = 0;                          // 0: terms 3+4, 1: term 2, 2: term-4 intermediate Z
+  int S = 6;                             // slices of this plan
   std::vector<int32_t> grp;              // problems [grp[g], grp[g+1])
   std::vector<int32_t> grp_blk;          // memory-plan block of each group (-1: any)
   std::vector<int64_t> tile_seg, row_seg, col_seg;
@@ -669,6 +670,19 @@ struct PlanHost {
   double tflops = 0, fl64 = 0;
 };
 
+}  // namespace
+
+// Slices per plan: the regrouped forms (term 1 as T x C, Z with Kronecker rows)
+// sum many more products of widely ranging size per output than the FP64
+// grouping, so they take one slice more than terms 2-4 (capped at 8).
+int rix_plan_slices(const rix_ctx *ctx, int kind) {
+  return kind >= 2 ? std::min(ctx->mx_S + 1, (int)rixtc::MAXS) : ctx->mx_S;
+}
+
+namespace {
+
+int plan_slices(const rix_ctx *ctx, int kind) { return rix_plan_slices(ctx, kind); }
+
 // Estimated rates on GB300 for the choice between the FP64 kernels and the
 // tensor-core regroupings: about 1 TFLOP/s for the FP64 kernels, about
 // 0.5 PFLOP/s issued for the sliced GEMM.
@@ -680,7 +694,7 @@ constexpr double FP64_RATE = 1.0e12, TC_RATE = 5.0e14;
 rix_status plan_host(rix_ctx *ctx, int kind, const std::vector<int64_t> &ptrZ, PlanHost &h, bool count_only,
                      int64_t *maps_out, int64_t *maxp_out, int64_t *total_out) {
   using namespace rixtc;
-  const int nat = ctx->nat, S = ctx->mx_S;
+  const int nat = ctx->nat, S = plan_slices(ctx, kind);
   auto &row1 = ctx->row1, &row2 = ctx->row2, &row3 = ctx->row3;
   auto find_sorted = [&](const std::vector<int64_t> &keys, int64_t lo, int64_t hi, int64_t key) {
     auto it = std::lower_bound(keys.begin() + lo, keys.begin() + hi, key);
@@ -906,6 +920,7 @@ rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
     if (s != RIX_OK) return s;
     rix_mx_plan *pl = new rix_mx_plan;
     pl->kind = kind;
+    pl->S = plan_slices(ctx, kind);
     (kind == 0 ? ctx->mx34 : kind == 1 ? ctx->mx2 : ctx->mxz) = pl;
     const int64_t budget = group_budget(maxp, total);
     // groups of consecutive problems within the budget and within one memory-plan block
@@ -920,7 +935,7 @@ rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
       }
       Prob &pr = h.probs[p];
       pr.aoff = cur;
-      pr.boff = cur + (int64_t)ctx->mx_S * pr.Mpad * pr.Kpad * 2;
+      pr.boff = cur + (int64_t)pl->S * pr.Mpad * pr.Kpad * 2;
       cur += h.pbytes[p];
     }
     maxgrp = std::max(maxgrp, cur);
@@ -1033,7 +1048,7 @@ struct Operand {
 rix_status run_group(rix_ctx *ctx, const rix_mx_plan *pl, size_t g, const Operand &ra, const Operand &cb,
                      const int64_t *offs, double *out, int64_t oshift, double oscale, cudaStream_t st) {
   using namespace rixtc;
-  const int S = ctx->mx_S;
+  const int S = pl->S;
   const int64_t r0 = pl->row_seg[g], r1 = pl->row_seg[g + 1];
   const int64_t c0 = pl->col_seg[g], c1 = pl->col_seg[g + 1];
   const int64_t t0 = pl->tile_seg[g], t1 = pl->tile_seg[g + 1];
@@ -1241,7 +1256,7 @@ rix_status rix_t1_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
   using rix::key_a;
   using rix::key_b;
   using rix::pair_key;
-  const int nat = ctx->nat, S = ctx->mx_S;
+  const int nat = ctx->nat, S = rix_plan_slices(ctx, 3);
   const int npairs = S * (S + 1) / 2;
   auto &row1 = ctx->row1, &row2 = ctx->row2, &row3 = ctx->row3;
   auto find_sorted = [&](const std::vector<int64_t> &keys, int64_t lo, int64_t hi, int64_t key) {
@@ -1470,7 +1485,7 @@ rix_status rix_mixed_t1(rix_ctx *ctx, int b, int64_t tbase, cudaStream_t st) {
   const rix_t1_plan *pl = ctx->mx1;
   if (!pl) return RIX_OK;
   gemm_attr();
-  const int S = ctx->mx_S;
+  const int S = rix_plan_slices(ctx, 3);
   __nv_bfloat16 *buf = (__nv_bfloat16 *)ctx->d_mx_buf;
   for (size_t g = 0; g + 1 < pl->grp_prob.size(); g++) {
     if (pl->grp_blk[g] != b || pl->grp_prob[g + 1] == pl->grp_prob[g]) continue;
