@@ -118,6 +118,7 @@ typedef struct {
   int32_t launches_build;          /* kernel launches of one rix_build_K (rix_energy adds 3) */
   double flops_term1_tc;           /* mixed mode: the term-1 FLOPs (FP64 grouping) moved to the tensor cores */
   double flops_z_tc;               /* mixed mode: the Z FLOPs (FP64 grouping) moved to the tensor cores */
+  int64_t tz_bytes;                /* the T and Z buffers (part of workspace_bytes) */
 } rix_stats_t;
 
 /* Set up a system: copies the host arrays, builds the pair list on the device

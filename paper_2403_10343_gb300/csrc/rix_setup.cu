@@ -773,6 +773,7 @@ static rix_status build_lists(rix_ctx *ctx) {
   TRY(rix_upload(ctx, &ctx->d_ordX34, ordX34)); ctx->n_ordX34 = ordX34.size();
   TRY(rix_alloc(ctx, &ctx->d_T, maxbuf));
   TRY(rix_alloc(ctx, &ctx->d_Z, maxbuf));
+  ctx->stats.tz_bytes = 2 * maxbuf * (int64_t)sizeof(double);
   if (ctx->opt.precision == RIX_MIXED_BF16) TRY(rix_mixed_plan(ctx, ptrZ));
   if (ctx->opt.verbose) fprintf(stderr, "rix: %d row block(s), T/Z buffers %.3g GB each\n", nblk, maxbuf * 8e-9);
   return RIX_OK;
