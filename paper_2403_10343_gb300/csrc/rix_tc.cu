@@ -31,6 +31,7 @@
 // timeout the kernel records an error and returns.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 
@@ -267,6 +268,7 @@ struct GemmArgs {
   const uint8_t *keepV;
   double oscale;           // scale of the added values (modes 0 and 1)
   int64_t xshift;          // mode 0: X + offK[x] - xshift is the output block
+  int ntiles;              // output tiles of the launch (persistent CTAs loop over them)
 };
 
 // Bits the fixed-point sum needs: products below 2^14, at most Kpad of them in
@@ -279,6 +281,42 @@ __host__ __device__ inline int fixed_point_drop(int Kpad, int S) {
   return bits > 62 ? bits - 62 : 0;
 }
 
+// Operands and sizes of output tile t (dense: t = nt * (Mpad / TM) + mt).
+struct TileInfo {
+  const Prob *pr;
+  const __nv_bfloat16 *gA, *gB;
+  const int *geA, *geB;
+  int mt, nt, Mpad, Npad, Kpad, M, N, drop;
+};
+
+__device__ __forceinline__ TileInfo tile_info(const GemmArgs &g, int t) {
+  TileInfo ti;
+  if (g.tiles) {
+    const int4 tt = g.tiles[t];
+    const Prob *pr = g.probs + tt.x;
+    ti.pr = pr;
+    ti.mt = tt.y;
+    ti.nt = tt.z;
+    ti.gA = (const __nv_bfloat16 *)((const char *)g.A + pr->aoff);
+    ti.gB = (const __nv_bfloat16 *)((const char *)g.B + pr->boff);
+    ti.geA = g.eA + pr->eaoff;
+    ti.geB = g.eB + pr->eboff;
+    ti.Mpad = pr->Mpad; ti.Npad = pr->Npad; ti.Kpad = pr->Kpad; ti.M = pr->M; ti.N = pr->N; ti.drop = pr->drop;
+  } else {
+    const int mtiles = g.Mpad / TM;
+    ti.pr = nullptr;
+    ti.mt = t % mtiles;
+    ti.nt = t / mtiles;
+    ti.gA = g.A; ti.gB = g.B; ti.geA = g.eA; ti.geB = g.eB;
+    ti.Mpad = g.Mpad; ti.Npad = g.Npad; ti.Kpad = g.Kpad; ti.M = g.M; ti.N = g.N; ti.drop = g.drop;
+  }
+  return ti;
+}
+
+// Persistent: CTA b handles tiles b, b + gridDim.x, ...  The shared-memory stage
+// ring and the accumulator barriers run on across tiles, so the copies and the
+// MMAs of a tile overlap the previous tile's epilogue (the drain warps release
+// tensor memory before they convert and scatter their sums).
 __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
   extern __shared__ __align__(1024) uint8_t smem[];
   // layout: [stage][A tiles S][B tiles S], then barriers, then TMEM address
@@ -293,26 +331,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
   int *abort_flag = (int *)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int mt = blockIdx.x, nt = blockIdx.y;
-  const __nv_bfloat16 *gA = g.A, *gB = g.B;
-  const int *geA = g.eA, *geB = g.eB;
-  int Mpad = g.Mpad, Npad = g.Npad, Kpad = g.Kpad, Mrows = g.M, Ncols = g.N, drop = g.drop;
-  const Prob *pr = nullptr;
-  if (g.tiles) {
-    const int4 t = g.tiles[blockIdx.x];
-    pr = g.probs + t.x;
-    mt = t.y;
-    nt = t.z;
-    gA = (const __nv_bfloat16 *)((const char *)g.A + pr->aoff);
-    gB = (const __nv_bfloat16 *)((const char *)g.B + pr->boff);
-    geA = g.eA + pr->eaoff;
-    geB = g.eB + pr->eboff;
-    Mpad = pr->Mpad; Npad = pr->Npad; Kpad = pr->Kpad; Mrows = pr->M; Ncols = pr->N; drop = pr->drop;
-  }
-  const int nk = Kpad / KC;
-  const int ngroups = (nk + GROUP - 1) / GROUP;
-  const int64_t a_tiles = (int64_t)(Mpad / TM) * nk;  // tiles per A plane
-  const int64_t b_tiles = (int64_t)(Npad / TN) * nk;
+  const int ntiles = g.ntiles;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < nst; i++) {
@@ -339,93 +358,117 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ producer
-    for (int c = 0; c < nk; c++) {
-      const int st = c % nst;
-      if (c >= nst && !mbar_wait(&empty[st], ((c / nst) - 1) & 1)) {
-        atomicExch(abort_flag, 1);
-        break;
+    uint32_t cg = 0;  // chunks issued by this CTA
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const TileInfo ti = tile_info(g, t);
+      const int nk = ti.Kpad / KC;
+      const int64_t a_tiles = (int64_t)(ti.Mpad / TM) * nk;  // tiles per A plane
+      const int64_t b_tiles = (int64_t)(ti.Npad / TN) * nk;
+      for (int c = 0; c < nk; c++, cg++) {
+        const int st = cg % nst;
+        if (cg >= (uint32_t)nst && !mbar_wait(&empty[st], ((cg / nst) - 1) & 1)) {
+          atomicExch(abort_flag, 1);
+          break;
+        }
+        if (*(volatile int *)abort_flag) break;
+        uint8_t *sa = smem + st * stage_bytes;
+        uint8_t *sb = sa + S * A_TILE;
+        mbar_expect_tx(&full[st], (uint32_t)stage_bytes);
+        for (int s = 0; s < S; s++) {
+          const char *ga = (const char *)ti.gA + ((int64_t)s * a_tiles + (int64_t)ti.mt * nk + c) * A_TILE;
+          bulk_g2s(sa + s * A_TILE, ga, A_TILE, &full[st]);
+          const char *gb = (const char *)ti.gB + ((int64_t)s * b_tiles + (int64_t)ti.nt * nk + c) * B_TILE;
+          bulk_g2s(sb + s * B_TILE, gb, B_TILE, &full[st]);
+        }
       }
       if (*(volatile int *)abort_flag) break;
-      uint8_t *sa = smem + st * stage_bytes;
-      uint8_t *sb = sa + S * A_TILE;
-      mbar_expect_tx(&full[st], (uint32_t)stage_bytes);
-      for (int s = 0; s < S; s++) {
-        const char *ga = (const char *)gA + ((int64_t)s * a_tiles + (int64_t)mt * nk + c) * A_TILE;
-        bulk_g2s(sa + s * A_TILE, ga, A_TILE, &full[st]);
-        const char *gb = (const char *)gB + ((int64_t)s * b_tiles + (int64_t)nt * nk + c) * B_TILE;
-        bulk_g2s(sb + s * B_TILE, gb, B_TILE, &full[st]);
-      }
     }
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------ MMA issuer
     const uint32_t idesc = idesc_bf16(TM, TN);
-    for (int c = 0; c < nk; c++) {
-      const int st = c % nst;
-      const int grp = c / GROUP;
-      if (c % GROUP == 0 && grp > 0 && !mbar_wait(accempty, (grp - 1) & 1)) {
-        atomicExch(abort_flag, 1);
-        break;
-      }
-      if (!mbar_wait(&full[st], (c / nst) & 1)) {
-        atomicExch(abort_flag, 1);
-        break;
+    uint32_t cg = 0, gg = 0;  // chunks consumed, accumulation groups completed
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const TileInfo ti = tile_info(g, t);
+      const int nk = ti.Kpad / KC;
+      for (int c = 0; c < nk; c++, cg++) {
+        const int st = cg % nst;
+        if (c % GROUP == 0 && gg > 0 && !mbar_wait(accempty, (gg - 1) & 1)) {
+          atomicExch(abort_flag, 1);
+          break;
+        }
+        if (!mbar_wait(&full[st], (cg / nst) & 1)) {
+          atomicExch(abort_flag, 1);
+          break;
+        }
+        if (*(volatile int *)abort_flag) break;
+        tc_fence_after();
+        const uint32_t sa = smem_u32(smem + st * stage_bytes);
+        const uint32_t sb = sa + S * A_TILE;
+        uint32_t fresh = (c % GROUP == 0) ? (1u << NACC) - 1 : 0u;  // accumulators still to overwrite
+        for (int s = 0; s < S; s++)
+          for (int u = 0; s + u < S; u++) {
+            const int a = s + u < NACC - 1 ? s + u : NACC - 1;
+            const uint32_t tcol = tmem + (uint32_t)(a * TN);
+            for (int kk = 0; kk < KC / 16; kk++) {
+              // K step kk covers core-matrix columns 2kk, 2kk+1 (LBO = 128 B apart)
+              const uint64_t ad = sdesc(sa + s * A_TILE + kk * 256, 128, (KC / 8) * 128);
+              const uint64_t bd = sdesc(sb + u * B_TILE + kk * 256, 128, (KC / 8) * 128);
+              mma_bf16(tcol, ad, bd, idesc, ((fresh >> a) & 1u) ? 0u : 1u);
+              fresh &= ~(1u << a);
+            }
+          }
+        mma_commit(&empty[st]);
+        if (c % GROUP == GROUP - 1 || c == nk - 1) {
+          mma_commit(accfull);
+          gg++;
+        }
       }
       if (*(volatile int *)abort_flag) break;
-      tc_fence_after();
-      const uint32_t sa = smem_u32(smem + st * stage_bytes);
-      const uint32_t sb = sa + S * A_TILE;
-      uint32_t fresh = (c % GROUP == 0) ? (1u << NACC) - 1 : 0u;  // accumulators still to overwrite
-      for (int s = 0; s < S; s++)
-        for (int t = 0; s + t < S; t++) {
-          const int a = s + t < NACC - 1 ? s + t : NACC - 1;
-          const uint32_t tcol = tmem + (uint32_t)(a * TN);
-          for (int kk = 0; kk < KC / 16; kk++) {
-            // K step kk covers core-matrix columns 2kk, 2kk+1 (LBO = 128 B apart)
-            const uint64_t ad = sdesc(sa + s * A_TILE + kk * 256, 128, (KC / 8) * 128);
-            const uint64_t bd = sdesc(sb + t * B_TILE + kk * 256, 128, (KC / 8) * 128);
-            mma_bf16(tcol, ad, bd, idesc, ((fresh >> a) & 1u) ? 0u : 1u);
-            fresh &= ~(1u << a);
-          }
-        }
-      mma_commit(&empty[st]);
-      if (c % GROUP == GROUP - 1 || c == nk - 1) mma_commit(accfull);
     }
   } else if (warp >= 4) {
-    // ------------------------------------------------------------ drain and fold
+    // ------------------------------------------------------------ drain, fold, epilogue
     constexpr int HN = TN / 2;           // columns per drain warp
     const int q = warp & 3;              // TMEM lane quadrant (a warp reaches lanes 32 (warp % 4) ..)
     const int h = (warp - 4) >> 2;       // column half
     const int row = q * 32 + lane;       // output row inside the tile
-    // accumulator units -> fixed point: 2^(7(S-1) - drop), exact in FP32
-    const float fscale = __int_as_float((127 + 7 * (S - 1) - drop) << 23);
-    int64_t acc[HN];
-#pragma unroll
-    for (int n = 0; n < HN; n++) acc[n] = 0;
+    uint32_t gg = 0;
     bool ok = true;
-    for (int grp = 0; grp < ngroups; grp++) {
-      if (!mbar_wait(accfull, grp & 1)) {
-        atomicExch(abort_flag, 1);
-        ok = false;
-        break;
-      }
-      tc_fence_after();
-      for (int a = 0; a < nacc; a++) {
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const TileInfo ti = tile_info(g, t);
+      const int nk = ti.Kpad / KC;
+      const int ngroups = (nk + GROUP - 1) / GROUP;
+      const int mt = ti.mt, nt = ti.nt, drop = ti.drop, Ncols = ti.N;
+      const Prob *pr = ti.pr;
+      const int *geA = ti.geA, *geB = ti.geB;
+      // accumulator units -> fixed point: 2^(7(S-1) - drop), exact in FP32
+      const float fscale = __int_as_float((127 + 7 * (S - 1) - drop) << 23);
+      int64_t acc[HN];
 #pragma unroll
-        for (int n0 = 0; n0 < HN; n0 += 16) {
-          uint32_t r[16];
-          tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * TN + h * HN + n0), r);
-          tmem_wait_ld();
-#pragma unroll
-          for (int j = 0; j < 16; j++)
-            acc[n0 + j] += (int64_t)__float2ll_rn(__fmul_rn(__uint_as_float(r[j]), fscale));
+      for (int n = 0; n < HN; n++) acc[n] = 0;
+      for (int grp = 0; grp < ngroups; grp++, gg++) {
+        if (!mbar_wait(accfull, gg & 1)) {
+          atomicExch(abort_flag, 1);
+          ok = false;
+          break;
         }
+        tc_fence_after();
+        for (int a = 0; a < nacc; a++) {
+#pragma unroll
+          for (int n0 = 0; n0 < HN; n0 += 16) {
+            uint32_t r[16];
+            tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * TN + h * HN + n0), r);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 16; j++)
+              acc[n0 + j] += (int64_t)__float2ll_rn(__fmul_rn(__uint_as_float(r[j]), fscale));
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(accempty);  // tensor memory free for the next group (or tile)
       }
-      tc_fence_before();
-      mbar_arrive(accempty);
-    }
-    if (ok) {
+      if (!ok) break;
       const int gr = mt * TM + row;
-      if (gr < Mrows) {
+      if (gr < ti.M) {
         const int er = geA[gr];
         // fully unrolled with predicates so acc[] stays in registers
         if (!pr) {
@@ -501,6 +544,18 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
   }
 }
 
+// CTAs of a persistent launch: one per SM (the kernel's shared memory allows one)
+inline int persistent_grid(int64_t ntiles) {
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+  }
+  return (int)std::min<int64_t>(ntiles, nsm);
+}
+
 }  // namespace rixtc
 
 using namespace rixtc;
@@ -540,7 +595,8 @@ extern "C" rix_status rix_gemm_sliced(const double *A, int64_t lda, const double
              nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   const int smem = smem_bytes(S);
   cudaFuncSetAttribute(k_gemm_sliced, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_gemm_sliced<<<dim3(Mpad / TM, Npad / TN), NTHR, smem, st>>>(g);
+  g.ntiles = (Mpad / TM) * (Npad / TN);
+  k_gemm_sliced<<<persistent_grid(g.ntiles), NTHR, smem, st>>>(g);
   cudaError_t e = cudaGetLastError();
   int herr = 0;
   cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st);
@@ -1067,7 +1123,8 @@ rix_status run_group(rix_ctx *ctx, const rix_mx_plan *pl, size_t g, const Operan
     ga.mode = 0;
     ga.oscale = oscale;
     ga.xshift = oshift;
-    k_gemm_sliced<<<(unsigned)(t1 - t0), NTHR, smem_bytes(S), st>>>(ga);
+    ga.ntiles = (int)(t1 - t0);
+    k_gemm_sliced<<<persistent_grid(t1 - t0), NTHR, smem_bytes(S), st>>>(ga);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -1504,7 +1561,8 @@ rix_status rix_mixed_t1(rix_ctx *ctx, int b, int64_t tbase, cudaStream_t st) {
       GemmArgs ga{buf, buf, pl->d_eA, pl->d_eB, nullptr, 0, 0, 0, 0, 0, 0, S, 1, 0, ctx->d_mx_err,
                   pl->d_tiles + t0, pl->d_probs, pl->d_rowinfo, pl->d_colinfo, nullptr, ctx->d_offK, ctx->d_X,
                   1, pl->d_qinfo, ctx->d_V, ctx->d_keepV, 0.5};
-      k_gemm_sliced<<<(unsigned)(t1 - t0), NTHR, smem_bytes(S), st>>>(ga);
+      ga.ntiles = (int)(t1 - t0);
+      k_gemm_sliced<<<persistent_grid(t1 - t0), NTHR, smem_bytes(S), st>>>(ga);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
