@@ -708,23 +708,28 @@ static rix_status build_lists(rix_ctx *ctx) {
   // block of middle atoms B, with T and Z buffers sized for the largest block.
   std::vector<int64_t> asz(nat);
   for (int a = 0; a < nat; a++) asz[a] = ctx->off2[row2[a + 1]] - ctx->off2[row2[a]];
-  int64_t avail;
+  int64_t avail0;
   {
     size_t fr = 0, to = 0;
     cudaMemGetInfo(&fr, &to);
-    avail = (int64_t)fr - ((int64_t)4 << 30);
+    avail0 = (int64_t)fr - ((int64_t)4 << 30);
     if (ctx->opt.max_workspace_bytes > 0)
-      avail = std::min<int64_t>(avail, ctx->opt.max_workspace_bytes - (int64_t)ctx->dev_bytes);
-    // still to come besides T and Z: the work-item arrays, the mixed-precision
-    // plan (estimate plus 5 %) and a little slack for allocation granularity
+      avail0 = std::min<int64_t>(avail0, ctx->opt.max_workspace_bytes - (int64_t)ctx->dev_bytes);
+    // still to come besides T and Z: the work-item arrays and a little slack
     const int64_t items = (int64_t)(itT.size() + itZ.size() + itU.size()) * (int64_t)sizeof(int2) +
                           (int64_t)(ordX12.size() + ordX34.size()) * (int64_t)sizeof(int32_t);
-    avail -= items + ((int64_t)64 << 10);
-    if (ctx->opt.precision == RIX_MIXED_BF16) avail -= rix_mixed_bytes(ctx, ptrZ) / 20 * 21;
+    avail0 -= items + ((int64_t)64 << 10);
   }
-  const int64_t per_buf = std::max<int64_t>(0, avail / 2 / (int64_t)sizeof(double));
-  ctx->blk_atom.assign(1, 0);
-  {
+  // blocks for a T/Z budget; in mixed precision the plans' size depends on the
+  // blocks (their problems split by block), so the split is redone until the
+  // plans fit beside the buffers
+  const bool mixed = ctx->opt.precision == RIX_MIXED_BF16;
+  ctx->nblk = 1;
+  ctx->blk_atom.clear();
+  int64_t mx_est = mixed ? rix_mixed_bytes(ctx, ptrZ) : 0;
+  for (int iter = 0;; iter++) {
+    const int64_t per_buf = std::max<int64_t>(0, (avail0 - mx_est) / 2 / (int64_t)sizeof(double));
+    ctx->blk_atom.assign(1, 0);
     int64_t cur = 0;
     for (int a = 0; a < nat; a++) {
       if (asz[a] > per_buf) {
@@ -738,8 +743,13 @@ static rix_status build_lists(rix_ctx *ctx) {
       cur += asz[a];
     }
     ctx->blk_atom.push_back(nat);
+    ctx->nblk = (int)ctx->blk_atom.size() - 1;
+    if (!mixed || iter == 4) break;
+    const int64_t need = rix_mixed_bytes(ctx, ptrZ);
+    if (need <= mx_est) break;
+    mx_est = need + need / 50;
   }
-  const int nblk = (int)ctx->blk_atom.size() - 1;
+  const int nblk = ctx->nblk;
   std::vector<int> blk_of(nat);
   int64_t maxbuf = 0;
   ctx->blk_base.assign(nblk, 0);

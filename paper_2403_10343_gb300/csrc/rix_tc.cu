@@ -11,24 +11,24 @@
 //
 // and every slice product A_s B_t is a sum of integers below 2^14 per term.
 // Slice s is stored pre-scaled by 2^-7(s-1) (exact in BF16), so a product
-// carries its own power of two.  Five FP32 accumulators in tensor memory
-// take the products with s+t = 2, 3, 4, 5 and s+t >= 6: the first four hold
-// integers (times 2^-7(s+t-2)) whose sums over a group of 256 K values stay
-// below 2^24, so the tensor cores accumulate them exactly; the fifth holds
-// terms at least 2^-28 below the leading one, where the tensor cores' FP32
-// accumulation costs about 2^-46 of the row x column x K scale.  After each
+// carries its own power of two.  Six FP32 accumulators in tensor memory take
+// the products with s+t = 2, 3, 4, 5, 6 and s+t >= 7: the first five hold
+// integers (times 2^-7(s+t-2)) whose sums over a group of 192 K values stay
+// below 2^24, so the tensor cores accumulate them exactly; the sixth holds
+// terms at least 2^-35 below the leading one, where the tensor cores' FP32
+// accumulation costs about 2^-53 of the row x column x K scale.  After each
 // group the accumulators are folded into a 64-bit fixed-point sum per output
 // element, and the FP64 result is formed once at the end.  The error is the
 // truncation of the operands after S digits (about 2^-7S of the row/column
-// scale), the dropped terms s+t > S+1 and the rounding of the fifth
+// scale), the dropped terms s+t > S+1 and the rounding of the sixth
 // accumulator.
 //
-// Kernel layout: one CTA per 128 x 96 output tile; warp 0 issues the bulk
-// copies (cp.async.bulk, mbarrier completion), one thread of warp 1 issues
-// tcgen05.mma (A and B from shared memory, accumulators in tensor memory),
-// warps 4-11 drain tensor memory (tcgen05.ld, two warps per 32-lane quadrant,
-// 48 columns each) into the fixed-point sums.  Every wait is bounded; on a
-// timeout the kernel records an error and returns.
+// Kernel layout: persistent CTAs over 128 x 80 output tiles; warp 0 issues the
+// bulk copies (cp.async.bulk, mbarrier completion), one thread of warp 1
+// issues tcgen05.mma (A and B from shared memory, accumulators in tensor
+// memory), warps 4-11 drain tensor memory (tcgen05.ld, two warps per 32-lane
+// quadrant, 40 columns each) into the fixed-point sums.  Every wait is
+// bounded; on a timeout the kernel records an error and returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -40,17 +40,17 @@
 namespace rixtc {
 
 constexpr int TM = 128;         // output rows per tile (one TMEM lane each)
-constexpr int TN = 96;          // output columns per tile
+constexpr int TN = 80;          // output columns per tile
 constexpr int KC = 32;          // K per pipeline stage
-constexpr int GROUP = 8;        // stages per exact accumulation group (256 K: 4 x 256 x 127^2 < 2^24)
-constexpr int NACC = 5;         // accumulators: s+t = 2, 3, 4, 5 and s+t >= 6 (480 TMEM columns)
+constexpr int GROUP = 6;        // stages per exact accumulation group (192 K: 5 x 192 x 127^2 < 2^24)
+constexpr int NACC = 6;         // accumulators: s+t = 2 .. 6 and s+t >= 7 (480 TMEM columns)
 constexpr int NTHR = 384;       // warps 0-3: copies, MMA, TMEM allocation; warps 4-11: drain
 constexpr int MAXS = 8;         // slices supported
 constexpr uint64_t WAIT_NS = 2000000000ull;  // a wait gives up after 2 s
 
 // bytes of one packed tile (no-swizzle K-major core matrices, 8 rows x 16 B)
 constexpr int A_TILE = TM * KC * 2;  // 8 KB
-constexpr int B_TILE = TN * KC * 2;  // 6 KB
+constexpr int B_TILE = TN * KC * 2;  // 5 KB
 
 constexpr int NSTAGE = 3;            // pipeline stages when they fit in shared memory
 constexpr int SMEM_LIMIT = 227 * 1024;
@@ -142,6 +142,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -452,15 +458,25 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
           break;
         }
         tc_fence_after();
+        static_assert(HN % 8 == 0, "drain columns come in groups of 8");
         for (int a = 0; a < nacc; a++) {
+          const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * TN + h * HN);
 #pragma unroll
-          for (int n0 = 0; n0 < HN; n0 += 16) {
+          for (int n0 = 0; n0 + 16 <= HN; n0 += 16) {
             uint32_t r[16];
-            tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * TN + h * HN + n0), r);
+            tmem_ld16(ta + n0, r);
             tmem_wait_ld();
 #pragma unroll
             for (int j = 0; j < 16; j++)
               acc[n0 + j] += (int64_t)__float2ll_rn(__fmul_rn(__uint_as_float(r[j]), fscale));
+          }
+          if (HN % 16) {
+            uint32_t r[8];
+            tmem_ld8(ta + (HN / 16) * 16, r);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+              acc[(HN / 16) * 16 + j] += (int64_t)__float2ll_rn(__fmul_rn(__uint_as_float(r[j]), fscale));
           }
         }
         tc_fence_before();
@@ -781,9 +797,11 @@ rix_status plan_host(rix_ctx *ctx, int kind, const std::vector<int64_t> &ptrZ, P
       }
     }
   }
-  const int nblk = (kind == 2 && !count_only) ? ctx->nblk : 1;
+  // the row blocks of the memory plan (one block while it is not known yet)
+  const bool have_blocks = (int)ctx->blk_atom.size() == ctx->nblk + 1;
+  const int nblk = (kind == 2 && have_blocks) ? ctx->nblk : 1;
   std::vector<int32_t> blk_of(nat, 0);
-  if (kind == 2 && !count_only)
+  if (kind == 2 && have_blocks)
     for (int b = 0; b < nblk; b++)
       for (int a = ctx->blk_atom[b]; a < ctx->blk_atom[b + 1]; a++) blk_of[a] = b;
   std::vector<int64_t> qs, zs;
@@ -1345,10 +1363,11 @@ rix_status rix_t1_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
       fl64_tc += f64;
     }
   }
-  // the memory plan is not known yet when only counting: treat all rows as one block
-  const int nblk = count_only ? 1 : ctx->nblk;
+  // the row blocks of the memory plan (one block while it is not known yet)
+  const bool have_blocks = (int)ctx->blk_atom.size() == ctx->nblk + 1;
+  const int nblk = have_blocks ? ctx->nblk : 1;
   std::vector<int32_t> blk_of(nat, 0);
-  if (!count_only)
+  if (have_blocks)
     for (int b = 0; b < nblk; b++)
       for (int a = ctx->blk_atom[b]; a < ctx->blk_atom[b + 1]; a++) blk_of[a] = b;
   std::vector<Prob> probs;
