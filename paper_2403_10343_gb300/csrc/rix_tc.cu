@@ -975,7 +975,7 @@ int64_t rix_mixed_bytes(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
     maps += m + (kind == 2 ? ctx->nat : 0);
     buf = std::max(buf, group_budget(maxp, total));
   }
-  return maps + buf + ((int64_t)64 << 20);
+  return maps + buf + (maps + buf) / 50 + ((int64_t)1 << 20);
 }
 
 rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
