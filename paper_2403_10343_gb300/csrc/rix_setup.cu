@@ -747,7 +747,7 @@ static rix_status build_lists(rix_ctx *ctx) {
     if (!mixed || iter == 4) break;
     const int64_t need = rix_mixed_bytes(ctx, ptrZ);
     if (need <= mx_est) break;
-    mx_est = need + need / 50;
+    mx_est = need;
   }
   const int nblk = ctx->nblk;
   std::vector<int> blk_of(nat);

@@ -975,7 +975,8 @@ int64_t rix_mixed_bytes(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
     maps += m + (kind == 2 ? ctx->nat : 0);
     buf = std::max(buf, group_budget(maxp, total));
   }
-  return maps + buf + (maps + buf) / 50 + ((int64_t)1 << 20);
+  // the count is exact for the maps and an upper bound for the slice buffer
+  return maps + buf + 4 * (int64_t)ctx->nat + ((int64_t)64 << 10);
 }
 
 rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {

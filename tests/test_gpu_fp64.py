@@ -235,11 +235,12 @@ def test_row_blocked_memory_plan(case, precision):
     assert full.stats()["n_row_blocks"] == 1
     full.close()
     ktol, etol = (K_TOL, E_TOL * abs(E_ref)) if precision == "fp64" else (1e-8, 1e-6)
-    seen = set()
-    for frac in (0.2, 0.35, 0.5, 0.65):   # take that share of the T and Z buffers away
+    seen, why = set(), []
+    for frac in (0.2, 0.35, 0.5, 0.65, 0.8):   # take that share of the T and Z buffers away
         try:
             ex, keys, K, E, _ = run_gpu(s, pk, max_workspace_bytes=int(w0 - frac * tz), precision=precision)
-        except RixError:
+        except RixError as err:
+            why.append(str(err))
             continue
         nb = ex.stats()["n_row_blocks"]
         seen.add(nb)
@@ -247,7 +248,7 @@ def test_row_blocked_memory_plan(case, precision):
         assert rel(K, K_ref) < ktol
         assert abs(E - E_ref) < etol
         ex.close()
-    assert max(seen) >= 2, seen
+    assert seen and max(seen) >= 2, (seen, w0, tz, why)
 
 
 def test_set_CV_from_host_arrays():
