@@ -85,19 +85,24 @@ __device__ __forceinline__ uint64_t now_ns() {
   return t;
 }
 
-// bounded wait for the phase with the given parity; returns false after WAIT_NS
+// bounded wait for the phase with the given parity; returns false after WAIT_NS.
+// try_wait may suspend the thread for up to SUSPEND_NS until the phase completes,
+// so waiting warps leave the issue slots to the copy and MMA threads.
+constexpr uint32_t SUSPEND_NS = 20000;
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   const uint32_t a = smem_u32(bar);
-  const uint64_t t0 = now_ns();
+  uint64_t t0 = 0;
   while (true) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(a), "r"(parity)
+        : "r"(a), "r"(parity), "r"(SUSPEND_NS)
         : "memory");
     if (ok) return true;
-    if (now_ns() - t0 > WAIT_NS) return false;
+    const uint64_t t = now_ns();
+    if (!t0) t0 = t;
+    else if (t - t0 > WAIT_NS) return false;
   }
 }
 
