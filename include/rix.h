@@ -101,6 +101,8 @@ typedef struct {
   int32_t profile;                 /* 1 = record a CUDA event after every stage of rix_build_K
                                       (skipped while the stream is being captured into a graph) */
   int32_t backward;                /* 1 = also plan rix_backward (extra product lists) */
+  int32_t block_atoms;             /* > 0: row blocks of at most this many atoms (the paper's manual
+                                      Fock-matrix block size); 0 = blocks only where memory requires */
 } rix_options;
 
 typedef struct {

@@ -736,7 +736,8 @@ static rix_status build_lists(rix_ctx *ctx) {
         ctx->last_error = "workspace too small for the intermediates of one atom";
         return RIX_ENOMEM;
       }
-      if (cur + asz[a] > per_buf) {
+      const bool full = ctx->opt.block_atoms > 0 && a - ctx->blk_atom.back() >= ctx->opt.block_atoms;
+      if (cur + asz[a] > per_buf || full) {
         ctx->blk_atom.push_back(a);
         cur = 0;
       }

@@ -35,7 +35,7 @@ class _System(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("n_slices", ctypes.c_int32),
                 ("max_workspace_bytes", ctypes.c_int64), ("verbose", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("backward", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("backward", ctypes.c_int32), ("block_atoms", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -120,7 +120,8 @@ def _dptr(t, name, dtype_size=8):
 
 
 def setup(xyz_bohr, species, nbas, naux, cell_bohr=None, cutoff_bohr=0.0, screen_tau=0.0,
-          precision="fp64", n_slices=0, max_workspace_bytes=0, verbose=0, profile=0, backward=0):
+          precision="fp64", n_slices=0, max_workspace_bytes=0, verbose=0, profile=0, backward=0,
+          block_atoms=0):
     """rix_setup: returns an opaque context handle (int)."""
     lib = load()
     keep = [np.ascontiguousarray(xyz_bohr, dtype=np.float64), np.ascontiguousarray(species, dtype=np.int32),
@@ -130,7 +131,8 @@ def setup(xyz_bohr, species, nbas, naux, cell_bohr=None, cutoff_bohr=0.0, screen
                    keep[3].ctypes.data, None if cell is None else cell.ctypes.data,
                    float(cutoff_bohr), float(screen_tau))
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    opt = _Options(prec, int(n_slices), int(max_workspace_bytes), int(verbose), int(profile), int(backward))
+    opt = _Options(prec, int(n_slices), int(max_workspace_bytes), int(verbose), int(profile), int(backward),
+                   int(block_atoms))
     h = ctypes.c_void_p()
     _check(lib.rix_setup(ctypes.byref(sysd), ctypes.byref(opt), ctypes.byref(h)))
     return h.value
@@ -245,9 +247,10 @@ class Exchange:
     """Convenience owner of one rix context plus its device-resident C and V."""
 
     def __init__(self, xyz_bohr, species, nbas, naux, cell_bohr=None, cutoff_bohr=0.0, screen_tau=0.0,
-                 precision="fp64", n_slices=0, max_workspace_bytes=0, verbose=0, profile=0, backward=0):
+                 precision="fp64", n_slices=0, max_workspace_bytes=0, verbose=0, profile=0, backward=0,
+          block_atoms=0):
         self.ctx = setup(xyz_bohr, species, nbas, naux, cell_bohr, cutoff_bohr, screen_tau, precision,
-                         n_slices, max_workspace_bytes, verbose, profile, backward)
+                         n_slices, max_workspace_bytes, verbose, profile, backward, block_atoms)
         self.c_elems, self.v_elems, self.d_elems, self.k_elems = layout_sizes(self.ctx)
 
     @classmethod

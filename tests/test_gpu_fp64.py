@@ -221,9 +221,29 @@ def test_pair_lists_of_all_workloads():
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("case", ["cluster24", "pbc2"])
-def test_row_blocked_memory_plan(case, precision):
-    """A workspace too small for T and Z forces the build into row blocks; results are unchanged
-    (in mixed precision the tensor-core problems are then split by block as well)."""
+def test_row_blocks_by_atom_count(case, precision):
+    """Row blocks of at most N atoms (the manual block size): results are unchanged, in mixed
+    precision with the tensor-core problems split by block."""
+    if case == "cluster24":
+        s = ri.config(0)
+    else:
+        s = _small_waters([[1.0, 1.2, 0.8], [3.9, 3.1, 3.3]], 11, side=6.0, cut=4.0)
+    pk = ri.generate(s)
+    kk, K_ref, E_ref, _ = exchange(s, pk)
+    ktol, etol = (K_TOL, E_TOL * abs(E_ref)) if precision == "fp64" else (1e-8, 1e-6)
+    for nb_atoms in (5, 2):
+        ex, keys, K, E, _ = run_gpu(s, pk, block_atoms=nb_atoms, precision=precision)
+        assert ex.stats()["n_row_blocks"] == -(-s.n_atoms // nb_atoms)
+        assert np.array_equal(keys, kk)
+        assert rel(K, K_ref) < ktol
+        assert abs(E - E_ref) < etol
+        ex.close()
+
+
+@pytest.mark.parametrize("case", ["cluster24", "pbc2"])
+def test_row_blocked_memory_plan(case):
+    """A workspace too small for T and Z forces the build into row blocks; results are unchanged."""
+    precision = "fp64"
     if case == "cluster24":
         s = ri.config(0)
     else:

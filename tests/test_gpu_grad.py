@@ -157,6 +157,24 @@ def test_autograd_function():
     assert E.item() < 0
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_backward_blocks_by_atom_count(precision):
+    """Adjoint with row blocks of at most 5 atoms equals the single-block adjoint."""
+    s = _small_pbc(seed=11, side=6.0, cut=4.0, nmol=2)
+    pk = ri.generate(s)
+    D = _dev(pk.D)
+    out = []
+    for nb_atoms in (0, 2):
+        ex = Exchange.from_system(s, backward=1, precision=precision, block_atoms=nb_atoms)
+        ex.set_CV(_dev(pk.C), _dev(pk.V))
+        assert ex.stats()["n_row_blocks"] == (1 if nb_atoms == 0 else 3)
+        out.append([x.cpu().numpy() for x in ex.backward(D, 1.0)])
+        ex.close()
+    tol = 1e-13 if precision == "fp64" else 1e-9
+    for g, r in zip(out[1], out[0]):
+        assert np.linalg.norm(g - r) <= tol * np.linalg.norm(r)
+
+
 @pytest.mark.parametrize("case", ["cluster24", "pbc2"])
 def test_backward_row_blocked_plan(case):
     """A workspace too small for T and Z splits the adjoint into row blocks
