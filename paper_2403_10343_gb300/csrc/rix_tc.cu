@@ -659,46 +659,90 @@ struct Src {
   int32_t outer, inner_st, inner_n, flag;
 };
 
-// One warp per packed row/column (rows/columns [n0, n0 + n) of the plan's
-// lists): exponent of its largest |x|, then all Kpad digit positions of every
-// slice (zeros past K), so a reused buffer needs no clearing.
-__global__ void k_pack_src(int64_t n0, int64_t n, const int64_t *prob_of, const Prob *probs, const Src *src,
-                           const double *__restrict__ X, int64_t shift, const double *__restrict__ X2,
-                           const uint8_t *keep, const uint8_t *keep2, int S, int is_b, __nv_bfloat16 *planes,
-                           int *e) {
+// ---------------------------------------------------------------- slicing in two passes
+// Pass 1 (one warp per packed row/column): the exponent of its largest |x|.
+// Pass 2 (one warp per 8 packed rows): lane -> row (lane & 7) and 8 consecutive
+// K values, so each warp writes whole core-matrix rows (16 B per slice, 256 B
+// contiguous per warp and slice).  The accessor gives element k of packed row w.
+template <class Acc>
+__global__ void k_slice_exp(int64_t n0, int64_t n, Acc acc, int *e) {
   const int64_t w = n0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (w >= n0 + n) return;
-  const Prob pr = probs[prob_of[w]];
-  const Src sr = src[w];
-  const int r = (int)(w - (is_b ? pr.coloff : pr.rowoff));
-  const int nkt = pr.Kpad / KC;
-  const int rows_pad = is_b ? pr.Npad : pr.Mpad;
-  const int trows = is_b ? TN : TM, tbytes = is_b ? B_TILE : A_TILE;
-  char *base = (char *)planes + (is_b ? pr.boff : pr.aoff);
-  const int64_t plane = (int64_t)(rows_pad / trows) * nkt * tbytes;
-  const bool live = sr.off >= 0 && (sr.flag < 0 || (keep[sr.flag] && (!keep2 || keep2[sr.flag])));
-  const double *x = X + (live ? sr.off - shift : 0);
-  const double *x2 = (live && sr.off2 >= 0) ? X2 + sr.off2 : nullptr;
-  const int Kt = pr.pad_;  // true K of the problem; positions Kt..Kpad get zero digits
-  auto elem = [&](int k) -> double {
-    if (!live || k >= Kt) return 0.0;
-    const int o = k / sr.inner_n, in = k - o * sr.inner_n;
-    const double v = x[(int64_t)o * sr.outer + (int64_t)in * sr.inner_st];
-    return x2 ? v * x2[in] : v;
-  };
+  const typename Acc::Row R = acc.row(w);
   int m = -2000;
-  for (int k = lane; k < Kt; k += 32) m = max(m, exp_of(fabs(elem(k))));
+  for (int k = lane; k < R.pr.Kpad; k += 32) m = max(m, exp_of(fabs(acc.at(R, k))));
   for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (lane == 0) e[(is_b ? pr.eboff : pr.eaoff) + r] = m;
-  for (int k = lane; k < pr.Kpad; k += 32) {
-    float d[MAXS];
-    digits_of(elem(k), m, S, d);
-    const int64_t off = ((int64_t)(r / trows) * nkt + k / KC) * tbytes + tile_off(r % trows, k % KC);
-    for (int s = 0; s < S; s++)
-      *(__nv_bfloat16 *)(base + s * plane + off) = __float2bfloat16_rn(d[s] * slice_scale(s));
+  if (lane == 0) e[(acc.is_b ? R.pr.eboff : R.pr.eaoff) + R.r] = m;
+}
+
+template <class Acc>
+__global__ void k_slice_dig(int64_t n0, int64_t n, Acc acc, int S, __nv_bfloat16 *planes, const int *e) {
+  const int64_t g8 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g8 * 8 >= n) return;  // n is a multiple of 8 (problems pad to whole tiles)
+  const int64_t w = n0 + g8 * 8 + (lane & 7);
+  const typename Acc::Row R = acc.row(w);
+  const int m = e[(acc.is_b ? R.pr.eboff : R.pr.eaoff) + R.r];
+  const int trows = acc.is_b ? TN : TM, tbytes = acc.is_b ? B_TILE : A_TILE;
+  const int rows_pad = acc.is_b ? R.pr.Npad : R.pr.Mpad;
+  const int nkt = R.pr.Kpad / KC;
+  char *base = (char *)planes + (acc.is_b ? R.pr.boff : R.pr.aoff);
+  const int64_t plane = (int64_t)(rows_pad / trows) * nkt * tbytes;
+  const int rt = R.r / trows, rr = R.r % trows;
+  for (int k0 = (lane >> 3) * 8; k0 < R.pr.Kpad; k0 += 32) {
+    uint32_t pk[MAXS][4];
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      float d0[MAXS], d1[MAXS];
+      digits_of(acc.at(R, k0 + j), m, S, d0);
+      digits_of(acc.at(R, k0 + j + 1), m, S, d1);
+#pragma unroll
+      for (int s2 = 0; s2 < MAXS; s2++) {
+        if (s2 < S) {
+          const __nv_bfloat162 h = __floats2bfloat162_rn(d0[s2] * slice_scale(s2), d1[s2] * slice_scale(s2));
+          pk[s2][j >> 1] = *reinterpret_cast<const uint32_t *>(&h);
+        }
+      }
+    }
+    const int64_t off = ((int64_t)rt * nkt + k0 / KC) * tbytes + tile_off(rr, k0 % KC);
+#pragma unroll
+    for (int s2 = 0; s2 < MAXS; s2++)
+      if (s2 < S) *reinterpret_cast<uint4 *>(base + s2 * plane + off) = make_uint4(pk[s2][0], pk[s2][1], pk[s2][2], pk[s2][3]);
   }
 }
+
+// element access of the generic plans (Src records)
+struct SrcAcc {
+  const int64_t *prob_of;
+  const Prob *probs;
+  const Src *src;
+  const double *X;
+  int64_t shift;
+  const double *X2;
+  const uint8_t *keep, *keep2;
+  int is_b;
+  struct Row {
+    Prob pr;
+    Src sr;
+    int r;
+    bool live;
+  };
+  __device__ Row row(int64_t w) const {
+    Row R;
+    R.pr = probs[prob_of[w]];
+    R.sr = src[w];
+    R.r = (int)(w - (is_b ? R.pr.coloff : R.pr.rowoff));
+    R.live = R.sr.off >= 0 && (R.sr.flag < 0 || (keep[R.sr.flag] && (!keep2 || keep2[R.sr.flag])));
+    return R;
+  }
+  __device__ double at(const Row &R, int k) const {
+    if (!R.live || k >= R.pr.pad_) return 0.0;
+    const int o = k / R.sr.inner_n, in = k - o * R.sr.inner_n;
+    const double v = X[R.sr.off - shift + (int64_t)o * R.sr.outer + (int64_t)in * R.sr.inner_st];
+    return R.sr.off2 >= 0 ? v * X2[R.sr.off2 + in] : v;
+  }
+};
 
 __global__ void k_flag_set(int n, const int32_t *idx, uint8_t *flags) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1134,14 +1178,16 @@ rix_status run_group(rix_ctx *ctx, const rix_mx_plan *pl, size_t g, const Operan
   const int64_t c0 = pl->col_seg[g], c1 = pl->col_seg[g + 1];
   const int64_t t0 = pl->tile_seg[g], t1 = pl->tile_seg[g + 1];
   __nv_bfloat16 *buf = (__nv_bfloat16 *)ctx->d_mx_buf;
-  if (r1 > r0)
-    k_pack_src<<<(unsigned)(((r1 - r0) * 32 + 255) / 256), 256, 0, st>>>(
-        r0, r1 - r0, pl->d_rowprob, pl->d_probs, pl->d_rowsrc, ra.x, ra.shift, ra.x2, ra.keep, ra.keep2, S, 0,
-        buf, pl->d_eA);
-  if (c1 > c0)
-    k_pack_src<<<(unsigned)(((c1 - c0) * 32 + 255) / 256), 256, 0, st>>>(
-        c0, c1 - c0, pl->d_colprob, pl->d_probs, pl->d_colsrc, cb.x, cb.shift, cb.x2, cb.keep, cb.keep2, S, 1,
-        buf, pl->d_eB);
+  if (r1 > r0) {
+    const SrcAcc a{pl->d_rowprob, pl->d_probs, pl->d_rowsrc, ra.x, ra.shift, ra.x2, ra.keep, ra.keep2, 0};
+    k_slice_exp<<<(unsigned)(((r1 - r0) * 32 + 255) / 256), 256, 0, st>>>(r0, r1 - r0, a, pl->d_eA);
+    k_slice_dig<<<(unsigned)(((r1 - r0) / 8 * 32 + 255) / 256), 256, 0, st>>>(r0, r1 - r0, a, S, buf, pl->d_eA);
+  }
+  if (c1 > c0) {
+    const SrcAcc b{pl->d_colprob, pl->d_probs, pl->d_colsrc, cb.x, cb.shift, cb.x2, cb.keep, cb.keep2, 1};
+    k_slice_exp<<<(unsigned)(((c1 - c0) * 32 + 255) / 256), 256, 0, st>>>(c0, c1 - c0, b, pl->d_eB);
+    k_slice_dig<<<(unsigned)(((c1 - c0) / 8 * 32 + 255) / 256), 256, 0, st>>>(c0, c1 - c0, b, S, buf, pl->d_eB);
+  }
   if (t1 > t0) {
     GemmArgs ga{buf, buf, pl->d_eA, pl->d_eB, nullptr, 0, 0, 0, 0, 0, 0, S, 1, 0, ctx->d_mx_err,
                 pl->d_tiles + t0, pl->d_probs, pl->d_rowinfo, pl->d_colinfo, pl->d_xmap, offs, out};
@@ -1235,84 +1281,88 @@ struct T1Ext {
 };
 
 // rows: element (q, P, i ; g, k) = T(A'_q, G'_g)[P][i][k]
-__global__ void k_pack_t1_rows(int64_t n0, int64_t n, const int64_t *prob_of, const Prob *probs,
-                               const T1Ext *ext, const int2 *rowinfo, const QInfo *qinfo, const int4 *kmap,
-                               const int64_t *segT, const double *__restrict__ T, int64_t tbase, int S,
-                               __nv_bfloat16 *planes, int *e) {
-  const int64_t w = n0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (w >= n0 + n) return;
-  const int64_t pi = prob_of[w];
-  const Prob pr = probs[pi];
-  const T1Ext ex = ext[pi];
-  const int r = (int)(w - pr.rowoff);
-  const int2 ri = rowinfo[w];
-  const int nkt = pr.Kpad / KC;
-  char *base = (char *)planes + pr.aoff;
-  const int64_t plane = (int64_t)(pr.Mpad / TM) * nkt * A_TILE;
-  int P = 0, i = 0, nbA = 1;
-  const int64_t *seg = nullptr;
-  if (ri.x >= 0) {
-    nbA = qinfo[pr.xoff + ri.x].nbA;
-    P = ri.y / nbA;
-    i = ri.y - P * nbA;
-    seg = segT + ex.segoff + (int64_t)ri.x * ex.ng;
-  }
-  auto elem = [&](int kk) -> double {
-    if (!seg) return 0.0;
-    const int4 km = kmap[ex.koff + kk];
-    if (km.x < 0) return 0.0;
-    const int64_t so = seg[km.x];
-    if (so < 0) return 0.0;
-    return T[so - tbase + ((int64_t)P * nbA + i) * km.z + km.y];
+struct T1RowAcc {
+  const int64_t *prob_of;
+  const Prob *probs;
+  const T1Ext *ext;
+  const int2 *rowinfo;
+  const QInfo *qinfo;
+  const int4 *kmap;
+  const int64_t *segT;
+  const double *T;
+  int64_t tbase;
+  static constexpr int is_b = 0;
+  struct Row {
+    Prob pr;
+    int64_t koff;
+    const int64_t *seg;
+    int r, P, i, nbA;
   };
-  int m = -2000;
-  for (int k = lane; k < pr.Kpad; k += 32) m = max(m, exp_of(fabs(elem(k))));
-  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (lane == 0) e[pr.eaoff + r] = m;
-  for (int k = lane; k < pr.Kpad; k += 32) {
-    float d[MAXS];
-    digits_of(elem(k), m, S, d);
-    const int64_t off = ((int64_t)(r / TM) * nkt + k / KC) * A_TILE + tile_off(r % TM, k % KC);
-    for (int s = 0; s < S; s++)
-      *(__nv_bfloat16 *)(base + s * plane + off) = __float2bfloat16_rn(d[s] * slice_scale(s));
+  __device__ Row row(int64_t w) const {
+    Row R;
+    const int64_t pi = prob_of[w];
+    R.pr = probs[pi];
+    const T1Ext ex = ext[pi];
+    R.koff = ex.koff;
+    R.r = (int)(w - R.pr.rowoff);
+    const int2 ri = rowinfo[w];
+    R.seg = nullptr;
+    R.P = R.i = 0;
+    R.nbA = 1;
+    if (ri.x >= 0) {
+      R.nbA = qinfo[R.pr.xoff + ri.x].nbA;
+      R.P = ri.y / R.nbA;
+      R.i = ri.y - R.P * R.nbA;
+      R.seg = segT + ex.segoff + (int64_t)ri.x * ex.ng;
+    }
+    return R;
   }
-}
+  __device__ double at(const Row &R, int kk) const {
+    if (!R.seg) return 0.0;
+    const int4 km = kmap[R.koff + kk];
+    if (km.x < 0) return 0.0;
+    const int64_t so = R.seg[km.x];
+    if (so < 0) return 0.0;
+    return T[so - tbase + ((int64_t)R.P * R.nbA + R.i) * km.z + km.y];
+  }
+};
 
 // columns: element (l, Q ; g, k) = C(G'_g, E')[Q on E'][k][l]
-__global__ void k_pack_t1_cols(int64_t n0, int64_t n, const int64_t *prob_of, const Prob *probs,
-                               const T1Ext *ext, const int4 *colinfo, const int4 *kmap, const int64_t *segC,
-                               const int32_t *gpair, const uint8_t *keepC, const double *__restrict__ C, int S,
-                               __nv_bfloat16 *planes, int *e) {
-  const int64_t w = n0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (w >= n0 + n) return;
-  const int64_t pi = prob_of[w];
-  const Prob pr = probs[pi];
-  const T1Ext ex = ext[pi];
-  const int c = (int)(w - pr.coloff);
-  const int4 ci = colinfo[w];  // (l, Q, nbE, naE)
-  const int nkt = pr.Kpad / KC;
-  char *base = (char *)planes + pr.boff;
-  const int64_t plane = (int64_t)(pr.Npad / TN) * nkt * B_TILE;
-  auto elem = [&](int kk) -> double {
-    if (ci.x < 0) return 0.0;
-    const int4 km = kmap[ex.koff + kk];
-    if (km.x < 0 || !keepC[gpair[ex.goff + km.x]]) return 0.0;
-    return C[segC[ex.goff + km.x] + ((int64_t)ci.y * km.z + km.y) * ci.z + ci.x];
+struct T1ColAcc {
+  const int64_t *prob_of;
+  const Prob *probs;
+  const T1Ext *ext;
+  const int4 *colinfo;
+  const int4 *kmap;
+  const int64_t *segC;
+  const int32_t *gpair;
+  const uint8_t *keepC;
+  const double *C;
+  static constexpr int is_b = 1;
+  struct Row {
+    Prob pr;
+    int64_t koff, goff;
+    int4 ci;
+    int r;
   };
-  int m = -2000;
-  for (int k = lane; k < pr.Kpad; k += 32) m = max(m, exp_of(fabs(elem(k))));
-  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (lane == 0) e[pr.eboff + c] = m;
-  for (int k = lane; k < pr.Kpad; k += 32) {
-    float d[MAXS];
-    digits_of(elem(k), m, S, d);
-    const int64_t off = ((int64_t)(c / TN) * nkt + k / KC) * B_TILE + tile_off(c % TN, k % KC);
-    for (int s = 0; s < S; s++)
-      *(__nv_bfloat16 *)(base + s * plane + off) = __float2bfloat16_rn(d[s] * slice_scale(s));
+  __device__ Row row(int64_t w) const {
+    Row R;
+    const int64_t pi = prob_of[w];
+    R.pr = probs[pi];
+    const T1Ext ex = ext[pi];
+    R.koff = ex.koff;
+    R.goff = ex.goff;
+    R.ci = colinfo[w];
+    R.r = (int)(w - R.pr.coloff);
+    return R;
   }
-}
+  __device__ double at(const Row &R, int kk) const {
+    if (R.ci.x < 0) return 0.0;
+    const int4 km = kmap[R.koff + kk];
+    if (km.x < 0 || !keepC[gpair[R.goff + km.x]]) return 0.0;
+    return C[segC[R.goff + km.x] + ((int64_t)R.ci.y * km.z + km.y) * R.ci.z + R.ci.x];
+  }
+};
 
 }  // namespace rixtc
 
@@ -1575,14 +1625,18 @@ rix_status rix_mixed_t1(rix_ctx *ctx, int b, int64_t tbase, cudaStream_t st) {
     const int64_t r0 = pl->row_seg[g], r1 = pl->row_seg[g + 1];
     const int64_t c0 = pl->col_seg[g], c1 = pl->col_seg[g + 1];
     const int64_t t0 = pl->tile_seg[g], t1 = pl->tile_seg[g + 1];
-    if (r1 > r0)
-      k_pack_t1_rows<<<(unsigned)(((r1 - r0) * 32 + 255) / 256), 256, 0, st>>>(
-          r0, r1 - r0, pl->d_rowprob, pl->d_probs, pl->d_ext, pl->d_rowinfo, pl->d_qinfo, pl->d_kmap, pl->d_segT,
-          ctx->d_T, tbase, S, buf, pl->d_eA);
-    if (c1 > c0)
-      k_pack_t1_cols<<<(unsigned)(((c1 - c0) * 32 + 255) / 256), 256, 0, st>>>(
-          c0, c1 - c0, pl->d_colprob, pl->d_probs, pl->d_ext, pl->d_colinfo, pl->d_kmap, pl->d_segC,
-          pl->d_gpair, ctx->d_keepC, ctx->d_C, S, buf, pl->d_eB);
+    if (r1 > r0) {
+      const T1RowAcc a{pl->d_rowprob, pl->d_probs, pl->d_ext, pl->d_rowinfo, pl->d_qinfo, pl->d_kmap, pl->d_segT,
+                       ctx->d_T, tbase};
+      k_slice_exp<<<(unsigned)(((r1 - r0) * 32 + 255) / 256), 256, 0, st>>>(r0, r1 - r0, a, pl->d_eA);
+      k_slice_dig<<<(unsigned)(((r1 - r0) / 8 * 32 + 255) / 256), 256, 0, st>>>(r0, r1 - r0, a, S, buf, pl->d_eA);
+    }
+    if (c1 > c0) {
+      const T1ColAcc b{pl->d_colprob, pl->d_probs, pl->d_ext, pl->d_colinfo, pl->d_kmap, pl->d_segC, pl->d_gpair,
+                       ctx->d_keepC, ctx->d_C};
+      k_slice_exp<<<(unsigned)(((c1 - c0) * 32 + 255) / 256), 256, 0, st>>>(c0, c1 - c0, b, pl->d_eB);
+      k_slice_dig<<<(unsigned)(((c1 - c0) / 8 * 32 + 255) / 256), 256, 0, st>>>(c0, c1 - c0, b, S, buf, pl->d_eB);
+    }
     if (t1 > t0) {
       GemmArgs ga{buf, buf, pl->d_eA, pl->d_eB, nullptr, 0, 0, 0, 0, 0, 0, S, 1, 0, ctx->d_mx_err,
                   pl->d_tiles + t0, pl->d_probs, pl->d_rowinfo, pl->d_colinfo, nullptr, ctx->d_offK, ctx->d_X,
