@@ -41,18 +41,18 @@ namespace rixtc {
 
 constexpr int TM = 128;         // output rows per tile (one TMEM lane each)
 constexpr int TN = 80;          // output columns per tile
-constexpr int KC = 16;          // K per pipeline stage (one MMA per slice pair)
-constexpr int GROUP = 12;       // stages per exact accumulation group (192 K: 5 x 192 x 127^2 < 2^24)
+constexpr int KC = 32;          // K per pipeline stage
+constexpr int GROUP = 6;        // stages per exact accumulation group (192 K: 5 x 192 x 127^2 < 2^24)
 constexpr int NACC = 6;         // accumulators: s+t = 2 .. 6 and s+t >= 7 (480 TMEM columns)
 constexpr int NTHR = 384;       // warps 0-3: copies, MMA, TMEM allocation; warps 4-11: drain
 constexpr int MAXS = 8;         // slices supported
 constexpr uint64_t WAIT_NS = 2000000000ull;  // a wait gives up after 2 s
 
 // bytes of one packed tile (no-swizzle K-major core matrices, 8 rows x 16 B)
-constexpr int A_TILE = TM * KC * 2;  // 4 KB
-constexpr int B_TILE = TN * KC * 2;  // 2.5 KB
+constexpr int A_TILE = TM * KC * 2;  // 8 KB
+constexpr int B_TILE = TN * KC * 2;  // 5 KB
 
-constexpr int NSTAGE = 4;            // pipeline stages when they fit in shared memory
+constexpr int NSTAGE = 3;            // pipeline stages when they fit in shared memory
 constexpr int SMEM_LIMIT = 227 * 1024;
 
 // stages that fit for S slices, and the dynamic shared memory they need
