@@ -308,3 +308,44 @@ def test_autotune_choice_and_cache(tmp_path, precision):
     assert open(cache).read().splitlines() == lines
     ex.close()
     ex2.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cluster_batch_in_one_context(precision):
+    """Three independent clusters in one context (one launch per stage): each cluster's K
+    equals its own context's K, and E_x is the sum."""
+    from paper_2403_10343_gb300.batch import ClusterBatch
+    cut = 4.0
+    systems = [_small_waters([[0, 0, 0], [2.8, 0.3, 0]], 5, cut=cut),
+               _small_waters([[0, 0, 0]], 6, cut=cut),
+               _small_waters([[0, 0, 0], [2.8, 0, 0], [0, 2.8, 0.4]], 7, cut=cut)]
+    pks = [ri.generate(s) for s in systems]
+    b = ClusterBatch([s.xyz for s in systems], [s.species for s in systems], ri.ang2bohr(cut))
+    s0 = systems[0]
+    ex = Exchange(b.xyz, b.species, s0.nbas, s0.naux, None, b.cutoff_bohr, 0.0, precision=precision)
+    C = np.concatenate([p.C for p in pks])
+    V = np.concatenate([p.V for p in pks])
+    D = np.concatenate([p.D for p in pks])
+    assert (ex.c_elems, ex.v_elems, ex.d_elems) == (C.size, V.size, D.size)
+    ex.set_CV(C, V)
+    Dd = _dev(D)
+    K = ex.build_K(Dd).cpu().numpy()
+    E = ex.energy(Dd, ex.build_K(Dd)).item()
+    keys = ex.k_keys()
+    nb = s0.nbas[b.species].astype(np.int64)
+    A, Ek, _ = ri.unpack_key(keys)
+    koff = np.concatenate([[0], np.cumsum(nb[A] * nb[Ek])])
+    e_sum = 0.0
+    for c, (s, pk) in enumerate(zip(systems, pks)):
+        exs, keys_s, K_s, E_s, _ = run_gpu(s, pk, precision=precision)
+        b0, b1 = b.ranges(keys)[c]
+        assert b1 - b0 == len(keys_s)
+        e0, e1 = int(koff[b0]), int(koff[b1])
+        if precision == "fp64":
+            assert np.array_equal(K[e0:e1], K_s)
+        else:
+            assert rel(K[e0:e1], K_s) < 1e-12
+        e_sum += E_s
+        exs.close()
+    assert abs(E - e_sum) < 1e-12 * abs(e_sum)
+    ex.close()
