@@ -156,6 +156,18 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
                : "r"(taddr));
 }
 
+// An FP32 accumulator value times 2^sh as an integer, with integer operations
+// only (the product is an integer for the exactly accumulated diagonals; below
+// the fixed-point unit the last accumulator is truncated, < 1 unit per group).
+__device__ __forceinline__ int64_t f32_fixed(uint32_t b, int sh) {
+  const int e = (int)((b >> 23) & 0xFF);
+  if (e == 0) return 0;  // zero; subnormals lie far below the fixed-point unit
+  const int64_t m = (int64_t)((b & 0x7FFFFFu) | 0x800000u);
+  const int s = e - 150 + sh;  // value = m 2^s
+  const int64_t v = s >= 0 ? (m << (s < 39 ? s : 39)) : (s > -40 ? (m >> -s) : 0);
+  return (b >> 31) ? -v : v;
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -452,8 +464,8 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
       const int mt = ti.mt, nt = ti.nt, drop = ti.drop, Ncols = ti.N;
       const Prob *pr = ti.pr;
       const int *geA = ti.geA, *geB = ti.geB;
-      // accumulator units -> fixed point: 2^(7(S-1) - drop), exact in FP32
-      const float fscale = __int_as_float((127 + 7 * (S - 1) - drop) << 23);
+      // accumulator units -> fixed point: scale by 2^(7(S-1) - drop)
+      const int fsh = 7 * (S - 1) - drop;
       int64_t acc[HN];
 #pragma unroll
       for (int n = 0; n < HN; n++) acc[n] = 0;
@@ -464,26 +476,21 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
           break;
         }
         tc_fence_after();
-        static_assert(HN % 8 == 0, "drain columns come in groups of 8");
+        static_assert(HN == 40, "drain loads: 16 + 16 + 8 columns");
         for (int a = 0; a < nacc; a++) {
+          // all loads of the accumulator in flight before one wait
           const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * TN + h * HN);
+          uint32_t r0[16], r1[16], r2[8];
+          tmem_ld16(ta, r0);
+          tmem_ld16(ta + 16, r1);
+          tmem_ld8(ta + 32, r2);
+          tmem_wait_ld();
 #pragma unroll
-          for (int n0 = 0; n0 + 16 <= HN; n0 += 16) {
-            uint32_t r[16];
-            tmem_ld16(ta + n0, r);
-            tmem_wait_ld();
+          for (int j = 0; j < 16; j++) acc[j] += f32_fixed(r0[j], fsh);
 #pragma unroll
-            for (int j = 0; j < 16; j++)
-              acc[n0 + j] += (int64_t)__float2ll_rn(__fmul_rn(__uint_as_float(r[j]), fscale));
-          }
-          if (HN % 16) {
-            uint32_t r[8];
-            tmem_ld8(ta + (HN / 16) * 16, r);
-            tmem_wait_ld();
+          for (int j = 0; j < 16; j++) acc[16 + j] += f32_fixed(r1[j], fsh);
 #pragma unroll
-            for (int j = 0; j < 8; j++)
-              acc[(HN / 16) * 16 + j] += (int64_t)__float2ll_rn(__fmul_rn(__uint_as_float(r[j]), fscale));
-          }
+          for (int j = 0; j < 8; j++) acc[32 + j] += f32_fixed(r2[j], fsh);
         }
         tc_fence_before();
         mbar_arrive(accempty);  // tensor memory free for the next group (or tile)
