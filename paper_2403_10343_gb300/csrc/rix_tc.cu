@@ -698,12 +698,16 @@ __global__ void k_slice_dig(int64_t n0, int64_t n, Acc acc, int S, __nv_bfloat16
   const int64_t plane = (int64_t)(rows_pad / trows) * nkt * tbytes;
   const int rt = R.r / trows, rr = R.r % trows;
   for (int k0 = (lane >> 3) * 8; k0 < R.pr.Kpad; k0 += 32) {
+    // the eight loads first (independent, so their latencies overlap), then the digits
+    double v[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) v[j] = acc.at(R, k0 + j);
     uint32_t pk[MAXS][4];
 #pragma unroll
     for (int j = 0; j < 8; j += 2) {
       float d0[MAXS], d1[MAXS];
-      digits_of(acc.at(R, k0 + j), m, S, d0);
-      digits_of(acc.at(R, k0 + j + 1), m, S, d1);
+      digits_of(v[j], m, S, d0);
+      digits_of(v[j + 1], m, S, d1);
 #pragma unroll
       for (int s2 = 0; s2 < MAXS; s2++) {
         if (s2 < S) {
