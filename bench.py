@@ -44,7 +44,7 @@ STAGE_KERNEL = {"flags": "k_flags", "T": "k_T", "U2": "k_U2", "X12": "k_X12",
                 "TC12": "k_gemm_sliced (terms 1 and 2)", "Z": "k_Z", "X34": "k_X34", "sym": "k_sym"}
 # in mixed precision the TC12 and X34 stages are packing kernels + k_gemm_sliced (TC12 is empty in FP64),
 # and the Z stage is k_Z for some middle atoms plus k_gemm_sliced for the others
-TENSOR_STAGE = {"X34": (0,), "TC12": (1, 2), "Z": (3,)}
+TENSOR_STAGE = {"X34": (0,), "TC12": (1, 2), "Z": (3,), "T": (4,)}
 
 
 def stage_flops(stats, st, precision):
@@ -65,6 +65,9 @@ def stage_fp64_share(stats, st, precision):
     if st == "Z":
         fz = stats["flops_stage"][3]
         return (fz - stats["flops_z_tc"]) / fz if fz > 0 else 0.0
+    if st == "T":
+        ft = stats["flops_stage"][0]
+        return (ft - stats["flops_t_tc"]) / ft if ft > 0 else 0.0
     return 1.0
 # FP64 peak of GB300 (recipe table: FP64 1.25 TFLOP/s), used when no measured FP64 peak exists.
 FP64_PEAK_TFLOPS_NOMINAL = 1.25
@@ -302,7 +305,7 @@ def roofline(args, precision, r):
                        "peak_source": f"bf16 sustained, {src}",
                        "fp64_equivalent_tflops": (stage_flops(stats, "X34", precision) +
                                                   stage_flops(stats, "TC12", precision) +
-                                                  stats["flops_z_tc"]) / (ms * 1e-3) / 1e12}
+                                                  stats["flops_z_tc"] + stats["flops_t_tc"]) / (ms * 1e-3) / 1e12}
             # the headline bound is the stage that takes longest: FP64 kernel or tensor-core stages
             if ms > stage_ms.get(dom, 0.0):
                 return roof_tc, roof_tc

@@ -115,12 +115,13 @@ typedef struct {
   int64_t workspace_bytes;         /* library-owned device memory */
   int32_t n_row_blocks;            /* row blocks of the memory plan (1 = all intermediates resident) */
   double flops_term2;              /* the term-2 part of flops_stage[2] (on the tensor cores when mixed) */
-  double tensor_flops_stage[4];    /* mixed mode: tensor FLOPs issued per build for terms 3+4, term 2,
-                                      term 1, term-4 intermediate Z */
+  double tensor_flops_stage[5];    /* mixed mode: tensor FLOPs issued per build for terms 3+4, term 2,
+                                      term 1, term-4 intermediate Z, T */
   int32_t launches_build;          /* kernel launches of one rix_build_K (rix_energy adds 3) */
   double flops_term1_tc;           /* mixed mode: the term-1 FLOPs (FP64 grouping) moved to the tensor cores */
   double flops_z_tc;               /* mixed mode: the Z FLOPs (FP64 grouping) moved to the tensor cores */
   int64_t tz_bytes;                /* the T and Z buffers (part of workspace_bytes) */
+  double flops_t_tc;               /* mixed mode: the T FLOPs moved to the tensor cores */
 } rix_stats_t;
 
 /* Set up a system: copies the host arrays, builds the pair list on the device

@@ -150,12 +150,13 @@ __global__ void __launch_bounds__(NT) k_T(const int2 *items, const int64_t *ptrT
                                           const double *__restrict__ C, const int64_t *offC,
                                           const double *__restrict__ D, const int64_t *offD,
                                           const uint8_t *keepC, const uint8_t *keepD, double *T,
-                                          int64_t tbase) {
+                                          int64_t tbase, const uint8_t *ttc) {
   extern __shared__ double sm[];
   const int tid = threadIdx.x;
   const int2 it = items[blockIdx.x];
   const int t = it.x, p0 = it.y;
   const int a = atomA2[t], g = atomB2[t];
+  if (ttc && ttc[a]) return;  // this row atom's T comes from the tensor cores
   const int nbA = nb[a], naA = na[a], nbG = nb[g];
   const int per = nbA * nbG;
   const int pt = max(1, NT * MAXE / per);
@@ -604,15 +605,25 @@ rix_status launch_X34_items(rix_ctx *ctx, int b, int64_t first, int64_t count, i
 
 }  // namespace
 
-// T(A,G') for the row atoms of block b (T buffer holds that block).
+// T(A,G') for the row atoms of block b (T buffer holds that block).  In mixed
+// precision the buffer is cleared first and the tensor cores add the T blocks
+// of their row atoms; k_T stores the others.
 rix_status rix_launch_T_block(rix_ctx *ctx, const double *D, int b, cudaStream_t st) {
   const int64_t nT = ctx->segT[b + 1] - ctx->segT[b];
-  if (!nT) return RIX_OK;
-  k_T<<<(unsigned)nT, NT, 64 * 64 * 8, st>>>(ctx->d_itT + ctx->segT[b], ctx->d_ptrT, ctx->d_LT, ctx->d_atomA2,
-                                             ctx->d_atomB2, ctx->d_off2, ctx->d_pB, ctx->d_nb, ctx->d_na, ctx->d_C,
-                                             ctx->d_offC, D, ctx->d_offD, ctx->d_keepC, ctx->d_keepD, ctx->d_T,
-                                             ctx->blk_base[b]);
-  return last(ctx, "k_T");
+  const bool tc = ctx->have_mx && ctx->n_ttc > 0;
+  if (tc) {
+    const int64_t n = ctx->off2[ctx->row2[ctx->blk_atom[b + 1]]] - ctx->blk_base[b];
+    RIX_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_T, 0, sizeof(double) * n, st));
+  }
+  if (nT) {
+    k_T<<<(unsigned)nT, NT, 64 * 64 * 8, st>>>(ctx->d_itT + ctx->segT[b], ctx->d_ptrT, ctx->d_LT, ctx->d_atomA2,
+                                               ctx->d_atomB2, ctx->d_off2, ctx->d_pB, ctx->d_nb, ctx->d_na,
+                                               ctx->d_C, ctx->d_offC, D, ctx->d_offD, ctx->d_keepC, ctx->d_keepD,
+                                               ctx->d_T, ctx->blk_base[b], tc ? ctx->d_ttc : nullptr);
+    rix_status s = last(ctx, "k_T");
+    if (s != RIX_OK) return s;
+  }
+  return tc ? rix_mixed_T(ctx, b, ctx->blk_base[b], D, st) : RIX_OK;
 }
 
 // Z(B;E') for the middle atoms of block b (Z buffer holds that block): the FP64

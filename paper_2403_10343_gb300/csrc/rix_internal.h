@@ -124,6 +124,9 @@ struct rix_ctx {
   struct rix_mx_plan *mx34 = nullptr, *mx2 = nullptr;
   struct rix_t1_plan *mx1 = nullptr;           // term 1 for the column atoms where it pays
   struct rix_mx_plan *mxz = nullptr;            // term-4 intermediate for the middle atoms where it pays
+  struct rix_tt_plan *mxt = nullptr;            // T for the row atoms where it pays
+  uint8_t *d_ttc = nullptr;                     // per atom: 1 if its T blocks come from the tensor cores
+  int n_ttc = 0;
   uint8_t *d_ztc = nullptr;                     // per atom: 1 if Z's terms through it run on the tensor cores
   int n_ztc = 0;
   uint8_t *d_t1tc = nullptr;                    // per atom: 1 if its term 1 runs on the tensor cores
@@ -200,6 +203,10 @@ rix_status rix_t1_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out);
 void rix_t1_plan_free(rix_ctx *ctx);
 rix_status rix_mixed_t1(rix_ctx *ctx, int b, int64_t tbase, cudaStream_t st);
 int32_t rix_t1_launches(const rix_ctx *ctx);
+rix_status rix_tt_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out);
+void rix_tt_plan_free(rix_ctx *ctx);
+rix_status rix_mixed_T(rix_ctx *ctx, int b, int64_t tbase, const double *D, cudaStream_t st);
+int32_t rix_tt_launches(const rix_ctx *ctx);
 
 // FP64 path launches (rix_fp64.cu)
 rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t st);

@@ -1025,9 +1025,10 @@ int64_t rix_mixed_bytes(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
   ctx->mx_S = ctx->opt.n_slices > 0 ? ctx->opt.n_slices : 6;
   int64_t maps = 0, buf = 0;
   {
-    int64_t t1 = 0;
+    int64_t t1 = 0, tt = 0;
     rix_t1_plan_build(ctx, true, &t1);  // maps plus its slice buffer
-    maps += t1;
+    rix_tt_plan_build(ctx, true, &tt);
+    maps += t1 + tt;
   }
   for (int kind = 0; kind < 3; kind++) {
     PlanHost h;
@@ -1138,6 +1139,10 @@ rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
     if ((s = rix_t1_plan_build(ctx, false, &t1buf)) != RIX_OK) return s;
     buf = std::max(buf, t1buf);
     tflops += ctx->stats.tensor_flops_stage[2];
+    int64_t ttbuf = 0;
+    if ((s = rix_tt_plan_build(ctx, false, &ttbuf)) != RIX_OK) return s;
+    buf = std::max(buf, ttbuf);
+    tflops += ctx->stats.tensor_flops_stage[4];
   }
   if ((s = rix_dev_alloc(ctx, (void **)&ctx->d_mx_buf, std::max<int64_t>(buf, 16))) != RIX_OK) return s;
   if ((s = rix_alloc(ctx, &ctx->d_mx_err, 4)) != RIX_OK) return s;
@@ -1154,7 +1159,7 @@ int32_t rix_launch_count(const rix_ctx *ctx) {
   int32_t n = 2 + 3 * ctx->nblk;
   if (ctx->have_mx) {
     n += 3 * (int32_t)(ctx->mx34->grp.size() - 1) + 3 * (int32_t)(ctx->mx2->grp.size() - 1) +
-         3 * (int32_t)(ctx->mxz->grp.size() - 1) + rix_t1_launches(ctx);
+         3 * (int32_t)(ctx->mxz->grp.size() - 1) + rix_t1_launches(ctx) + rix_tt_launches(ctx);
     if (ctx->n_t1tc < ctx->nat) n += ctx->nblk;  // k_X12 for the other column atoms
   } else {
     n += 2 * ctx->nblk;  // k_X12, k_X34
@@ -1164,6 +1169,7 @@ int32_t rix_launch_count(const rix_ctx *ctx) {
 
 void rix_mixed_free(rix_ctx *ctx) {
   rix_t1_plan_free(ctx);
+  rix_tt_plan_free(ctx);
   delete ctx->mx34;
   delete ctx->mx2;
   delete ctx->mxz;
@@ -1666,4 +1672,352 @@ rix_status rix_mixed_t1(rix_ctx *ctx, int b, int64_t tbase, cudaStream_t st) {
 
 int32_t rix_t1_launches(const rix_ctx *ctx) {
   return ctx->mx1 ? 3 * (int32_t)(ctx->mx1->grp_prob.size() - 1) : 0;
+}
+
+// ==========================================================================
+// T on the tensor cores, one problem per row atom A (for the row atoms where
+// it pays): T(A,G')[P][i][k] = sum_{B' near A} C(A,B')[P on A][i][j] D(B',G')[j][k]
+// as one GEMM with rows (P, i), K = (B', j) and columns (G', k) over A's 2-hop
+// blocks, D(B',G') taken as zero where (B',G') is not a pair.  Results are
+// added into the zeroed T buffer of the row block.
+// ==========================================================================
+namespace rixtc {
+
+struct TTExt {
+  int64_t koff;    // kmap offset (Kpad entries: (g, j, nb_B, -), g < 0 past K)
+  int64_t p1base;  // first pair (A, .) of the row atom
+  int32_t nbA, pad_;
+};
+
+// rows: element (P, i ; g, j) = C(A, B'_g)[P][i][j]
+struct TTRowAcc {
+  const int64_t *prob_of;
+  const Prob *probs;
+  const TTExt *ext;
+  const int2 *rowinfo;
+  const int4 *kmap;
+  const int64_t *offC;
+  const uint8_t *keepC;
+  const double *C;
+  static constexpr int is_b = 0;
+  struct Row {
+    Prob pr;
+    TTExt ex;
+    int r, lrow;
+    bool live;
+  };
+  __device__ Row row(int64_t w) const {
+    Row R;
+    const int64_t pi = prob_of[w];
+    R.pr = probs[pi];
+    R.ex = ext[pi];
+    R.r = (int)(w - R.pr.rowoff);
+    const int2 ri = rowinfo[w];
+    R.live = ri.x >= 0;
+    R.lrow = ri.y;
+    return R;
+  }
+  __device__ double at(const Row &R, int kk) const {
+    if (!R.live) return 0.0;
+    const int4 km = kmap[R.ex.koff + kk];
+    if (km.x < 0) return 0.0;
+    const int64_t p1 = R.ex.p1base + km.x;
+    if (!keepC[p1]) return 0.0;
+    return C[offC[p1] + (int64_t)R.lrow * km.z + km.y];  // (P nbA + i) nbB + j
+  }
+};
+
+// columns: element (t, k ; g, j) = D(B'_g, G'_t)[j][k], the pair found among T's products
+struct TTColAcc {
+  const int64_t *prob_of;
+  const Prob *probs;
+  const TTExt *ext;
+  const int4 *colinfo;  // (z, k, nb_G, t)
+  const int4 *kmap;
+  const int64_t *ptrT;
+  const int2 *LT;       // per T block: (pair (A,B'), pair (B',G')), sorted by the first
+  const int64_t *offD;
+  const uint8_t *keepD;
+  const double *D;
+  static constexpr int is_b = 1;
+  struct Row {
+    Prob pr;
+    TTExt ex;
+    int4 ci;
+    int r;
+    int64_t e0, e1;
+  };
+  __device__ Row row(int64_t w) const {
+    Row R;
+    const int64_t pi = prob_of[w];
+    R.pr = probs[pi];
+    R.ex = ext[pi];
+    R.ci = colinfo[w];
+    R.r = (int)(w - R.pr.coloff);
+    R.e0 = R.ci.x >= 0 ? ptrT[R.ci.w] : 0;
+    R.e1 = R.ci.x >= 0 ? ptrT[R.ci.w + 1] : 0;
+    return R;
+  }
+  __device__ double at(const Row &R, int kk) const {
+    if (R.ci.x < 0) return 0.0;
+    const int4 km = kmap[R.ex.koff + kk];
+    if (km.x < 0) return 0.0;
+    const int p1 = (int)(R.ex.p1base + km.x);
+    int64_t lo = R.e0, hi = R.e1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (LT[mid].x < p1) lo = mid + 1;
+      else hi = mid;
+    }
+    if (lo >= R.e1 || LT[lo].x != p1) return 0.0;
+    const int pD = LT[lo].y;
+    if (!keepD[pD]) return 0.0;
+    return D[offD[pD] + (int64_t)km.y * R.ci.z + R.ci.y];  // j nbG + k
+  }
+};
+
+__global__ void k_skip_flags(int n, const int32_t *idx, uint8_t *flags) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) flags[idx[t]] = 1;
+}
+
+}  // namespace rixtc
+
+struct rix_tt_plan {
+  std::vector<int32_t> grp_prob, grp_blk;
+  std::vector<int64_t> tile_seg, row_seg, col_seg;
+  int64_t buf_bytes = 0;
+  int S = 6;
+  Prob *d_probs = nullptr;
+  rixtc::TTExt *d_ext = nullptr;
+  int2 *d_rowinfo = nullptr;
+  int4 *d_colinfo = nullptr, *d_tiles = nullptr, *d_kmap = nullptr;
+  int64_t *d_rowprob = nullptr, *d_colprob = nullptr;
+  int32_t *d_xmap = nullptr;
+  int *d_eA = nullptr, *d_eB = nullptr;
+};
+
+// T plan: decide per row atom, build one problem per chosen atom (its block is the atom's).
+rix_status rix_tt_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) {
+  using namespace rixtc;
+  const int nat = ctx->nat, S = rix_plan_slices(ctx, 1);
+  const int npairs = S * (S + 1) / 2;
+  auto &row1 = ctx->row1, &row2 = ctx->row2;
+  std::vector<uint8_t> use(nat, 0);
+  double fl64 = 0;
+  for (int a = 0; a < nat; a++) {
+    const int nbA = ctx->nb_at[a], naA = ctx->na_at[a];
+    double f64 = 0;
+    int64_t K = 0, N = 0;
+    for (int64_t p1 = row1[a]; p1 < row1[a + 1]; p1++) {
+      const int b = ctx->pB[p1];
+      K += ctx->nb_at[b];
+      for (int64_t p2 = row1[b]; p2 < row1[b + 1]; p2++)
+        f64 += 2.0 * naA * nbA * ctx->nb_at[b] * ctx->nb_at[ctx->pB[p2]];
+    }
+    for (int64_t t = row2[a]; t < row2[a + 1]; t++) N += ctx->nb_at[rix::key_b(ctx->keys2[t])];
+    const double Mp = std::ceil((double)naA * nbA / TM) * TM, Np = std::ceil((double)N / TN) * TN,
+                 Kp = std::ceil((double)K / KC) * KC;
+    if (2.0 * Mp * Np * Kp * npairs / TC_RATE < f64 / FP64_RATE) {
+      use[a] = 1;
+      fl64 += f64;
+    }
+  }
+  const bool have_blocks = (int)ctx->blk_atom.size() == ctx->nblk + 1;
+  std::vector<int32_t> blk_of(nat, 0);
+  if (have_blocks)
+    for (int b = 0; b < ctx->nblk; b++)
+      for (int a = ctx->blk_atom[b]; a < ctx->blk_atom[b + 1]; a++) blk_of[a] = b;
+  std::vector<Prob> probs;
+  std::vector<TTExt> ext;
+  std::vector<int2> rowinfo;
+  std::vector<int4> colinfo, tiles, kmap;
+  std::vector<int64_t> rowprob, colprob, pbytes;
+  std::vector<int32_t> xmap, pblk;
+  int64_t eaoff = 0, eboff = 0, maps = 0, maxp = 0, total = 0;
+  double tflops = 0;
+  for (int a = 0; a < nat; a++) {
+    if (!use[a]) continue;
+    const int nbA = ctx->nb_at[a], naA = ctx->na_at[a];
+    int K = 0, N = 0;
+    for (int64_t p1 = row1[a]; p1 < row1[a + 1]; p1++) K += ctx->nb_at[ctx->pB[p1]];
+    const int nz = (int)(row2[a + 1] - row2[a]);
+    for (int64_t t = row2[a]; t < row2[a + 1]; t++) N += ctx->nb_at[rix::key_b(ctx->keys2[t])];
+    const int M = naA * nbA;
+    const int Mpad = std::max(TM, (M + TM - 1) / TM * TM), Npad = std::max(TN, (N + TN - 1) / TN * TN);
+    const int Kpad = std::max(KC, (K + KC - 1) / KC * KC);
+    const int64_t bytes = (int64_t)S * (Mpad + Npad) * Kpad * 2;
+    total += bytes;
+    maxp = std::max(maxp, bytes);
+    maps += (int64_t)Mpad * (8 + 8 + 4) + (int64_t)Npad * (16 + 8 + 4) + (int64_t)Kpad * 16 + (int64_t)nz * 4 +
+            (int64_t)(Mpad / TM) * (Npad / TN) * 16 + (int64_t)(sizeof(Prob) + sizeof(TTExt));
+    tflops += 2.0 * Mpad * Npad * Kpad * npairs;
+    if (count_only) continue;
+    const int pidx = (int)probs.size();
+    Prob pr{};
+    pr.M = M; pr.N = N; pr.Mpad = Mpad; pr.Npad = Npad; pr.Kpad = Kpad; pr.pad_ = K;
+    pr.nz = nz;
+    pr.drop = fixed_point_drop(Kpad, S);
+    pr.eaoff = eaoff; pr.eboff = eboff;
+    pr.rowoff = (int64_t)rowinfo.size();
+    pr.coloff = (int64_t)colinfo.size();
+    pr.xoff = (int64_t)xmap.size();
+    eaoff += Mpad;
+    eboff += Npad;
+    ext.push_back(TTExt{(int64_t)kmap.size(), row1[a], nbA, 0});
+    for (int64_t p1 = row1[a]; p1 < row1[a + 1]; p1++) {
+      const int nbB = ctx->nb_at[ctx->pB[p1]];
+      for (int j = 0; j < nbB; j++) kmap.push_back(make_int4((int)(p1 - row1[a]), j, nbB, 0));
+    }
+    for (int k = K; k < Kpad; k++) kmap.push_back(make_int4(-1, 0, 1, 0));
+    for (int r = 0; r < M; r++) {
+      rowinfo.push_back(make_int2(0, r));  // (P nbA + i)
+      rowprob.push_back(pidx);
+    }
+    for (int r = M; r < Mpad; r++) {
+      rowinfo.push_back(make_int2(-1, 0));
+      rowprob.push_back(pidx);
+    }
+    for (int64_t t = row2[a]; t < row2[a + 1]; t++) {
+      const int nbG = ctx->nb_at[rix::key_b(ctx->keys2[t])];
+      for (int k = 0; k < nbG; k++) {
+        colinfo.push_back(make_int4((int)(t - row2[a]), k, nbG, (int)t));
+        colprob.push_back(pidx);
+      }
+      xmap.push_back((int32_t)t);
+    }
+    for (int c = N; c < Npad; c++) {
+      colinfo.push_back(make_int4(-1, 0, 1, 0));
+      colprob.push_back(pidx);
+    }
+    for (int mt = 0; mt < Mpad / TM; mt++)
+      for (int nt = 0; nt < Npad / TN; nt++) tiles.push_back(make_int4(pidx, mt, nt, 0));
+    probs.push_back(pr);
+    pbytes.push_back(bytes);
+    pblk.push_back(blk_of[a]);
+  }
+  if (count_only) {
+    if (bytes_out) *bytes_out = maps + (total ? std::max(maxp, std::min(total, (int64_t)8 << 30)) : 0) + nat;
+    return RIX_OK;
+  }
+  rix_tt_plan *pl = new rix_tt_plan;
+  ctx->mxt = pl;
+  pl->S = S;
+  const int64_t budget = std::max(maxp, std::min(total, (int64_t)8 << 30));
+  pl->grp_prob.assign(1, 0);
+  int64_t cur = 0, maxgrp = 0;
+  for (int p = 0; p < (int)probs.size(); p++) {
+    if (p > 0 && (pblk[p] != pblk[p - 1] || cur + pbytes[p] > budget)) {
+      pl->grp_prob.push_back(p);
+      maxgrp = std::max(maxgrp, cur);
+      cur = 0;
+    }
+    probs[p].aoff = cur;
+    probs[p].boff = cur + (int64_t)S * probs[p].Mpad * probs[p].Kpad * 2;
+    cur += pbytes[p];
+  }
+  maxgrp = std::max(maxgrp, cur);
+  pl->grp_prob.push_back((int)probs.size());
+  pl->buf_bytes = probs.empty() ? 0 : maxgrp;
+  const size_t ng = pl->grp_prob.size() - 1;
+  pl->grp_blk.assign(ng, 0);
+  pl->tile_seg.assign(ng + 1, 0);
+  pl->row_seg.assign(ng + 1, 0);
+  pl->col_seg.assign(ng + 1, 0);
+  {
+    size_t ti = 0, ri = 0, ci = 0;
+    for (size_t g = 0; g < ng; g++) {
+      const int pend = pl->grp_prob[g + 1];
+      if (pl->grp_prob[g] < (int)pblk.size()) pl->grp_blk[g] = pblk[pl->grp_prob[g]];
+      while (ti < tiles.size() && tiles[ti].x < pend) ti++;
+      while (ri < rowprob.size() && rowprob[ri] < pend) ri++;
+      while (ci < colprob.size() && colprob[ci] < pend) ci++;
+      pl->tile_seg[g + 1] = ti;
+      pl->row_seg[g + 1] = ri;
+      pl->col_seg[g + 1] = ci;
+    }
+  }
+  rix_status s;
+  if ((s = rix_upload(ctx, &pl->d_probs, probs)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &pl->d_ext, ext)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &pl->d_rowinfo, rowinfo)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &pl->d_colinfo, colinfo)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &pl->d_tiles, tiles)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &pl->d_kmap, kmap)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &pl->d_rowprob, rowprob)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &pl->d_colprob, colprob)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &pl->d_xmap, xmap)) != RIX_OK) return s;
+  if ((s = rix_alloc(ctx, &pl->d_eA, std::max<int64_t>(eaoff, 1))) != RIX_OK) return s;
+  if ((s = rix_alloc(ctx, &pl->d_eB, std::max<int64_t>(eboff, 1))) != RIX_OK) return s;
+  std::vector<int32_t> on;
+  for (int a = 0; a < nat; a++)
+    if (use[a]) on.push_back(a);
+  if ((s = rix_alloc(ctx, &ctx->d_ttc, nat)) != RIX_OK) return s;
+  RIX_CUDA_TRY(ctx, cudaMemset(ctx->d_ttc, 0, nat));
+  if (!on.empty()) {
+    int32_t *d_on = nullptr;
+    if ((s = rix_upload(ctx, &d_on, on)) != RIX_OK) return s;
+    k_skip_flags<<<(unsigned)((on.size() + 255) / 256), 256>>>((int)on.size(), d_on, ctx->d_ttc);
+    RIX_CUDA_TRY(ctx, cudaDeviceSynchronize());
+  }
+  ctx->n_ttc = (int)on.size();
+  ctx->stats.tensor_flops_stage[4] = tflops;
+  ctx->stats.flops_t_tc = fl64;
+  if (ctx->opt.verbose)
+    fprintf(stderr, "rix mixed T: %zu of %d row atoms on the tensor cores, %zu GEMM tiles, %zu group(s)\n",
+            on.size(), nat, tiles.size(), ng);
+  if (bytes_out) *bytes_out = maxgrp;
+  return RIX_OK;
+}
+
+void rix_tt_plan_free(rix_ctx *ctx) {
+  delete ctx->mxt;
+  ctx->mxt = nullptr;
+}
+
+// T of the tensor-core row atoms of block b (T buffer of the block zeroed, at tbase).
+rix_status rix_mixed_T(rix_ctx *ctx, int b, int64_t tbase, const double *D, cudaStream_t st) {
+  using namespace rixtc;
+  const rix_tt_plan *pl = ctx->mxt;
+  if (!pl) return RIX_OK;
+  gemm_attr();
+  const int S = pl->S;
+  __nv_bfloat16 *buf = (__nv_bfloat16 *)ctx->d_mx_buf;
+  for (size_t g = 0; g + 1 < pl->grp_prob.size(); g++) {
+    if (pl->grp_blk[g] != b || pl->grp_prob[g + 1] == pl->grp_prob[g]) continue;
+    const int64_t r0 = pl->row_seg[g], r1 = pl->row_seg[g + 1];
+    const int64_t c0 = pl->col_seg[g], c1 = pl->col_seg[g + 1];
+    const int64_t t0 = pl->tile_seg[g], t1 = pl->tile_seg[g + 1];
+    if (r1 > r0) {
+      const TTRowAcc a{pl->d_rowprob, pl->d_probs, pl->d_ext, pl->d_rowinfo, pl->d_kmap, ctx->d_offC, ctx->d_keepC,
+                       ctx->d_C};
+      k_slice_exp<<<(unsigned)(((r1 - r0) * 32 + 255) / 256), 256, 0, st>>>(r0, r1 - r0, a, pl->d_eA);
+      k_slice_dig<<<(unsigned)(((r1 - r0) / 8 * 32 + 255) / 256), 256, 0, st>>>(r0, r1 - r0, a, S, buf, pl->d_eA);
+    }
+    if (c1 > c0) {
+      const TTColAcc bb{pl->d_colprob, pl->d_probs, pl->d_ext, pl->d_colinfo, pl->d_kmap, ctx->d_ptrT, ctx->d_LT,
+                        ctx->d_offD, ctx->d_keepD, D};
+      k_slice_exp<<<(unsigned)(((c1 - c0) * 32 + 255) / 256), 256, 0, st>>>(c0, c1 - c0, bb, pl->d_eB);
+      k_slice_dig<<<(unsigned)(((c1 - c0) / 8 * 32 + 255) / 256), 256, 0, st>>>(c0, c1 - c0, bb, S, buf, pl->d_eB);
+    }
+    if (t1 > t0) {
+      GemmArgs ga{buf, buf, pl->d_eA, pl->d_eB, nullptr, 0, 0, 0, 0, 0, 0, S, 1, 0, ctx->d_mx_err,
+                  pl->d_tiles + t0, pl->d_probs, pl->d_rowinfo, pl->d_colinfo, pl->d_xmap, ctx->d_off2, ctx->d_T};
+      ga.mode = 0;
+      ga.oscale = 1.0;
+      ga.xshift = tbase;
+      ga.ntiles = (int)(t1 - t0);
+      k_gemm_sliced<<<persistent_grid(t1 - t0), NTHR, smem_bytes(S), st>>>(ga);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      ctx->last_error = std::string("mixed T: ") + cudaGetErrorString(e);
+      return RIX_ECUDA;
+    }
+  }
+  return RIX_OK;
+}
+
+int32_t rix_tt_launches(const rix_ctx *ctx) {
+  return ctx->mxt ? 5 * (int32_t)(ctx->mxt->grp_prob.size() - 1) : 0;
 }

@@ -45,9 +45,9 @@ class _Stats(ctypes.Structure):
                 ("flops_stage", ctypes.c_double * 6), ("min_bytes", ctypes.c_double),
                 ("tensor_flops", ctypes.c_double), ("workspace_bytes", ctypes.c_int64),
                 ("n_row_blocks", ctypes.c_int32), ("flops_term2", ctypes.c_double),
-                ("tensor_flops_stage", ctypes.c_double * 4), ("launches_build", ctypes.c_int32),
+                ("tensor_flops_stage", ctypes.c_double * 5), ("launches_build", ctypes.c_int32),
                 ("flops_term1_tc", ctypes.c_double), ("flops_z_tc", ctypes.c_double),
-                ("tz_bytes", ctypes.c_int64)]
+                ("tz_bytes", ctypes.c_int64), ("flops_t_tc", ctypes.c_double)]
 
 
 _lib = None
