@@ -807,7 +807,8 @@ struct PlanHost {
 
 // Slices per plan: the regrouped forms (term 1 as T x C, Z with Kronecker rows)
 // sum many more products of widely ranging size per output than the FP64
-// grouping, so they take one slice more than terms 2-4 (capped at 8).
+// grouping, and T feeds every term, so these take one slice more than the
+// GEMMs of terms 2-4 (capped at 8).
 int rix_plan_slices(const rix_ctx *ctx, int kind) {
   return kind >= 2 ? std::min(ctx->mx_S + 1, (int)rixtc::MAXS) : ctx->mx_S;
 }
@@ -1800,7 +1801,8 @@ struct rix_tt_plan {
 // T plan: decide per row atom, build one problem per chosen atom (its block is the atom's).
 rix_status rix_tt_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) {
   using namespace rixtc;
-  const int nat = ctx->nat, S = rix_plan_slices(ctx, 1);
+  // T feeds every term, so it takes the extra slice as well
+  const int nat = ctx->nat, S = rix_plan_slices(ctx, 3);
   const int npairs = S * (S + 1) / 2;
   auto &row1 = ctx->row1, &row2 = ctx->row2;
   std::vector<uint8_t> use(nat, 0);
