@@ -1155,12 +1155,14 @@ rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
 }
 
 // Kernel launches of one rix_build_K: flags, per block T, U2 and Z, terms 1+2 and
-// terms 3+4 (FP64 per block) or per group two packs and a GEMM (mixed), symmetrise.
+// terms 3+4 (FP64 per block) or per group four slicing kernels and a GEMM
+// (mixed), symmetrise.
 int32_t rix_launch_count(const rix_ctx *ctx) {
   int32_t n = 2 + 3 * ctx->nblk;
   if (ctx->have_mx) {
-    n += 3 * (int32_t)(ctx->mx34->grp.size() - 1) + 3 * (int32_t)(ctx->mx2->grp.size() - 1) +
-         3 * (int32_t)(ctx->mxz->grp.size() - 1) + rix_t1_launches(ctx) + rix_tt_launches(ctx);
+    // per group: exponents and digits of both operands, then the GEMM
+    n += 5 * (int32_t)(ctx->mx34->grp.size() - 1) + 5 * (int32_t)(ctx->mx2->grp.size() - 1) +
+         5 * (int32_t)(ctx->mxz->grp.size() - 1) + rix_t1_launches(ctx) + rix_tt_launches(ctx);
     if (ctx->n_t1tc < ctx->nat) n += ctx->nblk;  // k_X12 for the other column atoms
   } else {
     n += 2 * ctx->nblk;  // k_X12, k_X34
@@ -1672,7 +1674,7 @@ rix_status rix_mixed_t1(rix_ctx *ctx, int b, int64_t tbase, cudaStream_t st) {
 }
 
 int32_t rix_t1_launches(const rix_ctx *ctx) {
-  return ctx->mx1 ? 3 * (int32_t)(ctx->mx1->grp_prob.size() - 1) : 0;
+  return ctx->mx1 ? 5 * (int32_t)(ctx->mx1->grp_prob.size() - 1) : 0;
 }
 
 // ==========================================================================
