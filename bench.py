@@ -47,6 +47,19 @@ STAGE_KERNEL = {"flags": "k_flags", "T": "k_T", "U2": "k_U2", "X12": "k_X12",
 TENSOR_STAGE = {"X34": (0,), "TC12": (1, 2), "Z": (3,), "T": (4,)}
 
 
+def screened(stats, cnt):
+    """The setup-time statistics with the FLOP counts replaced by those of this D after block screening."""
+    out = dict(stats)
+    out["flops_fp64_unscreened"] = stats["flops_fp64"]
+    out["flops_stage"] = [cnt[k] for k in ("T", "U2", "X12", "Z", "X34", "sym")]
+    out["flops_fp64"] = sum(out["flops_stage"])
+    out["flops_term2"] = cnt["term2"]
+    out["flops_term1_tc"] = cnt["term1_tc"]
+    out["flops_z_tc"] = cnt["z_tc"]
+    out["flops_t_tc"] = cnt["t_tc"]
+    return out
+
+
 def stage_flops(stats, st, precision):
     """Algorithmic FP64-equivalent FLOPs of one stage as the path runs it."""
     fs = stats["flops_stage"]
@@ -276,8 +289,7 @@ def measure(args, s, pk, precision, dev, world, rank, local):
         t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = t.item()
-    stats = ex.stats()
-    nblk = stats["n_row_blocks"]
+    stats = screened(ex.stats(), ex.count_flops(D))
     launches = stats["launches_build"] + 3  # build + energy kernels
     out = {"ms": ms, "e2e_ms": e2e_ms, "stage_ms": stage_ms, "stats": stats, "clocks": clocks, "graph": args.graph,
            "tiles": tiles,
@@ -398,6 +410,7 @@ def run_rix(args):
             "stage_ms": {k: round(v, 4) for k, v in r["stage_ms"].items()},
             "stage_roofline": stage_roofline(head, r),
             "alg_flops": stats["flops_fp64"],
+            "alg_flops_unscreened": stats["flops_fp64_unscreened"],
             "alg_tflops": stats["flops_fp64"] / (r["ms"] * 1e-3) / 1e12,
             "E_x": r["E_x"],
         }

@@ -216,6 +216,20 @@ rix_status rix_gemm_sliced(const double *A, int64_t lda, const double *B, int64_
 
 rix_status rix_stats(const rix_ctx *ctx, rix_stats_t *out);
 
+/* Algorithmic FLOPs (2 per multiply-add, the FP64 grouping of Eqs. 12a-d) that
+ * one rix_build_K with the density matrix D_dev (device, packed) performs
+ * after block screening (Sec. "Screening": products whose C, V or D block has
+ * no element of magnitude >= tau are skipped).  The counts of rix_stats_t
+ * include every product; these depend on D.  flops (host, 10 doubles):
+ * [0] T, [1] U2, [2] terms 1+2, [3] Z, [4] terms 3+4, [5] symmetrise, [6] the
+ * term-2 part of [2], [7] the part of [2] for the column atoms whose term 1
+ * runs on the tensor cores, [8] the part of [3] for the middle atoms whose Z
+ * products run on the tensor cores, [9] the part of [0] for the row atoms
+ * whose T runs on the tensor cores ([7]-[9] are 0 in FP64 mode; the tensor
+ * cores themselves do not skip screened products).  Needs rix_set_CV.
+ * Synchronises `stream`; ESTATE inside a graph capture. */
+rix_status rix_count_flops(rix_ctx *ctx, const double *D_dev, double *flops, void *stream);
+
 /* Device time of each stage of rix_build_K (ms), summed over the builds since
  * the previous call, and the number of builds: ms[0..7] = screening flags,
  * T, U2, terms 1+2 (FP64 kernel), terms 1 and 2 on the tensor cores (mixed

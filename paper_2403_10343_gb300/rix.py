@@ -80,6 +80,7 @@ def load():
     lib.rix_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
                                     ctypes.POINTER(ctypes.c_int32)]
     lib.rix_autotune.argtypes = [P, P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32), P]
+    lib.rix_count_flops.argtypes = [P, P, ctypes.POINTER(ctypes.c_double), P]
     lib.rix_strerror.restype = ctypes.c_char_p
     lib.rix_strerror.argtypes = [I]
     lib.rix_last_error.restype = ctypes.c_char_p
@@ -87,7 +88,8 @@ def load():
     lib.rix_destroy.argtypes = [P]
     for f in ("rix_setup", "rix_layout", "rix_layout_sizes", "rix_set_CV", "rix_build_K", "rix_energy",
               "rix_energy_noalloc",
-              "rix_backward", "rix_fold_gamma", "rix_stats", "rix_stage_times", "rix_gemm_sliced"):
+              "rix_backward", "rix_fold_gamma", "rix_stats", "rix_stage_times", "rix_gemm_sliced",
+              "rix_autotune", "rix_count_flops"):
         getattr(lib, f).restype = I
     _lib = lib
     return lib
@@ -201,6 +203,16 @@ def autotune(ctx, D, cache_path=None, stream=None):
     return tuple(out)
 
 
+COUNT_KEYS = ("T", "U2", "X12", "Z", "X34", "sym", "term2", "term1_tc", "z_tc", "t_tc")
+
+
+def count_flops(ctx, D, stream=None):
+    """rix_count_flops: FLOPs of one build with this D after block screening, by stage."""
+    out = (ctypes.c_double * 10)()
+    _check(load().rix_count_flops(ctx, _dptr(D, "D"), out, _stream(stream)), ctx)
+    return dict(zip(COUNT_KEYS, out))
+
+
 def fold_gamma(ctx, K, Kdense, stream=None):
     _check(load().rix_fold_gamma(ctx, _dptr(K, "K"), _dptr(Kdense, "Kdense"), _stream(stream)), ctx)
 
@@ -269,6 +281,9 @@ class Exchange:
 
     def autotune(self, D, cache_path=None, stream=None):
         return autotune(self.ctx, D, cache_path, stream)
+
+    def count_flops(self, D, stream=None):
+        return count_flops(self.ctx, D, stream)
 
     def build_K(self, D, K=None, stream=None):
         import torch
