@@ -137,6 +137,45 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
+// The MMAs of one K stage: slice pairs (s, u) with s + u < S, each into
+// accumulator min(s + u, NACC - 1), two K steps of 16.  ad0 / bd0 are the
+// descriptors of slice 0 of the stage; the others follow at fixed offsets (the
+// start-address field counts 16-byte units and stays below 2^14 in shared
+// memory).  In this order the first MMA into every accumulator is the one with
+// s = 0, kk = 0 and u <= NACC - 1; with open = 1 (the stage starts an
+// accumulation group) those overwrite their accumulator.
+template <int S>
+__device__ __forceinline__ void issue_stage(uint32_t tmem, uint64_t ad0, uint64_t bd0, uint32_t idesc,
+                                            uint32_t open) {
+#pragma unroll
+  for (int s = 0; s < S; s++)
+#pragma unroll
+    for (int u = 0; u < S - s; u++) {
+      const int a = s + u < NACC - 1 ? s + u : NACC - 1;
+#pragma unroll
+      for (int kk = 0; kk < KC / 16; kk++) {
+        const uint64_t ad = ad0 + (uint64_t)((s * A_TILE + kk * 256) >> 4);
+        const uint64_t bd = bd0 + (uint64_t)((u * B_TILE + kk * 256) >> 4);
+        const bool first = s == 0 && kk == 0 && u <= NACC - 1;
+        mma_bf16(tmem + (uint32_t)(a * TN), ad, bd, idesc, first ? 1u - open : 1u);
+      }
+    }
+}
+
+__device__ __forceinline__ void issue_stage_s(int S, uint32_t tmem, uint64_t ad0, uint64_t bd0, uint32_t idesc,
+                                              uint32_t open) {
+  switch (S) {
+    case 1: issue_stage<1>(tmem, ad0, bd0, idesc, open); break;
+    case 2: issue_stage<2>(tmem, ad0, bd0, idesc, open); break;
+    case 3: issue_stage<3>(tmem, ad0, bd0, idesc, open); break;
+    case 4: issue_stage<4>(tmem, ad0, bd0, idesc, open); break;
+    case 5: issue_stage<5>(tmem, ad0, bd0, idesc, open); break;
+    case 6: issue_stage<6>(tmem, ad0, bd0, idesc, open); break;
+    case 7: issue_stage<7>(tmem, ad0, bd0, idesc, open); break;
+    default: issue_stage<8>(tmem, ad0, bd0, idesc, open); break;
+  }
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
@@ -156,9 +195,11 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
                : "r"(taddr));
 }
 
-// An FP32 accumulator value times 2^sh as an integer, with integer operations
-// only (the product is an integer for the exactly accumulated diagonals; below
-// the fixed-point unit the last accumulator is truncated, < 1 unit per group).
+// An FP32 accumulator value times 2^sh as a 64-bit integer, truncated toward
+// zero, with integer operations only (the conversion instructions with a
+// 64-bit side run at the FP64 rate).  Used for the last accumulator, which
+// holds several diagonals and is not an integer in its own units; below the
+// fixed-point unit it is truncated (< 1 unit per group).
 __device__ __forceinline__ int64_t f32_fixed(uint32_t b, int sh) {
   const int e = (int)((b >> 23) & 0xFF);
   if (e == 0) return 0;  // zero; subnormals lie far below the fixed-point unit
@@ -166,6 +207,53 @@ __device__ __forceinline__ int64_t f32_fixed(uint32_t b, int sh) {
   const int s = e - 150 + sh;  // value = m 2^s
   const int64_t v = s >= 0 ? (m << (s < 39 ? s : 39)) : (s > -40 ? (m >> -s) : 0);
   return (b >> 31) ? -v : v;
+}
+
+// Drain of one exactly accumulated diagonal a into the fixed-point sums: the
+// FP32 value is an integer I times 2^-7a with |I| < 2^24, so I = trunc(v 2^7a)
+// is exact in a 32-bit conversion, and I 2^L (L = 7(S-1) - drop - 7a, the same
+// for the whole tile) is added with one 32 x 32 -> 64-bit multiply-add: for
+// 0 <= L <= 37 as (I 2^pre) 2^(L-pre) with pre = max(0, L - 30), both factors
+// within 32 bits (|I 2^pre| < 2^31); other L by a 64-bit shift.
+template <int N>
+__device__ __forceinline__ void drain_exact(int64_t *acc, const uint32_t (&r)[N], int a, int L) {
+  const float up = __int_as_float((127 + 7 * a) << 23);
+  if (L >= 0 && L <= 37) {
+    const int pre = L > 30 ? L - 30 : 0;
+    const int32_t mul = 1 << (L - pre);
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+      const int32_t I = __float2int_rz(__uint_as_float(r[j]) * up);
+      acc[j] += (int64_t)(I << pre) * (int64_t)mul;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+      const int64_t I = __float2int_rz(__uint_as_float(r[j]) * up);
+      acc[j] += L >= 0 ? (I << (L < 63 ? L : 63)) : (I >> (-L < 63 ? -L : 63));
+    }
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void drain_any(int64_t *acc, const uint32_t (&r)[N], int sh) {
+#pragma unroll
+  for (int j = 0; j < N; j++) acc[j] += f32_fixed(r[j], sh);
+}
+
+// x 2^sc as a double, built with integer operations (the FP64 pipe is the
+// scarcest unit here): the leading 53 bits of |x|, truncated toward zero
+// (relative error below 2^-52).  Exponents outside the normal range go
+// through ldexp.
+__device__ __forceinline__ double fixed_to_double(int64_t x, int sc) {
+  if (x == 0) return 0.0;
+  const uint64_t sgn = (uint64_t)x & (1ull << 63);
+  const uint64_t ax = sgn ? (uint64_t)(-x) : (uint64_t)x;
+  const int lz = __clzll((long long)ax);
+  const int E = 1023 + 63 - lz + sc;
+  if (E <= 0 || E >= 2047) return ldexp((double)x, sc);
+  const uint64_t mant = ((ax << lz) >> 11) & ((1ull << 52) - 1);
+  return __longlong_as_double((long long)(sgn | ((uint64_t)E << 52) | mant));
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -428,19 +516,9 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
         tc_fence_after();
         const uint32_t sa = smem_u32(smem + st * stage_bytes);
         const uint32_t sb = sa + S * A_TILE;
-        uint32_t fresh = (c % GROUP == 0) ? (1u << NACC) - 1 : 0u;  // accumulators still to overwrite
-        for (int s = 0; s < S; s++)
-          for (int u = 0; s + u < S; u++) {
-            const int a = s + u < NACC - 1 ? s + u : NACC - 1;
-            const uint32_t tcol = tmem + (uint32_t)(a * TN);
-            for (int kk = 0; kk < KC / 16; kk++) {
-              // K step kk covers core-matrix columns 2kk, 2kk+1 (LBO = 128 B apart)
-              const uint64_t ad = sdesc(sa + s * A_TILE + kk * 256, 128, (KC / 8) * 128);
-              const uint64_t bd = sdesc(sb + u * B_TILE + kk * 256, 128, (KC / 8) * 128);
-              mma_bf16(tcol, ad, bd, idesc, ((fresh >> a) & 1u) ? 0u : 1u);
-              fresh &= ~(1u << a);
-            }
-          }
+        // K step kk covers core-matrix columns 2kk, 2kk+1 (LBO = 128 B apart)
+        issue_stage_s(S, tmem, sdesc(sa, 128, (KC / 8) * 128), sdesc(sb, 128, (KC / 8) * 128), idesc,
+                      c % GROUP == 0 ? 1u : 0u);
         mma_commit(&empty[st]);
         if (c % GROUP == GROUP - 1 || c == nk - 1) {
           mma_commit(accfull);
@@ -466,6 +544,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
       const int *geA = ti.geA, *geB = ti.geB;
       // accumulator units -> fixed point: scale by 2^(7(S-1) - drop)
       const int fsh = 7 * (S - 1) - drop;
+      const int nexact = S < NACC ? S : NACC - 1;  // accumulators holding one diagonal, exactly
       int64_t acc[HN];
 #pragma unroll
       for (int n = 0; n < HN; n++) acc[n] = 0;
@@ -485,12 +564,15 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
           tmem_ld16(ta + 16, r1);
           tmem_ld8(ta + 32, r2);
           tmem_wait_ld();
-#pragma unroll
-          for (int j = 0; j < 16; j++) acc[j] += f32_fixed(r0[j], fsh);
-#pragma unroll
-          for (int j = 0; j < 16; j++) acc[16 + j] += f32_fixed(r1[j], fsh);
-#pragma unroll
-          for (int j = 0; j < 8; j++) acc[32 + j] += f32_fixed(r2[j], fsh);
+          if (a < nexact) {
+            drain_exact(acc, r0, a, fsh - 7 * a);
+            drain_exact(acc + 16, r1, a, fsh - 7 * a);
+            drain_exact(acc + 32, r2, a, fsh - 7 * a);
+          } else {
+            drain_any(acc, r0, fsh);
+            drain_any(acc + 16, r1, fsh);
+            drain_any(acc + 32, r2, fsh);
+          }
         }
         tc_fence_before();
         mbar_arrive(accempty);  // tensor memory free for the next group (or tile)
@@ -506,7 +588,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
             const int gc = nt * TN + h * HN + n;
             if (gc < Ncols) {
               const int sc = er + geB[gc] - 7 * (S + 1) + drop;
-              const double v = ldexp((double)acc[n], sc);
+              const double v = fixed_to_double(acc[n], sc);
               double *dst = g.C + (int64_t)gr * g.ldc + gc;
               if (g.accumulate) *dst += v;
               else *dst = v;
@@ -534,7 +616,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
                       part = 0.0;
                     }
                     const int sc = er + geB[gc] - 7 * (S + 1) + drop;
-                    part = fma(g.V[qi.voff + (int64_t)P * ci.w + ci.y], ldexp((double)acc[n], sc), part);
+                    part = fma(g.V[qi.voff + (int64_t)P * ci.w + ci.y], fixed_to_double(acc[n], sc), part);
                   }
                 }
               }
@@ -552,7 +634,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
                 const int4 ci = g.colinfo[pr->coloff + gc];
                 if (ci.x >= 0) {
                   const int sc = er + geB[gc] - 7 * (S + 1) + drop;
-                  const double v = ldexp((double)acc[n], sc);
+                  const double v = fixed_to_double(acc[n], sc);
                   atomicAdd(g.X + (g.offK[xrow[ci.x]] - g.xshift) + (int64_t)ri.y * ci.z + ci.y, g.oscale * v);
                 }
               }
