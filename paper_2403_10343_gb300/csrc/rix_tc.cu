@@ -42,7 +42,20 @@ namespace rixtc {
 constexpr int TM = 128;         // output rows per tile (one TMEM lane each)
 constexpr int TN = 80;          // output columns per tile
 constexpr int KC = 32;          // K per pipeline stage
-constexpr int GROUP = 6;        // stages per exact accumulation group (192 K: 5 x 192 x 127^2 < 2^24)
+// Accumulation groups.  Accumulator a < NACC-1 holds diagonal a (a + 1 slice
+// pairs) and stays an exact integer below 2^24 in its own units over
+// (a + 1) * stages * KC * 127^2 < 2^24 stages.  Diagonals 2-4 are folded every
+// GROUP = 6 stages (192 K); diagonals 0 and 1 and the last accumulator
+// (s+t >= NACC-1, FP32 rounding) every 2 * GROUP, which saves a quarter of
+// the folding work.  PART_MASK: the accumulators folded at the half-way point.
+constexpr int GROUP = 6;
+constexpr uint32_t PART_MASK = (1u << 2) | (1u << 3) | (1u << 4);
+constexpr bool exact_over(int a, int stages) {
+  return (int64_t)(a + 1) * stages * KC * 127 * 127 < ((int64_t)1 << 24);
+}
+static_assert(exact_over(0, 2 * GROUP) && exact_over(1, 2 * GROUP) && exact_over(2, GROUP) &&
+                  exact_over(3, GROUP) && exact_over(4, GROUP),
+              "accumulation groups must stay exact");
 constexpr int NACC = 6;         // accumulators: s+t = 2 .. 6 and s+t >= 7 (480 TMEM columns)
 constexpr int NTHR = 384;       // warps 0-3: copies, MMA, TMEM allocation; warps 4-11: drain
 constexpr int MAXS = 8;         // slices supported
@@ -142,8 +155,8 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
 // descriptors of slice 0 of the stage; the others follow at fixed offsets (the
 // start-address field counts 16-byte units and stays below 2^14 in shared
 // memory).  In this order the first MMA into every accumulator is the one with
-// s = 0, kk = 0 and u <= NACC - 1; with open = 1 (the stage starts an
-// accumulation group) those overwrite their accumulator.
+// s = 0, kk = 0 and u <= NACC - 1; for the accumulators whose bit is set in
+// open (a group of them starts at this stage) it overwrites the accumulator.
 template <int S>
 __device__ __forceinline__ void issue_stage(uint32_t tmem, uint64_t ad0, uint64_t bd0, uint32_t idesc,
                                             uint32_t open) {
@@ -157,7 +170,7 @@ __device__ __forceinline__ void issue_stage(uint32_t tmem, uint64_t ad0, uint64_
         const uint64_t ad = ad0 + (uint64_t)((s * A_TILE + kk * 256) >> 4);
         const uint64_t bd = bd0 + (uint64_t)((u * B_TILE + kk * 256) >> 4);
         const bool first = s == 0 && kk == 0 && u <= NACC - 1;
-        mma_bf16(tmem + (uint32_t)(a * TN), ad, bd, idesc, first ? 1u - open : 1u);
+        mma_bf16(tmem + (uint32_t)(a * TN), ad, bd, idesc, first ? 1u - ((open >> a) & 1u) : 1u);
       }
     }
 }
@@ -235,10 +248,36 @@ __device__ __forceinline__ void drain_exact(int64_t *acc, const uint32_t (&r)[N]
   }
 }
 
+// Drain of the last accumulator (s+t >= NACC-1, not an integer in any one
+// unit): trunc(v 2^sh) in the fixed point.  For sh <= 35 one 32-bit conversion
+// (|v 2^sh| < 2^31).  Otherwise x = v 2^35 (|x| < 2^25) is split exactly into
+// 8 h (x + 1.5 2^26 rounds it to a multiple of 8; h is read from the bits) and
+// a remainder |r| <= 4, which is scaled by 2^(sh-35) and converted; the sum of
+// the two parts differs from trunc(v 2^sh) by < 1 unit.  This keeps the
+// conversion unit, not the integer pipe, the busy one.
 template <int N>
 __device__ __forceinline__ void drain_any(int64_t *acc, const uint32_t (&r)[N], int sh) {
+  if (sh <= 35) {
+    const float p2 = __int_as_float((127 + sh) << 23);
 #pragma unroll
-  for (int j = 0; j < N; j++) acc[j] += f32_fixed(r[j], sh);
+    for (int j = 0; j < N; j++) acc[j] += __float2int_rz(__uint_as_float(r[j]) * p2);
+  } else if (sh <= 63) {
+    const float M = 100663296.f;  // 1.5 * 2^26
+    const uint32_t Mb = __float_as_uint(M);
+    const float p2 = __int_as_float((127 + sh - 35) << 23);
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+      const float x = __uint_as_float(r[j]) * 34359738368.f;  // 2^35
+      const float t = x + M;
+      const int32_t h8 = (int32_t)(__float_as_uint(t) - Mb);
+      const float rem = x - (t - M);
+      const int32_t lo = __float2int_rz(rem * p2);
+      acc[j] += ((int64_t)h8 << (sh - 32)) + lo;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < N; j++) acc[j] += f32_fixed(r[j], sh);
+  }
 }
 
 // x 2^sc as a double, built with integer operations (the FP64 pipe is the
@@ -504,7 +543,8 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
       const int nk = ti.Kpad / KC;
       for (int c = 0; c < nk; c++, cg++) {
         const int st = cg % nst;
-        if (c % GROUP == 0 && gg > 0 && !mbar_wait(accempty, (gg - 1) & 1)) {
+        const int gpos = c % (2 * GROUP);
+        if (gpos % GROUP == 0 && gg > 0 && !mbar_wait(accempty, (gg - 1) & 1)) {
           atomicExch(abort_flag, 1);
           break;
         }
@@ -517,10 +557,11 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
         const uint32_t sa = smem_u32(smem + st * stage_bytes);
         const uint32_t sb = sa + S * A_TILE;
         // K step kk covers core-matrix columns 2kk, 2kk+1 (LBO = 128 B apart)
-        issue_stage_s(S, tmem, sdesc(sa, 128, (KC / 8) * 128), sdesc(sb, 128, (KC / 8) * 128), idesc,
-                      c % GROUP == 0 ? 1u : 0u);
+        // c = 0 or gpos = 0: every accumulator starts a group; gpos = GROUP: those of PART_MASK
+        const uint32_t open = c == 0 || gpos == 0 ? 0xFFu : gpos == GROUP ? PART_MASK : 0u;
+        issue_stage_s(S, tmem, sdesc(sa, 128, (KC / 8) * 128), sdesc(sb, 128, (KC / 8) * 128), idesc, open);
         mma_commit(&empty[st]);
-        if (c % GROUP == GROUP - 1 || c == nk - 1) {
+        if (gpos % GROUP == GROUP - 1 || c == nk - 1) {
           mma_commit(accfull);
           gg++;
         }
@@ -549,6 +590,9 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
 #pragma unroll
       for (int n = 0; n < HN; n++) acc[n] = 0;
       for (int grp = 0; grp < ngroups; grp++, gg++) {
+        // group grp ends after stage min(GROUP (grp + 1), nk) - 1; at odd grp and at the tile's
+        // end every accumulator is folded, at even grp those of PART_MASK
+        const uint32_t fold = (grp & 1) || grp == ngroups - 1 ? 0xFFu : PART_MASK;
         if (!mbar_wait(accfull, gg & 1)) {
           atomicExch(abort_flag, 1);
           ok = false;
@@ -557,6 +601,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
         tc_fence_after();
         static_assert(HN == 40, "drain loads: 16 + 16 + 8 columns");
         for (int a = 0; a < nacc; a++) {
+          if (!((fold >> a) & 1u)) continue;
           // all loads of the accumulator in flight before one wait
           const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * TN + h * HN);
           uint32_t r0[16], r1[16], r2[8];
