@@ -810,8 +810,37 @@ __global__ void k_slice_exp(int64_t n0, int64_t n, Acc acc, int *e) {
   if (lane == 0) e[(acc.is_b ? R.pr.eboff : R.pr.eaoff) + R.r] = m;
 }
 
-template <class Acc>
-__global__ void k_slice_dig(int64_t n0, int64_t n, Acc acc, int S, __nv_bfloat16 *planes, const int *e) {
+// Digit s of two values as a packed BF16 pair (low half: x0), with integer
+// and FMA-pipe operations only (the conversion unit is the scarce one): the
+// 7-bit digit d is made exact in FP32 through the 2^23 trick, scaled by
+// 2^-7s in the same FMA (exact: at most 7 significant bits), and its top 16
+// bits are its BF16 encoding; the signs are applied to the pair at the end.
+template <int S>
+__device__ __forceinline__ void digit_pairs(double x0, double x1, int e, uint32_t (&w)[S]) {
+  uint64_t fr[2];
+  uint32_t sg = 0;
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const uint64_t b = (uint64_t)__double_as_longlong(h ? x1 : x0);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    const uint64_t m = (b & ((1ull << 52) - 1)) | (1ull << 52);
+    const int sh = 12 + (ex - 1023) - e;  // fraction |x| / 2^e as a 64-bit fixed point: m << sh
+    fr[h] = ex == 0 ? 0 : sh >= 0 ? m << sh : (sh > -64 ? m >> -sh : 0);
+    sg |= (uint32_t)(b >> 63) << (15 + 16 * h);
+  }
+#pragma unroll
+  for (int t = 0; t < S; t++) {
+    const float sc = __int_as_float((127 - 7 * t) << 23);  // 2^-7t
+    const uint32_t d0 = (uint32_t)(fr[0] >> (57 - 7 * t)) & 127u;
+    const uint32_t d1 = (uint32_t)(fr[1] >> (57 - 7 * t)) & 127u;
+    const float f0 = __fmaf_rn(__uint_as_float(0x4B000000u | d0), sc, -8388608.f * sc);
+    const float f1 = __fmaf_rn(__uint_as_float(0x4B000000u | d1), sc, -8388608.f * sc);
+    w[t] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632) ^ sg;
+  }
+}
+
+template <class Acc, int S>
+__global__ void k_slice_dig(int64_t n0, int64_t n, Acc acc, __nv_bfloat16 *planes, const int *e) {
   const int64_t g8 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (g8 * 8 >= n) return;  // n is a multiple of 8 (problems pad to whole tiles)
@@ -829,24 +858,30 @@ __global__ void k_slice_dig(int64_t n0, int64_t n, Acc acc, int S, __nv_bfloat16
     double v[8];
 #pragma unroll
     for (int j = 0; j < 8; j++) v[j] = acc.at(R, k0 + j);
-    uint32_t pk[MAXS][4];
+    uint32_t pk[4][S];
 #pragma unroll
-    for (int j = 0; j < 8; j += 2) {
-      float d0[MAXS], d1[MAXS];
-      digits_of(v[j], m, S, d0);
-      digits_of(v[j + 1], m, S, d1);
-#pragma unroll
-      for (int s2 = 0; s2 < MAXS; s2++) {
-        if (s2 < S) {
-          const __nv_bfloat162 h = __floats2bfloat162_rn(d0[s2] * slice_scale(s2), d1[s2] * slice_scale(s2));
-          pk[s2][j >> 1] = *reinterpret_cast<const uint32_t *>(&h);
-        }
-      }
-    }
+    for (int j = 0; j < 4; j++) digit_pairs<S>(v[2 * j], v[2 * j + 1], m, pk[j]);
     const int64_t off = ((int64_t)rt * nkt + k0 / KC) * tbytes + tile_off(rr, k0 % KC);
 #pragma unroll
-    for (int s2 = 0; s2 < MAXS; s2++)
-      if (s2 < S) *reinterpret_cast<uint4 *>(base + s2 * plane + off) = make_uint4(pk[s2][0], pk[s2][1], pk[s2][2], pk[s2][3]);
+    for (int t = 0; t < S; t++)
+      *reinterpret_cast<uint4 *>(base + t * plane + off) = make_uint4(pk[0][t], pk[1][t], pk[2][t], pk[3][t]);
+  }
+}
+
+// k_slice_dig over rows [n0, n0 + n) (n a multiple of 8) for S slices
+template <class Acc>
+void launch_slice_dig(int64_t n0, int64_t n, const Acc &acc, int S, __nv_bfloat16 *planes, const int *e,
+                      cudaStream_t st) {
+  const unsigned grid = (unsigned)((n / 8 * 32 + 255) / 256);
+  switch (S) {
+    case 1: k_slice_dig<Acc, 1><<<grid, 256, 0, st>>>(n0, n, acc, planes, e); break;
+    case 2: k_slice_dig<Acc, 2><<<grid, 256, 0, st>>>(n0, n, acc, planes, e); break;
+    case 3: k_slice_dig<Acc, 3><<<grid, 256, 0, st>>>(n0, n, acc, planes, e); break;
+    case 4: k_slice_dig<Acc, 4><<<grid, 256, 0, st>>>(n0, n, acc, planes, e); break;
+    case 5: k_slice_dig<Acc, 5><<<grid, 256, 0, st>>>(n0, n, acc, planes, e); break;
+    case 6: k_slice_dig<Acc, 6><<<grid, 256, 0, st>>>(n0, n, acc, planes, e); break;
+    case 7: k_slice_dig<Acc, 7><<<grid, 256, 0, st>>>(n0, n, acc, planes, e); break;
+    default: k_slice_dig<Acc, 8><<<grid, 256, 0, st>>>(n0, n, acc, planes, e); break;
   }
 }
 
@@ -1328,12 +1363,12 @@ rix_status run_group(rix_ctx *ctx, const rix_mx_plan *pl, size_t g, const Operan
   if (r1 > r0) {
     const SrcAcc a{pl->d_rowprob, pl->d_probs, pl->d_rowsrc, ra.x, ra.shift, ra.x2, ra.keep, ra.keep2, 0};
     k_slice_exp<<<(unsigned)(((r1 - r0) * 32 + 255) / 256), 256, 0, st>>>(r0, r1 - r0, a, pl->d_eA);
-    k_slice_dig<<<(unsigned)(((r1 - r0) / 8 * 32 + 255) / 256), 256, 0, st>>>(r0, r1 - r0, a, S, buf, pl->d_eA);
+    launch_slice_dig(r0, r1 - r0, a, S, buf, pl->d_eA, st);
   }
   if (c1 > c0) {
     const SrcAcc b{pl->d_colprob, pl->d_probs, pl->d_colsrc, cb.x, cb.shift, cb.x2, cb.keep, cb.keep2, 1};
     k_slice_exp<<<(unsigned)(((c1 - c0) * 32 + 255) / 256), 256, 0, st>>>(c0, c1 - c0, b, pl->d_eB);
-    k_slice_dig<<<(unsigned)(((c1 - c0) / 8 * 32 + 255) / 256), 256, 0, st>>>(c0, c1 - c0, b, S, buf, pl->d_eB);
+    launch_slice_dig(c0, c1 - c0, b, S, buf, pl->d_eB, st);
   }
   if (t1 > t0) {
     GemmArgs ga{buf, buf, pl->d_eA, pl->d_eB, nullptr, 0, 0, 0, 0, 0, 0, S, 1, 0, ctx->d_mx_err,
@@ -1776,13 +1811,13 @@ rix_status rix_mixed_t1(rix_ctx *ctx, int b, int64_t tbase, cudaStream_t st) {
       const T1RowAcc a{pl->d_rowprob, pl->d_probs, pl->d_ext, pl->d_rowinfo, pl->d_qinfo, pl->d_kmap, pl->d_segT,
                        ctx->d_T, tbase};
       k_slice_exp<<<(unsigned)(((r1 - r0) * 32 + 255) / 256), 256, 0, st>>>(r0, r1 - r0, a, pl->d_eA);
-      k_slice_dig<<<(unsigned)(((r1 - r0) / 8 * 32 + 255) / 256), 256, 0, st>>>(r0, r1 - r0, a, S, buf, pl->d_eA);
+      launch_slice_dig(r0, r1 - r0, a, S, buf, pl->d_eA, st);
     }
     if (c1 > c0) {
       const T1ColAcc b{pl->d_colprob, pl->d_probs, pl->d_ext, pl->d_colinfo, pl->d_kmap, pl->d_segC, pl->d_gpair,
                        ctx->d_keepC, ctx->d_C};
       k_slice_exp<<<(unsigned)(((c1 - c0) * 32 + 255) / 256), 256, 0, st>>>(c0, c1 - c0, b, pl->d_eB);
-      k_slice_dig<<<(unsigned)(((c1 - c0) / 8 * 32 + 255) / 256), 256, 0, st>>>(c0, c1 - c0, b, S, buf, pl->d_eB);
+      launch_slice_dig(c0, c1 - c0, b, S, buf, pl->d_eB, st);
     }
     if (t1 > t0) {
       GemmArgs ga{buf, buf, pl->d_eA, pl->d_eB, nullptr, 0, 0, 0, 0, 0, 0, S, 1, 0, ctx->d_mx_err,
@@ -2123,13 +2158,13 @@ rix_status rix_mixed_T(rix_ctx *ctx, int b, int64_t tbase, const double *D, cuda
       const TTRowAcc a{pl->d_rowprob, pl->d_probs, pl->d_ext, pl->d_rowinfo, pl->d_kmap, ctx->d_offC, ctx->d_keepC,
                        ctx->d_C};
       k_slice_exp<<<(unsigned)(((r1 - r0) * 32 + 255) / 256), 256, 0, st>>>(r0, r1 - r0, a, pl->d_eA);
-      k_slice_dig<<<(unsigned)(((r1 - r0) / 8 * 32 + 255) / 256), 256, 0, st>>>(r0, r1 - r0, a, S, buf, pl->d_eA);
+      launch_slice_dig(r0, r1 - r0, a, S, buf, pl->d_eA, st);
     }
     if (c1 > c0) {
       const TTColAcc bb{pl->d_colprob, pl->d_probs, pl->d_ext, pl->d_colinfo, pl->d_kmap, ctx->d_ptrT, ctx->d_LT,
                         ctx->d_offD, ctx->d_keepD, D};
       k_slice_exp<<<(unsigned)(((c1 - c0) * 32 + 255) / 256), 256, 0, st>>>(c0, c1 - c0, bb, pl->d_eB);
-      k_slice_dig<<<(unsigned)(((c1 - c0) / 8 * 32 + 255) / 256), 256, 0, st>>>(c0, c1 - c0, bb, S, buf, pl->d_eB);
+      launch_slice_dig(c0, c1 - c0, bb, S, buf, pl->d_eB, st);
     }
     if (t1 > t0) {
       GemmArgs ga{buf, buf, pl->d_eA, pl->d_eB, nullptr, 0, 0, 0, 0, 0, 0, S, 1, 0, ctx->d_mx_err,
