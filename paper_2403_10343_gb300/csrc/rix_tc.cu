@@ -2,26 +2,29 @@
 //
 // C = A B with A [M x K], B [K x N] in FP64.  Every row of A (column of B) is
 // scaled by a power of two 2^e so that |x| < 2^e, and its 64-bit fixed-point
-// fraction |x| / 2^e is cut into S signed 7-bit digits (integers in
-// [-127, 127], exact in BF16).  This is the error-free splitting of Ozaki,
-// Ogita, Oishi and Rump (2012) with per-row/column exponents.  With
-// a = sum_s a_s 2^-7s and b = sum_t b_t 2^-7t,
+// fraction |x| / 2^e is written with S balanced base-2^7 digits: the leading
+// one in [0, 128], the others in [-64, 63], the last rounded to nearest (all
+// exact in BF16, the sign of x applied to every digit).  This is the
+// error-free splitting of Ozaki, Ogita, Oishi and Rump (2012) with
+// per-row/column exponents and balanced digits.  With a = sum_s a_s 2^-7s and
+// b = sum_t b_t 2^-7t,
 //
 //   A B = 2^(eA + eB) sum_{s+t <= S+1} 2^{-7(s+t)} (A_s B_t)
 //
-// and every slice product A_s B_t is a sum of integers below 2^14 per term.
+// and every slice product A_s B_t is a sum of integers: below 2^14 on the
+// leading diagonal, 2^13 where one digit is a leading one and 2^12 otherwise.
 // Slice s is stored pre-scaled by 2^-7(s-1) (exact in BF16), so a product
 // carries its own power of two.  Six FP32 accumulators in tensor memory take
-// the products with s+t = 2, 3, 4, 5, 6 and s+t >= 7: the first five hold
-// integers (times 2^-7(s+t-2)) whose sums over a group of 192 K values stay
-// below 2^24, so the tensor cores accumulate them exactly; the sixth holds
+// the products with s+t = 2, 3, 4, 5, 6 and s+t >= 7: by those bounds the
+// first five hold integers (times 2^-7(s+t-2)) below 2^24 over a group of 512
+// K values, so the tensor cores accumulate them exactly; the sixth holds
 // terms at least 2^-35 below the leading one, where the tensor cores' FP32
 // accumulation costs about 2^-53 of the row x column x K scale.  After each
 // group the accumulators are folded into a 64-bit fixed-point sum per output
 // element, and the FP64 result is formed once at the end.  The error is the
-// truncation of the operands after S digits (about 2^-7S of the row/column
-// scale), the dropped terms s+t > S+1 and the rounding of the sixth
-// accumulator.
+// rounding of the operands to S digits (at most half a unit of 2^-7S of the
+// row/column scale), the dropped terms s+t > S+1 and the rounding of the
+// sixth accumulator.
 //
 // Kernel layout: persistent CTAs over 128 x 80 output tiles; warp 0 issues the
 // bulk copies (cp.async.bulk, mbarrier completion), one thread of warp 1
@@ -42,19 +45,16 @@ namespace rixtc {
 constexpr int TM = 128;         // output rows per tile (one TMEM lane each)
 constexpr int TN = 80;          // output columns per tile
 constexpr int KC = 32;          // K per pipeline stage
-// Accumulation groups.  Accumulator a < NACC-1 holds diagonal a (a + 1 slice
-// pairs) and stays an exact integer below 2^24 in its own units over
-// (a + 1) * stages * KC * 127^2 < 2^24 stages.  Diagonals 2-4 are folded every
-// GROUP = 6 stages (192 K); diagonals 0 and 1 and the last accumulator
-// (s+t >= NACC-1, FP32 rounding) every 2 * GROUP, which saves a quarter of
-// the folding work.  PART_MASK: the accumulators folded at the half-way point.
-constexpr int GROUP = 6;
-constexpr uint32_t PART_MASK = (1u << 2) | (1u << 3) | (1u << 4);
-constexpr bool exact_over(int a, int stages) {
-  return (int64_t)(a + 1) * stages * KC * 127 * 127 < ((int64_t)1 << 24);
+// Accumulation groups of GROUP K stages (512 K values).  Accumulator a < NACC-1
+// holds diagonal a: pairs (0, a) and (a, 0) with a leading digit (<= 128)
+// and a balanced one (<= 64), and a - 1 pairs of balanced digits (a = 0: the
+// one pair of leading digits), so its sum stays an integer below 2^24.
+constexpr int GROUP = 16;
+constexpr int64_t diag_bound(int a) {  // largest |sum over one K value| of diagonal a
+  return a == 0 ? 128 * 128 : 2 * 128 * 64 + (int64_t)(a - 1) * 64 * 64;
 }
-static_assert(exact_over(0, 2 * GROUP) && exact_over(1, 2 * GROUP) && exact_over(2, GROUP) &&
-                  exact_over(3, GROUP) && exact_over(4, GROUP),
+constexpr bool exact_group(int a) { return diag_bound(a) * GROUP * KC < ((int64_t)1 << 24); }
+static_assert(exact_group(0) && exact_group(1) && exact_group(2) && exact_group(3) && exact_group(4),
               "accumulation groups must stay exact");
 constexpr int NACC = 6;         // accumulators: s+t = 2 .. 6 and s+t >= 7 (480 TMEM columns)
 constexpr int NTHR = 384;       // warps 0-3: copies, MMA, TMEM allocation; warps 4-11: drain
@@ -315,20 +315,40 @@ __device__ __forceinline__ int exp_of(double x) {
   return ex == 0 ? -2000 : ex - 1023 + 1;  // zero and subnormals count as tiny
 }
 
-// digit s (1-based) of |x| / 2^e in base 2^7, with the sign of x
-__device__ __forceinline__ void digits_of(double x, int e, int S, float *d) {
-  uint64_t b = (uint64_t)__double_as_longlong(x);
-  int ex = (int)((b >> 52) & 0x7FF);
-  for (int s = 0; s < S; s++) d[s] = 0.f;
-  if (ex == 0) return;
-  uint64_t m = (b & ((1ull << 52) - 1)) | (1ull << 52);
-  int sh = 12 + (ex - 1023) - e;  // fraction bits: frac = m << sh (sh <= 11)
-  uint64_t frac;
-  if (sh >= 0) frac = m << sh;
-  else if (sh > -64) frac = m >> (-sh);
-  else frac = 0;
+// |x| / 2^e as a 64-bit fixed-point fraction (0 for zero and subnormal x)
+__device__ __forceinline__ uint64_t frac_of(uint64_t b, int e) {
+  const int ex = (int)((b >> 52) & 0x7FF);
+  const uint64_t m = (b & ((1ull << 52) - 1)) | (1ull << 52);
+  const int sh = 12 + (ex - 1023) - e;  // fraction bits: frac = m << sh (sh <= 11)
+  return ex == 0 ? 0 : sh >= 0 ? m << sh : (sh > -64 ? m >> -sh : 0);
+}
+
+// The S balanced base-2^7 digits of a fraction, leading digit first: the
+// plain digits (fr >> (57 - 7t)) & 127 are rounded at digit S - 1 (the next
+// bit) and folded from the last one up, a digit >= 64 becoming digit - 128
+// with a carry into the one before; the leading digit takes the last carry
+// and lies in [0, 128], the others in [-64, 63].
+template <int S>
+__device__ __forceinline__ void balanced_digits(uint64_t fr, int (&d)[S]) {
+  int carry = (int)((fr >> (63 - 7 * S)) & 1u);
+#pragma unroll
+  for (int t = S - 1; t >= 1; t--) {
+    const int c = (int)((fr >> (57 - 7 * t)) & 127u) + carry;
+    carry = c >= 64;
+    d[t] = c - (carry << 7);
+  }
+  d[0] = (int)(fr >> 57) + carry;
+}
+
+// digit s (0-based) of x: balanced digit of |x| / 2^e with the sign of x
+template <int S>
+__device__ __forceinline__ void digits_of(double x, int e, float (&d)[S]) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  int di[S];
+  balanced_digits<S>(frac_of(b, e), di);
   const float sg = (b >> 63) ? -1.f : 1.f;
-  for (int s = 0; s < S; s++) d[s] = sg * (float)((frac >> (64 - 7 * (s + 1))) & 127u);
+#pragma unroll
+  for (int t = 0; t < S; t++) d[t] = sg * (float)di[t];
 }
 
 // 2^-7s as a float (exact): slice s (0-based) is stored pre-scaled by it
@@ -357,22 +377,40 @@ __global__ void k_col_exp(const double *X, int64_t ld, int Kd, int Cn, int Cpad,
 
 // Pack "rows" of an operand into slice tiles.  Element (r, k) is X[r*sr + k*sk].
 // Output: planes[s][rt][kt] tiles of `rows_per_tile` x KC BF16 digits.
+template <int S>
 __global__ void k_pack(const double *X, int64_t sr, int64_t sk, int R, int Kd, int Rpad, int Kpad, const int *e,
-                       int S, int rows_per_tile, __nv_bfloat16 *planes) {
+                       int rows_per_tile, __nv_bfloat16 *planes) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t total = (int64_t)Rpad * Kpad;
   if (idx >= total) return;
   const int r = (int)(idx / Kpad), k = (int)(idx % Kpad);
   const double x = (r < R && k < Kd) ? X[(int64_t)r * sr + (int64_t)k * sk] : 0.0;
-  float d[MAXS];
-  digits_of(x, e[r], S, d);
+  float d[S];
+  digits_of<S>(x, e[r], d);
   const int rt = r / rows_per_tile, kt = k / KC;
   const int64_t tile_bytes = (int64_t)rows_per_tile * KC * 2;
   const int64_t ntile = (int64_t)(Rpad / rows_per_tile) * (Kpad / KC);
   const int64_t tbase = ((int64_t)rt * (Kpad / KC) + kt) * tile_bytes + tile_off(r % rows_per_tile, k % KC);
   char *base = (char *)planes;
-  for (int s = 0; s < S; s++)
-    *(__nv_bfloat16 *)(base + (int64_t)s * ntile * tile_bytes + tbase) = __float2bfloat16_rn(d[s] * slice_scale(s));
+#pragma unroll
+  for (int t = 0; t < S; t++)
+    *(__nv_bfloat16 *)(base + (int64_t)t * ntile * tile_bytes + tbase) = __float2bfloat16_rn(d[t] * slice_scale(t));
+}
+
+void launch_pack(const double *X, int64_t sr, int64_t sk, int R, int Kd, int Rpad, int Kpad, const int *e, int S,
+                 int rows_per_tile, __nv_bfloat16 *planes, cudaStream_t st) {
+  const int64_t n = (int64_t)Rpad * Kpad;
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  switch (S) {
+    case 1: k_pack<1><<<grid, 256, 0, st>>>(X, sr, sk, R, Kd, Rpad, Kpad, e, rows_per_tile, planes); break;
+    case 2: k_pack<2><<<grid, 256, 0, st>>>(X, sr, sk, R, Kd, Rpad, Kpad, e, rows_per_tile, planes); break;
+    case 3: k_pack<3><<<grid, 256, 0, st>>>(X, sr, sk, R, Kd, Rpad, Kpad, e, rows_per_tile, planes); break;
+    case 4: k_pack<4><<<grid, 256, 0, st>>>(X, sr, sk, R, Kd, Rpad, Kpad, e, rows_per_tile, planes); break;
+    case 5: k_pack<5><<<grid, 256, 0, st>>>(X, sr, sk, R, Kd, Rpad, Kpad, e, rows_per_tile, planes); break;
+    case 6: k_pack<6><<<grid, 256, 0, st>>>(X, sr, sk, R, Kd, Rpad, Kpad, e, rows_per_tile, planes); break;
+    case 7: k_pack<7><<<grid, 256, 0, st>>>(X, sr, sk, R, Kd, Rpad, Kpad, e, rows_per_tile, planes); break;
+    default: k_pack<8><<<grid, 256, 0, st>>>(X, sr, sk, R, Kd, Rpad, Kpad, e, rows_per_tile, planes); break;
+  }
 }
 
 // ------------------------------------------------------------------ the GEMM
@@ -543,8 +581,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
       const int nk = ti.Kpad / KC;
       for (int c = 0; c < nk; c++, cg++) {
         const int st = cg % nst;
-        const int gpos = c % (2 * GROUP);
-        if (gpos % GROUP == 0 && gg > 0 && !mbar_wait(accempty, (gg - 1) & 1)) {
+        if (c % GROUP == 0 && gg > 0 && !mbar_wait(accempty, (gg - 1) & 1)) {
           atomicExch(abort_flag, 1);
           break;
         }
@@ -557,11 +594,10 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
         const uint32_t sa = smem_u32(smem + st * stage_bytes);
         const uint32_t sb = sa + S * A_TILE;
         // K step kk covers core-matrix columns 2kk, 2kk+1 (LBO = 128 B apart)
-        // c = 0 or gpos = 0: every accumulator starts a group; gpos = GROUP: those of PART_MASK
-        const uint32_t open = c == 0 || gpos == 0 ? 0xFFu : gpos == GROUP ? PART_MASK : 0u;
+        const uint32_t open = c % GROUP == 0 ? 0xFFu : 0u;  // every accumulator starts a group
         issue_stage_s(S, tmem, sdesc(sa, 128, (KC / 8) * 128), sdesc(sb, 128, (KC / 8) * 128), idesc, open);
         mma_commit(&empty[st]);
-        if (gpos % GROUP == GROUP - 1 || c == nk - 1) {
+        if (c % GROUP == GROUP - 1 || c == nk - 1) {
           mma_commit(accfull);
           gg++;
         }
@@ -590,9 +626,6 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
 #pragma unroll
       for (int n = 0; n < HN; n++) acc[n] = 0;
       for (int grp = 0; grp < ngroups; grp++, gg++) {
-        // group grp ends after stage min(GROUP (grp + 1), nk) - 1; at odd grp and at the tile's
-        // end every accumulator is folded, at even grp those of PART_MASK
-        const uint32_t fold = (grp & 1) || grp == ngroups - 1 ? 0xFFu : PART_MASK;
         if (!mbar_wait(accfull, gg & 1)) {
           atomicExch(abort_flag, 1);
           ok = false;
@@ -601,7 +634,6 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
         tc_fence_after();
         static_assert(HN == 40, "drain loads: 16 + 16 + 8 columns");
         for (int a = 0; a < nacc; a++) {
-          if (!((fold >> a) & 1u)) continue;
           // all loads of the accumulator in flight before one wait
           const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * TN + h * HN);
           uint32_t r0[16], r1[16], r2[8];
@@ -738,15 +770,8 @@ extern "C" rix_status rix_gemm_sliced(const double *A, int64_t lda, const double
   cudaMemsetAsync(err, 0, 4, st);
   k_row_exp<<<(Mpad + 7) / 8, dim3(32, 8), 0, st>>>(A, lda, M, K, Mpad, eA);
   k_col_exp<<<(Npad + 127) / 128, 128, 0, st>>>(B, ldb, K, N, Npad, eB);
-  {
-    const int64_t n = (int64_t)Mpad * Kpad;
-    k_pack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(A, lda, 1, M, K, Mpad, Kpad, eA, S, TM, Ap);
-  }
-  {
-    // B^T as rows: element (n, k) = B[k*ldb + n]
-    const int64_t n = (int64_t)Npad * Kpad;
-    k_pack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(B, 1, ldb, N, K, Npad, Kpad, eB, S, TN, Bp);
-  }
+  launch_pack(A, lda, 1, M, K, Mpad, Kpad, eA, S, TM, Ap, st);
+  launch_pack(B, 1, ldb, N, K, Npad, Kpad, eB, S, TN, Bp, st);  // B^T as rows: element (n, k) = B[k*ldb + n]
   GemmArgs g{Ap, Bp, eA, eB, C, ldc, M, N, Mpad, Npad, Kpad, S, 0, fixed_point_drop(Kpad, S), err,
              nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   const int smem = smem_bytes(S);
@@ -805,36 +830,39 @@ __global__ void k_slice_exp(int64_t n0, int64_t n, Acc acc, int *e) {
   if (w >= n0 + n) return;
   const typename Acc::Row R = acc.row(w);
   int m = -2000;
-  for (int k = lane; k < R.pr.Kpad; k += 32) m = max(m, exp_of(fabs(acc.at(R, k))));
+  // four elements per lane in flight (their gathers are independent)
+  for (int k = lane; k < R.pr.Kpad; k += 128) {
+    double v[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) v[j] = k + 32 * j < R.pr.Kpad ? acc.at(R, k + 32 * j) : 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; j++) m = max(m, exp_of(fabs(v[j])));
+  }
   for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if (lane == 0) e[(acc.is_b ? R.pr.eboff : R.pr.eaoff) + R.r] = m;
 }
 
-// Digit s of two values as a packed BF16 pair (low half: x0), with integer
+// Digit t of two values as a packed BF16 pair (low half: x0), with integer
 // and FMA-pipe operations only (the conversion unit is the scarce one): the
-// 7-bit digit d is made exact in FP32 through the 2^23 trick, scaled by
-// 2^-7s in the same FMA (exact: at most 7 significant bits), and its top 16
-// bits are its BF16 encoding; the signs are applied to the pair at the end.
+// balanced digit d (|d| <= 128) is made exact in FP32 by adding it to the bits
+// of 1.5 2^23, scaled by 2^-7t in the same FMA (exact: at most 8 significant
+// bits, 128 being a power of two), and its top 16 bits are its BF16 encoding;
+// the signs of the values are applied to the pair at the end.
 template <int S>
 __device__ __forceinline__ void digit_pairs(double x0, double x1, int e, uint32_t (&w)[S]) {
-  uint64_t fr[2];
+  int d[2][S];
   uint32_t sg = 0;
 #pragma unroll
   for (int h = 0; h < 2; h++) {
     const uint64_t b = (uint64_t)__double_as_longlong(h ? x1 : x0);
-    const int ex = (int)((b >> 52) & 0x7FF);
-    const uint64_t m = (b & ((1ull << 52) - 1)) | (1ull << 52);
-    const int sh = 12 + (ex - 1023) - e;  // fraction |x| / 2^e as a 64-bit fixed point: m << sh
-    fr[h] = ex == 0 ? 0 : sh >= 0 ? m << sh : (sh > -64 ? m >> -sh : 0);
+    balanced_digits<S>(frac_of(b, e), d[h]);
     sg |= (uint32_t)(b >> 63) << (15 + 16 * h);
   }
 #pragma unroll
   for (int t = 0; t < S; t++) {
     const float sc = __int_as_float((127 - 7 * t) << 23);  // 2^-7t
-    const uint32_t d0 = (uint32_t)(fr[0] >> (57 - 7 * t)) & 127u;
-    const uint32_t d1 = (uint32_t)(fr[1] >> (57 - 7 * t)) & 127u;
-    const float f0 = __fmaf_rn(__uint_as_float(0x4B000000u | d0), sc, -8388608.f * sc);
-    const float f1 = __fmaf_rn(__uint_as_float(0x4B000000u | d1), sc, -8388608.f * sc);
+    const float f0 = __fmaf_rn(__uint_as_float(0x4B400000u + (uint32_t)d[0][t]), sc, -12582912.f * sc);
+    const float f1 = __fmaf_rn(__uint_as_float(0x4B400000u + (uint32_t)d[1][t]), sc, -12582912.f * sc);
     w[t] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632) ^ sg;
   }
 }
