@@ -1007,10 +1007,11 @@ namespace {
 
 int plan_slices(const rix_ctx *ctx, int kind) { return rix_plan_slices(ctx, kind); }
 
-// Estimated rates on GB300 for the choice between the FP64 kernels and the
-// tensor-core regroupings: about 1 TFLOP/s for the FP64 kernels, about
-// 0.5 PFLOP/s issued for the sliced GEMM.
-constexpr double FP64_RATE = 1.0e12, TC_RATE = 5.0e14;
+// Rates measured on GB300 (the (H2O)64 and 768-atom ice builds) for the
+// choice between an FP64 kernel and a tensor-core regrouping: the FP64 kernels
+// of term 1 (k_X12, ~0.7 TFLOP/s), of Z (k_Z, ~1.2) and of T (k_T, ~1.0), and
+// the sliced GEMM with its slicing kernels (~0.75 PFLOP/s issued).
+constexpr double FP64_RATE_T1 = 0.7e12, FP64_RATE_Z = 1.2e12, FP64_RATE_T = 1.0e12, TC_RATE = 7.5e14;
 
 // Build the problems of one plan (see the section comment for the three kinds).
 // count_only: no host arrays, just the map bytes, the largest problem's slices
@@ -1043,7 +1044,7 @@ rix_status plan_host(rix_ctx *ctx, int kind, const std::vector<int64_t> &ptrZ, P
       const double Mp = std::ceil(M / TM) * TM, Np = std::ceil(sE / TN) * TN,
                    Kp = std::ceil(naG * nbG / KC) * KC;
       const double tc = 2.0 * Mp * Np * Kp * npairs;
-      if (sE > 0 && tc / TC_RATE < f64 / FP64_RATE) {
+      if (sE > 0 && tc / TC_RATE < f64 / FP64_RATE_Z) {
         h.use[g] = 1;
         h.fl64 += f64;
       }
@@ -1625,7 +1626,7 @@ rix_status rix_t1_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
     const double Mp = (double)((M + TM - 1) / TM * TM), Np = (double)((naE * nbE + TN - 1) / TN * TN),
                  Kp = (double)((K + KC - 1) / KC * KC);
     const double tc = 2.0 * Mp * Np * Kp * npairs;
-    if (tc / TC_RATE < f64 / FP64_RATE) {
+    if (tc / TC_RATE < f64 / FP64_RATE_T1) {
       use[e] = 1;
       fl64_tc += f64;
     }
@@ -2012,7 +2013,7 @@ rix_status rix_tt_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
     for (int64_t t = row2[a]; t < row2[a + 1]; t++) N += ctx->nb_at[rix::key_b(ctx->keys2[t])];
     const double Mp = std::ceil((double)naA * nbA / TM) * TM, Np = std::ceil((double)N / TN) * TN,
                  Kp = std::ceil((double)K / KC) * KC;
-    if (2.0 * Mp * Np * Kp * npairs / TC_RATE < f64 / FP64_RATE) {
+    if (2.0 * Mp * Np * Kp * npairs / TC_RATE < f64 / FP64_RATE_T) {
       use[a] = 1;
       fl64 += f64;
     }
