@@ -204,7 +204,8 @@ def measure(args, s, pk, precision, dev, world, rank, local):
     cap = 0
     if s.n_atoms > 1000:
         cap = int(torch.cuda.mem_get_info(dev)[0] - (24 << 30))
-    ex = Exchange.from_system(s, precision=precision, profile=1, max_workspace_bytes=cap)
+    kw = {"n_slices": args.slices} if precision == "mixed" else {}
+    ex = Exchange.from_system(s, precision=precision, profile=1, max_workspace_bytes=cap, **kw)
     assert np.array_equal(ex.pair_keys(), pk.keys)
     ex.set_CV(pk.C, pk.V)          # straight from host memory (copied into library storage)
     D = torch.from_numpy(pk.D).to(dev)
@@ -396,7 +397,7 @@ def run_rix(args):
             "vs_baseline": None, "dtype": "f64" if head == "fp64" else "bf16-slices+f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD_NAMES[args.config], "precision": head,
-                       "n_slices": 6 if head == "mixed" else None,
+                       "n_slices": args.slices if head == "mixed" else None,
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}",
                        "timing": "CUDA graph replay" if args.graph else "eager launches",
                        "autotuned_tiles_x12_z_x34": r["tiles"]},
@@ -431,6 +432,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--graph", type=int, default=1, help="1: time CUDA graph replays of one step (default)")
     ap.add_argument("--autotune", type=int, default=1, help="1: rix_autotune before the warm-up (default)")
+    ap.add_argument("--slices", type=int, default=6,
+                    help="mixed path: BF16 slices per operand (the regrouped plans take one more); 3 = the "
+                         "three-term split")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
