@@ -60,7 +60,7 @@ __global__ void k_cnt_U2(int64_t np, const int32_t *pA, const int32_t *pB, const
 // Terms 1 and 2 of X(A,E'), the tests of the FP64 kernel: term 1 needs C(G',E')
 // and V(A,E'), term 2 needs C(G',E') and V(A,G').
 __global__ void k_cnt_X12(int64_t n2, const int64_t *ptr, const rix::X12Entry *L, const int32_t *atomA2,
-                          const int32_t *atomB2, const int32_t *map2to1, const int32_t *pA, const int32_t *pB,
+                          const int32_t *atomB2, const int32_t *map2to1, const int32_t *pA,
                           const int32_t *nb, const int32_t *na, const uint8_t *keepC, const uint8_t *keepV,
                           const uint8_t *t1tc, double *out) {
   double all = 0.0, t2 = 0.0, t1tc_s = 0.0;
@@ -82,7 +82,6 @@ __global__ void k_cnt_X12(int64_t n2, const int64_t *ptr, const rix::X12Entry *L
   add_out(out, 2, all + t2);
   add_out(out, 6, t2);
   add_out(out, 7, t1tc_s);
-  (void)pB;
 }
 
 // Z(B,E') <- D(B,G') V(B,G') C(G',E'): 2 na_B na_G nb_G nb_E + 2 na_B nb_B nb_G nb_E per kept product.
@@ -153,8 +152,7 @@ extern "C" rix_status rix_count_flops(rix_ctx *ctx, const double *D, double *flo
     k_cnt_U2<<<grid_for(ctx->np), CNT_THREADS, 0, st>>>(ctx->np, ctx->d_pA, ctx->d_pB, ctx->d_nb, ctx->d_na,
                                                         ctx->d_keepV, d_out);
     k_cnt_X12<<<grid_for(n2), CNT_THREADS, 0, st>>>(n2, ctx->d_ptrX12, ctx->d_LX12, ctx->d_atomA2,
-                                                    ctx->d_atomB2, ctx->d_map2to1, ctx->d_pA, ctx->d_pB,
-                                                    ctx->d_nb, ctx->d_na, ctx->d_keepC, ctx->d_keepV,
+                                                    ctx->d_atomB2, ctx->d_map2to1, ctx->d_pA, ctx->d_nb, ctx->d_na, ctx->d_keepC, ctx->d_keepV,
                                                     ctx->d_t1tc, d_out);
     k_cnt_Z<<<grid_for(n2), CNT_THREADS, 0, st>>>(n2, ctx->d_ptrZ, ctx->d_LZ, ctx->d_atomA2, ctx->d_atomB2,
                                                   ctx->d_pB, ctx->d_nb, ctx->d_na, ctx->d_keepC, ctx->d_keepV,
