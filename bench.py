@@ -432,7 +432,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--graph", type=int, default=1, help="1: time CUDA graph replays of one step (default)")
     ap.add_argument("--autotune", type=int, default=1, help="1: rix_autotune before the warm-up (default)")
-    ap.add_argument("--slices", type=int, default=6,
+    ap.add_argument("--slices", type=int, default=5,
                     help="mixed path: BF16 slices per operand (the regrouped plans take one more); 3 = the "
                          "three-term split")
     args = ap.parse_args()

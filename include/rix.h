@@ -95,7 +95,8 @@ typedef struct {
 
 typedef struct {
   int32_t precision;               /* rix_precision */
-  int32_t n_slices;                /* mixed mode: BF16 slices per operand (0 = default) */
+  int32_t n_slices;                /* mixed mode: BF16 slices per operand, 1..8 (0 = default, 5; the
+                                      regrouped plans take one more) */
   int64_t max_workspace_bytes;     /* 0 = no limit beyond the device's free memory */
   int32_t verbose;                 /* 0 = silent */
   int32_t profile;                 /* 1 = record a CUDA event after every stage of rix_build_K

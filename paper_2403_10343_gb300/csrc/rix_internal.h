@@ -120,7 +120,7 @@ struct rix_ctx {
   int64_t *d_bofs = nullptr;            // global basis offset of each atom
   // mixed precision: terms 3+4 and term 2 as batched sliced GEMMs on the tensor cores
   bool have_mx = false;
-  int32_t mx_S = 6;
+  int32_t mx_S = 5;
   struct rix_mx_plan *mx34 = nullptr, *mx2 = nullptr;
   struct rix_t1_plan *mx1 = nullptr;           // term 1 for the column atoms where it pays
   struct rix_mx_plan *mxz = nullptr;            // term-4 intermediate for the middle atoms where it pays
