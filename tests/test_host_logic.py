@@ -1,0 +1,92 @@
+"""Host-side logic without a GPU.
+
+* The ctypes structures of the binding have the size and field offsets of the
+  C structures in include/rix.h (compiled here with the host C compiler), so
+  no option or statistic is read from the wrong place.
+* The bench's FLOP bookkeeping: the screened counts replace the setup-time
+  ones, and each stage's rate is quoted on the pipe that runs it.
+"""
+import ctypes
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+from paper_2403_10343_gb300 import rix  # noqa: E402
+import bench  # noqa: E402
+
+
+def _c_layout(struct, fields):
+    """sizeof and offsetof of a C struct of include/rix.h, from the host compiler."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    lines = [f'printf("%zu\\n", sizeof({struct}));']
+    lines += [f'printf("%zu\\n", offsetof({struct}, {f}));' for f in fields]
+    src = ("#include <stddef.h>\n#include <stdio.h>\n#include \"rix.h\"\nint main(void) {\n"
+           + "\n".join(lines) + "\nreturn 0;\n}\n")
+    with tempfile.TemporaryDirectory() as d:
+        c, exe = os.path.join(d, "l.c"), os.path.join(d, "l")
+        open(c, "w").write(src)
+        subprocess.run([cc, "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
+    return int(out[0]), [int(x) for x in out[1:]]
+
+
+@pytest.mark.parametrize("py, c", [(rix._System, "rix_system"), (rix._Options, "rix_options"),
+                                   (rix._Stats, "rix_stats_t")])
+def test_binding_structs_match_header(py, c):
+    names = [f for f, _ in py._fields_]
+    size, offs = _c_layout(c, names)
+    assert ctypes.sizeof(py) == size
+    assert [getattr(py, f).offset for f in names] == offs
+
+
+STATS = {
+    "flops_stage": [10.0, 1.0, 40.0, 20.0, 8.0, 2.0], "flops_fp64": 81.0, "flops_term2": 6.0,
+    "flops_term1_tc": 30.0, "flops_z_tc": 20.0, "flops_t_tc": 10.0, "tensor_flops": 1e4,
+    "tensor_flops_stage": [1e3, 2e3, 3e3, 2.5e3, 1.5e3],
+}
+
+
+def test_screened_counts_replace_setup_counts():
+    cnt = {"T": 5.0, "U2": 1.0, "X12": 30.0, "Z": 12.0, "X34": 8.0, "sym": 2.0, "term2": 4.0,
+           "term1_tc": 20.0, "z_tc": 12.0, "t_tc": 5.0}
+    s = bench.screened(STATS, cnt)
+    assert s["flops_stage"] == [5.0, 1.0, 30.0, 12.0, 8.0, 2.0]
+    assert s["flops_fp64"] == 58.0 and s["flops_fp64_unscreened"] == 81.0
+    assert (s["flops_term2"], s["flops_term1_tc"], s["flops_z_tc"], s["flops_t_tc"]) == (4.0, 20.0, 12.0, 5.0)
+    assert s["tensor_flops"] == STATS["tensor_flops"]  # issued tensor FLOPs do not depend on screening
+
+
+def test_stage_split_between_pipes():
+    # FP64 build: every stage on the FP64 pipe with its whole count
+    for st, i in (("T", 0), ("U2", 1), ("X12", 2), ("Z", 3), ("X34", 4)):
+        assert bench.stage_flops(STATS, st, "fp64") == STATS["flops_stage"][i]
+        assert bench.stage_fp64_share(STATS, st, "fp64") == 1.0
+    # mixed build: terms 1 (moved part) and 2 form TC12, the FP64 kernel keeps the rest of X12
+    assert bench.stage_flops(STATS, "TC12", "mixed") == 36.0
+    assert bench.stage_flops(STATS, "X12", "mixed") == 4.0
+    assert bench.stage_fp64_share(STATS, "X34", "mixed") == 0.0
+    assert bench.stage_fp64_share(STATS, "Z", "mixed") == 0.0
+    assert bench.stage_fp64_share(STATS, "T", "mixed") == 0.0
+
+
+def test_roofline_picks_the_longest_stage():
+    r = {"stats": STATS, "stage_ms": {"T": 1.0, "U2": 0.5, "X12": 10.0, "Z": 4.0, "X34": 2.0}}
+    roof, _ = bench.roofline(None, "fp64", r)
+    assert roof["kernel"] == "k_X12" and roof["bound"] == "alu"
+    assert abs(roof["achieved"] - 40.0 / 1e-2 / 1e12) < 1e-18
+    assert abs(roof["frac"] - roof["achieved"] / roof["peak"]) < 1e-18
+    # mixed: the tensor-core stages together take longer than any FP64 stage
+    r = {"stats": STATS, "stage_ms": {"T": 1.0, "U2": 0.5, "X12": 0.1, "TC12": 5.0, "Z": 4.0, "X34": 2.0}}
+    roof, tc = bench.roofline(None, "mixed", r)
+    assert roof is tc and roof["bound"] == "tensor"
+    ms = 1.0 + 5.0 + 4.0 + 2.0
+    assert abs(roof["achieved"] - STATS["tensor_flops"] / (ms * 1e-3) / 1e12) < 1e-12
