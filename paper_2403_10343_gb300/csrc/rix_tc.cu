@@ -210,9 +210,10 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
 
 // An FP32 accumulator value times 2^sh as a 64-bit integer, truncated toward
 // zero, with integer operations only (the conversion instructions with a
-// 64-bit side run at the FP64 rate).  Used for the last accumulator, which
-// holds several diagonals and is not an integer in its own units; below the
-// fixed-point unit it is truncated (< 1 unit per group).
+// 64-bit side run at the FP64 rate).  The general fallback of drain_any for
+// the last accumulator, which holds several diagonals and is not an integer in
+// its own units; below the fixed-point unit it is truncated (< 1 unit per
+// group).
 __device__ __forceinline__ int64_t f32_fixed(uint32_t b, int sh) {
   const int e = (int)((b >> 23) & 0xFF);
   if (e == 0) return 0;  // zero; subnormals lie far below the fixed-point unit
