@@ -102,7 +102,8 @@ class Clocks:
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
-        self.path = tempfile.mktemp(suffix=".csv")
+        self.dir = tempfile.mkdtemp(prefix="rix_clocks")
+        self.path = os.path.join(self.dir, "clocks.csv")
         self.gpu = gpu_index
         self.proc = None
 
@@ -139,6 +140,10 @@ class Clocks:
                     if v.lower() == "active":
                         reasons.add(nm)
             os.unlink(self.path)
+        except OSError:
+            pass
+        try:
+            os.rmdir(self.dir)
         except OSError:
             pass
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
