@@ -117,6 +117,10 @@ class Clocks:
 
     def stop(self):
         if self.proc is None:
+            try:
+                os.rmdir(self.dir)
+            except OSError:
+                pass
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         time.sleep(0.3)
         self.proc.terminate()
