@@ -68,7 +68,7 @@ typedef enum {
   RIX_ECUDA = 3,         /* a CUDA call failed; rix_last_error() has the message */
   RIX_ENOTSYM = 4,       /* C or V violates the pair symmetry */
   RIX_ETIMEOUT = 5,      /* a bounded device wait ran out */
-  RIX_EUNSUPPORTED = 6,  /* valid request this build does not support */
+  RIX_EUNSUPPORTED = 6,  /* valid request the library does not support */
   RIX_ESTATE = 7         /* call out of order (e.g. build before set_CV) */
 } rix_status;
 
