@@ -203,6 +203,17 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def max_over_ranks(x, world, dev):
+    """The largest value over the ranks: the job's step time is its slowest rank's."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
 def measure(args, s, pk, precision, dev, world, rank, local):
     """Warm up, time args.steps builds (+ energy) and the end-to-end variant; returns a dict."""
     import torch
@@ -269,10 +280,7 @@ def measure(args, s, pk, precision, dev, world, rank, local):
     clocks = clk.stop()
     ms = e0.elapsed_time(e1) / args.steps
     ex.stage_times()
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
+    ms = max_over_ranks(ms, world, dev)
     # end to end through the same API with host buffers: D in, K and E_x out, every step
     Dh = torch.from_numpy(pk.D).pin_memory()
     Kh = torch.empty(ex.k_elems, dtype=torch.float64).pin_memory()
@@ -295,10 +303,7 @@ def measure(args, s, pk, precision, dev, world, rank, local):
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.steps
     ex.stage_times()
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = t.item()
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
     stats = screened(ex.stats(), ex.count_flops(D))
     launches = stats["launches_build"] + 3  # build + energy kernels
     out = {"ms": ms, "e2e_ms": e2e_ms, "stage_ms": stage_ms, "stats": stats, "clocks": clocks, "graph": args.graph,
