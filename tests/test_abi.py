@@ -34,3 +34,41 @@ def test_strerror_without_gpu():
     lib.rix_strerror.restype = ctypes.c_char_p
     assert lib.rix_strerror(0) == b"ok"
     assert lib.rix_strerror(4).startswith(b"C or V")
+
+
+def test_invalid_arguments_fail_before_any_device_work():
+    """The documented argument checks return RIX_EINVAL without touching a GPU."""
+    from paper_2403_10343_gb300 import build, rix
+    lib = ctypes.CDLL(build.build())
+    P = ctypes.c_void_p
+    lib.rix_setup.argtypes = [ctypes.POINTER(rix._System), ctypes.POINTER(rix._Options), ctypes.POINTER(P)]
+    out = P(123)
+    assert lib.rix_setup(None, None, ctypes.byref(out)) == 1 and not out.value
+    xyz = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
+    sp = (ctypes.c_int32 * 1)(0)
+    nb, na = (ctypes.c_int32 * 1)(14), (ctypes.c_int32 * 1)(56)
+    good = dict(n_atoms=1, xyz_bohr=ctypes.cast(xyz, P), species=ctypes.cast(sp, P), n_species=1,
+                nbas_per_species=ctypes.cast(nb, P), naux_per_species=ctypes.cast(na, P), cell_bohr=None,
+                cutoff_bohr=0.0, screen_tau=0.0)
+    cell = (ctypes.c_double * 9)(10, 0, 0, 0, 10, 0, 0, 0, 10)
+    bad_cases = [
+        dict(good, n_atoms=0),                              # no atoms
+        dict(good, species=ctypes.cast((ctypes.c_int32 * 1)(1), P)),  # species id out of range
+        dict(good, cell_bohr=ctypes.cast(cell, P)),         # periodic cell without a cutoff
+        dict(good, nbas_per_species=ctypes.cast((ctypes.c_int32 * 1)(65), P)),  # block above 64
+        dict(good, xyz_bohr=ctypes.cast((ctypes.c_double * 3)(0.0, float("nan"), 0.0), P)),
+    ]
+    for kw in bad_cases:
+        sysd = rix._System(**kw)
+        assert lib.rix_setup(ctypes.byref(sysd), None, ctypes.byref(out)) == 1, kw
+        assert not out.value
+    opt = rix._Options(7, 0, 0, 0, 0, 0, 0)                # unknown precision
+    sysd = rix._System(**good)
+    assert lib.rix_setup(ctypes.byref(sysd), ctypes.byref(opt), ctypes.byref(out)) == 1
+    lib.rix_stats.argtypes = [P, P]
+    assert lib.rix_stats(None, None) == 1
+    lib.rix_last_error.restype = ctypes.c_char_p
+    lib.rix_last_error.argtypes = [P]
+    assert lib.rix_last_error(None) == b""
+    lib.rix_destroy.argtypes = [P]
+    lib.rix_destroy(None)                                   # a no-op
