@@ -123,6 +123,7 @@ typedef struct {
   double flops_z_tc;               /* mixed mode: the Z FLOPs (FP64 grouping) moved to the tensor cores */
   int64_t tz_bytes;                /* the T and Z buffers (part of workspace_bytes) */
   double flops_t_tc;               /* mixed mode: the T FLOPs moved to the tensor cores */
+  int64_t nbasis;                  /* basis functions per cell (the side of rix_fold_gamma's matrix) */
 } rix_stats_t;
 
 /* Set up a system: copies the host arrays, builds the pair list on the device
@@ -185,8 +186,9 @@ rix_status rix_energy(rix_ctx *ctx, const double *D_dev, const double *K_dev,
  * 512 KB device array owned by the library (kept on every GPU that loads it
  * until exit).  Contexts with more than 16,777,216 pairs are rejected
  * (RIX_EINVAL).  Every call on a device shares that array: calls whose work
- * overlaps on the GPU race.  The first call on a device looks up the array's
- * address, so make it before any stream capture begins.  Asynchronous. */
+ * overlaps on the GPU race.  rix_setup looks up the array's address with the
+ * context's device current, so this call makes no CUDA runtime call besides
+ * its kernel launches.  Asynchronous. */
 rix_status rix_energy_noalloc(rix_ctx *ctx, const double *D_dev, const double *K_dev,
                               double *Ex_dev, void *stream);
 
@@ -215,6 +217,27 @@ rix_status rix_fold_gamma(rix_ctx *ctx, const double *K_dev, double *Kdense_dev,
  * buffers on `stream` and synchronises it.  ETIMEOUT if a device wait ran out. */
 rix_status rix_gemm_sliced(const double *A, int64_t lda, const double *B, int64_t ldb, double *C,
                            int64_t ldc, int32_t M, int32_t N, int32_t K, int32_t n_slices, void *stream);
+
+/* Test hook for the bounded waits (no counterpart in the paper): runs the
+ * sliced-GEMM kernel on a small zero problem (M = 130, N = 90, K = 70, three
+ * slices) whose MMA issuer waits on a shared-memory barrier that nothing
+ * completes; every wait of the launch gives up after wait_ns (1 .. 2e9), the
+ * kernel waits for its own bulk copies, frees its tensor memory and records the
+ * timeout.  ctx == NULL: synchronises `stream` and returns RIX_ETIMEOUT when
+ * that path worked.  ctx != NULL: the kernel records the timeout in the
+ * context's status word, the call returns RIX_OK without synchronising, and
+ * rix_check (or the context's next entry point) reports RIX_ETIMEOUT.  The
+ * stream and the CUDA context stay usable either way.  RIX_EINVAL for a
+ * wait_ns out of range.  Allocates its operands on `stream`. */
+rix_status rix_test_stalled_gemm(rix_ctx *ctx, int64_t wait_ns, void *stream);
+
+/* Synchronises `stream` and reports the device-side status of the context:
+ * RIX_ETIMEOUT if a bounded wait of one of its kernels gave up since the last
+ * report (the results of that call are invalid; the flag is then cleared),
+ * RIX_ECUDA if the stream holds a CUDA error.  rix_build_K, rix_energy,
+ * rix_energy_noalloc, rix_backward and rix_set_CV make the same report at
+ * entry for work that has already completed.  ESTATE inside a graph capture. */
+rix_status rix_check(rix_ctx *ctx, void *stream);
 
 rix_status rix_stats(const rix_ctx *ctx, rix_stats_t *out);
 

@@ -710,6 +710,7 @@ extern "C" rix_status rix_backward(rix_ctx *ctx, const double *D, double gEx, do
     ctx->last_error = "context set up without rix_options.backward";
     return RIX_ESTATE;
   }
+  if (rix_status s0 = rix_take_err(ctx)) return s0;
   cudaStream_t st = (cudaStream_t)stream;
   if (!g_bwd_attr) {
     cudaFuncSetAttribute(kb_ZV, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_BIG * 8);

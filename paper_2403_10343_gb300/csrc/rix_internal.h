@@ -133,7 +133,11 @@ struct rix_ctx {
   int n_t1tc = 0;
   void *d_mx_buf = nullptr;                     // slices of one group of problems
   int64_t mx_buf_bytes = 0;
-  int *d_mx_err = nullptr;
+  int *d_mx_err = nullptr;                      // = d_err (the GEMM kernels' timeout flag)
+  // status word of the bounded device waits, in mapped pinned host memory: a kernel
+  // that gave up sets it, and the next entry point (or rix_check) reports it
+  int *h_err = nullptr, *d_err = nullptr;
+  double *noalloc_scratch = nullptr;            // device address of rix_energy_noalloc's fixed array
   std::vector<int64_t> offU_h;                  // U2 offsets per pair (host copy)
 
   // memory plan: row blocks of consecutive atoms; item segments per block
@@ -167,6 +171,11 @@ struct rix_ctx {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<cudaEvent_t> ev_pending;  // NSTAGE + 1 per recorded build
 };
+
+// RIX_ETIMEOUT (and the flag cleared) if a bounded device wait of an earlier call gave up
+rix_status rix_take_err(rix_ctx *ctx);
+// looks up the device address of rix_energy_noalloc's fixed array for this context (rix_noalloc.cu)
+rix_status rix_noalloc_attach(rix_ctx *ctx);
 
 // record the stage boundary `i` of the current build (no-op without profiling)
 rix_status rix_prof_mark(rix_ctx *ctx, int i, cudaStream_t st);

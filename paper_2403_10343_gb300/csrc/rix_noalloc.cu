@@ -17,25 +17,30 @@
 //    call's partial sums; each call overwrites every slot it reads, so nothing
 //    needs clearing, but calls whose work overlaps on the GPU (different
 //    streams, or another context on the same device) race on it;
-//  * the first call on a device looks up the array's device address
-//    (cudaGetSymbolAddress) with that device current; make that first call
-//    before any stream capture is started.
-#include <mutex>
-
+//  * the array's device address is looked up once per context, in rix_setup,
+//    with the context's device current (host code cannot use the array's name:
+//    on the host it is only a stand-in for the device symbol), so the entry
+//    point itself makes no CUDA runtime call besides its two kernel launches.
 #include "rix_internal.h"
 
 #define RIX_NOALLOC_MAX_PARTIALS 65536
-#define RIX_NOALLOC_MAX_DEVICES 64
 
 static __device__ __align__(256) double g_noalloc_partials[RIX_NOALLOC_MAX_PARTIALS];
 
 rix_status rix_launch_energy_partials(rix_ctx *ctx, const double *D, const double *K, double *Ex,
                                       double *partials, cudaStream_t st);
 
-namespace {
-std::mutex g_mu;
-double *g_addr[RIX_NOALLOC_MAX_DEVICES] = {nullptr};
-}  // namespace
+rix_status rix_noalloc_attach(rix_ctx *ctx) {
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->last_error = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+    return RIX_ECUDA;
+  }
+  ctx->noalloc_scratch = (double *)p;
+  return RIX_OK;
+}
 
 extern "C" rix_status rix_energy_noalloc(rix_ctx *ctx, const double *D, const double *K, double *Ex,
                                          void *stream) {
@@ -44,28 +49,11 @@ extern "C" rix_status rix_energy_noalloc(rix_ctx *ctx, const double *D, const do
     ctx->last_error = "rix_energy_noalloc: more than 16,777,216 pairs (fixed scratch of 65536 partial sums)";
     return RIX_EINVAL;
   }
-  int dev = 0;
-  RIX_CUDA_TRY(ctx, cudaGetDevice(&dev));
-  if (dev < 0 || dev >= RIX_NOALLOC_MAX_DEVICES) {
-    ctx->last_error = "rix_energy_noalloc: device ordinal beyond 63";
-    return RIX_EUNSUPPORTED;
+  if (!ctx->noalloc_scratch) {
+    ctx->last_error = "rix_energy_noalloc: scratch address not set up";
+    return RIX_ESTATE;
   }
-  double *scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-      // host code cannot use g_noalloc_partials directly: its host-side name
-      // is only a stand-in, so fetch the device address once per device
-      void *p = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-      if (e != cudaSuccess) {
-        cudaGetLastError();
-        ctx->last_error = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
-        return RIX_ECUDA;
-      }
-      g_addr[dev] = (double *)p;
-    }
-    scratch = g_addr[dev];
-  }
-  return rix_launch_energy_partials(ctx, D, K, Ex, scratch, (cudaStream_t)stream);
+  rix_status s = rix_take_err(ctx);
+  if (s != RIX_OK) return s;
+  return rix_launch_energy_partials(ctx, D, K, Ex, ctx->noalloc_scratch, (cudaStream_t)stream);
 }

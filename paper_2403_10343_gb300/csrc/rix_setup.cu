@@ -907,6 +907,14 @@ extern "C" rix_status rix_setup(const rix_system *sys, const rix_options *opt, r
   if ((s = rix_alloc(ctx, &ctx->d_keepC, np)) != RIX_OK) return fail(s);
   if ((s = rix_alloc(ctx, &ctx->d_keepV, np)) != RIX_OK) return fail(s);
   if ((s = rix_alloc(ctx, &ctx->d_keepD, np)) != RIX_OK) return fail(s);
+  if (cudaHostAlloc((void **)&ctx->h_err, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer((void **)&ctx->d_err, ctx->h_err, 0) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->last_error = "mapped status word";
+    return fail(RIX_ECUDA);
+  }
+  *(volatile int *)ctx->h_err = 0;
+  if ((s = rix_noalloc_attach(ctx)) != RIX_OK) return fail(s);
   if ((s = build_lists(ctx)) != RIX_OK) return fail(s);
   ctx->stats.workspace_bytes = (int64_t)ctx->dev_bytes;
   *out = ctx;
@@ -946,6 +954,7 @@ extern "C" rix_status rix_set_CV(rix_ctx *ctx, const double *C, const double *V,
   int32_t bad = 0;
   RIX_CUDA_TRY(ctx, cudaMemcpyAsync(&bad, ctx->d_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   RIX_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  if ((s = rix_take_err(ctx)) != RIX_OK) return s;
   if (bad) {
     ctx->have_cv = false;
     ctx->last_error = "C or V blocks differ from their transposed partners";
@@ -957,14 +966,39 @@ extern "C" rix_status rix_set_CV(rix_ctx *ctx, const double *C, const double *V,
   return RIX_OK;
 }
 
+rix_status rix_take_err(rix_ctx *ctx) {
+  if (ctx->h_err && *(volatile int *)ctx->h_err) {
+    *(volatile int *)ctx->h_err = 0;
+    ctx->last_error = "a bounded device wait of an earlier call ran out; its results are invalid";
+    return RIX_ETIMEOUT;
+  }
+  return RIX_OK;
+}
+
+extern "C" rix_status rix_check(rix_ctx *ctx, void *stream) {
+  if (!ctx) return RIX_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (st && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+    ctx->last_error = "rix_check synchronises the stream and cannot run inside a graph capture";
+    return RIX_ESTATE;
+  }
+  RIX_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  return rix_take_err(ctx);
+}
+
 extern "C" rix_status rix_build_K(rix_ctx *ctx, const double *D, double *K, void *stream) {
   if (!ctx || !D || !K) return RIX_EINVAL;
   if (!ctx->have_cv) return RIX_ESTATE;
+  rix_status s = rix_take_err(ctx);
+  if (s != RIX_OK) return s;
   return rix_fp64_build(ctx, D, K, (cudaStream_t)stream);
 }
 
 extern "C" rix_status rix_energy(rix_ctx *ctx, const double *D, const double *K, double *Ex, void *stream) {
   if (!ctx || !D || !K || !Ex) return RIX_EINVAL;
+  rix_status s = rix_take_err(ctx);
+  if (s != RIX_OK) return s;
   return rix_launch_energy(ctx, D, K, Ex, (cudaStream_t)stream);
 }
 
@@ -979,6 +1013,7 @@ extern "C" rix_status rix_stats(const rix_ctx *ctx, rix_stats_t *out) {
   out->workspace_bytes = (int64_t)ctx->dev_bytes;
   out->n_row_blocks = ctx->nblk;
   out->launches_build = rix_launch_count(ctx);
+  out->nbasis = ctx->nbasis;
   return RIX_OK;
 }
 
@@ -1045,5 +1080,6 @@ extern "C" void rix_destroy(rix_ctx *ctx) {
   for (auto e : ctx->ev_pending) cudaEventDestroy(e);
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
   for (auto &b : ctx->bufs) cudaFree(b.p);
+  if (ctx->h_err) cudaFreeHost(ctx->h_err);
   delete ctx;
 }

@@ -74,7 +74,7 @@ __host__ __device__ inline int n_stages(int S) {
   const int fit = (SMEM_LIMIT - 256) / st;
   return fit >= NSTAGE ? NSTAGE : (fit >= 2 ? fit : 1);
 }
-__host__ __device__ inline int smem_bytes(int S) { return n_stages(S) * S * (A_TILE + B_TILE) + 8 * (2 * NSTAGE + 2) + 16; }
+__host__ __device__ inline int smem_bytes(int S) { return n_stages(S) * S * (A_TILE + B_TILE) + 8 * (2 * NSTAGE + 4) + 16; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -103,7 +103,7 @@ __device__ __forceinline__ uint64_t now_ns() {
 // try_wait may suspend the thread for up to SUSPEND_NS until the phase completes,
 // so waiting warps leave the issue slots to the copy and MMA threads.
 constexpr uint32_t SUSPEND_NS = 20000;
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns = WAIT_NS) {
   const uint32_t a = smem_u32(bar);
   uint64_t t0 = 0;
   while (true) {
@@ -116,7 +116,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     if (ok) return true;
     const uint64_t t = now_ns();
     if (!t0) t0 = t;
-    else if (t - t0 > WAIT_NS) return false;
+    else if (t - t0 > limit_ns) return false;
   }
 }
 
@@ -459,6 +459,8 @@ struct GemmArgs {
   double oscale;           // scale of the added values (modes 0 and 1)
   int64_t xshift;          // mode 0: X + offK[x] - xshift is the output block
   int ntiles;              // output tiles of the launch (persistent CTAs loop over them)
+  uint64_t wait_ns = WAIT_NS;  // limit of every bounded wait
+  int stall = 0;           // 1: the MMA issuer waits on a barrier nothing completes (timeout test)
 };
 
 // Bits the fixed-point sum needs: products below 2^14, at most Kpad of them in
@@ -517,7 +519,9 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
   uint64_t *empty = full + NSTAGE;
   uint64_t *accfull = empty + NSTAGE;
   uint64_t *accempty = accfull + 1;
-  uint32_t *tmem_slot = (uint32_t *)(accempty + 1);
+  uint64_t *mmadone = accempty + 1;  // the MMA issuer's last commit (no MMA in flight at exit)
+  uint64_t *never = mmadone + 1;     // completed by nothing: the stall of the timeout test
+  uint32_t *tmem_slot = (uint32_t *)(never + 1);
   int *abort_flag = (int *)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -530,6 +534,8 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
     }
     mbar_init(accfull, 1);
     mbar_init(accempty, NTHR - 128);
+    mbar_init(mmadone, 1);
+    mbar_init(never, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -545,22 +551,28 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  uint32_t issued_chunks = 0;  // producer thread: chunks whose copies it issued
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ producer
     uint32_t cg = 0;  // chunks issued by this CTA
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    bool aborted = false;
+    for (int t = blockIdx.x; t < ntiles && !aborted; t += gridDim.x) {
       const TileInfo ti = tile_info(g, t);
       const int nk = ti.Kpad / KC;
       const int64_t a_tiles = (int64_t)(ti.Mpad / TM) * nk;  // tiles per A plane
       const int64_t b_tiles = (int64_t)(ti.Npad / TN) * nk;
       for (int c = 0; c < nk; c++, cg++) {
         const int st = cg % nst;
-        if (cg >= (uint32_t)nst && !mbar_wait(&empty[st], ((cg / nst) - 1) & 1)) {
+        if (cg >= (uint32_t)nst && !mbar_wait(&empty[st], ((cg / nst) - 1) & 1, g.wait_ns)) {
           atomicExch(abort_flag, 1);
+          aborted = true;
           break;
         }
-        if (*(volatile int *)abort_flag) break;
+        if (*(volatile int *)abort_flag) {
+          aborted = true;
+          break;
+        }
         uint8_t *sa = smem + st * stage_bytes;
         uint8_t *sb = sa + S * A_TILE;
         mbar_expect_tx(&full[st], (uint32_t)stage_bytes);
@@ -571,22 +583,25 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
           bulk_g2s(sb + s * B_TILE, gb, B_TILE, &full[st]);
         }
       }
-      if (*(volatile int *)abort_flag) break;
+      if (*(volatile int *)abort_flag) aborted = true;
     }
+    issued_chunks = cg;
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------ MMA issuer
     const uint32_t idesc = idesc_bf16(TM, TN);
     uint32_t cg = 0, gg = 0;  // chunks consumed, accumulation groups completed
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    bool issued = false;
+    if (g.stall && !mbar_wait(never, 0, g.wait_ns)) atomicExch(abort_flag, 1);
+    for (int t = blockIdx.x; t < ntiles && !*(volatile int *)abort_flag; t += gridDim.x) {
       const TileInfo ti = tile_info(g, t);
       const int nk = ti.Kpad / KC;
       for (int c = 0; c < nk; c++, cg++) {
         const int st = cg % nst;
-        if (c % GROUP == 0 && gg > 0 && !mbar_wait(accempty, (gg - 1) & 1)) {
+        if (c % GROUP == 0 && gg > 0 && !mbar_wait(accempty, (gg - 1) & 1, g.wait_ns)) {
           atomicExch(abort_flag, 1);
           break;
         }
-        if (!mbar_wait(&full[st], (cg / nst) & 1)) {
+        if (!mbar_wait(&full[st], (cg / nst) & 1, g.wait_ns)) {
           atomicExch(abort_flag, 1);
           break;
         }
@@ -597,6 +612,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
         // K step kk covers core-matrix columns 2kk, 2kk+1 (LBO = 128 B apart)
         const uint32_t open = c % GROUP == 0 ? 0xFFu : 0u;  // every accumulator starts a group
         issue_stage_s(S, tmem, sdesc(sa, 128, (KC / 8) * 128), sdesc(sb, 128, (KC / 8) * 128), idesc, open);
+        issued = true;
         mma_commit(&empty[st]);
         if (c % GROUP == GROUP - 1 || c == nk - 1) {
           mma_commit(accfull);
@@ -604,6 +620,11 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
         }
       }
       if (*(volatile int *)abort_flag) break;
+    }
+    if (issued) {
+      // every MMA this thread issued has completed before tensor memory is freed
+      mma_commit(mmadone);
+      mbar_wait(mmadone, 0);
     }
   } else if (warp >= 4) {
     // ------------------------------------------------------------ drain, fold, epilogue
@@ -627,7 +648,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
 #pragma unroll
       for (int n = 0; n < HN; n++) acc[n] = 0;
       for (int grp = 0; grp < ngroups; grp++, gg++) {
-        if (!mbar_wait(accfull, gg & 1)) {
+        if (!mbar_wait(accfull, gg & 1, g.wait_ns)) {
           atomicExch(abort_flag, 1);
           ok = false;
           break;
@@ -724,7 +745,19 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
   }
   tc_fence_before();
   __syncthreads();
-  if (*(volatile int *)abort_flag && threadIdx.x == 0) atomicExch(g.err, 1);
+  if (*(volatile int *)abort_flag) {
+    if (warp == 0 && lane == 0) {
+      // after an abort the MMAs may not have consumed every chunk: no bulk copy may
+      // still be writing shared memory when the CTA exits, so wait (bounded) for the
+      // last chunk issued on every stage (earlier ones completed before their stage
+      // was reused)
+      const uint32_t cg = issued_chunks;
+      const uint32_t first = cg > (uint32_t)nst ? cg - (uint32_t)nst : 0u;
+      for (uint32_t c2 = first; c2 < cg; c2++) mbar_wait(&full[c2 % nst], (c2 / nst) & 1);
+      *(volatile int *)g.err = 1;  // may be mapped host memory
+    }
+    __syncthreads();
+  }
   if (warp == 2) {
     uint32_t ncols = 32;
     while (ncols < (uint32_t)(nacc * TN)) ncols <<= 1;
@@ -750,43 +783,84 @@ inline int persistent_grid(int64_t ntiles) {
 using namespace rixtc;
 
 // C[M x N] (row-major, ldc) = A[M x K] (row-major, lda) * B[K x N] (row-major, ldb),
-// all FP64 device pointers; scratch for the slices is allocated here.
-extern "C" rix_status rix_gemm_sliced(const double *A, int64_t lda, const double *B, int64_t ldb, double *C,
-                                      int64_t ldc, int32_t M, int32_t N, int32_t K, int32_t n_slices,
-                                      void *stream) {
-  if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0 || n_slices < 1 || n_slices > MAXS) return RIX_EINVAL;
-  if (lda < K || ldb < N || ldc < N) return RIX_EINVAL;
-  cudaStream_t st = (cudaStream_t)stream;
+// all FP64 device pointers; scratch for the slices is allocated here.  stall and
+// wait_ns serve the timeout test only (rix_test_stalled_gemm).
+static rix_status gemm_sliced_impl(const double *A, int64_t lda, const double *B, int64_t ldb, double *C,
+                                   int64_t ldc, int32_t M, int32_t N, int32_t K, int32_t n_slices,
+                                   cudaStream_t st, int stall, uint64_t wait_ns, int *ext_err) {
   const int S = n_slices;
   const int Mpad = (M + TM - 1) / TM * TM, Npad = (N + TN - 1) / TN * TN, Kpad = (K + KC - 1) / KC * KC;
   const size_t pa = (size_t)S * Mpad * Kpad * 2, pb = (size_t)S * Npad * Kpad * 2;
   void *buf = nullptr;
   const size_t bytes = pa + pb + (size_t)(Mpad + Npad) * 4 + 16;
-  if (cudaMallocAsync(&buf, bytes, st) != cudaSuccess) return RIX_ENOMEM;
+  if (cudaMallocAsync(&buf, bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    return RIX_ENOMEM;
+  }
   __nv_bfloat16 *Ap = (__nv_bfloat16 *)buf;
   __nv_bfloat16 *Bp = (__nv_bfloat16 *)((char *)buf + pa);
   int *eA = (int *)((char *)buf + pa + pb);
   int *eB = eA + Mpad;
-  int *err = eB + Npad;
-  cudaMemsetAsync(err, 0, 4, st);
-  k_row_exp<<<(Mpad + 7) / 8, dim3(32, 8), 0, st>>>(A, lda, M, K, Mpad, eA);
-  k_col_exp<<<(Npad + 127) / 128, 128, 0, st>>>(B, ldb, K, N, Npad, eB);
-  launch_pack(A, lda, 1, M, K, Mpad, Kpad, eA, S, TM, Ap, st);
-  launch_pack(B, 1, ldb, N, K, Npad, Kpad, eB, S, TN, Bp, st);  // B^T as rows: element (n, k) = B[k*ldb + n]
-  GemmArgs g{Ap, Bp, eA, eB, C, ldc, M, N, Mpad, Npad, Kpad, S, 0, fixed_point_drop(Kpad, S), err,
-             nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  const int smem = smem_bytes(S);
-  cudaFuncSetAttribute(k_gemm_sliced, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  g.ntiles = (Mpad / TM) * (Npad / TN);
-  k_gemm_sliced<<<persistent_grid(g.ntiles), NTHR, smem, st>>>(g);
-  cudaError_t e = cudaGetLastError();
+  int *err = ext_err ? ext_err : eB + Npad;
+  cudaError_t e = ext_err ? cudaSuccess : cudaMemsetAsync(err, 0, 4, st);
+  if (e == cudaSuccess) {
+    k_row_exp<<<(Mpad + 7) / 8, dim3(32, 8), 0, st>>>(A, lda, M, K, Mpad, eA);
+    k_col_exp<<<(Npad + 127) / 128, 128, 0, st>>>(B, ldb, K, N, Npad, eB);
+    launch_pack(A, lda, 1, M, K, Mpad, Kpad, eA, S, TM, Ap, st);
+    launch_pack(B, 1, ldb, N, K, Npad, Kpad, eB, S, TN, Bp, st);  // B^T as rows: element (n, k) = B[k*ldb + n]
+    GemmArgs g{Ap, Bp, eA, eB, C, ldc, M, N, Mpad, Npad, Kpad, S, 0, fixed_point_drop(Kpad, S), err,
+               nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    g.ntiles = (Mpad / TM) * (Npad / TN);
+    g.stall = stall;
+    g.wait_ns = wait_ns;
+    const int smem = smem_bytes(S);
+    e = cudaFuncSetAttribute(k_gemm_sliced, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) {
+      k_gemm_sliced<<<persistent_grid(g.ntiles), NTHR, smem, st>>>(g);
+      e = cudaGetLastError();
+    }
+  }
   int herr = 0;
-  cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st);
-  cudaStreamSynchronize(st);
-  cudaFreeAsync(buf, st);
-  if (e != cudaSuccess) return RIX_ECUDA;
-  if (herr) return RIX_ETIMEOUT;
-  return RIX_OK;
+  if (ext_err) {  // asynchronous: the status goes to the caller's status word
+    const cudaError_t ef = cudaFreeAsync(buf, st);
+    return (e == cudaSuccess && ef == cudaSuccess) ? RIX_OK : RIX_ECUDA;
+  }
+  // the kernel's status is read only after the stream has finished without a CUDA error
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost);
+  const cudaError_t ef = cudaFreeAsync(buf, st);
+  if (e == cudaSuccess) e = ef;
+  if (e != cudaSuccess) {
+    return RIX_ECUDA;
+  }
+  return herr ? RIX_ETIMEOUT : RIX_OK;
+}
+
+extern "C" rix_status rix_gemm_sliced(const double *A, int64_t lda, const double *B, int64_t ldb, double *C,
+                                      int64_t ldc, int32_t M, int32_t N, int32_t K, int32_t n_slices,
+                                      void *stream) {
+  if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0 || n_slices < 1 || n_slices > MAXS) return RIX_EINVAL;
+  if (lda < K || ldb < N || ldc < N) return RIX_EINVAL;
+  return gemm_sliced_impl(A, lda, B, ldb, C, ldc, M, N, K, n_slices, (cudaStream_t)stream, 0, WAIT_NS, nullptr);
+}
+
+extern "C" rix_status rix_test_stalled_gemm(rix_ctx *ctx, int64_t wait_ns, void *stream) {
+  if (wait_ns <= 0 || wait_ns > (int64_t)WAIT_NS) return RIX_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int M = 130, N = 90, K = 70;  // two row tiles, two column tiles, three K stages
+  double *buf = nullptr;
+  const size_t n = (size_t)M * K + (size_t)K * N + (size_t)M * N;
+  if (cudaMallocAsync((void **)&buf, n * sizeof(double), st) != cudaSuccess) {
+    cudaGetLastError();
+    return RIX_ENOMEM;
+  }
+  cudaMemsetAsync(buf, 0, n * sizeof(double), st);
+  rix_status s = gemm_sliced_impl(buf, K, buf + (size_t)M * K, N, buf + (size_t)M * K + (size_t)K * N, N, M, N, K,
+                                  3, st, 1, (uint64_t)wait_ns, ctx ? ctx->d_err : nullptr);
+  if (cudaFreeAsync(buf, st) != cudaSuccess) return RIX_ECUDA;
+  if (ctx) return s;  // reported later by rix_check or the next entry point
+  if (cudaStreamSynchronize(st) != cudaSuccess) return RIX_ECUDA;
+  return s;
 }
 
 // ==========================================================================
@@ -1344,8 +1418,7 @@ rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
     tflops += ctx->stats.tensor_flops_stage[4];
   }
   if ((s = rix_dev_alloc(ctx, (void **)&ctx->d_mx_buf, std::max<int64_t>(buf, 16))) != RIX_OK) return s;
-  if ((s = rix_alloc(ctx, &ctx->d_mx_err, 4)) != RIX_OK) return s;
-  RIX_CUDA_TRY(ctx, cudaMemset(ctx->d_mx_err, 0, 4));
+  ctx->d_mx_err = ctx->d_err;
   ctx->mx_buf_bytes = buf;
   ctx->stats.tensor_flops = tflops;
   ctx->have_mx = true;

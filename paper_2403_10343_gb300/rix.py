@@ -47,7 +47,7 @@ class _Stats(ctypes.Structure):
                 ("n_row_blocks", ctypes.c_int32), ("flops_term2", ctypes.c_double),
                 ("tensor_flops_stage", ctypes.c_double * 5), ("launches_build", ctypes.c_int32),
                 ("flops_term1_tc", ctypes.c_double), ("flops_z_tc", ctypes.c_double),
-                ("tz_bytes", ctypes.c_int64), ("flops_t_tc", ctypes.c_double)]
+                ("tz_bytes", ctypes.c_int64), ("flops_t_tc", ctypes.c_double), ("nbasis", ctypes.c_int64)]
 
 
 _lib = None
@@ -81,6 +81,8 @@ def load():
                                     ctypes.POINTER(ctypes.c_int32)]
     lib.rix_autotune.argtypes = [P, P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32), P]
     lib.rix_count_flops.argtypes = [P, P, ctypes.POINTER(ctypes.c_double), P]
+    lib.rix_check.argtypes = [P, P]
+    lib.rix_test_stalled_gemm.argtypes = [P, ctypes.c_int64, P]
     lib.rix_strerror.restype = ctypes.c_char_p
     lib.rix_strerror.argtypes = [I]
     lib.rix_last_error.restype = ctypes.c_char_p
@@ -89,7 +91,7 @@ def load():
     for f in ("rix_setup", "rix_layout", "rix_layout_sizes", "rix_set_CV", "rix_build_K", "rix_energy",
               "rix_energy_noalloc",
               "rix_backward", "rix_fold_gamma", "rix_stats", "rix_stage_times", "rix_gemm_sliced",
-              "rix_autotune", "rix_count_flops"):
+              "rix_autotune", "rix_count_flops", "rix_check", "rix_test_stalled_gemm"):
         getattr(lib, f).restype = I
     _lib = lib
     return lib
@@ -113,12 +115,29 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _dptr(t, name, dtype_size=8):
+def _dptr(t, name, min_numel=1, device=None):
+    """Device pointer of a contiguous float64 CUDA tensor holding at least min_numel elements.
+
+    The kernels index these buffers by the context's layout, so a wrong dtype, a
+    short tensor or one on another GPU would make them read or write out of bounds.
+    """
     if t is None:
         return None
+    import torch
     if not t.is_cuda or not t.is_contiguous():
         raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    if t.dtype != torch.float64:
+        raise ValueError(f"{name} must be float64, got {t.dtype}")
+    if t.numel() < min_numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, the layout needs {min_numel}")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, expected {device}")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _sizes(ctx):
+    """(c_elems, v_elems, d_elems, k_elems) of a context."""
+    return layout_sizes(ctx)
 
 
 def setup(xyz_bohr, species, nbas, naux, cell_bohr=None, cutoff_bohr=0.0, screen_tau=0.0,
@@ -172,34 +191,60 @@ def _any_ptr(x, name):
     return _dptr(x, name)
 
 
+def _host_numel(x):
+    return x.size if isinstance(x, np.ndarray) else x.numel()
+
+
 def set_CV(ctx, C, V, stream=None):
     """rix_set_CV; C and V may be CUDA tensors or host arrays (copied either way)."""
+    c, v, _, _ = _sizes(ctx)
+    for x, name, n in ((C, "C", c), (V, "V", v)):
+        if _host_numel(x) < n:
+            raise ValueError(f"{name} holds {_host_numel(x)} elements, the layout needs {n}")
     _check(load().rix_set_CV(ctx, _any_ptr(C, "C"), _any_ptr(V, "V"), _stream(stream)), ctx)
 
 
 def build_K(ctx, D, K, stream=None):
-    _check(load().rix_build_K(ctx, _dptr(D, "D"), _dptr(K, "K"), _stream(stream)), ctx)
+    _, _, d, k = _sizes(ctx)
+    _check(load().rix_build_K(ctx, _dptr(D, "D", d), _dptr(K, "K", k, D.device), _stream(stream)), ctx)
 
 
 def energy(ctx, D, K, Ex, stream=None):
-    _check(load().rix_energy(ctx, _dptr(D, "D"), _dptr(K, "K"), _dptr(Ex, "Ex"), _stream(stream)), ctx)
+    _, _, d, k = _sizes(ctx)
+    _check(load().rix_energy(ctx, _dptr(D, "D", d), _dptr(K, "K", k, D.device), _dptr(Ex, "Ex", 1, D.device),
+                             _stream(stream)), ctx)
 
 
 def energy_noalloc(ctx, D, K, Ex, stream=None):
     """rix_energy_noalloc: the energy reduction without any device allocation."""
-    _check(load().rix_energy_noalloc(ctx, _dptr(D, "D"), _dptr(K, "K"), _dptr(Ex, "Ex"), _stream(stream)), ctx)
+    _, _, d, k = _sizes(ctx)
+    _check(load().rix_energy_noalloc(ctx, _dptr(D, "D", d), _dptr(K, "K", k, D.device),
+                                     _dptr(Ex, "Ex", 1, D.device), _stream(stream)), ctx)
 
 
 def backward(ctx, D, gEx, dD=None, dC=None, dV=None, stream=None):
-    _check(load().rix_backward(ctx, _dptr(D, "D"), float(gEx), _dptr(dD, "dD"), _dptr(dC, "dC"),
-                               _dptr(dV, "dV"), _stream(stream)), ctx)
+    c, v, d, _ = _sizes(ctx)
+    dev = D.device
+    _check(load().rix_backward(ctx, _dptr(D, "D", d), float(gEx), _dptr(dD, "dD", d, dev), _dptr(dC, "dC", c, dev),
+                               _dptr(dV, "dV", v, dev), _stream(stream)), ctx)
+
+
+def check(ctx, stream=None):
+    """rix_check: synchronise and raise if a bounded device wait of the context gave up."""
+    _check(load().rix_check(ctx, _stream(stream)), ctx)
+
+
+def stalled_gemm(wait_ns, ctx=None, stream=None):
+    """rix_test_stalled_gemm: the status (ctx None: RIX_ETIMEOUT when the timeout path worked)."""
+    return load().rix_test_stalled_gemm(ctx, int(wait_ns), _stream(stream))
 
 
 def autotune(ctx, D, cache_path=None, stream=None):
     """rix_autotune: returns the chosen tile budgets (doubles) of k_X12, k_Z, k_X34."""
     out = (ctypes.c_int32 * 3)()
     path = None if cache_path is None else os.fsencode(cache_path)
-    _check(load().rix_autotune(ctx, _dptr(D, "D"), path, out, _stream(stream)), ctx)
+    _, _, d, _ = _sizes(ctx)
+    _check(load().rix_autotune(ctx, _dptr(D, "D", d), path, out, _stream(stream)), ctx)
     return tuple(out)
 
 
@@ -209,12 +254,16 @@ COUNT_KEYS = ("T", "U2", "X12", "Z", "X34", "sym", "term2", "term1_tc", "z_tc", 
 def count_flops(ctx, D, stream=None):
     """rix_count_flops: FLOPs of one build with this D after block screening, by stage."""
     out = (ctypes.c_double * 10)()
-    _check(load().rix_count_flops(ctx, _dptr(D, "D"), out, _stream(stream)), ctx)
+    _, _, d, _ = _sizes(ctx)
+    _check(load().rix_count_flops(ctx, _dptr(D, "D", d), out, _stream(stream)), ctx)
     return dict(zip(COUNT_KEYS, out))
 
 
 def fold_gamma(ctx, K, Kdense, stream=None):
-    _check(load().rix_fold_gamma(ctx, _dptr(K, "K"), _dptr(Kdense, "Kdense"), _stream(stream)), ctx)
+    _, _, _, k = _sizes(ctx)
+    nbasis = int(stats(ctx)["nbasis"])
+    _check(load().rix_fold_gamma(ctx, _dptr(K, "K", k), _dptr(Kdense, "Kdense", nbasis * nbasis, K.device),
+                                 _stream(stream)), ctx)
 
 
 def stats(ctx):
@@ -231,11 +280,15 @@ def gemm_sliced(A, B, n_slices, C=None, stream=None):
     import torch
     M, K = A.shape
     K2, N = B.shape
-    assert K == K2
+    if K != K2:
+        raise ValueError("inner dimensions differ")
     if C is None:
         C = torch.empty((M, N), dtype=torch.float64, device=A.device)
-    _check(load().rix_gemm_sliced(_dptr(A, "A"), A.stride(0), _dptr(B, "B"), B.stride(0), _dptr(C, "C"),
-                                  C.stride(0), M, N, K, int(n_slices), _stream(stream)))
+    if tuple(C.shape) != (M, N):
+        raise ValueError("C must be M x N")
+    _check(load().rix_gemm_sliced(_dptr(A, "A", M * K), A.stride(0), _dptr(B, "B", K * N, A.device), B.stride(0),
+                                  _dptr(C, "C", M * N, A.device), C.stride(0), M, N, K, int(n_slices),
+                                  _stream(stream)))
     return C
 
 
@@ -277,7 +330,11 @@ class Exchange:
         return layout(self.ctx, RIX_LIST_K)[0]
 
     def set_CV(self, C, V, stream=None):
+        self._cv_stamp = None  # the autograd wrapper reloads on its next call
         set_CV(self.ctx, C, V, stream)
+
+    def check(self, stream=None):
+        check(self.ctx, stream)
 
     def autotune(self, D, cache_path=None, stream=None):
         return autotune(self.ctx, D, cache_path, stream)
