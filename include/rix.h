@@ -205,6 +205,32 @@ rix_status rix_backward(rix_ctx *ctx, const double *D_dev, double gEx,
  * (I, L global basis indices), row-major nbasis x nbasis.  Asynchronous. */
 rix_status rix_fold_gamma(rix_ctx *ctx, const double *K_dev, double *Kdense_dev, void *stream);
 
+/* Bloch sums of an image-resolved K (the paper's Eq. 3, Fock operator in k
+ * space): for each of the n_k points kappa (host, [n_k][3], fractional
+ * coordinates in the reciprocal basis b_c with b_c . a_d = 2 pi delta_cd),
+ *   Kk[q][I][L] = sum_n exp(2 pi i kappa_q . n) K(A,E,n)[i][l]
+ * (I, L global basis indices).  K_dev: packed on the K list (device); Kk_dev:
+ * device, n_k consecutive row-major nbasis x nbasis complex matrices stored
+ * as interleaved (re, im) doubles, fully overwritten.  kappa = 0 gives the
+ * Gamma fold of rix_fold_gamma with zero imaginary parts.  A cluster accepts
+ * only kappa = 0 (EINVAL otherwise).  Asynchronous; one kernel per k point. */
+rix_status rix_bloch(rix_ctx *ctx, const double *K_dev, int32_t n_k, const double *kfrac, double *Kk_dev,
+                     void *stream);
+
+/* Collinear spin (the spin index sigma of the paper's Eqs. 3-5; the spin
+ * channels double the work): D_dev holds n_spin (1 or 2) packed densities back
+ * to back (d_elems each, the per-spin density matrices D^up, D^dn without the
+ * closed-shell factor 2), K_dev receives n_spin packed K arrays (k_elems
+ * each): K^sigma = K(D^sigma), one build per channel.  Asynchronous. */
+rix_status rix_build_K_spin(rix_ctx *ctx, int32_t n_spin, const double *D_dev, double *K_dev, void *stream);
+
+/* Exchange energy of spin-resolved D and K (layout as rix_build_K_spin):
+ * E_x = -1/2 sum_sigma Tr(D^sigma K^sigma) for n_spin = 2 (equal to -1/4
+ * Tr(D K) of the closed shell when D^up = D^dn = D/2), -1/4 Tr(D K) for
+ * n_spin = 1.  Ex_dev: one device double.  Asynchronous. */
+rix_status rix_energy_spin(rix_ctx *ctx, int32_t n_spin, const double *D_dev, const double *K_dev, double *Ex_dev,
+                           void *stream);
+
 /* C = A B for FP64 device matrices (row-major, leading dimensions in elements;
  * C overwritten) computed on the BF16 tensor cores by error-free slicing: each
  * row of A and column of B is scaled by its own power of two and written with

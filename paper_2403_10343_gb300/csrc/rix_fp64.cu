@@ -485,7 +485,8 @@ __global__ void k_energy(int64_t np, const int32_t *pA, const int32_t *pB, const
   if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
-__global__ void k_energy_final(int64_t n, const double *part, double *Ex) {
+// *Ex = scale * sum(part) (accumulate: *Ex += ...); scale -1/4 for the closed-shell energy
+__global__ void k_energy_final(int64_t n, const double *part, double *Ex, double scale, int accumulate) {
   __shared__ double red[1024];
   double s = 0.0;
   for (int64_t i = threadIdx.x; i < n; i += 1024) s += part[i];
@@ -495,7 +496,7 @@ __global__ void k_energy_final(int64_t n, const double *part, double *Ex) {
     if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *Ex = -0.25 * red[0];
+  if (threadIdx.x == 0) *Ex = accumulate ? *Ex + scale * red[0] : scale * red[0];
 }
 
 // ------------------------------------------------------------------ Gamma fold
@@ -814,7 +815,20 @@ rix_status rix_launch_energy(rix_ctx *ctx, const double *D, const double *K, dou
                                                    ctx->d_nb, D, ctx->d_offD, ctx->d_keepD, K, ctx->d_offK,
                                                    ctx->d_epart);
   if ((s = last(ctx, "k_energy")) != RIX_OK) return s;
-  k_energy_final<<<1, 1024, 0, st>>>(ctx->n_epart, ctx->d_epart, Ex);
+  k_energy_final<<<1, 1024, 0, st>>>(ctx->n_epart, ctx->d_epart, Ex, -0.25, 0);
+  return last(ctx, "k_energy_final");
+}
+
+// scale * sum over the D pattern of <D(E,A,-n), K(A,E,n)> into (or added to) *Ex
+rix_status rix_launch_energy_scaled(rix_ctx *ctx, const double *D, const double *K, double *Ex, double scale,
+                                    int accumulate, cudaStream_t st) {
+  rix_status s;
+  if ((s = rix_launch_flags(ctx, D, ctx->d_offD, ctx->np, ctx->d_keepD, st)) != RIX_OK) return s;
+  k_energy<<<(unsigned)ctx->n_epart, 256, 0, st>>>(ctx->np, ctx->d_pA, ctx->d_pB, ctx->d_partner1, ctx->d_map1to3,
+                                                   ctx->d_nb, D, ctx->d_offD, ctx->d_keepD, K, ctx->d_offK,
+                                                   ctx->d_epart);
+  if ((s = last(ctx, "k_energy")) != RIX_OK) return s;
+  k_energy_final<<<1, 1024, 0, st>>>(ctx->n_epart, ctx->d_epart, Ex, scale, accumulate);
   return last(ctx, "k_energy_final");
 }
 
@@ -828,7 +842,7 @@ rix_status rix_launch_energy_partials(rix_ctx *ctx, const double *D, const doubl
                                                    ctx->d_nb, D, ctx->d_offD, ctx->d_keepD, K, ctx->d_offK,
                                                    partials);
   if ((s = last(ctx, "k_energy")) != RIX_OK) return s;
-  k_energy_final<<<1, 1024, 0, st>>>(ctx->n_epart, partials, Ex);
+  k_energy_final<<<1, 1024, 0, st>>>(ctx->n_epart, partials, Ex, -0.25, 0);
   return last(ctx, "k_energy_final");
 }
 

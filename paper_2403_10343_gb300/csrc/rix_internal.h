@@ -118,6 +118,7 @@ struct rix_ctx {
   int64_t *d_fold = nullptr;
   int64_t nbasis = 0;
   int64_t *d_bofs = nullptr;            // global basis offset of each atom
+  char4 *d_n3 = nullptr;                // image vector (n1, n2, n3) of every K block
   // mixed precision: terms 3+4 and term 2 as batched sliced GEMMs on the tensor cores
   bool have_mx = false;
   int32_t mx_S = 5;

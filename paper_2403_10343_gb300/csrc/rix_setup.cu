@@ -695,6 +695,14 @@ static rix_status build_lists(rix_ctx *ctx) {
   TRY(rix_upload(ctx, &ctx->d_LX34, LX34));
   TRY(rix_upload(ctx, &ctx->d_fold, fold)); ctx->n_fold = (int64_t)fold.size() - 1;
   TRY(rix_upload(ctx, &ctx->d_bofs, bofs));
+  {
+    // image vector of every K block (the Bloch phases of rix_bloch)
+    std::vector<char4> n3(nk);
+    for (int64_t x = 0; x < nk; x++)
+      n3[x] = make_char4((signed char)key_n(keys3[x], 0), (signed char)key_n(keys3[x], 1),
+                         (signed char)key_n(keys3[x], 2), 0);
+    TRY(rix_upload(ctx, &ctx->d_n3, n3));
+  }
   TRY(rix_alloc(ctx, &ctx->d_U, offU[np]));
   TRY(rix_alloc(ctx, &ctx->d_X, ctx->offK[nk]));
   ctx->n_epart = (np + 255) / 256;

@@ -814,7 +814,9 @@ static rix_status gemm_sliced_impl(const double *A, int64_t lda, const double *B
     g.stall = stall;
     g.wait_ns = wait_ns;
     const int smem = smem_bytes(S);
-    e = cudaFuncSetAttribute(k_gemm_sliced, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    // the same (largest) limit the build's launches set: a smaller one would make
+    // their later launches with more slices fail
+    e = cudaFuncSetAttribute(k_gemm_sliced, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
     if (e == cudaSuccess) {
       k_gemm_sliced<<<persistent_grid(g.ntiles), NTHR, smem, st>>>(g);
       e = cudaGetLastError();

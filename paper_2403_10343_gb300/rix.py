@@ -82,6 +82,9 @@ def load():
     lib.rix_autotune.argtypes = [P, P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32), P]
     lib.rix_count_flops.argtypes = [P, P, ctypes.POINTER(ctypes.c_double), P]
     lib.rix_check.argtypes = [P, P]
+    lib.rix_bloch.argtypes = [P, P, ctypes.c_int32, P, P, P]
+    lib.rix_build_K_spin.argtypes = [P, ctypes.c_int32, P, P, P]
+    lib.rix_energy_spin.argtypes = [P, ctypes.c_int32, P, P, P, P]
     lib.rix_test_stalled_gemm.argtypes = [P, ctypes.c_int64, P]
     lib.rix_strerror.restype = ctypes.c_char_p
     lib.rix_strerror.argtypes = [I]
@@ -91,7 +94,8 @@ def load():
     for f in ("rix_setup", "rix_layout", "rix_layout_sizes", "rix_set_CV", "rix_build_K", "rix_energy",
               "rix_energy_noalloc",
               "rix_backward", "rix_fold_gamma", "rix_stats", "rix_stage_times", "rix_gemm_sliced",
-              "rix_autotune", "rix_count_flops", "rix_check", "rix_test_stalled_gemm"):
+              "rix_autotune", "rix_count_flops", "rix_check", "rix_test_stalled_gemm", "rix_bloch",
+              "rix_build_K_spin", "rix_energy_spin"):
         getattr(lib, f).restype = I
     _lib = lib
     return lib
@@ -227,6 +231,33 @@ def backward(ctx, D, gEx, dD=None, dC=None, dV=None, stream=None):
     dev = D.device
     _check(load().rix_backward(ctx, _dptr(D, "D", d), float(gEx), _dptr(dD, "dD", d, dev), _dptr(dC, "dC", c, dev),
                                _dptr(dV, "dV", v, dev), _stream(stream)), ctx)
+
+
+def bloch(ctx, K, kfrac, Kk, stream=None):
+    """rix_bloch: Kk (complex128 CUDA tensor [n_k, nbasis, nbasis]) = Bloch sums of K at kfrac [n_k, 3]."""
+    import torch
+    kf = np.ascontiguousarray(kfrac, dtype=np.float64).reshape(-1, 3)
+    nbasis = int(stats(ctx)["nbasis"])
+    if Kk.dtype != torch.complex128 or not Kk.is_cuda or not Kk.is_contiguous():
+        raise ValueError("Kk must be a contiguous complex128 CUDA tensor")
+    if Kk.numel() < len(kf) * nbasis * nbasis:
+        raise ValueError("Kk is too small for n_k nbasis x nbasis matrices")
+    _, _, _, k = _sizes(ctx)
+    _check(load().rix_bloch(ctx, _dptr(K, "K", k), len(kf), kf.ctypes.data, ctypes.c_void_p(Kk.data_ptr()),
+                            _stream(stream)), ctx)
+
+
+def build_K_spin(ctx, D, K, n_spin=2, stream=None):
+    """rix_build_K_spin: D [n_spin * d_elems], K [n_spin * k_elems] (per-spin arrays back to back)."""
+    _, _, d, k = _sizes(ctx)
+    _check(load().rix_build_K_spin(ctx, int(n_spin), _dptr(D, "D", n_spin * d), _dptr(K, "K", n_spin * k, D.device),
+                                   _stream(stream)), ctx)
+
+
+def energy_spin(ctx, D, K, Ex, n_spin=2, stream=None):
+    _, _, d, k = _sizes(ctx)
+    _check(load().rix_energy_spin(ctx, int(n_spin), _dptr(D, "D", n_spin * d), _dptr(K, "K", n_spin * k, D.device),
+                                  _dptr(Ex, "Ex", 1, D.device), _stream(stream)), ctx)
 
 
 def check(ctx, stream=None):

@@ -284,7 +284,12 @@ class Packed:
             out.append((sel, img[sel], r[sel]))
         return out
 
-    def gen_D(self):
+    def gen_D(self, weights=None):
+        """D = sum_m w_m c_m c_m^T over the localised orbitals (w_m = 2: closed shell).
+
+        weights (optional, one per orbital) gives other occupations, e.g. the
+        per-spin densities of a collinear spin-polarised state (w_m in {0, 1}).
+        """
         s = self.system
         D = np.zeros(int(self.offD[-1]), dtype=np.float64)
         nb = s.nbas[s.species].astype(np.int64)
@@ -307,11 +312,23 @@ class Packed:
             pr = pos[aof[:, None], aof[None, :]]
             okr = ok[aof[:, None], aof[None, :]]
             dst = self.offD[pr] + iof[:, None] * nbs[aof][None, :] + iof[None, :]
-            val = 2.0 * np.outer(c, c)
+            w = 2.0 if weights is None else float(weights[m])
+            if w == 0.0:
+                continue
+            val = w * np.outer(c, c)
             D[dst[okr]] += val[okr]
-        self.D = D
-        self.D_dropped = dropped
+        if weights is None:
+            self.D = D
+            self.D_dropped = dropped
         return D
+
+    def gen_D_spin(self):
+        """Per-spin densities (D_up, D_dn) of a spin-polarised state: every orbital singly occupied
+        in both channels except every fifth one, which the down channel leaves empty."""
+        n = len(self.system.orbital_centres)
+        up = np.ones(n)
+        dn = np.where(np.arange(n) % 5 == 4, 0.0, 1.0)
+        return self.gen_D(up), self.gen_D(dn)
 
 
 def generate(system, C=True, V=True, D=True):
