@@ -173,6 +173,17 @@ rix_status rix_autotune(rix_ctx *ctx, const double *D_dev, const char *cache_pat
  * call has completed.  ESTATE before rix_set_CV. */
 rix_status rix_build_K(rix_ctx *ctx, const double *D_dev, double *K_dev, void *stream);
 
+/* Incremental build for the SCF loop (the paper's exchange matrix is rebuilt
+ * from the unmixed density every iteration, Sec. "Evaluation of the EXX
+ * matrix in real space"): K_dev += K(dD_dev), with dD = D_new - D_old in the
+ * packed D layout.  K is linear in D, so K(D_old) + K(dD) = K(D_new); blocks
+ * of dD below screen_tau are skipped like blocks of D, so once the density
+ * settles most of dD is screened out and the build does less work.  The same
+ * stages, precision and synchronisation behaviour as rix_build_K
+ * (asynchronous, no allocation, graph-capturable); K_dev is read and
+ * updated. */
+rix_status rix_build_K_delta(rix_ctx *ctx, const double *dD_dev, double *K_dev, void *stream);
+
 /* *Ex_dev = -1/4 sum over the D pattern of <D(E,A,-n), K(A,E,n)>_F, a
  * deterministic FP64 tree reduction.  Ex_dev is one device double. */
 rix_status rix_energy(rix_ctx *ctx, const double *D_dev, const double *K_dev,

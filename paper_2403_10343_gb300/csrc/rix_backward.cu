@@ -20,7 +20,6 @@
 
 using namespace rix;
 
-rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t st);
 
 namespace {
 

@@ -443,8 +443,10 @@ __global__ void __launch_bounds__(NT) k_X34(const int32_t *ord, const int64_t *p
 }
 
 // ------------------------------------------------------------------ K = X + X^T (image flipped)
+// K(A,E,n) = X(A,E,n) + X(E,A,-n)^T (accumulate: added to K)
 __global__ void k_sym(int64_t nk, const int32_t *atomA3, const int32_t *atomB3, const int32_t *partner3,
-                      const int32_t *nb, const int64_t *offK, const double *__restrict__ X, double *K) {
+                      const int32_t *nb, const int64_t *offK, const double *__restrict__ X, double *K,
+                      int accumulate) {
   const int64_t x = blockIdx.x;
   if (x >= nk) return;
   const int nbA = nb[atomA3[x]], nbE = nb[atomB3[x]];
@@ -452,7 +454,8 @@ __global__ void k_sym(int64_t nk, const int32_t *atomA3, const int32_t *atomB3, 
   double *k = K + offK[x];
   for (int el = threadIdx.x; el < nbA * nbE; el += blockDim.x) {
     const int i = el / nbE, l = el - i * nbE;
-    k[el] = xa[el] + xb[l * nbA + i];
+    const double v = xa[el] + xb[l * nbA + i];
+    k[el] = accumulate ? k[el] + v : v;
   }
 }
 
@@ -635,7 +638,7 @@ rix_status rix_launch_Z_block(rix_ctx *ctx, const double *D, int b, cudaStream_t
   return s;
 }
 
-rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t st) {
+rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t st, int accumulate) {
   set_attrs();
   rix_status s;
   if ((s = rix_prof_mark(ctx, 0, st)) != RIX_OK) return s;
@@ -679,7 +682,7 @@ rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t
   }
   if ((s = rix_prof_mark(ctx, 7, st)) != RIX_OK) return s;
   k_sym<<<(unsigned)ctx->nk, 128, 0, st>>>(ctx->nk, ctx->d_atomA3, ctx->d_atomB3, ctx->d_partner3, ctx->d_nb,
-                                           ctx->d_offK, ctx->d_X, K);
+                                           ctx->d_offK, ctx->d_X, K, accumulate);
   if ((s = last(ctx, "k_sym")) != RIX_OK) return s;
   return rix_prof_mark(ctx, 8, st);
 }

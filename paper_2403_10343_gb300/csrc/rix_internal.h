@@ -219,7 +219,7 @@ rix_status rix_mixed_T(rix_ctx *ctx, int b, int64_t tbase, const double *D, cuda
 int32_t rix_tt_launches(const rix_ctx *ctx);
 
 // FP64 path launches (rix_fp64.cu)
-rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t st);
+rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t st, int accumulate = 0);
 rix_status rix_launch_T_block(rix_ctx *ctx, const double *D, int b, cudaStream_t st);
 rix_status rix_launch_Z_block(rix_ctx *ctx, const double *D, int b, cudaStream_t st);
 rix_status rix_launch_flags(rix_ctx *ctx, const double *arr, const int64_t *off, int64_t n,

@@ -1003,6 +1003,14 @@ extern "C" rix_status rix_build_K(rix_ctx *ctx, const double *D, double *K, void
   return rix_fp64_build(ctx, D, K, (cudaStream_t)stream);
 }
 
+extern "C" rix_status rix_build_K_delta(rix_ctx *ctx, const double *dD, double *K, void *stream) {
+  if (!ctx || !dD || !K) return RIX_EINVAL;
+  if (!ctx->have_cv) return RIX_ESTATE;
+  rix_status s = rix_take_err(ctx);
+  if (s != RIX_OK) return s;
+  return rix_fp64_build(ctx, dD, K, (cudaStream_t)stream, 1);
+}
+
 extern "C" rix_status rix_energy(rix_ctx *ctx, const double *D, const double *K, double *Ex, void *stream) {
   if (!ctx || !D || !K || !Ex) return RIX_EINVAL;
   rix_status s = rix_take_err(ctx);

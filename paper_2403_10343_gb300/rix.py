@@ -82,6 +82,7 @@ def load():
     lib.rix_autotune.argtypes = [P, P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32), P]
     lib.rix_count_flops.argtypes = [P, P, ctypes.POINTER(ctypes.c_double), P]
     lib.rix_check.argtypes = [P, P]
+    lib.rix_build_K_delta.argtypes = [P, P, P, P]
     lib.rix_bloch.argtypes = [P, P, ctypes.c_int32, P, P, P]
     lib.rix_build_K_spin.argtypes = [P, ctypes.c_int32, P, P, P]
     lib.rix_energy_spin.argtypes = [P, ctypes.c_int32, P, P, P, P]
@@ -95,7 +96,7 @@ def load():
               "rix_energy_noalloc",
               "rix_backward", "rix_fold_gamma", "rix_stats", "rix_stage_times", "rix_gemm_sliced",
               "rix_autotune", "rix_count_flops", "rix_check", "rix_test_stalled_gemm", "rix_bloch",
-              "rix_build_K_spin", "rix_energy_spin"):
+              "rix_build_K_spin", "rix_energy_spin", "rix_build_K_delta"):
         getattr(lib, f).restype = I
     _lib = lib
     return lib
@@ -211,6 +212,12 @@ def set_CV(ctx, C, V, stream=None):
 def build_K(ctx, D, K, stream=None):
     _, _, d, k = _sizes(ctx)
     _check(load().rix_build_K(ctx, _dptr(D, "D", d), _dptr(K, "K", k, D.device), _stream(stream)), ctx)
+
+
+def build_K_delta(ctx, dD, K, stream=None):
+    """rix_build_K_delta: K += K(dD) (incremental build)."""
+    _, _, d, k = _sizes(ctx)
+    _check(load().rix_build_K_delta(ctx, _dptr(dD, "dD", d), _dptr(K, "K", k, dD.device), _stream(stream)), ctx)
 
 
 def energy(ctx, D, K, Ex, stream=None):

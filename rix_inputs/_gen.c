@@ -80,12 +80,19 @@ void fill_V(int64_t np, const int64_t *offV, const uint8_t *rep, const int64_t *
             for (int Q = 0; Q < nb; Q++) {
                 const double sP = sig[sigA[p] + P], sQ = sig[sigB[p] + Q];
                 const double g1 = sqrt(2.0 * (sP * sP + sQ * sQ));
-                const double g2 = sqrt(g1 * g1 + 1.0 / (omega * omega));
                 double x;
-                if (R < 1e-3 * g1)
-                    x = two_sqrt_pi * ((1.0 / g1 - 1.0 / g2) - (R * R / 3.0) * (1.0 / (g1 * g1 * g1) - 1.0 / (g2 * g2 * g2)));
-                else
-                    x = (erf(R / g1) - erf(R / g2)) / R;
+                if (omega > 0) {
+                    const double g2 = sqrt(g1 * g1 + 1.0 / (omega * omega));
+                    if (R < 1e-3 * g1)
+                        x = two_sqrt_pi * ((1.0 / g1 - 1.0 / g2) - (R * R / 3.0) * (1.0 / (g1 * g1 * g1) - 1.0 / (g2 * g2 * g2)));
+                    else
+                        x = (erf(R / g1) - erf(R / g2)) / R;
+                } else {  /* full range (PBE0): the omega -> 0 limit, plain Coulomb of two Gaussians */
+                    if (R < 1e-3 * g1)
+                        x = two_sqrt_pi * ((1.0 / g1) - (R * R / 3.0) * (1.0 / (g1 * g1 * g1)));
+                    else
+                        x = erf(R / g1) / R;
+                }
                 v[(int64_t)P * nb + Q] = x;
                 vq[(int64_t)Q * na + P] = x;
             }

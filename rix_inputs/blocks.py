@@ -177,11 +177,16 @@ def pair_list(system):
 
 def coulomb_sr(R, sP, sQ, omega):
     """Short-range (erfc-screened) Coulomb interaction of two unit s-Gaussian
-    charges of widths sP, sQ at distance R (bohr); broadcasts."""
+    charges of widths sP, sQ at distance R (bohr); broadcasts.  omega <= 0:
+    the full-range (PBE0) interaction erf(R/g1)/R."""
     g1 = np.sqrt(2.0 * (sP * sP + sQ * sQ))
-    g2 = np.sqrt(g1 * g1 + 1.0 / (omega * omega))
     small = R < 1e-3 * g1
     Rs = np.where(small, 1.0, R)
+    if omega <= 0:
+        full = erf(Rs / g1) / Rs
+        ser = (2.0 / math.sqrt(math.pi)) * ((1.0 / g1) - (R * R / 3.0) * (1.0 / g1 ** 3))
+        return np.where(small, ser, full)
+    g2 = np.sqrt(g1 * g1 + 1.0 / (omega * omega))
     full = (erf(Rs / g1) - erf(Rs / g2)) / Rs
     ser = (2.0 / math.sqrt(math.pi)) * ((1.0 / g1 - 1.0 / g2) - (R * R / 3.0) * (1.0 / g1 ** 3 - 1.0 / g2 ** 3))
     return np.where(small, ser, full)
@@ -262,7 +267,7 @@ class Packed:
         dist = np.ascontiguousarray(self.dist, dtype=np.float64)
         offV = np.ascontiguousarray(self.offV, dtype=np.int64)
         _genlib().fill_V(self.n_pairs, _p(offV), _p(rep), _p(part), _p(naA), _p(naB), _p(sigA), _p(sigB), _p(sig),
-                         _p(dist), OMEGA, _p(V))
+                         _p(dist), float(getattr(s, "omega", OMEGA)), _p(V))
         self.V = V
         return V
 

@@ -55,6 +55,7 @@ class System:
     tau: float = 0.0                # block screening threshold; <= 0 means none
     orbital_centres: np.ndarray = None  # [n_occ] atom index of each occupied orbital centre
     meta: dict = field(default_factory=dict)
+    omega: float = OMEGA            # range separation of V (bohr^-1); <= 0: full-range Coulomb (PBE0)
 
     @property
     def n_atoms(self):
@@ -274,6 +275,12 @@ CONFIG_NAMES = {
     3: "perovskite-like periodic, 1536 atoms, 8 A images",
     4: "ice-like periodic, 3072 atoms, 8 A images",
 }
+
+
+def full_range(system):
+    """The same workload with the full-range Coulomb metric of PBE0 (omega -> 0) instead of HSE06's."""
+    import dataclasses
+    return dataclasses.replace(system, name=system.name + " (PBE0 kernel)", omega=0.0)
 
 
 def config(i):

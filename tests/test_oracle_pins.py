@@ -350,3 +350,37 @@ def test_sampled_blocks_equal_full_rows(periodic):
     assert set(got) == {k for k in full if int(ri.pack_key(k[0], k[1], np.array(k[2]))) in set(kk[pick].tolist())}
     for key, blk in got.items():
         assert np.array_equal(blk, full[key])
+
+
+def test_full_range_generator_is_plain_gaussian_coulomb():
+    """PBE0 kernel (omega <= 0): every generated V element is erf(R/g1)/R (R -> 0: 2/(sqrt(pi) g1)),
+    the omega -> 0 limit of the HSE06 form, and it exceeds the short-range one everywhere."""
+    from scipy.special import erf
+    s = ri.full_range(ri.config(0))
+    pk = ri.generate(s, C=False, D=False)
+    hse = ri.generate(ri.config(0), C=False, D=False)
+    sp = s.species
+    for p in range(0, pk.n_pairs, 7):
+        a, b = pk.A[p], pk.B[p]
+        g1 = np.sqrt(2 * (s.sigma[sp[a]][:, None] ** 2 + s.sigma[sp[b]][None, :] ** 2))
+        R = pk.dist[p]
+        ref = 2 / np.sqrt(np.pi) / g1 if R == 0 else erf(R / g1) / R
+        got = pk.V[pk.offV[p]:pk.offV[p + 1]].reshape(g1.shape)
+        assert np.allclose(got, ref, rtol=1e-14, atol=0)
+        assert (got > hse.V[hse.offV[p]:hse.offV[p + 1]].reshape(g1.shape)).all()
+
+
+def test_delta_build_is_linear_in_D():
+    """K(D1) + K(D2 - D1) = K(D2): what an incremental build relies on (oracle, no screening)."""
+    s = ri.config(0)
+    pk = ri.generate(s)
+    D2 = pk.D
+    Du, _ = pk.gen_D_spin()
+    D1 = 0.9 * D2 + 0.1 * Du
+    Ks = []
+    for D in (D1, D2 - D1, D2):
+        o = Oracle(s)
+        o.set_data(pk.C, pk.V, D)
+        o.kpattern()
+        Ks.append(o.build_K())
+    assert np.abs(Ks[0] + Ks[1] - Ks[2]).max() < 1e-13 * np.abs(Ks[2]).max()
