@@ -212,6 +212,27 @@ rix_status rix_energy_noalloc(rix_ctx *ctx, const double *D_dev, const double *K
 rix_status rix_backward(rix_ctx *ctx, const double *D_dev, double gEx,
                         double *dD_dev, double *dC_dev, double *dV_dev, void *stream);
 
+/* Force and stress chain of E_x (the paper's Secs. "EXX force and stress
+ * contributions" and "Computation of Forces and Stress"), one Cartesian
+ * component c (0, 1, 2) per call, the paper's split of this work into three
+ * parts to bound memory.  C(A,B,n) and V(A,B,n) depend on the geometry
+ * through the pair vector r_p = x_B + n . a - x_A.  Inputs (device, packed):
+ * dEdC [c_elems], dEdV [v_elems] from rix_backward (either may be NULL to
+ * leave that part out), and the caller's derivatives of the stored C and V
+ * entries with respect to component c of their pair's r_p, dCdr_c
+ * [c_elems], dVdr_c [v_elems].  With g_p = sum_e dE/dC_pe dC_pe/d(r_p)_c
+ * (+ the V part):
+ *   F_dev[X]   = -dE/dx_X,c = sum over the pairs p = (X, B, n) of (g_p - g_(B,X,-n))
+ *                (n_atoms doubles, overwritten; may be NULL)
+ *   stress_dev = row c of (1/Omega) dE/d eps, eps the homogeneous strain that maps
+ *                every r_p to (1 + eps) r_p: stress_dev[b] = (1/Omega) sum_p g_p (r_p)_b
+ *                (3 doubles, overwritten; periodic only, may be NULL).
+ * D is held fixed (its own geometry dependence belongs to the SCF).  Fixed
+ * summation order (deterministic); asynchronous; no allocation. */
+rix_status rix_force_stress(rix_ctx *ctx, int32_t c, const double *dEdC_dev, const double *dEdV_dev,
+                            const double *dCdr_c_dev, const double *dVdr_c_dev, double *F_dev, double *stress_dev,
+                            void *stream);
+
 /* Gamma-point fold of an image-resolved K: Kdense[I][L] = sum_n K(A,E,n)[i][l]
  * (I, L global basis indices), row-major nbasis x nbasis.  Asynchronous. */
 rix_status rix_fold_gamma(rix_ctx *ctx, const double *K_dev, double *Kdense_dev, void *stream);

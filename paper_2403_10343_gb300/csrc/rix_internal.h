@@ -119,6 +119,10 @@ struct rix_ctx {
   int64_t nbasis = 0;
   int64_t *d_bofs = nullptr;            // global basis offset of each atom
   char4 *d_n3 = nullptr;                // image vector (n1, n2, n3) of every K block
+  int64_t *d_row1 = nullptr;            // first pair of every atom [nat+1]
+  double *d_rvec = nullptr;             // pair vector r_p = x_B + n . cell - x_A of every pair [np][3]
+  double *d_gpair = nullptr;            // force chain: dE/dr_p (one Cartesian component) per pair
+  double volume = 0.0;                  // cell volume (bohr^3), 0 for a cluster
   // mixed precision: terms 3+4 and term 2 as batched sliced GEMMs on the tensor cores
   bool have_mx = false;
   int32_t mx_S = 5;

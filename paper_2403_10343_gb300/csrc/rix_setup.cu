@@ -915,6 +915,25 @@ extern "C" rix_status rix_setup(const rix_system *sys, const rix_options *opt, r
   if ((s = rix_alloc(ctx, &ctx->d_keepC, np)) != RIX_OK) return fail(s);
   if ((s = rix_alloc(ctx, &ctx->d_keepV, np)) != RIX_OK) return fail(s);
   if ((s = rix_alloc(ctx, &ctx->d_keepD, np)) != RIX_OK) return fail(s);
+  {
+    // pair vectors (the geometry the force and stress chain differentiates through)
+    std::vector<double> rv(3 * (size_t)np);
+    for (int64_t p = 0; p < np; p++)
+      for (int c = 0; c < 3; c++) {
+        double sh = 0.0;
+        if (ctx->periodic)
+          for (int d = 0; d < 3; d++) sh += (double)ctx->pn[3 * p + d] * ctx->cell[3 * d + c];
+        rv[3 * p + c] = (ctx->xyz[3 * ctx->pB[p] + c] + sh) - ctx->xyz[3 * ctx->pA[p] + c];
+      }
+    if ((s = rix_upload(ctx, &ctx->d_rvec, rv)) != RIX_OK) return fail(s);
+    if ((s = rix_upload(ctx, &ctx->d_row1, ctx->row1)) != RIX_OK) return fail(s);
+    if ((s = rix_alloc(ctx, &ctx->d_gpair, np)) != RIX_OK) return fail(s);
+    if (ctx->periodic) {
+      const double *a = ctx->cell;
+      ctx->volume = std::fabs(a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
+                              a[2] * (a[3] * a[7] - a[4] * a[6]));
+    }
+  }
   if (cudaHostAlloc((void **)&ctx->h_err, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
       cudaHostGetDevicePointer((void **)&ctx->d_err, ctx->h_err, 0) != cudaSuccess) {
     cudaGetLastError();

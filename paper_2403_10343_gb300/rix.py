@@ -83,6 +83,7 @@ def load():
     lib.rix_count_flops.argtypes = [P, P, ctypes.POINTER(ctypes.c_double), P]
     lib.rix_check.argtypes = [P, P]
     lib.rix_build_K_delta.argtypes = [P, P, P, P]
+    lib.rix_force_stress.argtypes = [P, ctypes.c_int32, P, P, P, P, P, P, P]
     lib.rix_bloch.argtypes = [P, P, ctypes.c_int32, P, P, P]
     lib.rix_build_K_spin.argtypes = [P, ctypes.c_int32, P, P, P]
     lib.rix_energy_spin.argtypes = [P, ctypes.c_int32, P, P, P, P]
@@ -96,7 +97,7 @@ def load():
               "rix_energy_noalloc",
               "rix_backward", "rix_fold_gamma", "rix_stats", "rix_stage_times", "rix_gemm_sliced",
               "rix_autotune", "rix_count_flops", "rix_check", "rix_test_stalled_gemm", "rix_bloch",
-              "rix_build_K_spin", "rix_energy_spin", "rix_build_K_delta"):
+              "rix_build_K_spin", "rix_energy_spin", "rix_build_K_delta", "rix_force_stress"):
         getattr(lib, f).restype = I
     _lib = lib
     return lib
@@ -265,6 +266,16 @@ def energy_spin(ctx, D, K, Ex, n_spin=2, stream=None):
     _, _, d, k = _sizes(ctx)
     _check(load().rix_energy_spin(ctx, int(n_spin), _dptr(D, "D", n_spin * d), _dptr(K, "K", n_spin * k, D.device),
                                   _dptr(Ex, "Ex", 1, D.device), _stream(stream)), ctx)
+
+
+def force_stress(ctx, c, dEdC, dEdV, dCdr_c, dVdr_c, F=None, stress=None, stream=None):
+    """rix_force_stress: component c of the forces [n_atoms] and row c of the stress [3] (device tensors)."""
+    cel, vel, _, _ = _sizes(ctx)
+    nat = int(stats(ctx)["n_atoms"])
+    dev = (dEdC if dEdC is not None else dEdV).device
+    _check(load().rix_force_stress(ctx, int(c), _dptr(dEdC, "dEdC", cel), _dptr(dEdV, "dEdV", vel, dev),
+                                   _dptr(dCdr_c, "dCdr_c", cel, dev), _dptr(dVdr_c, "dVdr_c", vel, dev),
+                                   _dptr(F, "F", nat, dev), _dptr(stress, "stress", 3, dev), _stream(stream)), ctx)
 
 
 def check(ctx, stream=None):

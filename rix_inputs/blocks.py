@@ -271,6 +271,49 @@ class Packed:
         self.V = V
         return V
 
+    def pair_vectors(self):
+        """r_p = x_B + n . cell - x_A of every pair in its own orientation (bohr), [n_pairs, 3]."""
+        s = self.system
+        r = s.xyz[self.B] - s.xyz[self.A]
+        if s.cell is not None:
+            r = r + self.n.astype(np.float64) @ s.cell
+        return r
+
+    def gen_derivatives(self):
+        """Derivatives of the generated C and V with respect to each pair's vector r_p.
+
+        The generators make C(A,B,n) = g exp(-0.8 |r_p|) with draws g that do not
+        depend on the geometry and V_PQ = v(|r_p|; sigma_P, sigma_Q), so
+          dC/dr_p = -0.8 C r_p / |r_p|,   dV/dr_p = v'(|r_p|) r_p / |r_p|,
+          v'(R) = (2/sqrt(pi)) (exp(-R^2/g1^2)/g1 - exp(-R^2/g2^2)/g2) / R - v(R) / R
+        (the g2 terms absent for the full-range metric), and both vanish for
+        the on-site pairs (r_p = 0).  Returns (dC [3, c_elems], dV [3, v_elems])
+        in the packed layouts: what a caller passes to the force/stress chain.
+        """
+        s = self.system
+        r = self.pair_vectors()
+        R = np.sqrt((r * r).sum(axis=1))
+        rhat = np.where(R[:, None] > 0, r / np.where(R > 0, R, 1.0)[:, None], 0.0)
+        dC = (-0.8 * np.repeat(rhat, self.sizeC, axis=0) * self.C[:, None]).T.copy()
+        dV = np.zeros((3, int(self.offV[-1])))
+        omega = float(getattr(s, "omega", OMEGA))
+        sp = s.species
+        for p in range(self.n_pairs):
+            if R[p] == 0.0:
+                continue
+            sP = s.sigma[sp[self.A[p]]][:, None]
+            sQ = s.sigma[sp[self.B[p]]][None, :]
+            g1 = np.sqrt(2.0 * (sP * sP + sQ * sQ))
+            Rp = R[p]
+            v = self.V[self.offV[p]:self.offV[p + 1]].reshape(g1.shape)
+            d = np.exp(-Rp * Rp / (g1 * g1)) / g1
+            if omega > 0:
+                g2 = np.sqrt(g1 * g1 + 1.0 / (omega * omega))
+                d = d - np.exp(-Rp * Rp / (g2 * g2)) / g2
+            dv = (2.0 / math.sqrt(math.pi)) * d / Rp - v / Rp
+            dV[:, self.offV[p]:self.offV[p + 1]] = rhat[p][:, None] * dv.reshape(1, -1)
+        return dC, dV
+
     def orbitals(self):
         """Support of each orbital: list of (atoms, image vectors, distances in bohr)."""
         s = self.system
