@@ -459,6 +459,7 @@ struct GemmArgs {
   double oscale;           // scale of the added values (modes 0 and 1)
   int64_t xshift;          // mode 0: X + offK[x] - xshift is the output block
   int ntiles;              // output tiles of the launch (persistent CTAs loop over them)
+  const uint8_t *row_live = nullptr;  // batched mode: per row tile (tiles[t].w), 0 = all its rows are zero
   uint64_t wait_ns = WAIT_NS;  // limit of every bounded wait
   int stall = 0;           // 1: the MMA issuer waits on a barrier nothing completes (timeout test)
 };
@@ -479,6 +480,7 @@ struct TileInfo {
   const __nv_bfloat16 *gA, *gB;
   const int *geA, *geB;
   int mt, nt, Mpad, Npad, Kpad, M, N, drop;
+  bool live;  // false: the tile's A rows are all zero (screened), every role skips it
 };
 
 __device__ __forceinline__ TileInfo tile_info(const GemmArgs &g, int t) {
@@ -494,6 +496,7 @@ __device__ __forceinline__ TileInfo tile_info(const GemmArgs &g, int t) {
     ti.geA = g.eA + pr->eaoff;
     ti.geB = g.eB + pr->eboff;
     ti.Mpad = pr->Mpad; ti.Npad = pr->Npad; ti.Kpad = pr->Kpad; ti.M = pr->M; ti.N = pr->N; ti.drop = pr->drop;
+    ti.live = !g.row_live || g.row_live[tt.w];
   } else {
     const int mtiles = g.Mpad / TM;
     ti.pr = nullptr;
@@ -501,6 +504,7 @@ __device__ __forceinline__ TileInfo tile_info(const GemmArgs &g, int t) {
     ti.nt = t / mtiles;
     ti.gA = g.A; ti.gB = g.B; ti.geA = g.eA; ti.geB = g.eB;
     ti.Mpad = g.Mpad; ti.Npad = g.Npad; ti.Kpad = g.Kpad; ti.M = g.M; ti.N = g.N; ti.drop = g.drop;
+    ti.live = true;
   }
   return ti;
 }
@@ -559,6 +563,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
     bool aborted = false;
     for (int t = blockIdx.x; t < ntiles && !aborted; t += gridDim.x) {
       const TileInfo ti = tile_info(g, t);
+      if (!ti.live) continue;  // all-zero rows: no copies (the other roles skip it too)
       const int nk = ti.Kpad / KC;
       const int64_t a_tiles = (int64_t)(ti.Mpad / TM) * nk;  // tiles per A plane
       const int64_t b_tiles = (int64_t)(ti.Npad / TN) * nk;
@@ -594,6 +599,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
     if (g.stall && !mbar_wait(never, 0, g.wait_ns)) atomicExch(abort_flag, 1);
     for (int t = blockIdx.x; t < ntiles && !*(volatile int *)abort_flag; t += gridDim.x) {
       const TileInfo ti = tile_info(g, t);
+      if (!ti.live) continue;
       const int nk = ti.Kpad / KC;
       for (int c = 0; c < nk; c++, cg++) {
         const int st = cg % nst;
@@ -636,6 +642,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       const TileInfo ti = tile_info(g, t);
+      if (!ti.live) continue;  // its output is zero: nothing to drain or add
       const int nk = ti.Kpad / KC;
       const int ngroups = (nk + GROUP - 1) / GROUP;
       const int mt = ti.mt, nt = ti.nt, drop = ti.drop, Ncols = ti.N;
@@ -1022,6 +1029,20 @@ struct SrcAcc {
   }
 };
 
+// live[r] = 1 if any pair of row tile r has a kept V and a kept D block
+__global__ void k_rt_live(int64_t n, const int2 *rt, const int32_t *rtq, const uint8_t *keepV, const uint8_t *keepD,
+                          uint8_t *live) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int2 e = rt[r];
+  uint8_t v = 0;
+  for (int i = 0; i < e.y; i++) {
+    const int q = rtq[e.x + i];
+    v |= keepV[q] & keepD[q];
+  }
+  live[r] = v;
+}
+
 __global__ void k_flag_set(int n, const int32_t *idx, uint8_t *flags) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) flags[idx[t]] = 1;
@@ -1048,6 +1069,11 @@ struct rix_mx_plan {
   rixtc::Src *d_rowsrc = nullptr, *d_colsrc = nullptr;
   int32_t *d_xmap = nullptr;
   int *d_eA = nullptr, *d_eB = nullptr;
+  // kind 2: row tiles whose rows all come from screened (V, D) blocks are skipped per build
+  int64_t n_rt = 0;
+  int2 *d_rt = nullptr;
+  int32_t *d_rtq = nullptr;
+  uint8_t *d_rtlive = nullptr;
 };
 
 namespace {
@@ -1066,6 +1092,8 @@ struct PlanHost {
   std::vector<rixtc::Src> rowsrc, colsrc;
   std::vector<int32_t> xmap;
   std::vector<uint8_t> use;                // kind 2: middle atoms that run here
+  std::vector<int2> rt;                    // kind 2: per row tile, (first, count) of its pairs in rtq
+  std::vector<int32_t> rtq;                // kind 2: pair (B, G') of each row group, per row tile
   int64_t eaoff = 0, eboff = 0;
   double tflops = 0, fl64 = 0;
 };
@@ -1168,7 +1196,8 @@ rix_status plan_host(rix_ctx *ctx, int kind, const std::vector<int64_t> &ptrZ, P
       total += bytes;
       maxp = std::max(maxp, bytes);
       // xmap, rowinfo + rowprob + rowsrc + exponent, colinfo + colprob + colsrc + exponent, tiles
-      maps += (int64_t)qs.size() * zs.size() * 4 + (int64_t)Mpad * (8 + 8 + 32 + 4) +
+      maps += (kind == 2 ? (int64_t)(Mpad / TM) * 21 : 0) +
+              (int64_t)qs.size() * zs.size() * 4 + (int64_t)Mpad * (8 + 8 + 32 + 4) +
               (int64_t)Npad * (16 + 8 + 32 + 4) + (int64_t)(Mpad / TM) * (Npad / TN) * 16 + (int64_t)sizeof(Prob);
       h.tflops += 2.0 * Mpad * Npad * Kpad * npairs;
       if (count_only) continue;
@@ -1264,8 +1293,28 @@ rix_status plan_host(rix_ctx *ctx, int kind, const std::vector<int64_t> &ptrZ, P
           h.xmap.push_back((int32_t)x);
         }
       }
+      const int rt0 = (int)h.rt.size();
+      if (kind == 2) {
+        // row tile mt covers rows [128 mt, 128 mt + 128): the pairs (B, G') of the row groups there
+        std::vector<int> qend(qs.size());
+        int acc = 0;
+        for (size_t qi = 0; qi < qs.size(); qi++) {
+          const int a = ctx->pB[qs[qi]];
+          acc += ctx->na_at[a] * ctx->nb_at[a];
+          qend[qi] = acc;
+        }
+        size_t q0 = 0;
+        for (int mt = 0; mt < Mpad / TM; mt++) {
+          const int lo = mt * TM, hi = std::min(M, lo + TM);
+          while (q0 < qs.size() && qend[q0] <= lo) q0++;
+          const int first = (int)h.rtq.size();
+          for (size_t qi = q0; qi < qs.size() && (qi == 0 ? 0 : qend[qi - 1]) < hi; qi++)
+            h.rtq.push_back(ctx->partner1[qs[qi]]);
+          h.rt.push_back(make_int2(first, (int)h.rtq.size() - first));
+        }
+      }
       for (int nt = 0; nt < Npad / TN; nt++)
-        for (int mt = 0; mt < Mpad / TM; mt++) h.tiles.push_back(make_int4(pidx, mt, nt, 0));
+        for (int mt = 0; mt < Mpad / TM; mt++) h.tiles.push_back(make_int4(pidx, mt, nt, kind == 2 ? rt0 + mt : 0));
       h.probs.push_back(pr);
       h.pbytes.push_back(bytes);
       // Z of terms 3+4 is resident per block of its middle atom; kind 2 rows per block
@@ -1387,6 +1436,12 @@ rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
     if ((s = rix_upload(ctx, &pl->d_xmap, h.xmap)) != RIX_OK) return s;
     if ((s = rix_alloc(ctx, &pl->d_eA, std::max<int64_t>(h.eaoff, 1))) != RIX_OK) return s;
     if ((s = rix_alloc(ctx, &pl->d_eB, std::max<int64_t>(h.eboff, 1))) != RIX_OK) return s;
+    if (kind == 2 && !h.rt.empty()) {
+      pl->n_rt = (int64_t)h.rt.size();
+      if ((s = rix_upload(ctx, &pl->d_rt, h.rt)) != RIX_OK) return s;
+      if ((s = rix_upload(ctx, &pl->d_rtq, h.rtq)) != RIX_OK) return s;
+      if ((s = rix_alloc(ctx, &pl->d_rtlive, pl->n_rt)) != RIX_OK) return s;
+    }
     if (kind == 2) {
       // middle atoms whose term-4 intermediate runs here: k_Z skips them
       std::vector<int32_t> on;
@@ -1437,6 +1492,7 @@ int32_t rix_launch_count(const rix_ctx *ctx) {
     n += 5 * (int32_t)(ctx->mx34->grp.size() - 1) + 5 * (int32_t)(ctx->mx2->grp.size() - 1) +
          5 * (int32_t)(ctx->mxz->grp.size() - 1) + rix_t1_launches(ctx) + rix_tt_launches(ctx);
     if (ctx->n_t1tc < ctx->nat) n += ctx->nblk;  // k_X12 for the other column atoms
+    if (ctx->mxz->n_rt > 0) n += ctx->nblk;      // row-tile liveness of the Z plan
   } else {
     n += 2 * ctx->nblk;  // k_X12, k_X34
   }
@@ -1488,6 +1544,7 @@ rix_status run_group(rix_ctx *ctx, const rix_mx_plan *pl, size_t g, const Operan
     ga.oscale = oscale;
     ga.xshift = oshift;
     ga.ntiles = (int)(t1 - t0);
+    ga.row_live = pl->d_rtlive;  // kind 2: skip row tiles of screened (V, D) blocks
     k_gemm_sliced<<<persistent_grid(t1 - t0), NTHR, smem_bytes(S), st>>>(ga);
   }
   cudaError_t e = cudaGetLastError();
@@ -1542,6 +1599,10 @@ rix_status rix_mixed_z(rix_ctx *ctx, int blk, int64_t zbase, const double *D, cu
   const rix_mx_plan *pl = ctx->mxz;
   const Operand rows{ctx->d_V, 0, D, ctx->d_keepV, ctx->d_keepD};
   const Operand cols{ctx->d_C, 0, nullptr, ctx->d_keepC, nullptr};
+  if (pl->n_rt > 0) {
+    rixtc::k_rt_live<<<(unsigned)((pl->n_rt + 255) / 256), 256, 0, st>>>(pl->n_rt, pl->d_rt, pl->d_rtq, ctx->d_keepV,
+                                                                         ctx->d_keepD, pl->d_rtlive);
+  }
   for (size_t g = 0; g + 1 < pl->grp.size(); g++) {
     if (pl->grp_blk[g] != blk) continue;
     rix_status s = run_group(ctx, pl, g, rows, cols, ctx->d_off2, ctx->d_Z, zbase, 0.5, st);
