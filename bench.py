@@ -154,25 +154,67 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def oracle_sample(system, pk, rows):
-    """Time the FP64 oracle on a row sample; return (seconds, sample FLOPs, full FLOPs, threads)."""
-    from oracle.oracle import Oracle
-    o = Oracle(system)
-    o.set_data(pk.C, pk.V, pk.D)
-    o.kpattern()
-    o.build_K(dry=True)
-    full = o.flops()
-    o.kpattern(rows)
-    t0 = time.perf_counter()
-    o.build_K()
-    dt = time.perf_counter() - t0
-    return dt, o.flops(), full, Oracle.threads()
+class OracleSampler:
+    """The FP64 oracle on a bounded row sample of a workload, scaled to a full build.
+
+    The full build's FLOP count comes from the oracle's own dry run (counted
+    once); each timed sample builds the K rows of the sample atoms and is
+    scaled by the exact FLOP ratio.
+    """
+
+    def __init__(self, system, pk):
+        from oracle.oracle import Oracle
+        self.Oracle = Oracle
+        self.o = Oracle(system)
+        self.o.set_data(pk.C, pk.V, pk.D)
+        self.o.kpattern()
+        self.o.build_K(dry=True)
+        self.full = self.o.flops()
+
+    def run(self, rows, threads=0):
+        if threads:
+            self.Oracle.set_threads(threads)
+        try:
+            self.o.kpattern(rows)
+            t0 = time.perf_counter()
+            self.o.build_K()
+            dt = time.perf_counter() - t0
+            used = self.Oracle.threads()
+        finally:
+            if threads:
+                self.Oracle.set_threads(0)
+        return dt, self.o.flops(), used
+
+    def ms_full(self, rows, threads=0):
+        dt, sf, used = self.run(rows, threads)
+        return dt * self.full / sf * 1e3, dt, sf, used
 
 
 def sample_rows(system, n_mol=1):
     """A whole molecule (or the first atoms) near the middle of the atom list."""
     mid = (system.n_atoms // 2) // 3 * 3
     return list(range(mid, min(system.n_atoms, mid + 3 * n_mol)))
+
+
+def light_row(system):
+    """One atom of the lightest species near the middle (a bounded single-thread sample)."""
+    sp = int(np.argmin(system.nbas * system.naux))
+    atoms = np.nonzero(system.species == sp)[0]
+    return [int(atoms[len(atoms) // 2])]
+
+
+def cpu_baseline(system, pk, sampler=None):
+    """The oracle on the host cores: all cores on a molecule's rows, one core on one light row."""
+    smp = sampler or OracleSampler(system, pk)
+    rows = sample_rows(system)
+    ms, dt, sf, used = smp.ms_full(rows)
+    one = light_row(system)
+    ms1, dt1, sf1, _ = smp.ms_full(one, threads=1)
+    return {"value": ms, "unit": "ms", "cores": used, "kind": "oracle",
+            "sample": f"rows {rows} of {system.n_atoms} atoms ({sf:.3g} of {smp.full:.3g} FLOP, {dt:.1f} s on "
+                      f"{used} threads), scaled to a full build by the oracle's own FLOP count",
+            "single_thread": {"value": ms1, "unit": "ms", "cores": 1,
+                              "sample": f"row {one} ({sf1:.3g} FLOP, {dt1:.1f} s on 1 thread), scaled likewise"}}
 
 
 def run_reference(args):
@@ -182,21 +224,22 @@ def run_reference(args):
     import rix_inputs as ri
     s = ri.config(args.config)
     pk = ri.generate(s)
-    rows = sample_rows(s)
+    smp = OracleSampler(s, pk)
+    rows = light_row(s) if s.n_atoms > 1000 else sample_rows(s)
     for _ in range(args.warmup):
-        oracle_sample(s, pk, rows[:1])
-    times, sf, ff, thr = [], 0, 0, 1
+        smp.run(rows)
+    times, sf, used = [], 0.0, 1
     for _ in range(args.steps):
-        dt, sf, ff, thr = oracle_sample(s, pk, rows)
-        times.append(dt * ff / sf * 1e3)
+        ms, dt, sf, used = smp.ms_full(rows)
+        times.append(ms)
     ms = float(np.mean(times))
     line = {
         "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAMES[args.config], "precision": "fp64", "l2": "inputs larger than L2"},
-        "cpu_baseline": {"value": ms, "unit": "ms", "cores": thr, "kind": "oracle",
-                         "sample": f"rows {rows} of {s.n_atoms} ({sf:.3g} of {ff:.3g} FLOP), "
+        "cpu_baseline": {"value": ms, "unit": "ms", "cores": used, "kind": "oracle",
+                         "sample": f"each step: rows {rows} of {s.n_atoms} ({sf:.3g} of {smp.full:.3g} FLOP), "
                                    f"time scaled by the oracle's own FLOP ratio"},
         "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -214,8 +257,15 @@ def max_over_ranks(x, world, dev):
     return t.item()
 
 
-def measure(args, s, pk, precision, dev, world, rank, local):
-    """Warm up, time args.steps builds (+ energy) and the end-to-end variant; returns a dict."""
+# DRAM bytes per issued slice-pair K stage of k_gemm_sliced (one 128 x 80 tile x 32 K
+# values x one slice pair), from the ncu capture summarised in profiles/ (None: not measured
+# for the kernel as it stands)
+GEMM_DRAM_BYTES_PER_STAGE_PAIR = None
+GEMM_STAGE_PAIR_FLOPS = 2.0 * 128 * 80 * 32
+
+
+def measure(args, s, pk, precision, dev, world, steps, warmup, graph, e2e_steps):
+    """Warm up, time `steps` builds (+ energy) and the end-to-end variant; returns a dict."""
     import torch
     import torch.distributed as dist
     from paper_2403_10343_gb300.rix import Exchange
@@ -225,7 +275,8 @@ def measure(args, s, pk, precision, dev, world, rank, local):
     if s.n_atoms > 1000:
         cap = int(torch.cuda.mem_get_info(dev)[0] - (24 << 30))
     kw = {"n_slices": args.slices} if precision == "mixed" else {}
-    ex = Exchange.from_system(s, precision=precision, profile=1, max_workspace_bytes=cap, verbose=args.verbose,
+    prof = 2 if (precision == "mixed" and not graph) else 1
+    ex = Exchange.from_system(s, precision=precision, profile=prof, max_workspace_bytes=cap, verbose=args.verbose,
                               **kw)
     assert np.array_equal(ex.pair_keys(), pk.keys)
     ex.set_CV(pk.C, pk.V)          # straight from host memory (copied into library storage)
@@ -233,7 +284,7 @@ def measure(args, s, pk, precision, dev, world, rank, local):
     K = torch.empty(ex.k_elems, dtype=torch.float64, device=dev)
     Ex = torch.empty(1, dtype=torch.float64, device=dev)
     tiles = None
-    if args.autotune:
+    if args.autotune and precision == "fp64":
         # tile budgets of the FP64 contraction kernels, timed on this system (not in the timed region)
         tiles = ex.autotune(D, os.path.join(tempfile.gettempdir(), "rix_tiles.txt"))
 
@@ -241,14 +292,13 @@ def measure(args, s, pk, precision, dev, world, rank, local):
         ex.build_K(Dd, K)
         ex.energy(Dd, K, Ex)
 
-    # warm-up steps run eagerly and carry the per-stage CUDA events
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step(D)
     torch.cuda.synchronize()
     stage_ms, nb = ex.stage_times()
-    stage_ms = {k: v / max(1, nb) for k, v in stage_ms.items()}
-    eager_ms = None
-    if args.graph:
+    if prof == 2:
+        ex.gemm_profile()
+    if graph:
         # one step captured into a CUDA graph; the timed steps are replays
         g = torch.cuda.CUDAGraph()
         cs = torch.cuda.Stream(device=dev)
@@ -269,18 +319,27 @@ def measure(args, s, pk, precision, dev, world, rank, local):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clk = Clocks(local)
+    clk = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
     clk.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(st)
-    for _ in range(args.steps):
+    for _ in range(steps):
         run()
     e1.record(st)
     torch.cuda.synchronize()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    ex.stage_times()
+    ms = e0.elapsed_time(e1) / steps
+    if not graph:
+        # per-stage and per-GEMM-launch events recorded inside the timed region
+        sm, nb = ex.stage_times()
+        stage_ms = sm
+    stage_ms = {k: v / max(1, nb) for k, v in stage_ms.items()}
+    gemm = None
+    if prof == 2:
+        gms, glaunch, gpairs = ex.gemm_profile()
+        gemm = {"ms_per_build": gms / steps, "launches_per_build": glaunch / steps,
+                "stage_pairs_per_build": gpairs / steps}
     ms = max_over_ranks(ms, world, dev)
     # end to end through the same API with host buffers: D in, K and E_x out, every step
     Dh = torch.from_numpy(pk.D).pin_memory()
@@ -291,9 +350,9 @@ def measure(args, s, pk, precision, dev, world, rank, local):
         dist.barrier()
     torch.cuda.synchronize()
     e0.record(st)
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         Dd.copy_(Dh, non_blocking=True)
-        if args.graph:
+        if graph:
             D.copy_(Dd)        # the graph reads D
             run()
         else:
@@ -302,68 +361,75 @@ def measure(args, s, pk, precision, dev, world, rank, local):
         Exh.copy_(Ex, non_blocking=True)
     e1.record(st)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
     ex.stage_times()
+    if prof == 2:
+        ex.gemm_profile()
     e2e_ms = max_over_ranks(e2e_ms, world, dev)
     stats = screened(ex.stats(), ex.count_flops(D))
     launches = stats["launches_build"] + 3  # build + energy kernels
-    out = {"ms": ms, "e2e_ms": e2e_ms, "stage_ms": stage_ms, "stats": stats, "clocks": clocks, "graph": args.graph,
-           "tiles": tiles,
-           "E_x": Ex.item(), "K": K, "launches": launches, "h2d": int(D.numel() * 8), "d2h": int(K.numel() * 8 + 8)}
+    out = {"ms": ms, "e2e_ms": e2e_ms, "stage_ms": stage_ms, "stats": stats, "clocks": clocks, "graph": graph,
+           "tiles": tiles, "gemm": gemm, "E_x": Exh.item(), "E_x_dev": Ex.item(), "K": K, "launches": launches,
+           "h2d": int(D.numel() * 8), "d2h": int(K.numel() * 8 + 8), "steps": steps, "warmup": warmup,
+           "e2e_steps": e2e_steps}
     ex.close()
     return out
 
 
-def roofline(args, precision, r):
+def tensor_alg_flops(stats):
+    """Algorithmic FP64-equivalent FLOPs (screened, unpadded, 2 per multiply-add) done by k_gemm_sliced."""
+    return (stats["flops_t_tc"] + stats["flops_term1_tc"] + stats["flops_term2"] + stats["flops_z_tc"] +
+            stats["flops_stage"][4])
+
+
+def roofline(precision, r):
+    """The dominant kernel's roofline.
+
+    Mixed: k_gemm_sliced, achieved = the algorithmic FP64-equivalent FLOPs of
+    the work it does per build / its summed launch time per build (CUDA events
+    around every launch in the timed region), against the measured sustained
+    BF16 peak; the BF16 FLOPs it issued (every slice pair, padded tiles) are
+    reported beside it.  FP64: the longest FP64 stage on the FP64 pipe.
+    """
     stats, stage_ms = r["stats"], r["stage_ms"]
     pk_peaks, src = peaks()
+    if precision == "mixed" and r.get("gemm"):
+        gm = r["gemm"]
+        alg = tensor_alg_flops(stats)
+        t = gm["ms_per_build"] * 1e-3
+        peak = pk_peaks["bf16_tflops_sustained"]
+        issued = gm["stage_pairs_per_build"] * GEMM_STAGE_PAIR_FLOPS
+        per_launch = gm["stage_pairs_per_build"] / max(1.0, gm["launches_per_build"])
+        traffic = None if GEMM_DRAM_BYTES_PER_STAGE_PAIR is None else GEMM_DRAM_BYTES_PER_STAGE_PAIR * per_launch
+        return {"bound": "tensor", "kernel": "k_gemm_sliced", "achieved": alg / t / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "frac": alg / t / 1e12 / peak, "traffic": traffic,
+                "traffic_unit": "bytes per launch",
+                "peak_source": f"bf16 sustained (a kernel timed inside a long step), {src}",
+                "alg_flops_per_build": alg, "kernel_ms_per_build": gm["ms_per_build"],
+                "launches_per_build": gm["launches_per_build"],
+                "issued_bf16_flops_per_build": issued, "issued_tflops": issued / t / 1e12,
+                "issued_frac": issued / t / 1e12 / peak,
+                "alg_definition": "FP64-equivalent, screened, unpadded: T, terms 1-4 and Z products moved to the "
+                                  "tensor cores (2 FLOP per multiply-add)"}
     fp64_stages = [k for k in ("T", "U2", "X12", "Z", "X34") if stage_fp64_share(stats, k, precision) >= 0.5]
     dom = max(fp64_stages, key=lambda k: stage_ms.get(k, 0.0))
     flops = stage_flops(stats, dom, precision) * stage_fp64_share(stats, dom, precision)
     achieved = flops / (stage_ms[dom] * 1e-3) / 1e12
-    roof_tc = None
-    if precision == "mixed":
-        # terms 1-4 and Z on the tensor cores: issued BF16 FLOPs (all slice pairs, padded tiles)
-        ms = sum(stage_ms.get(k, 0.0) for k in TENSOR_STAGE if stage_fp64_share(stats, k, precision) < 0.5)
-        if ms > 0:
-            tc = stats["tensor_flops"] / (ms * 1e-3) / 1e12
-            peak_tc = pk_peaks["bf16_tflops_sustained"]
-            roof_tc = {"bound": "tensor", "kernel": "k_gemm_sliced (+ packing): terms 1-4 and Z",
-                       "achieved": tc, "peak": peak_tc, "unit": "TFLOP/s", "frac": tc / peak_tc, "traffic": None,
-                       "peak_source": f"bf16 sustained, {src}",
-                       "fp64_equivalent_tflops": (stage_flops(stats, "X34", precision) +
-                                                  stage_flops(stats, "TC12", precision) +
-                                                  stats["flops_z_tc"] + stats["flops_t_tc"]) / (ms * 1e-3) / 1e12}
-            # the headline bound is the stage that takes longest: FP64 kernel or tensor-core stages
-            if ms > stage_ms.get(dom, 0.0):
-                return roof_tc, roof_tc
     peak = pk_peaks.get("fp64_tflops", FP64_PEAK_TFLOPS_NOMINAL)
-    roof = {"bound": "alu", "kernel": STAGE_KERNEL[dom], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+    return {"bound": "alu", "kernel": STAGE_KERNEL[dom], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": None,
             "peak_source": "FP64 pipe, nominal 1.25 TFLOP/s (recipe table); measured DFMA 1.01, DMMA 1.06"}
-    return roof, roof_tc
 
 
-def stage_roofline(precision, r):
-    """Every stage: algorithmic FP64-equivalent FLOPs over its event time, against the pipe it runs on."""
+def stage_rates(precision, r):
+    """Every stage: its event time and its algorithmic FP64-equivalent FLOP rate."""
     stats, stage_ms = r["stats"], r["stage_ms"]
-    pk_peaks, src = peaks()
     out = {}
     for st in ("T", "U2", "X12", "TC12", "Z", "X34"):
         ms = stage_ms.get(st, 0.0)
         fl = stage_flops(stats, st, precision)
-        if ms <= 0 or fl <= 0:
-            continue
-        ach = fl / (ms * 1e-3) / 1e12
-        if precision == "mixed" and st in TENSOR_STAGE and stage_fp64_share(stats, st, precision) < 0.5:
-            tc = sum(stats["tensor_flops_stage"][i] for i in TENSOR_STAGE[st]) / (ms * 1e-3) / 1e12
-            peak = pk_peaks["bf16_tflops_sustained"]
-            out[st] = {"ms": round(ms, 4), "pipe": "tensor (bf16 slices)", "issued_tflops": round(tc, 2),
-                       "peak": peak, "frac": round(tc / peak, 4), "fp64_equivalent_tflops": round(ach, 3)}
-        else:
-            peak = pk_peaks.get("fp64_tflops", FP64_PEAK_TFLOPS_NOMINAL)
-            out[st] = {"ms": round(ms, 4), "pipe": "fp64", "achieved_tflops": round(ach, 4), "peak": peak,
-                       "frac": round(ach / peak, 4)}
+        if ms > 0 and fl > 0:
+            out[st] = {"ms": round(ms, 4), "alg_tflops": round(fl / (ms * 1e-3) / 1e12, 4)}
     return out
 
 
@@ -382,28 +448,35 @@ def run_rix(args):
 
     s = ri.config(args.config)
     pk = ri.generate(s)
-    precs = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
-    res = {p: measure(args, s, pk, p, dev, world, rank, local) for p in precs}
+    big = s.n_atoms > 1000
+    graph = (not big) if args.graph < 0 else bool(args.graph)
+    precs = ["mixed", "fp64"] if args.precision == "both" else [args.precision]
+    res = {}
+    for p in precs:
+        if p == "fp64" and "mixed" in precs and big:
+            # the FP64 path of the large workloads takes minutes per build: a shorter run, labelled
+            res[p] = measure(args, s, pk, p, dev, world, 1, 0, False, 1)
+        else:
+            res[p] = measure(args, s, pk, p, dev, world, args.steps, args.warmup, graph,
+                             min(args.steps, 3) if big else args.steps)
     head = "mixed" if "mixed" in res else "fp64"
     r = res[head]
-    roof, roof_tc = roofline(args, head, r)
+    roof = roofline(head, r)
     extra = {}
     if len(res) == 2:
         K64, Km = res["fp64"]["K"], res["mixed"]["K"]
-        extra["fp64"] = {"ms": res["fp64"]["ms"], "e2e_ms": res["fp64"]["e2e_ms"], "E_x": res["fp64"]["E_x"],
-                         "stage_ms": {k: round(v, 4) for k, v in res["fp64"]["stage_ms"].items()},
-                         "roofline": roofline(args, "fp64", res["fp64"])[0],
-                         "stage_roofline": stage_roofline("fp64", res["fp64"])}
-        extra["mixed_vs_fp64"] = {"dE_x_Ha": res["mixed"]["E_x"] - res["fp64"]["E_x"],
+        r64 = res["fp64"]
+        extra["fp64"] = {"ms": r64["ms"], "steps": r64["steps"], "warmup": r64["warmup"],
+                         "e2e_ms": r64["e2e_ms"], "E_x": r64["E_x"],
+                         "stage_ms": {k: round(v, 4) for k, v in r64["stage_ms"].items()},
+                         "roofline": roofline("fp64", r64), "stage_rates": stage_rates("fp64", r64),
+                         "note": "timed over fewer steps than the mixed path" if r64["steps"] < args.steps else ""}
+        extra["mixed_vs_fp64"] = {"dE_x_Ha": res["mixed"]["E_x"] - r64["E_x"],
                                   "K_rel_fro": float(torch.linalg.norm(Km - K64) / torch.linalg.norm(K64)),
-                                  "speedup": res["fp64"]["ms"] / res["mixed"]["ms"]}
+                                  "speedup": r64["ms"] / res["mixed"]["ms"]}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rows = sample_rows(s)
-        dt, sf, ff, thr = oracle_sample(s, pk, rows)
-        cpu = {"value": dt * ff / sf * 1e3, "unit": "ms", "cores": thr, "kind": "oracle",
-               "sample": f"rows {rows} of {s.n_atoms} ({sf:.3g} of {ff:.3g} FLOP, {dt:.1f} s), "
-                         f"scaled to a full build by the oracle's own FLOP ratio"}
+        cpu = cpu_baseline(s, pk)
     if rank == 0:
         stats = r["stats"]
         line = {
@@ -414,17 +487,16 @@ def run_rix(args):
             "config": {"workload": WORKLOAD_NAMES[args.config], "precision": head,
                        "n_slices": args.slices if head == "mixed" else None,
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}",
-                       "timing": "CUDA graph replay" if args.graph else "eager launches",
+                       "timing": "CUDA graph replay" if r["graph"] else "eager launches",
                        "autotuned_tiles_x12_z_x34": r["tiles"]},
             "e2e": {"value": r["e2e_ms"], "unit": "ms", "h2d_bytes_per_step": r["h2d"],
-                    "d2h_bytes_per_step": r["d2h"]},
+                    "d2h_bytes_per_step": r["d2h"], "steps": r["e2e_steps"]},
             "gpu_launches": r["launches"] * args.steps,
             "clocks": r["clocks"],
             "roofline": roof,
-            "roofline_tensor_stage": roof_tc,
             "cpu_baseline": cpu,
             "stage_ms": {k: round(v, 4) for k, v in r["stage_ms"].items()},
-            "stage_roofline": stage_roofline(head, r),
+            "stage_rates": stage_rates(head, r),
             "alg_flops": stats["flops_fp64"],
             "alg_flops_unscreened": stats["flops_fp64_unscreened"],
             "alg_tflops": stats["flops_fp64"] / (r["ms"] * 1e-3) / 1e12,
@@ -441,12 +513,15 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--config", type=int, default=4,
+                    help="workload 0-4 (default 4: the largest single-GPU one, the 3,072-atom ice supercell)")
     ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
     ap.add_argument("--impl", default="rix", choices=["rix", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--graph", type=int, default=1, help="1: time CUDA graph replays of one step (default)")
-    ap.add_argument("--autotune", type=int, default=1, help="1: rix_autotune before the warm-up (default)")
+    ap.add_argument("--graph", type=int, default=-1,
+                    help="1: time CUDA graph replays of one step; 0: eager launches (with per-GEMM events); "
+                         "-1 (default): replays for the small workloads, eager for the 1,000+ atom ones")
+    ap.add_argument("--autotune", type=int, default=1, help="1: rix_autotune of the FP64 path (default)")
     ap.add_argument("--slices", type=int, default=5,
                     help="mixed path: BF16 slices per operand (the regrouped plans take one more); 3 = the "
                          "three-term split")

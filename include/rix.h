@@ -100,7 +100,9 @@ typedef struct {
   int64_t max_workspace_bytes;     /* 0 = no limit beyond the device's free memory */
   int32_t verbose;                 /* 0 = silent */
   int32_t profile;                 /* 1 = record a CUDA event after every stage of rix_build_K
-                                      (skipped while the stream is being captured into a graph) */
+                                      (skipped while the stream is being captured into a graph);
+                                      2 = also an event pair around every sliced-GEMM launch
+                                      (rix_gemm_profile) */
   int32_t backward;                /* 1 = also plan rix_backward (extra product lists) */
   int32_t block_atoms;             /* > 0: row blocks of at most this many atoms (the paper's manual
                                       Fock-matrix block size); 0 = blocks only where memory requires */
@@ -323,6 +325,16 @@ rix_status rix_count_flops(rix_ctx *ctx, const double *D_dev, double *flops, voi
  * (the events are recorded on the build's stream); synchronises on the last
  * recorded event.  EUNSUPPORTED without profiling. */
 rix_status rix_stage_times(rix_ctx *ctx, double *ms, int32_t n, int32_t *n_builds);
+/* Per-kernel measurement of the tensor-core GEMM (needs rix_options.profile = 2
+ * and mixed precision): device time of every k_gemm_sliced launch enqueued
+ * since the previous call, from the event pairs around each launch (none are
+ * recorded while a stream is being captured), summed into *ms; *launches the
+ * number of launches; *chunks the K stages they issued (one output tile of
+ * 128 x 80 by 32 K values) times the slice pairs per stage, so that the BF16
+ * FLOPs issued are *chunks x 2 x 128 x 80 x 32.  Synchronises on the last event; resets the
+ * counts.  EUNSUPPORTED otherwise. */
+rix_status rix_gemm_profile(rix_ctx *ctx, double *ms, int64_t *launches, int64_t *chunks);
+
 const char *rix_strerror(rix_status s);
 const char *rix_last_error(const rix_ctx *ctx);
 void rix_destroy(rix_ctx *ctx);

@@ -54,6 +54,7 @@ def _load():
             lib.orc_energy.argtypes = [P, P, P]
             lib.orc_destroy.argtypes = [P]
             lib.orc_threads.restype = ctypes.c_int
+            lib.orc_set_threads.argtypes = [ctypes.c_int]
             lib.orc_set_terms.argtypes = [P, ctypes.c_int]
             lib.orc_build_K_ex.restype = ctypes.c_int
             lib.orc_build_K_ex.argtypes = [P, P, ctypes.c_int]
@@ -97,6 +98,11 @@ class Oracle:
     @staticmethod
     def threads():
         return _load().orc_threads()
+
+    @staticmethod
+    def set_threads(n):
+        """Threads of the row loops (0: every processor)."""
+        _load().orc_set_threads(int(n))
 
     def set_terms(self, mask):
         """Restrict the sum to a subset of the four terms (bit t-1 = term t)."""

@@ -795,3 +795,13 @@ int orc_threads(void) {
     return 1;
 #endif
 }
+
+/* Thread count of the OpenMP loops over rows (n <= 0: every processor); the
+ * arithmetic of each row does not depend on it. */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+#else
+    (void)n;
+#endif
+}

@@ -144,6 +144,9 @@ struct rix_ctx {
   int *h_err = nullptr, *d_err = nullptr;
   double *noalloc_scratch = nullptr;            // device address of rix_energy_noalloc's fixed array
   std::vector<int64_t> offU_h;                  // U2 offsets per pair (host copy)
+  // rix_options.profile >= 2: an event pair around every sliced-GEMM launch, and its K stages
+  std::vector<cudaEvent_t> gemm_ev, gemm_ev_pool;
+  unsigned long long *d_gemm_chunks = nullptr;
 
   // memory plan: row blocks of consecutive atoms; item segments per block
   int32_t nblk = 1;

@@ -1114,6 +1114,8 @@ extern "C" void rix_destroy(rix_ctx *ctx) {
   rix_mixed_free(ctx);
   for (auto e : ctx->ev_pending) cudaEventDestroy(e);
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  for (auto e : ctx->gemm_ev) cudaEventDestroy(e);
+  for (auto e : ctx->gemm_ev_pool) cudaEventDestroy(e);
   for (auto &b : ctx->bufs) cudaFree(b.p);
   if (ctx->h_err) cudaFreeHost(ctx->h_err);
   delete ctx;

@@ -460,6 +460,7 @@ struct GemmArgs {
   int64_t xshift;          // mode 0: X + offK[x] - xshift is the output block
   int ntiles;              // output tiles of the launch (persistent CTAs loop over them)
   const uint8_t *row_live = nullptr;  // batched mode: per row tile (tiles[t].w), 0 = all its rows are zero
+  unsigned long long *chunks = nullptr;  // profiling: K stages (tile x 32 K) issued times slice pairs, all CTAs
   uint64_t wait_ns = WAIT_NS;  // limit of every bounded wait
   int stall = 0;           // 1: the MMA issuer waits on a barrier nothing completes (timeout test)
 };
@@ -591,6 +592,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
       if (*(volatile int *)abort_flag) aborted = true;
     }
     issued_chunks = cg;
+    if (g.chunks && cg) atomicAdd(g.chunks, (unsigned long long)cg * (unsigned long long)(S * (S + 1) / 2));
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------ MMA issuer
     const uint32_t idesc = idesc_bf16(TM, TN);
@@ -1476,6 +1478,8 @@ rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
   }
   if ((s = rix_dev_alloc(ctx, (void **)&ctx->d_mx_buf, std::max<int64_t>(buf, 16))) != RIX_OK) return s;
   ctx->d_mx_err = ctx->d_err;
+  if ((s = rix_alloc(ctx, &ctx->d_gemm_chunks, 1)) != RIX_OK) return s;
+  RIX_CUDA_TRY(ctx, cudaMemset(ctx->d_gemm_chunks, 0, sizeof(unsigned long long)));
   ctx->mx_buf_bytes = buf;
   ctx->stats.tensor_flops = tflops;
   ctx->have_mx = true;
@@ -1509,6 +1513,8 @@ void rix_mixed_free(rix_ctx *ctx) {
 }
 
 namespace {
+
+rix_status launch_gemm(rix_ctx *ctx, GemmArgs ga, int64_t ntiles, int S, cudaStream_t st);
 
 struct Operand {
   const double *x;
@@ -1545,12 +1551,45 @@ rix_status run_group(rix_ctx *ctx, const rix_mx_plan *pl, size_t g, const Operan
     ga.xshift = oshift;
     ga.ntiles = (int)(t1 - t0);
     ga.row_live = pl->d_rtlive;  // kind 2: skip row tiles of screened (V, D) blocks
-    k_gemm_sliced<<<persistent_grid(t1 - t0), NTHR, smem_bytes(S), st>>>(ga);
+    rix_status ls = launch_gemm(ctx, ga, t1 - t0, S, st);
+    if (ls != RIX_OK) return ls;
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     ctx->last_error = std::string("mixed GEMM: ") + cudaGetErrorString(e);
     return RIX_ECUDA;
+  }
+  return RIX_OK;
+}
+
+// One batched GEMM launch of the build; with rix_options.profile >= 2 (and the
+// stream not capturing) it is bracketed by a pair of events and counts its K
+// stages, for the per-kernel roofline (rix_gemm_profile).
+rix_status launch_gemm(rix_ctx *ctx, GemmArgs ga, int64_t ntiles, int S, cudaStream_t st) {
+  bool prof = ctx->opt.profile >= 2;
+  if (prof) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (st != nullptr && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+      prof = false;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (prof) {
+    for (cudaEvent_t *e : {&e0, &e1}) {
+      if (!ctx->gemm_ev_pool.empty()) {
+        *e = ctx->gemm_ev_pool.back();
+        ctx->gemm_ev_pool.pop_back();
+      } else {
+        RIX_CUDA_TRY(ctx, cudaEventCreate(e));
+      }
+    }
+    ga.chunks = (unsigned long long *)ctx->d_gemm_chunks;
+    RIX_CUDA_TRY(ctx, cudaEventRecord(e0, st));
+  }
+  k_gemm_sliced<<<persistent_grid(ntiles), NTHR, smem_bytes(S), st>>>(ga);
+  if (prof) {
+    RIX_CUDA_TRY(ctx, cudaEventRecord(e1, st));
+    ctx->gemm_ev.push_back(e0);
+    ctx->gemm_ev.push_back(e1);
   }
   return RIX_OK;
 }
@@ -1996,7 +2035,8 @@ rix_status rix_mixed_t1(rix_ctx *ctx, int b, int64_t tbase, cudaStream_t st) {
                   pl->d_tiles + t0, pl->d_probs, pl->d_rowinfo, pl->d_colinfo, nullptr, ctx->d_offK, ctx->d_X,
                   1, pl->d_qinfo, ctx->d_V, ctx->d_keepV, 0.5};
       ga.ntiles = (int)(t1 - t0);
-      k_gemm_sliced<<<persistent_grid(t1 - t0), NTHR, smem_bytes(S), st>>>(ga);
+      rix_status ls = launch_gemm(ctx, ga, t1 - t0, S, st);
+      if (ls != RIX_OK) return ls;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -2345,7 +2385,8 @@ rix_status rix_mixed_T(rix_ctx *ctx, int b, int64_t tbase, const double *D, cuda
       ga.oscale = 1.0;
       ga.xshift = tbase;
       ga.ntiles = (int)(t1 - t0);
-      k_gemm_sliced<<<persistent_grid(t1 - t0), NTHR, smem_bytes(S), st>>>(ga);
+      rix_status ls = launch_gemm(ctx, ga, t1 - t0, S, st);
+      if (ls != RIX_OK) return ls;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -2358,4 +2399,24 @@ rix_status rix_mixed_T(rix_ctx *ctx, int b, int64_t tbase, const double *D, cuda
 
 int32_t rix_tt_launches(const rix_ctx *ctx) {
   return ctx->mxt ? 5 * (int32_t)(ctx->mxt->grp_prob.size() - 1) : 0;
+}
+
+extern "C" rix_status rix_gemm_profile(rix_ctx *ctx, double *ms, int64_t *launches, int64_t *chunks) {
+  if (!ctx || !ms || !launches || !chunks) return RIX_EINVAL;
+  if (ctx->opt.profile < 2 || !ctx->have_mx) return RIX_EUNSUPPORTED;
+  *ms = 0.0;
+  *launches = (int64_t)ctx->gemm_ev.size() / 2;
+  if (!ctx->gemm_ev.empty()) RIX_CUDA_TRY(ctx, cudaEventSynchronize(ctx->gemm_ev.back()));
+  for (size_t i = 0; i + 1 < ctx->gemm_ev.size(); i += 2) {
+    float t = 0.f;
+    RIX_CUDA_TRY(ctx, cudaEventElapsedTime(&t, ctx->gemm_ev[i], ctx->gemm_ev[i + 1]));
+    *ms += t;
+  }
+  for (auto e : ctx->gemm_ev) ctx->gemm_ev_pool.push_back(e);
+  ctx->gemm_ev.clear();
+  unsigned long long c = 0;
+  RIX_CUDA_TRY(ctx, cudaMemcpy(&c, ctx->d_gemm_chunks, sizeof c, cudaMemcpyDeviceToHost));
+  RIX_CUDA_TRY(ctx, cudaMemset(ctx->d_gemm_chunks, 0, sizeof c));
+  *chunks = (int64_t)c;
+  return RIX_OK;
 }

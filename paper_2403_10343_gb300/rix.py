@@ -84,6 +84,8 @@ def load():
     lib.rix_check.argtypes = [P, P]
     lib.rix_build_K_delta.argtypes = [P, P, P, P]
     lib.rix_force_stress.argtypes = [P, ctypes.c_int32, P, P, P, P, P, P, P]
+    lib.rix_gemm_profile.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                                     ctypes.POINTER(ctypes.c_int64)]
     lib.rix_bloch.argtypes = [P, P, ctypes.c_int32, P, P, P]
     lib.rix_build_K_spin.argtypes = [P, ctypes.c_int32, P, P, P]
     lib.rix_energy_spin.argtypes = [P, ctypes.c_int32, P, P, P, P]
@@ -97,7 +99,8 @@ def load():
               "rix_energy_noalloc",
               "rix_backward", "rix_fold_gamma", "rix_stats", "rix_stage_times", "rix_gemm_sliced",
               "rix_autotune", "rix_count_flops", "rix_check", "rix_test_stalled_gemm", "rix_bloch",
-              "rix_build_K_spin", "rix_energy_spin", "rix_build_K_delta", "rix_force_stress"):
+              "rix_build_K_spin", "rix_energy_spin", "rix_build_K_delta", "rix_force_stress",
+              "rix_gemm_profile"):
         getattr(lib, f).restype = I
     _lib = lib
     return lib
@@ -352,6 +355,13 @@ def stage_times(ctx):
     return dict(zip(STAGES, list(ms))), nb.value
 
 
+def gemm_profile(ctx):
+    """rix_gemm_profile: (summed ms, launches, K stages) of the sliced-GEMM launches since the last call."""
+    ms, n, ch = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load().rix_gemm_profile(ctx, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(ch)), ctx)
+    return ms.value, n.value, ch.value
+
+
 def destroy(ctx):
     if ctx:
         load().rix_destroy(ctx)
@@ -430,6 +440,9 @@ class Exchange:
 
     def stage_times(self):
         return stage_times(self.ctx)
+
+    def gemm_profile(self):
+        return gemm_profile(self.ctx)
 
     def close(self):
         if getattr(self, "ctx", None):

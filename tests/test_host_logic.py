@@ -80,13 +80,22 @@ def test_stage_split_between_pipes():
 
 def test_roofline_picks_the_longest_stage():
     r = {"stats": STATS, "stage_ms": {"T": 1.0, "U2": 0.5, "X12": 10.0, "Z": 4.0, "X34": 2.0}}
-    roof, _ = bench.roofline(None, "fp64", r)
+    roof = bench.roofline("fp64", r)
     assert roof["kernel"] == "k_X12" and roof["bound"] == "alu"
     assert abs(roof["achieved"] - 40.0 / 1e-2 / 1e12) < 1e-18
     assert abs(roof["frac"] - roof["achieved"] / roof["peak"]) < 1e-18
-    # mixed: the tensor-core stages together take longer than any FP64 stage
-    r = {"stats": STATS, "stage_ms": {"T": 1.0, "U2": 0.5, "X12": 0.1, "TC12": 5.0, "Z": 4.0, "X34": 2.0}}
-    roof, tc = bench.roofline(None, "mixed", r)
-    assert roof is tc and roof["bound"] == "tensor"
-    ms = 1.0 + 5.0 + 4.0 + 2.0
-    assert abs(roof["achieved"] - STATS["tensor_flops"] / (ms * 1e-3) / 1e12) < 1e-12
+
+
+def test_tensor_roofline_uses_algorithmic_flops_over_kernel_time():
+    # mixed: k_gemm_sliced, algorithmic FLOPs of the tensor-core work over its launch time
+    gemm = {"ms_per_build": 2.0, "launches_per_build": 4.0, "stage_pairs_per_build": 1000.0}
+    r = {"stats": STATS, "stage_ms": {"TC12": 5.0}, "gemm": gemm}
+    roof = bench.roofline("mixed", r)
+    alg = 10.0 + 30.0 + 6.0 + 20.0 + 8.0          # T, term 1, term 2, Z on the tensor cores + terms 3+4
+    assert bench.tensor_alg_flops(STATS) == alg
+    assert roof["kernel"] == "k_gemm_sliced" and roof["bound"] == "tensor"
+    assert abs(roof["achieved"] - alg / 2e-3 / 1e12) < 1e-24
+    assert abs(roof["frac"] - roof["achieved"] / roof["peak"]) < 1e-24
+    issued = 1000.0 * 2 * 128 * 80 * 32
+    assert roof["issued_bf16_flops_per_build"] == issued
+    assert abs(roof["issued_tflops"] - issued / 2e-3 / 1e12) < 1e-9
