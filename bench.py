@@ -274,7 +274,7 @@ def measure(args, s, pk, precision, dev, world, steps, warmup, graph, e2e_steps)
     cap = 0
     if s.n_atoms > 1000:
         cap = int(torch.cuda.mem_get_info(dev)[0] - (24 << 30))
-    kw = {"n_slices": args.slices} if precision == "mixed" else {}
+    kw = {"n_slices": args.slices, "n_slices_regrouped": args.slices_regrouped} if precision == "mixed" else {}
     prof = 2 if (precision == "mixed" and not graph) else 1
     ex = Exchange.from_system(s, precision=precision, profile=prof, max_workspace_bytes=cap, verbose=args.verbose,
                               **kw)
@@ -486,6 +486,7 @@ def run_rix(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD_NAMES[args.config], "precision": head,
                        "n_slices": args.slices if head == "mixed" else None,
+                       "n_slices_regrouped": (args.slices_regrouped or args.slices + 1) if head == "mixed" else None,
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}",
                        "timing": "CUDA graph replay" if r["graph"] else "eager launches",
                        "autotuned_tiles_x12_z_x34": r["tiles"]},
@@ -525,6 +526,8 @@ def main():
     ap.add_argument("--slices", type=int, default=5,
                     help="mixed path: BF16 slices per operand (the regrouped plans take one more); 3 = the "
                          "three-term split")
+    ap.add_argument("--slices-regrouped", type=int, default=0,
+                    help="mixed path: slices of the regrouped plans (term 1, Z, T); 0 = --slices + 1")
     ap.add_argument("--verbose", type=int, default=0, help="1: the library prints its plan to stderr")
     args = ap.parse_args()
     if args.impl == "reference":

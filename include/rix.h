@@ -106,6 +106,8 @@ typedef struct {
   int32_t backward;                /* 1 = also plan rix_backward (extra product lists) */
   int32_t block_atoms;             /* > 0: row blocks of at most this many atoms (the paper's manual
                                       Fock-matrix block size); 0 = blocks only where memory requires */
+  int32_t n_slices_regrouped;      /* mixed mode: slices of the regrouped plans (term 1 as T x C, the
+                                      term-4 intermediate, T), 1..8; 0 = n_slices + 1 */
 } rix_options;
 
 typedef struct {

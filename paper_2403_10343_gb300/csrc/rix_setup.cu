@@ -815,6 +815,8 @@ extern "C" rix_status rix_setup(const rix_system *sys, const rix_options *opt, r
   for (int i = 0; i < 3 * sys->n_atoms; i++)
     if (!std::isfinite(sys->xyz_bohr[i])) return RIX_EINVAL;
   if (opt && opt->precision != RIX_FP64 && opt->precision != RIX_MIXED_BF16) return RIX_EINVAL;
+  if (opt && (opt->n_slices < 0 || opt->n_slices > 8 || opt->n_slices_regrouped < 0 || opt->n_slices_regrouped > 8))
+    return RIX_EINVAL;
 
   rix_ctx *ctx = new rix_ctx();
   if (opt) ctx->opt = *opt;

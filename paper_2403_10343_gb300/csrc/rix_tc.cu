@@ -1107,7 +1107,9 @@ struct PlanHost {
 // grouping, and T feeds every term, so these take one slice more than the
 // GEMMs of terms 2-4 (capped at 8).
 int rix_plan_slices(const rix_ctx *ctx, int kind) {
-  return kind >= 2 ? std::min(ctx->mx_S + 1, (int)rixtc::MAXS) : ctx->mx_S;
+  if (kind < 2) return ctx->mx_S;
+  const int r = ctx->opt.n_slices_regrouped;
+  return r > 0 ? std::min(r, (int)rixtc::MAXS) : std::min(ctx->mx_S + 1, (int)rixtc::MAXS);
 }
 
 namespace {

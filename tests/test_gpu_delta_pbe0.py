@@ -45,9 +45,9 @@ def _rel(a, b):
 def test_delta_build_equals_full_build(prec):
     s = ri.config(0)
     pk = ri.generate(s)
-    Du, _ = pk.gen_D_spin()
+    _, Dd = pk.gen_D_spin()
     D2 = pk.D
-    D1 = 0.9 * D2 + 0.1 * Du
+    D1 = 0.9 * D2 + 0.2 * Dd                           # not proportional to D2
     kk, K_ref, E_ref = _oracle_K(s, pk, D2)
     ex = rix.Exchange.from_system(s, precision=prec)
     ex.set_CV(_dev(pk.C), _dev(pk.V))
@@ -64,7 +64,7 @@ def test_delta_build_equals_full_build(prec):
 def test_delta_build_with_screening_skips_blocks():
     s = ri.config(1)                                   # 8 A cutoff, tau = 1e-10
     pk = ri.generate(s)
-    Du, _ = pk.gen_D_spin()
+    _, Dd = pk.gen_D_spin()
     # density change on the pairs touching the first water; elsewhere below tau
     near = np.isin(pk.A, [0, 1, 2]) | np.isin(pk.B, [0, 1, 2])
     dD = np.zeros_like(pk.D)
@@ -72,7 +72,7 @@ def test_delta_build_with_screening_skips_blocks():
     for p in range(pk.n_pairs):
         sl = slice(pk.offD[p], pk.offD[p + 1])
         if near[p]:
-            dD[sl] = 1e-2 * (Du[sl] - 0.5 * pk.D[sl])
+            dD[sl] = 1e-2 * (Dd[sl] - 0.5 * pk.D[sl])     # one orbital of every five emptied
         else:
             tiny[sl] = 1e-12 * np.sign(pk.D[sl])       # |x| < tau: screened out by both sides
     dD = dD + tiny
@@ -100,6 +100,7 @@ def test_delta_build_with_screening_skips_blocks():
     sel = np.nonzero(np.isin(A, rows))[0]
     sub = np.concatenate([got[off[x]:off[x + 1]] for x in sel])
     assert np.array_equal(keys[sel], kr)
+    assert np.linalg.norm(Kr) > 0
     err = _rel(sub, Kr)
     print(f"delta build with screening: rows vs oracle K(dD) {err:.2e}; FLOPs {f_delta:.3e} of {f_full:.3e}")
     # K - K1 subtracts two numbers of K's size: its error is relative to K, not to K(dD)

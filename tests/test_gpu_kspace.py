@@ -55,7 +55,8 @@ def test_bloch_sums(case, prec):
     err = np.abs(got - ref).max() / scale
     print(f"{case} {prec}: Bloch sums max error {err:.2e} of the largest element")
     assert err < TOL[prec][0]
-    assert np.array_equal(got[0].real, Kg.cpu().numpy()) and not got[0].imag.any()
+    # (the fold and the Bloch kernel sum a pair's images in different orders)
+    assert np.abs(got[0].real - Kg.cpu().numpy()).max() < 1e-15 * scale and not got[0].imag.any()
     ex.close()
 
 
