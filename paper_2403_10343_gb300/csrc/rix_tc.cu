@@ -460,6 +460,9 @@ struct GemmArgs {
   int64_t xshift;          // mode 0: X + offK[x] - xshift is the output block
   int ntiles;              // output tiles of the launch (persistent CTAs loop over them)
   const uint8_t *row_live = nullptr;  // batched mode: per row tile (tiles[t].w), 0 = all its rows are zero
+  // batched mode: per (problem, column tile) a bit mask of the K stages whose B tile is not all
+  // zero, (Kpad / 32 + 63) / 64 words at kmask + tiles[t].w; stages without a bit are skipped
+  const unsigned long long *kmask = nullptr;
   unsigned long long *chunks = nullptr;  // profiling: K stages (tile x 32 K) issued times slice pairs, all CTAs
   uint64_t wait_ns = WAIT_NS;  // limit of every bounded wait
   int stall = 0;           // 1: the MMA issuer waits on a barrier nothing completes (timeout test)
@@ -482,7 +485,13 @@ struct TileInfo {
   const int *geA, *geB;
   int mt, nt, Mpad, Npad, Kpad, M, N, drop;
   bool live;  // false: the tile's A rows are all zero (screened), every role skips it
+  const unsigned long long *km;  // live K stages (nullptr: all)
+  int nlive;                      // number of live K stages
 };
+
+__device__ __forceinline__ bool stage_live(const TileInfo &ti, int c) {
+  return !ti.km || ((ti.km[c >> 6] >> (c & 63)) & 1ull);
+}
 
 __device__ __forceinline__ TileInfo tile_info(const GemmArgs &g, int t) {
   TileInfo ti;
@@ -498,6 +507,15 @@ __device__ __forceinline__ TileInfo tile_info(const GemmArgs &g, int t) {
     ti.geB = g.eB + pr->eboff;
     ti.Mpad = pr->Mpad; ti.Npad = pr->Npad; ti.Kpad = pr->Kpad; ti.M = pr->M; ti.N = pr->N; ti.drop = pr->drop;
     ti.live = !g.row_live || g.row_live[tt.w];
+    ti.km = nullptr;
+    ti.nlive = ti.Kpad / KC;
+    if (g.kmask) {
+      ti.km = g.kmask + tt.w;
+      int n = 0;
+      for (int w = 0; w < (ti.nlive + 63) / 64; w++) n += __popcll(ti.km[w]);
+      ti.nlive = n;
+      ti.live = n > 0;
+    }
   } else {
     const int mtiles = g.Mpad / TM;
     ti.pr = nullptr;
@@ -506,6 +524,8 @@ __device__ __forceinline__ TileInfo tile_info(const GemmArgs &g, int t) {
     ti.gA = g.A; ti.gB = g.B; ti.geA = g.eA; ti.geB = g.eB;
     ti.Mpad = g.Mpad; ti.Npad = g.Npad; ti.Kpad = g.Kpad; ti.M = g.M; ti.N = g.N; ti.drop = g.drop;
     ti.live = true;
+    ti.km = nullptr;
+    ti.nlive = ti.Kpad / KC;
   }
   return ti;
 }
@@ -568,7 +588,8 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
       const int nk = ti.Kpad / KC;
       const int64_t a_tiles = (int64_t)(ti.Mpad / TM) * nk;  // tiles per A plane
       const int64_t b_tiles = (int64_t)(ti.Npad / TN) * nk;
-      for (int c = 0; c < nk; c++, cg++) {
+      for (int c = 0; c < nk; c++) {
+        if (!stage_live(ti, c)) continue;  // an all-zero B tile: neither copied nor multiplied
         const int st = cg % nst;
         if (cg >= (uint32_t)nst && !mbar_wait(&empty[st], ((cg / nst) - 1) & 1, g.wait_ns)) {
           atomicExch(abort_flag, 1);
@@ -588,6 +609,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
           const char *gb = (const char *)ti.gB + ((int64_t)s * b_tiles + (int64_t)ti.nt * nk + c) * B_TILE;
           bulk_g2s(sb + s * B_TILE, gb, B_TILE, &full[st]);
         }
+        cg++;
       }
       if (*(volatile int *)abort_flag) aborted = true;
     }
@@ -603,9 +625,11 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
       const TileInfo ti = tile_info(g, t);
       if (!ti.live) continue;
       const int nk = ti.Kpad / KC;
-      for (int c = 0; c < nk; c++, cg++) {
+      int lc = 0;  // live K stages issued for this tile
+      for (int c = 0; c < nk; c++) {
+        if (!stage_live(ti, c)) continue;
         const int st = cg % nst;
-        if (c % GROUP == 0 && gg > 0 && !mbar_wait(accempty, (gg - 1) & 1, g.wait_ns)) {
+        if (lc % GROUP == 0 && gg > 0 && !mbar_wait(accempty, (gg - 1) & 1, g.wait_ns)) {
           atomicExch(abort_flag, 1);
           break;
         }
@@ -618,14 +642,16 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
         const uint32_t sa = smem_u32(smem + st * stage_bytes);
         const uint32_t sb = sa + S * A_TILE;
         // K step kk covers core-matrix columns 2kk, 2kk+1 (LBO = 128 B apart)
-        const uint32_t open = c % GROUP == 0 ? 0xFFu : 0u;  // every accumulator starts a group
+        const uint32_t open = lc % GROUP == 0 ? 0xFFu : 0u;  // every accumulator starts a group
         issue_stage_s(S, tmem, sdesc(sa, 128, (KC / 8) * 128), sdesc(sb, 128, (KC / 8) * 128), idesc, open);
         issued = true;
         mma_commit(&empty[st]);
-        if (c % GROUP == GROUP - 1 || c == nk - 1) {
+        if (lc % GROUP == GROUP - 1 || lc == ti.nlive - 1) {
           mma_commit(accfull);
           gg++;
         }
+        lc++;
+        cg++;
       }
       if (*(volatile int *)abort_flag) break;
     }
@@ -645,8 +671,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       const TileInfo ti = tile_info(g, t);
       if (!ti.live) continue;  // its output is zero: nothing to drain or add
-      const int nk = ti.Kpad / KC;
-      const int ngroups = (nk + GROUP - 1) / GROUP;
+      const int ngroups = (ti.nlive + GROUP - 1) / GROUP;  // accumulation groups of live K stages
       const int mt = ti.mt, nt = ti.nt, drop = ti.drop, Ncols = ti.N;
       const Prob *pr = ti.pr;
       const int *geA = ti.geA, *geB = ti.geB;
@@ -2155,6 +2180,30 @@ struct TTColAcc {
   }
 };
 
+// K-stage masks of the T plan: for every product (C(A,B'), D(B',G')) of a T block with kept
+// blocks, the stages covering B' in problem A and the column tiles covering G' get their bit.
+// One warp per T block.
+__global__ void k_tt_mask(int64_t n2, const int64_t *ptrT, const int2 *LT, const int32_t *pB, const int32_t *atomB2,
+                          const int32_t *nb, const uint8_t *keepC, const uint8_t *keepD, const int32_t *kpos1,
+                          const int2 *tmask, const int32_t *tmw, unsigned long long *mask) {
+  const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= n2) return;
+  const int2 tm = tmask[t];
+  if (tm.y < 0) return;
+  const int W = tmw[t];
+  const int nt0 = tm.x / TN, nt1 = (tm.x + nb[atomB2[t]] - 1) / TN;
+  for (int64_t e = ptrT[t] + lane; e < ptrT[t + 1]; e += 32) {
+    const int2 en = LT[e];
+    if (!keepC[en.x] || !keepD[en.y]) continue;
+    const int k0 = kpos1[en.x];
+    const int c0 = k0 / KC, c1 = (k0 + nb[pB[en.x]] - 1) / KC;
+    for (int nt = nt0; nt <= nt1; nt++)
+      for (int c = c0; c <= c1; c++)
+        atomicOr(mask + tm.y + (int64_t)nt * W + (c >> 6), 1ull << (c & 63));
+  }
+}
+
 __global__ void k_skip_flags(int n, const int32_t *idx, uint8_t *flags) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) flags[idx[t]] = 1;
@@ -2174,6 +2223,13 @@ struct rix_tt_plan {
   int64_t *d_rowprob = nullptr, *d_colprob = nullptr;
   int32_t *d_xmap = nullptr;
   int *d_eA = nullptr, *d_eB = nullptr;
+  // K-stage masks: per (problem, column tile) the stages whose D tile is not all zero,
+  // set per build from the D screening flags (most (B', G') are not D pairs or are screened)
+  int64_t n_mask = 0;
+  unsigned long long *d_mask = nullptr;
+  int32_t *d_kpos1 = nullptr;   // per pair (A, B'): K offset of B' in problem A (-1: A not here)
+  int2 *d_tmask = nullptr;      // per T block (A, G'): (column offset in problem A, mask base), -1 if none
+  int32_t *d_tmw = nullptr;     // per T block: mask words per column tile of its problem
 };
 
 // T plan: decide per row atom, build one problem per chosen atom (its block is the atom's).
@@ -2214,6 +2270,14 @@ rix_status rix_tt_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
   std::vector<int4> colinfo, tiles, kmap;
   std::vector<int64_t> rowprob, colprob, pbytes;
   std::vector<int32_t> xmap, pblk;
+  std::vector<int32_t> kpos1, tmw;
+  std::vector<int2> tmask;
+  if (!count_only) {
+    kpos1.assign(ctx->np, -1);
+    tmask.assign(ctx->n2, make_int2(-1, -1));
+    tmw.assign(ctx->n2, 0);
+  }
+  int64_t n_mask = 0;
   int64_t eaoff = 0, eboff = 0, maps = 0, maxp = 0, total = 0;
   double tflops = 0;
   for (int a = 0; a < nat; a++) {
@@ -2229,8 +2293,10 @@ rix_status rix_tt_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
     const int64_t bytes = (int64_t)S * (Mpad + Npad) * Kpad * 2;
     total += bytes;
     maxp = std::max(maxp, bytes);
+    const int mwords = (Kpad / KC + 63) / 64;
     maps += (int64_t)Mpad * (8 + 8 + 4) + (int64_t)Npad * (16 + 8 + 4) + (int64_t)Kpad * 16 + (int64_t)nz * 4 +
-            (int64_t)(Mpad / TM) * (Npad / TN) * 16 + (int64_t)(sizeof(Prob) + sizeof(TTExt));
+            (int64_t)(Mpad / TM) * (Npad / TN) * 16 + (int64_t)(sizeof(Prob) + sizeof(TTExt)) +
+            (int64_t)(Npad / TN) * mwords * 8 + (int64_t)(row1[a + 1] - row1[a]) * 4 + (int64_t)nz * 12;
     tflops += 2.0 * Mpad * Npad * Kpad * npairs;
     if (count_only) continue;
     const int pidx = (int)probs.size();
@@ -2245,6 +2311,21 @@ rix_status rix_tt_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
     eaoff += Mpad;
     eboff += Npad;
     ext.push_back(TTExt{(int64_t)kmap.size(), row1[a], nbA, 0});
+    const int64_t mbase = n_mask;
+    n_mask += (int64_t)(Npad / TN) * mwords;
+    {
+      int kp = 0;
+      for (int64_t p1 = row1[a]; p1 < row1[a + 1]; p1++) {
+        kpos1[p1] = kp;
+        kp += ctx->nb_at[ctx->pB[p1]];
+      }
+      int np2 = 0;
+      for (int64_t t = row2[a]; t < row2[a + 1]; t++) {
+        tmask[t] = make_int2(np2, (int)mbase);
+        tmw[t] = mwords;
+        np2 += ctx->nb_at[rix::key_b(ctx->keys2[t])];
+      }
+    }
     for (int64_t p1 = row1[a]; p1 < row1[a + 1]; p1++) {
       const int nbB = ctx->nb_at[ctx->pB[p1]];
       for (int j = 0; j < nbB; j++) kmap.push_back(make_int4((int)(p1 - row1[a]), j, nbB, 0));
@@ -2271,7 +2352,7 @@ rix_status rix_tt_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
       colprob.push_back(pidx);
     }
     for (int mt = 0; mt < Mpad / TM; mt++)
-      for (int nt = 0; nt < Npad / TN; nt++) tiles.push_back(make_int4(pidx, mt, nt, 0));
+      for (int nt = 0; nt < Npad / TN; nt++) tiles.push_back(make_int4(pidx, mt, nt, (int)(mbase + nt * mwords)));
     probs.push_back(pr);
     pbytes.push_back(bytes);
     pblk.push_back(blk_of[a]);
@@ -2327,6 +2408,13 @@ rix_status rix_tt_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
   if ((s = rix_upload(ctx, &pl->d_rowprob, rowprob)) != RIX_OK) return s;
   if ((s = rix_upload(ctx, &pl->d_colprob, colprob)) != RIX_OK) return s;
   if ((s = rix_upload(ctx, &pl->d_xmap, xmap)) != RIX_OK) return s;
+  pl->n_mask = n_mask;
+  if (n_mask > 0) {
+    if ((s = rix_alloc(ctx, &pl->d_mask, n_mask)) != RIX_OK) return s;
+    if ((s = rix_upload(ctx, &pl->d_kpos1, kpos1)) != RIX_OK) return s;
+    if ((s = rix_upload(ctx, &pl->d_tmask, tmask)) != RIX_OK) return s;
+    if ((s = rix_upload(ctx, &pl->d_tmw, tmw)) != RIX_OK) return s;
+  }
   if ((s = rix_alloc(ctx, &pl->d_eA, std::max<int64_t>(eaoff, 1))) != RIX_OK) return s;
   if ((s = rix_alloc(ctx, &pl->d_eB, std::max<int64_t>(eboff, 1))) != RIX_OK) return s;
   std::vector<int32_t> on;
@@ -2363,6 +2451,13 @@ rix_status rix_mixed_T(rix_ctx *ctx, int b, int64_t tbase, const double *D, cuda
   gemm_attr();
   const int S = pl->S;
   __nv_bfloat16 *buf = (__nv_bfloat16 *)ctx->d_mx_buf;
+  if (b == 0 && pl->n_mask > 0) {
+    // which K stages of every column tile meet a kept D block (D changes every build)
+    RIX_CUDA_TRY(ctx, cudaMemsetAsync(pl->d_mask, 0, sizeof(unsigned long long) * pl->n_mask, st));
+    k_tt_mask<<<(unsigned)((ctx->n2 * 32 + 255) / 256), 256, 0, st>>>(
+        ctx->n2, ctx->d_ptrT, ctx->d_LT, ctx->d_pB, ctx->d_atomB2, ctx->d_nb, ctx->d_keepC, ctx->d_keepD,
+        pl->d_kpos1, pl->d_tmask, pl->d_tmw, pl->d_mask);
+  }
   for (size_t g = 0; g + 1 < pl->grp_prob.size(); g++) {
     if (pl->grp_blk[g] != b || pl->grp_prob[g + 1] == pl->grp_prob[g]) continue;
     const int64_t r0 = pl->row_seg[g], r1 = pl->row_seg[g + 1];
@@ -2387,6 +2482,7 @@ rix_status rix_mixed_T(rix_ctx *ctx, int b, int64_t tbase, const double *D, cuda
       ga.oscale = 1.0;
       ga.xshift = tbase;
       ga.ntiles = (int)(t1 - t0);
+      ga.kmask = pl->d_mask;  // skip the K stages whose D tile is all zero
       rix_status ls = launch_gemm(ctx, ga, t1 - t0, S, st);
       if (ls != RIX_OK) return ls;
     }
@@ -2400,7 +2496,7 @@ rix_status rix_mixed_T(rix_ctx *ctx, int b, int64_t tbase, const double *D, cuda
 }
 
 int32_t rix_tt_launches(const rix_ctx *ctx) {
-  return ctx->mxt ? 5 * (int32_t)(ctx->mxt->grp_prob.size() - 1) : 0;
+  return ctx->mxt ? 5 * (int32_t)(ctx->mxt->grp_prob.size() - 1) + (ctx->mxt->n_mask > 0 ? 1 : 0) : 0;
 }
 
 extern "C" rix_status rix_gemm_profile(rix_ctx *ctx, double *ms, int64_t *launches, int64_t *chunks) {
