@@ -21,7 +21,8 @@
  * A pair (A, B, n1, n2, n3) joins atom A in cell 0 to atom B in cell
  * n = n1 a1 + n2 a2 + n3 a3.  The pair list holds every pair with
  * |x_B + n - x_A| < cutoff (every pair at n = 0 when cutoff <= 0, cluster only),
- * sorted lexicographically by (A, B, n1, n2, n3), and is exactly symmetric:
+ * or the caller's list (rix_system.pairs), sorted lexicographically by
+ * (A, B, n1, n2, n3); the cutoff list is exactly symmetric:
  * the distance is evaluated in the orientation with A < B (or A == B and
  * n > 0 lexicographically) as dx_c = (x_B,c + s_c) - x_A,c with
  * s_c = (n1 a1_c + n2 a2_c) + n3 a3_c and d^2 = (dx_0^2 + dx_1^2) + dx_2^2,
@@ -91,6 +92,12 @@ typedef struct {
   const double *cell_bohr;         /* [3][3] rows = lattice vectors; NULL = cluster */
   double cutoff_bohr;              /* pair cutoff; <= 0 = all pairs (cluster only) */
   double screen_tau;               /* block screening threshold; <= 0 = none */
+  int64_t n_pairs;                 /* optional caller-supplied pair list (0 / NULL: built from the cutoff) */
+  const int32_t *pairs;            /* [n_pairs][5] = (A, B, n1, n2, n3), host, any order; it must be
+                                      symmetric (with every (A,B,n) also (B,A,-n)), free of duplicates,
+                                      with atoms in range, |n_c| <= 42 and n = 0 for a cluster (EINVAL
+                                      otherwise, before any device work); the cutoff then only names the
+                                      system, the list decides which blocks exist */
 } rix_system;
 
 typedef struct {

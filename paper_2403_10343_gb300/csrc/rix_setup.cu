@@ -842,6 +842,37 @@ extern "C" rix_status rix_setup(const rix_system *sys, const rix_options *opt, r
     return s;
   };
 
+  rix_status s;
+  const bool user_pairs = sys->pairs != nullptr || sys->n_pairs != 0;
+  if (user_pairs) {
+    // ---------------------------------------------- the caller's pair list (host, validated here)
+    if (!sys->pairs || sys->n_pairs <= 0 || sys->n_pairs >= INT32_MAX) {
+      ctx->last_error = "pairs: need n_pairs > 0 entries";
+      return fail(RIX_EINVAL);
+    }
+    std::vector<int64_t> keys((size_t)sys->n_pairs);
+    for (int64_t p = 0; p < sys->n_pairs; p++) {
+      const int32_t *e = sys->pairs + 5 * p;
+      bool ok = e[0] >= 0 && e[0] < ctx->nat && e[1] >= 0 && e[1] < ctx->nat;
+      for (int c = 0; c < 3; c++) ok = ok && e[2 + c] >= -42 && e[2 + c] <= 42 && (ctx->periodic || e[2 + c] == 0);
+      if (!ok) {
+        ctx->last_error = "pairs: atom out of range, or an image beyond +-42 (three hops must stay within +-127), "
+                          "or an image in a cluster";
+        return fail(RIX_EINVAL);
+      }
+      keys[p] = pair_key(e[0], e[1], e[2], e[3], e[4]);
+    }
+    std::sort(keys.begin(), keys.end());
+    if (std::adjacent_find(keys.begin(), keys.end()) != keys.end()) {
+      ctx->last_error = "pairs: duplicate entry";
+      return fail(RIX_EINVAL);
+    }
+    ctx->keys1.swap(keys);
+    ctx->np = (int64_t)ctx->keys1.size();
+    ctx->row1.assign(ctx->nat + 1, 0);
+    for (int64_t p = 0; p < ctx->np; p++) ctx->row1[key_a(ctx->keys1[p]) + 1]++;
+    for (int a = 0; a < ctx->nat; a++) ctx->row1[a + 1] += ctx->row1[a];
+  } else {
   // ------------------------------------------------ pair list on the device
   int nr[3];
   image_range(ctx, nr);
@@ -852,7 +883,6 @@ extern "C" rix_status rix_setup(const rix_system *sys, const rix_options *opt, r
     }
   double *d_xyz = nullptr, *d_cell = nullptr;
   int64_t *d_counts = nullptr, *d_rowptr = nullptr, *d_keys = nullptr;
-  rix_status s;
   if ((s = rix_alloc(ctx, &d_xyz, 3 * (size_t)ctx->nat)) != RIX_OK) return fail(s);
   if ((s = rix_alloc(ctx, &d_cell, 9)) != RIX_OK) return fail(s);
   if ((s = rix_alloc(ctx, &d_counts, ctx->nat + 1)) != RIX_OK) return fail(s);
@@ -879,6 +909,7 @@ extern "C" rix_status rix_setup(const rix_system *sys, const rix_options *opt, r
   if (cudaMemcpy(ctx->keys1.data(), d_keys, sizeof(int64_t) * ctx->np, cudaMemcpyDeviceToHost) != cudaSuccess) {
     ctx->last_error = std::string("pair fill: ") + cudaGetErrorString(cudaGetLastError());
     return fail(RIX_ECUDA);
+  }
   }
   // decode
   const int64_t np = ctx->np;

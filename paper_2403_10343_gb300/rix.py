@@ -29,7 +29,8 @@ class _System(ctypes.Structure):
     _fields_ = [("n_atoms", ctypes.c_int32), ("xyz_bohr", ctypes.c_void_p), ("species", ctypes.c_void_p),
                 ("n_species", ctypes.c_int32), ("nbas_per_species", ctypes.c_void_p),
                 ("naux_per_species", ctypes.c_void_p), ("cell_bohr", ctypes.c_void_p),
-                ("cutoff_bohr", ctypes.c_double), ("screen_tau", ctypes.c_double)]
+                ("cutoff_bohr", ctypes.c_double), ("screen_tau", ctypes.c_double),
+                ("n_pairs", ctypes.c_int64), ("pairs", ctypes.c_void_p)]
 
 
 class _Options(ctypes.Structure):
@@ -152,15 +153,17 @@ def _sizes(ctx):
 
 def setup(xyz_bohr, species, nbas, naux, cell_bohr=None, cutoff_bohr=0.0, screen_tau=0.0,
           precision="fp64", n_slices=0, max_workspace_bytes=0, verbose=0, profile=0, backward=0,
-          block_atoms=0, n_slices_regrouped=0):
-    """rix_setup: returns an opaque context handle (int)."""
+          block_atoms=0, n_slices_regrouped=0, pairs=None):
+    """rix_setup: returns an opaque context handle (int).  pairs: optional [n, 5] (A, B, n1, n2, n3)."""
     lib = load()
     keep = [np.ascontiguousarray(xyz_bohr, dtype=np.float64), np.ascontiguousarray(species, dtype=np.int32),
             np.ascontiguousarray(nbas, dtype=np.int32), np.ascontiguousarray(naux, dtype=np.int32)]
     cell = None if cell_bohr is None else np.ascontiguousarray(cell_bohr, dtype=np.float64)
+    pl = None if pairs is None else np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 5)
     sysd = _System(len(keep[1]), keep[0].ctypes.data, keep[1].ctypes.data, len(keep[2]), keep[2].ctypes.data,
                    keep[3].ctypes.data, None if cell is None else cell.ctypes.data,
-                   float(cutoff_bohr), float(screen_tau))
+                   float(cutoff_bohr), float(screen_tau), 0 if pl is None else len(pl),
+                   None if pl is None else pl.ctypes.data)
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     opt = _Options(prec, int(n_slices), int(max_workspace_bytes), int(verbose), int(profile), int(backward),
                    int(block_atoms), int(n_slices_regrouped))
@@ -373,10 +376,10 @@ class Exchange:
 
     def __init__(self, xyz_bohr, species, nbas, naux, cell_bohr=None, cutoff_bohr=0.0, screen_tau=0.0,
                  precision="fp64", n_slices=0, max_workspace_bytes=0, verbose=0, profile=0, backward=0,
-                 block_atoms=0, n_slices_regrouped=0):
+                 block_atoms=0, n_slices_regrouped=0, pairs=None):
         self.ctx = setup(xyz_bohr, species, nbas, naux, cell_bohr, cutoff_bohr, screen_tau, precision,
                          n_slices, max_workspace_bytes, verbose, profile, backward, block_atoms,
-                         n_slices_regrouped)
+                         n_slices_regrouped, pairs)
         self.c_elems, self.v_elems, self.d_elems, self.k_elems = layout_sizes(self.ctx)
 
     @classmethod

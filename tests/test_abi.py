@@ -72,3 +72,32 @@ def test_invalid_arguments_fail_before_any_device_work():
     assert lib.rix_last_error(None) == b""
     lib.rix_destroy.argtypes = [P]
     lib.rix_destroy(None)                                   # a no-op
+
+
+def test_caller_pair_list_is_validated_before_any_device_work():
+    """rix_system.pairs: out-of-range atoms, images in a cluster, duplicates and lists that are
+    not symmetric are rejected with RIX_EINVAL (no GPU needed to get there)."""
+    from paper_2403_10343_gb300 import build, rix
+    lib = ctypes.CDLL(build.build())
+    P = ctypes.c_void_p
+    lib.rix_setup.argtypes = [ctypes.POINTER(rix._System), ctypes.POINTER(rix._Options), ctypes.POINTER(P)]
+    xyz = (ctypes.c_double * 6)(0.0, 0.0, 0.0, 1.5, 0.0, 0.0)
+    sp = (ctypes.c_int32 * 2)(0, 0)
+    nb, na = (ctypes.c_int32 * 1)(5), (ctypes.c_int32 * 1)(16)
+    out = P(123)
+
+    def setup(rows, cell=None, n=None):
+        arr = (ctypes.c_int32 * (5 * max(1, len(rows))))(*[v for r in rows for v in r])
+        sysd = rix._System(2, ctypes.cast(xyz, P), ctypes.cast(sp, P), 1, ctypes.cast(nb, P), ctypes.cast(na, P),
+                           cell, 10.0 if cell else 0.0, 0.0, len(rows) if n is None else n, ctypes.cast(arr, P))
+        return lib.rix_setup(ctypes.byref(sysd), None, ctypes.byref(out))
+
+    onsite = [(0, 0, 0, 0, 0), (1, 1, 0, 0, 0)]
+    assert setup(onsite + [(0, 2, 0, 0, 0), (2, 0, 0, 0, 0)]) == 1          # atom out of range
+    assert setup(onsite + [(0, 1, 1, 0, 0), (1, 0, -1, 0, 0)]) == 1         # image in a cluster
+    assert setup(onsite + [(0, 1, 0, 0, 0), (0, 1, 0, 0, 0), (1, 0, 0, 0, 0)]) == 1  # duplicate
+    assert setup(onsite + [(0, 1, 0, 0, 0)]) == 1                           # (1, 0) missing: not symmetric
+    assert setup(onsite, n=0) == 1                                          # pointer without a count
+    cell = (ctypes.c_double * 9)(30, 0, 0, 0, 30, 0, 0, 0, 30)
+    assert setup(onsite + [(0, 1, 43, 0, 0), (1, 0, -43, 0, 0)], cell=ctypes.cast(cell, P)) == 1  # beyond +-42
+    assert not out.value

@@ -349,3 +349,29 @@ def test_cluster_batch_in_one_context(precision):
         exs.close()
     assert abs(E - e_sum) < 1e-12 * abs(e_sum)
     ex.close()
+
+
+def test_caller_supplied_pair_list():
+    """rix_system.pairs: the pair list of a smaller cutoff, given explicitly (shuffled) to a context
+    set up with a larger cutoff, gives exactly the build of a context with the smaller cutoff, and
+    the oracle's K for that cutoff."""
+    o = np.array([[1.0, 1.2, 0.8], [3.9, 3.1, 3.3]])
+    big = _small_waters(o, seed=17, side=6.0, cut=4.8)
+    small = _small_waters(o, seed=17, side=6.0, cut=4.0)
+    pk = ri.generate(small)
+    keys, A, B, n = ri.pair_list(small)
+    rows = np.concatenate([A[:, None], B[:, None], n], axis=1)
+    rows = rows[np.random.default_rng(2).permutation(len(rows))]
+    ex_ref, kk_ref, K_ref, E_ref, _ = run_gpu(small, pk)
+    ex = Exchange.from_system(big, pairs=rows)
+    assert np.array_equal(ex.pair_keys(), pk.keys)
+    ex.set_CV(_dev(pk.C), _dev(pk.V))
+    D = _dev(pk.D)
+    K = ex.build_K(D)
+    E = ex.energy(D, K).item()
+    assert np.array_equal(ex.k_keys(), kk_ref)
+    assert np.array_equal(K.cpu().numpy(), K_ref) and E == E_ref
+    kk, Ko, Eo, _ = exchange(small, pk)
+    assert rel(K.cpu().numpy(), Ko) < K_TOL
+    ex.close()
+    ex_ref.close()
