@@ -244,6 +244,22 @@ rix_status rix_force_stress(rix_ctx *ctx, int32_t c, const double *dEdC_dev, con
                             const double *dCdr_c_dev, const double *dVdr_c_dev, double *F_dev, double *stress_dev,
                             void *stream);
 
+/* RI-LVL coefficient fit (the paper's Eq. 8 with the pair-restricted Coulomb
+ * metric of Eq. 10; part of its "Initialization" stage, once per geometry):
+ *   C(I,J,n)^mu_ij = sum_{nu in P(IJ)} (ij|nu) [(V^{IJ} + lambda 1)^{-1}]_{nu mu}
+ * with P(IJ) = aux(I) then aux(J) (aux(I) alone on-site), V^{IJ} assembled
+ * from the on-site blocks V(I,I,0), V(J,J,0) and the pair block V(I,J,n).
+ * V_dev: packed V (RIX_LIST_V layout), eri_dev: the three-centre integrals
+ * (ij|nu) in the packed C layout, C_dev: output, packed C (all device).  Each
+ * representative pair is factored by Cholesky and solved on the device; its
+ * partner receives the transposed numbers, so C is exactly pair-symmetric
+ * (rix_set_CV accepts it).  lambda >= 0 shifts the metric's diagonal (a
+ * Tikhonov fit) for metrics that are numerically singular; EINVAL if a shifted
+ * metric is still not positive definite.  Allocates its workspace (up to
+ * 1 GB) on `stream` and synchronises it. */
+rix_status rix_fit_C(rix_ctx *ctx, const double *V_dev, const double *eri_dev, double lambda, double *C_dev,
+                     void *stream);
+
 /* Gamma-point fold of an image-resolved K: Kdense[I][L] = sum_n K(A,E,n)[i][l]
  * (I, L global basis indices), row-major nbasis x nbasis.  Asynchronous. */
 rix_status rix_fold_gamma(rix_ctx *ctx, const double *K_dev, double *Kdense_dev, void *stream);

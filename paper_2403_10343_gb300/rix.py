@@ -86,6 +86,7 @@ def load():
     lib.rix_check.argtypes = [P, P]
     lib.rix_build_K_delta.argtypes = [P, P, P, P]
     lib.rix_force_stress.argtypes = [P, ctypes.c_int32, P, P, P, P, P, P, P]
+    lib.rix_fit_C.argtypes = [P, P, P, ctypes.c_double, P, P]
     lib.rix_gemm_profile.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_int64)]
     lib.rix_bloch.argtypes = [P, P, ctypes.c_int32, P, P, P]
@@ -102,7 +103,7 @@ def load():
               "rix_backward", "rix_fold_gamma", "rix_stats", "rix_stage_times", "rix_gemm_sliced",
               "rix_autotune", "rix_count_flops", "rix_check", "rix_test_stalled_gemm", "rix_bloch",
               "rix_build_K_spin", "rix_energy_spin", "rix_build_K_delta", "rix_force_stress",
-              "rix_gemm_profile"):
+              "rix_gemm_profile", "rix_fit_C"):
         getattr(lib, f).restype = I
     _lib = lib
     return lib
@@ -283,6 +284,17 @@ def force_stress(ctx, c, dEdC, dEdV, dCdr_c, dVdr_c, F=None, stress=None, stream
     _check(load().rix_force_stress(ctx, int(c), _dptr(dEdC, "dEdC", cel), _dptr(dEdV, "dEdV", vel, dev),
                                    _dptr(dCdr_c, "dCdr_c", cel, dev), _dptr(dVdr_c, "dVdr_c", vel, dev),
                                    _dptr(F, "F", nat, dev), _dptr(stress, "stress", 3, dev), _stream(stream)), ctx)
+
+
+def fit_C(ctx, V, eri, lam=0.0, C=None, stream=None):
+    """rix_fit_C: RI coefficients from the three-centre integrals (packed C layout) and the metric V."""
+    import torch
+    cel, vel, _, _ = _sizes(ctx)
+    if C is None:
+        C = torch.empty(cel, dtype=torch.float64, device=eri.device)
+    _check(load().rix_fit_C(ctx, _dptr(V, "V", vel), _dptr(eri, "eri", cel, V.device), float(lam),
+                            _dptr(C, "C", cel, V.device), _stream(stream)), ctx)
+    return C
 
 
 def check(ctx, stream=None):
