@@ -115,6 +115,13 @@ typedef struct {
                                       Fock-matrix block size); 0 = blocks only where memory requires */
   int32_t n_slices_regrouped;      /* mixed mode: slices of the regrouped plans (term 1 as T x C, the
                                       term-4 intermediate, T), 1..8; 0 = n_slices + 1 */
+  int32_t reuse_forward;           /* rix_backward's recompute switch.  0 (default): recompute T, U2, Z
+                                      and K from D.  1: when the plan has one row block and the
+                                      preceding call on the context was rix_build_K with the same D
+                                      pointer (the caller guarantees D and that K are unchanged since),
+                                      reuse the intermediates and K that build left resident; otherwise
+                                      recompute.  The adjoint overwrites them, so a second rix_backward
+                                      recomputes. */
 } rix_options;
 
 typedef struct {

@@ -719,14 +719,22 @@ extern "C" rix_status rix_backward(rix_ctx *ctx, const double *D, double gEx, do
     cudaFuncSetAttribute(kb_C12, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_BIG * 8);
     g_bwd_attr = true;
   }
-  // forward recompute: flags, T, U2, Z and K (U2 stays complete; T and Z hold the last block)
-  rix_status s = rix_fp64_build(ctx, D, ctx->d_Kbuf, st);
-  if (s != RIX_OK) return s;
+  // forward recompute: flags, T, U2, Z and K (U2 stays complete; T and Z hold the last block),
+  // unless the preceding build of this D left them resident and the caller asked to reuse them
+  const double *Kf = ctx->d_Kbuf;
+  rix_status s = RIX_OK;
+  if (ctx->opt.reuse_forward && ctx->fwd_valid && ctx->fwd_D == D && ctx->nblk == 1) {
+    Kf = ctx->fwd_K;
+  } else {
+    s = rix_fp64_build(ctx, D, ctx->d_Kbuf, st);
+    if (s != RIX_OK) return s;
+  }
+  ctx->fwd_valid = false;  // the adjoint overwrites T and Z below
   const double sX = -0.5 * gEx;
   const int64_t np = ctx->np;
   if (dD) {
     kb_dD<<<(unsigned)np, 128, 0, st>>>(np, ctx->d_pA, ctx->d_pB, ctx->d_map1to3, ctx->d_nb, ctx->d_offD,
-                                        ctx->d_offK, ctx->d_Kbuf, -0.5 * gEx, dD);
+                                        ctx->d_offK, Kf, -0.5 * gEx, dD);
     if ((s = last_err(ctx, "kb_dD")) != RIX_OK) return s;
   }
   if (!dC && !dV) return RIX_OK;

@@ -130,6 +130,7 @@ unsigned grid_for(int64_t n) {
 }  // namespace
 
 extern "C" rix_status rix_count_flops(rix_ctx *ctx, const double *D, double *flops, void *stream) {
+  if (ctx) ctx->fwd_valid = false;  // the D screening flags follow this D
   if (!ctx || !D || !flops) return RIX_EINVAL;
   if (!ctx->have_cv) return RIX_ESTATE;
   cudaStream_t st = (cudaStream_t)stream;

@@ -747,6 +747,7 @@ extern "C" rix_status rix_autotune(rix_ctx *ctx, const double *D, const char *ca
     ctx->last_error = "rix_autotune times kernels and cannot run inside a graph capture";
     return RIX_ESTATE;
   }
+  ctx->fwd_valid = false;  // the timing runs overwrite the intermediates
   const std::string key = tune_key(ctx);
   if (cache_path && *cache_path) {
     if (FILE *f = fopen(cache_path, "r")) {

@@ -123,6 +123,11 @@ struct rix_ctx {
   double *d_rvec = nullptr;             // pair vector r_p = x_B + n . cell - x_A of every pair [np][3]
   double *d_gpair = nullptr;            // force chain: dE/dr_p (one Cartesian component) per pair
   double volume = 0.0;                  // cell volume (bohr^3), 0 for a cluster
+  // the preceding rix_build_K (rix_options.reuse_forward): its D and K, and whether T, U2 and Z
+  // still hold its intermediates (one row block, nothing else has run since)
+  const double *fwd_D = nullptr;
+  const double *fwd_K = nullptr;
+  bool fwd_valid = false;
   // mixed precision: terms 3+4 and term 2 as batched sliced GEMMs on the tensor cores
   bool have_mx = false;
   int32_t mx_S = 5;

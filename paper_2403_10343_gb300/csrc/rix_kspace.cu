@@ -110,6 +110,7 @@ extern "C" rix_status rix_energy_spin(rix_ctx *ctx, int32_t n_spin, const double
   if (s != RIX_OK) return s;
   const int64_t nd = ctx->offD[ctx->np], nk = ctx->offK[ctx->nk];
   const double scale = n_spin == 1 ? -0.25 : -0.5;
+  ctx->fwd_valid = false;
   for (int sgm = 0; sgm < n_spin; sgm++) {
     s = rix_launch_energy_scaled(ctx, D + sgm * nd, K + sgm * nk, Ex, scale, sgm > 0, (cudaStream_t)stream);
     if (s != RIX_OK) return s;

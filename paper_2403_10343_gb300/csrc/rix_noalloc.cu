@@ -55,5 +55,6 @@ extern "C" rix_status rix_energy_noalloc(rix_ctx *ctx, const double *D, const do
   }
   rix_status s = rix_take_err(ctx);
   if (s != RIX_OK) return s;
+  if (D != ctx->fwd_D) ctx->fwd_valid = false;  // the D screening flags follow this D
   return rix_launch_energy_partials(ctx, D, K, Ex, ctx->noalloc_scratch, (cudaStream_t)stream);
 }

@@ -1020,6 +1020,7 @@ extern "C" rix_status rix_set_CV(rix_ctx *ctx, const double *C, const double *V,
     ctx->last_error = "C or V blocks differ from their transposed partners";
     return RIX_ENOTSYM;
   }
+  ctx->fwd_valid = false;
   if ((s = rix_launch_flags(ctx, ctx->d_C, ctx->d_offC, ctx->np, ctx->d_keepC, st)) != RIX_OK) return s;
   if ((s = rix_launch_flags(ctx, ctx->d_V, ctx->d_offV, ctx->np, ctx->d_keepV, st)) != RIX_OK) return s;
   ctx->have_cv = true;
@@ -1052,7 +1053,14 @@ extern "C" rix_status rix_build_K(rix_ctx *ctx, const double *D, double *K, void
   if (!ctx->have_cv) return RIX_ESTATE;
   rix_status s = rix_take_err(ctx);
   if (s != RIX_OK) return s;
-  return rix_fp64_build(ctx, D, K, (cudaStream_t)stream);
+  ctx->fwd_valid = false;
+  s = rix_fp64_build(ctx, D, K, (cudaStream_t)stream);
+  if (s == RIX_OK && ctx->nblk == 1) {
+    ctx->fwd_D = D;
+    ctx->fwd_K = K;
+    ctx->fwd_valid = true;
+  }
+  return s;
 }
 
 extern "C" rix_status rix_build_K_delta(rix_ctx *ctx, const double *dD, double *K, void *stream) {
@@ -1060,6 +1068,7 @@ extern "C" rix_status rix_build_K_delta(rix_ctx *ctx, const double *dD, double *
   if (!ctx->have_cv) return RIX_ESTATE;
   rix_status s = rix_take_err(ctx);
   if (s != RIX_OK) return s;
+  ctx->fwd_valid = false;
   return rix_fp64_build(ctx, dD, K, (cudaStream_t)stream, 1);
 }
 
@@ -1067,6 +1076,7 @@ extern "C" rix_status rix_energy(rix_ctx *ctx, const double *D, const double *K,
   if (!ctx || !D || !K || !Ex) return RIX_EINVAL;
   rix_status s = rix_take_err(ctx);
   if (s != RIX_OK) return s;
+  if (D != ctx->fwd_D) ctx->fwd_valid = false;  // the D screening flags follow this D
   return rix_launch_energy(ctx, D, K, Ex, (cudaStream_t)stream);
 }
 

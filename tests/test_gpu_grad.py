@@ -241,3 +241,26 @@ def test_grad_config1_against_dense_definition():
     dDm = mx.backward(D, 1.0, want=("D",))[0].cpu().numpy()
     mx.close()
     assert np.linalg.norm(dD - dDm) <= 1e-8 * np.linalg.norm(dD)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_backward_reusing_the_forward(prec):
+    """rix_options.reuse_forward: rix_backward right after rix_build_K of the same D reuses the
+    build's intermediates and K instead of recomputing them, with the same gradients."""
+    import rix_inputs as ri
+    s = ri.config(0)
+    pk = ri.generate(s)
+    dev = torch.device("cuda")
+    C, V, D = (torch.from_numpy(x).to(dev) for x in (pk.C, pk.V, pk.D))
+    out = {}
+    for reuse in (0, 1):
+        ex = Exchange.from_system(s, precision=prec, backward=1, reuse_forward=reuse)
+        ex.set_CV(C, V)
+        ex.build_K(D)
+        out[reuse] = [g.cpu().numpy() for g in ex.backward(D, 1.0)]
+        again = [g.cpu().numpy() for g in ex.backward(D, 1.0)]   # nothing left to reuse: recomputed
+        for a, b in zip(out[reuse], again):
+            assert np.abs(a - b).max() <= (0 if prec == "fp64" else 1e-9) * np.abs(a).max()
+        ex.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.abs(a - b).max() <= (0 if prec == "fp64" else 1e-9) * np.abs(a).max()
