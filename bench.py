@@ -2,19 +2,20 @@
 """Benchmark of the exchange build: K-build time per SCF iteration.
 
 One step = one rix_build_K + rix_energy on the resident inputs of the
-workload (default: the (H2O)64 cluster, 192 atoms, nbasis 1536, 8 A cutoff),
-captured once into a CUDA graph and replayed (--graph 0: eager launches).
-Prints one JSON line; per-stage times come from CUDA events of the eager
-warm-up steps.
+workload (default: the largest single-GPU workload, the ice-like supercell of
+3,072 atoms, nbasis 24,576, 8 A images), launched eagerly (--graph 1: one
+step captured into a CUDA graph and replayed).  Prints one JSON line; the
+per-stage times and the per-launch times of the tensor-core GEMM come from
+CUDA events recorded inside the timed region.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--config 1] [--precision both|fp64|mixed]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config 4] [--precision both|fp64|mixed]
 
-By default both paths run; the headline value is the mixed path (terms 3+4 on
-the BF16 tensor cores by error-free slicing), with the FP64 path's time and the
-mixed-vs-FP64 errors in the same line.
+By default both paths run; the headline value is the mixed path (the
+contraction stages on the BF16 tensor cores by error-free slicing), with the
+FP64 path's time and the mixed-vs-FP64 errors in the same line.
   python bench.py --impl reference ...   (the FP64 CPU oracle on a bounded row sample)
 
-Inputs are synthetic (seeded), larger than L2 (C alone is 0.87 GB for the
+Inputs are synthetic (seeded), larger than L2 (C alone is 24.6 GB for the
 default workload), so no L2 flush is needed between steps.  With N > 1 (one
 process per GPU under torchrun) every rank runs an independent replica of the
 whole build (the build is not sharded across GPUs).
@@ -449,7 +450,8 @@ def run_rix(args):
     s = ri.config(args.config)
     pk = ri.generate(s)
     big = s.n_atoms > 1000
-    graph = (not big) if args.graph < 0 else bool(args.graph)
+    # eager launches by default, so that the per-launch GEMM events fall inside the timed region
+    graph = bool(args.graph)
     precs = ["mixed", "fp64"] if args.precision == "both" else [args.precision]
     res = {}
     for p in precs:
@@ -519,9 +521,9 @@ def main():
     ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
     ap.add_argument("--impl", default="rix", choices=["rix", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--graph", type=int, default=-1,
-                    help="1: time CUDA graph replays of one step; 0: eager launches (with per-GEMM events); "
-                         "-1 (default): replays for the small workloads, eager for the 1,000+ atom ones")
+    ap.add_argument("--graph", type=int, default=0,
+                    help="1: time CUDA graph replays of one step; 0 (default): eager launches, with CUDA events "
+                         "around every tensor-core GEMM launch for the kernel roofline")
     ap.add_argument("--autotune", type=int, default=1, help="1: rix_autotune of the FP64 path (default)")
     ap.add_argument("--slices", type=int, default=5,
                     help="mixed path: BF16 slices per operand (the regrouped plans take one more); 3 = the "
