@@ -122,6 +122,14 @@ typedef struct {
                                       reuse the intermediates and K that build left resident; otherwise
                                       recompute.  The adjoint overwrites them, so a second rix_backward
                                       recomputes. */
+  double product_tau;              /* product screening (the paper's norm screening of block products,
+                                      Sec. "Evaluation of the EXX matrix in real space"): a product of
+                                      blocks whose max-norms multiply to less than product_tau is
+                                      skipped -- C(A,B') D(B',G') in T, V(B,G') D(B,G') C(G',E') in Z
+                                      (row tiles of V D on the tensor cores, against the largest C
+                                      block of G').  An approximation whose error is the skipped
+                                      products'; 0 = off (only input blocks below screen_tau are
+                                      dropped).  The adjoint does not apply it. */
 } rix_options;
 
 typedef struct {

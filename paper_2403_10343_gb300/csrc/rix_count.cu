@@ -29,7 +29,8 @@ __device__ __forceinline__ void add_out(double *out, int i, double v) {
 // T(A,G') <- C(A,B') D(B',G'): 2 na_A nb_A nb_B nb_G per kept product.
 __global__ void k_cnt_T(int64_t n2, const int64_t *ptrT, const int2 *LT, const int32_t *atomA2,
                         const int32_t *atomB2, const int32_t *pB, const int32_t *nb, const int32_t *na,
-                        const uint8_t *keepC, const uint8_t *keepD, const uint8_t *ttc, double *out) {
+                        const uint8_t *keepC, const uint8_t *keepD, const uint8_t *ttc, rix::PScreen ps,
+                        double *out) {
   double all = 0.0, tc = 0.0;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n2; t += (int64_t)gridDim.x * blockDim.x) {
     const int a = atomA2[t], g = atomB2[t];
@@ -37,7 +38,7 @@ __global__ void k_cnt_T(int64_t n2, const int64_t *ptrT, const int2 *LT, const i
     double s = 0.0;
     for (int64_t e = ptrT[t]; e < ptrT[t + 1]; e++) {
       const int2 en = LT[e];
-      if (keepC[en.x] && keepD[en.y]) s += f * nb[pB[en.x]];
+      if (keepC[en.x] && keepD[en.y] && !ps.drop2(en.x, en.y)) s += f * nb[pB[en.x]];
     }
     all += s;
     if (ttc && ttc[a]) tc += s;
@@ -88,13 +89,13 @@ __global__ void k_cnt_X12(int64_t n2, const int64_t *ptr, const rix::X12Entry *L
 __global__ void k_cnt_Z(int64_t n2, const int64_t *ptrZ, const int2 *LZ, const int32_t *atomA2,
                         const int32_t *atomB2, const int32_t *pB, const int32_t *nb, const int32_t *na,
                         const uint8_t *keepC, const uint8_t *keepV, const uint8_t *keepD, const uint8_t *ztc,
-                        double *out) {
+                        rix::PScreen ps, double *out) {
   double all = 0.0, tc = 0.0;
   for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < n2; z += (int64_t)gridDim.x * blockDim.x) {
     const int b = atomA2[z], e = atomB2[z];
     for (int64_t x = ptrZ[z]; x < ptrZ[z + 1]; x++) {
       const int2 en = LZ[x];
-      if (!keepD[en.x] || !keepV[en.x] || !keepC[en.y]) continue;
+      if (!keepD[en.x] || !keepV[en.x] || !keepC[en.y] || ps.drop3(en.x, en.x, en.y)) continue;
       const int g = pB[en.x];
       const double f = 2.0 * na[b] * na[g] * nb[g] * nb[e] + 2.0 * na[b] * nb[b] * nb[g] * nb[e];
       all += f;
@@ -140,7 +141,7 @@ extern "C" rix_status rix_count_flops(rix_ctx *ctx, const double *D, double *flo
     return RIX_ESTATE;
   }
   rix_status s;
-  if ((s = rix_launch_flags(ctx, D, ctx->d_offD, ctx->np, ctx->d_keepD, st)) != RIX_OK) return s;
+  if ((s = rix_launch_flags(ctx, D, ctx->d_offD, ctx->np, ctx->d_keepD, st, ctx->d_normD)) != RIX_OK) return s;
   double *d_out = nullptr;
   RIX_CUDA_TRY(ctx, cudaMallocAsync((void **)&d_out, 10 * sizeof(double), st));
   rix_status r = RIX_OK;
@@ -149,7 +150,7 @@ extern "C" rix_status rix_count_flops(rix_ctx *ctx, const double *D, double *flo
     const int64_t n2 = ctx->stats.n_pairs2, nk = ctx->stats.n_kblocks;
     k_cnt_T<<<grid_for(n2), CNT_THREADS, 0, st>>>(n2, ctx->d_ptrT, ctx->d_LT, ctx->d_atomA2, ctx->d_atomB2,
                                                   ctx->d_pB, ctx->d_nb, ctx->d_na, ctx->d_keepC, ctx->d_keepD,
-                                                  ctx->d_ttc, d_out);
+                                                  ctx->d_ttc, rix_pscreen(ctx), d_out);
     k_cnt_U2<<<grid_for(ctx->np), CNT_THREADS, 0, st>>>(ctx->np, ctx->d_pA, ctx->d_pB, ctx->d_nb, ctx->d_na,
                                                         ctx->d_keepV, d_out);
     k_cnt_X12<<<grid_for(n2), CNT_THREADS, 0, st>>>(n2, ctx->d_ptrX12, ctx->d_LX12, ctx->d_atomA2,
@@ -157,7 +158,7 @@ extern "C" rix_status rix_count_flops(rix_ctx *ctx, const double *D, double *flo
                                                     ctx->d_t1tc, d_out);
     k_cnt_Z<<<grid_for(n2), CNT_THREADS, 0, st>>>(n2, ctx->d_ptrZ, ctx->d_LZ, ctx->d_atomA2, ctx->d_atomB2,
                                                   ctx->d_pB, ctx->d_nb, ctx->d_na, ctx->d_keepC, ctx->d_keepV,
-                                                  ctx->d_keepD, ctx->d_ztc, d_out);
+                                                  ctx->d_keepD, ctx->d_ztc, rix_pscreen(ctx), d_out);
     k_cnt_X34<<<grid_for(nk), CNT_THREADS, 0, st>>>(nk, ctx->d_ptrX34, ctx->d_LX34, ctx->d_atomA3,
                                                     ctx->d_atomB3, ctx->d_pB, ctx->d_nb, ctx->d_na, ctx->d_keepC,
                                                     d_out);

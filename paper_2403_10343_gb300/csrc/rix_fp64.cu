@@ -97,18 +97,22 @@ __global__ void k_pairs(int nat, const double *xyz, const double *cell, int peri
 
 // ------------------------------------------------------------------ screening flags
 // keep[b] = max |block b| >= tau (always 1 when tau <= 0); one warp per block.
-__global__ void k_flags(const double *arr, const int64_t *off, int64_t n, double tau, uint8_t *keep) {
+// norm (optional): the block's max |x| rounded up to a float (product screening).
+__global__ void k_flags(const double *arr, const int64_t *off, int64_t n, double tau, uint8_t *keep, float *norm) {
   int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (w >= n) return;
-  if (!(tau > 0)) {
+  if (!(tau > 0) && !norm) {
     if (lane == 0) keep[w] = 1;
     return;
   }
   double m = 0;
   for (int64_t i = off[w] + lane; i < off[w + 1]; i += 32) m = fmax(m, fabs(arr[i]));
   for (int s = 16; s; s >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, s));
-  if (lane == 0) keep[w] = m >= tau;
+  if (lane == 0) {
+    keep[w] = !(tau > 0) || m >= tau;
+    if (norm) norm[w] = __double2float_ru(m);
+  }
 }
 
 // ------------------------------------------------------------------ symmetry check of C and V
@@ -150,7 +154,7 @@ __global__ void __launch_bounds__(NT) k_T(const int2 *items, const int64_t *ptrT
                                           const double *__restrict__ C, const int64_t *offC,
                                           const double *__restrict__ D, const int64_t *offD,
                                           const uint8_t *keepC, const uint8_t *keepD, double *T,
-                                          int64_t tbase, const uint8_t *ttc) {
+                                          int64_t tbase, const uint8_t *ttc, PScreen ps) {
   extern __shared__ double sm[];
   const int tid = threadIdx.x;
   const int2 it = items[blockIdx.x];
@@ -167,7 +171,7 @@ __global__ void __launch_bounds__(NT) k_T(const int2 *items, const int64_t *ptrT
   for (int r = 0; r < MAXE; r++) acc[r] = 0.0;
   for (int64_t e = ptrT[t]; e < ptrT[t + 1]; e++) {
     const int2 en = LT[e];
-    if (!keepC[en.x] || !keepD[en.y]) continue;
+    if (!keepC[en.x] || !keepD[en.y] || ps.drop2(en.x, en.y)) continue;
     const int nbB = nb[pB[en.x]];
     const double *Dg = D + offD[en.y];
     __syncthreads();
@@ -321,7 +325,7 @@ __global__ void __launch_bounds__(NT) k_Z(const int2 *items, const int64_t *ptrZ
                                           const double *__restrict__ V, const int64_t *offV,
                                           const double *__restrict__ D, const int64_t *offD,
                                           const uint8_t *keepC, const uint8_t *keepV, const uint8_t *keepD,
-                                          double *Z, int64_t zbase, int smb, const uint8_t *ztc) {
+                                          double *Z, int64_t zbase, int smb, const uint8_t *ztc, PScreen ps) {
   extern __shared__ double sm[];
   const int tid = threadIdx.x;
   const int2 it = items[blockIdx.x];
@@ -337,7 +341,7 @@ __global__ void __launch_bounds__(NT) k_Z(const int2 *items, const int64_t *ptrZ
   for (int r = 0; r < MAXE; r++) acc[r] = 0.0;
   for (int64_t x = ptrZ[z]; x < ptrZ[z + 1]; x++) {
     const int2 en = LZ[x];
-    if (!keepD[en.x] || !keepV[en.x] || !keepC[en.y]) continue;
+    if (!keepD[en.x] || !keepV[en.x] || !keepC[en.y] || ps.drop3(en.x, en.x, en.y)) continue;
     const int g = pB[en.x];
     if (ztc && ztc[g]) continue;  // this middle atom's part runs on the tensor cores
     const int nbG = nb[g], naG = na[g];
@@ -543,11 +547,25 @@ rix_status rix_launch_pairs(rix_ctx *ctx, const double *d_xyz, const double *d_c
 }
 
 rix_status rix_launch_flags(rix_ctx *ctx, const double *arr, const int64_t *off, int64_t n, uint8_t *keep,
-                            cudaStream_t st) {
+                            cudaStream_t st, float *norm) {
   if (n == 0) return RIX_OK;
   const int64_t blocks = (n * 32 + 255) / 256;
-  k_flags<<<(unsigned)blocks, 256, 0, st>>>(arr, off, n, ctx->tau, keep);
+  k_flags<<<(unsigned)blocks, 256, 0, st>>>(arr, off, n, ctx->tau, keep, ctx->opt.product_tau > 0 ? norm : nullptr);
   return last(ctx, "k_flags");
+}
+
+// out[a] = max over the pairs (a, .) of norm (one thread per atom)
+__global__ void k_atom_max(int nat, const int64_t *row1, const float *norm, float *out) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nat) return;
+  float m = 0.f;
+  for (int64_t p = row1[a]; p < row1[a + 1]; p++) m = fmaxf(m, norm[p]);
+  out[a] = m;
+}
+
+rix_status rix_launch_atom_max(rix_ctx *ctx, const float *norm, float *out, cudaStream_t st) {
+  k_atom_max<<<(ctx->nat + 127) / 128, 128, 0, st>>>(ctx->nat, ctx->d_row1, norm, out);
+  return last(ctx, "k_atom_max");
 }
 
 rix_status rix_launch_symcheck(rix_ctx *ctx, cudaStream_t st) {
@@ -579,7 +597,7 @@ rix_status launch_Z_items(rix_ctx *ctx, const double *D, int b, int64_t first, i
                                             ctx->d_atomA2, ctx->d_atomB2, ctx->d_off2, ctx->d_pB, ctx->d_nb,
                                             ctx->d_na, ctx->d_C, ctx->d_offC, ctx->d_V, ctx->d_offV, D, ctx->d_offD,
                                             ctx->d_keepC, ctx->d_keepV, ctx->d_keepD, ctx->d_Z, ctx->blk_base[b],
-                                            smb, ctx->have_mx ? ctx->d_ztc : nullptr);
+                                            smb, ctx->have_mx ? ctx->d_ztc : nullptr, rix_pscreen(ctx));
   return last(ctx, "k_Z");
 }
 
@@ -623,7 +641,8 @@ rix_status rix_launch_T_block(rix_ctx *ctx, const double *D, int b, cudaStream_t
     k_T<<<(unsigned)nT, NT, 64 * 64 * 8, st>>>(ctx->d_itT + ctx->segT[b], ctx->d_ptrT, ctx->d_LT, ctx->d_atomA2,
                                                ctx->d_atomB2, ctx->d_off2, ctx->d_pB, ctx->d_nb, ctx->d_na,
                                                ctx->d_C, ctx->d_offC, D, ctx->d_offD, ctx->d_keepC, ctx->d_keepD,
-                                               ctx->d_T, ctx->blk_base[b], tc ? ctx->d_ttc : nullptr);
+                                               ctx->d_T, ctx->blk_base[b], tc ? ctx->d_ttc : nullptr,
+                                               rix_pscreen(ctx));
     rix_status s = last(ctx, "k_T");
     if (s != RIX_OK) return s;
   }
@@ -642,7 +661,7 @@ rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t
   set_attrs();
   rix_status s;
   if ((s = rix_prof_mark(ctx, 0, st)) != RIX_OK) return s;
-  if ((s = rix_launch_flags(ctx, D, ctx->d_offD, ctx->np, ctx->d_keepD, st)) != RIX_OK) return s;
+  if ((s = rix_launch_flags(ctx, D, ctx->d_offD, ctx->np, ctx->d_keepD, st, ctx->d_normD)) != RIX_OK) return s;
   if ((s = rix_prof_mark(ctx, 1, st)) != RIX_OK) return s;
   RIX_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_X, 0, sizeof(double) * ctx->offK[ctx->nk], st));
   // terms 1 and 2, one block of row atoms at a time (T resident for the block)

@@ -18,6 +18,17 @@
 
 namespace rix {
 
+// Product screening (rix_options.product_tau): a product of blocks whose max-norms
+// multiply to less than tau is skipped.  tau = 0: off.
+struct PScreen {
+  const float *nC, *nV, *nD;
+  float tau;
+  __device__ __forceinline__ bool drop2(int c, int d) const { return tau > 0.f && nC[c] * nD[d] < tau; }
+  __device__ __forceinline__ bool drop3(int v, int d, int c) const {
+    return tau > 0.f && nV[v] * nD[d] * nC[c] < tau;
+  }
+};
+
 // Pair key: A << 44 | B << 24 | (n1+128) << 16 | (n2+128) << 8 | (n3+128).
 __host__ __device__ inline int64_t pair_key(int64_t a, int64_t b, int n1, int n2, int n3) {
   return (a << 44) | (b << 24) | ((int64_t)(n1 + 128) << 16) | ((int64_t)(n2 + 128) << 8) |
@@ -109,6 +120,8 @@ struct rix_ctx {
   // inputs and intermediates
   double *d_C = nullptr, *d_V = nullptr;
   uint8_t *d_keepC = nullptr, *d_keepV = nullptr, *d_keepD = nullptr;
+  float *d_normC = nullptr, *d_normV = nullptr, *d_normD = nullptr;  // block max-norms (product screening)
+  float *d_maxCatom = nullptr;          // per atom G: the largest norm of its C blocks (G, .)
   double *d_T = nullptr, *d_Z = nullptr, *d_U = nullptr, *d_X = nullptr;
   double *d_epart = nullptr;            // energy partial sums
   int32_t *d_flag = nullptr;            // device status word
@@ -235,7 +248,11 @@ rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t
 rix_status rix_launch_T_block(rix_ctx *ctx, const double *D, int b, cudaStream_t st);
 rix_status rix_launch_Z_block(rix_ctx *ctx, const double *D, int b, cudaStream_t st);
 rix_status rix_launch_flags(rix_ctx *ctx, const double *arr, const int64_t *off, int64_t n,
-                            uint8_t *keep, cudaStream_t st);
+                            uint8_t *keep, cudaStream_t st, float *norm = nullptr);
+rix_status rix_launch_atom_max(rix_ctx *ctx, const float *norm, float *out, cudaStream_t st);
+inline rix::PScreen rix_pscreen(const rix_ctx *ctx) {
+  return rix::PScreen{ctx->d_normC, ctx->d_normV, ctx->d_normD, (float)ctx->opt.product_tau};
+}
 rix_status rix_launch_symcheck(rix_ctx *ctx, cudaStream_t st);
 rix_status rix_launch_energy(rix_ctx *ctx, const double *D, const double *K, double *Ex,
                              cudaStream_t st);

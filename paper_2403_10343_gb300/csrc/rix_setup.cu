@@ -817,6 +817,7 @@ extern "C" rix_status rix_setup(const rix_system *sys, const rix_options *opt, r
   if (opt && opt->precision != RIX_FP64 && opt->precision != RIX_MIXED_BF16) return RIX_EINVAL;
   if (opt && (opt->n_slices < 0 || opt->n_slices > 8 || opt->n_slices_regrouped < 0 || opt->n_slices_regrouped > 8))
     return RIX_EINVAL;
+  if (opt && !(opt->product_tau >= 0.0)) return RIX_EINVAL;
 
   rix_ctx *ctx = new rix_ctx();
   if (opt) ctx->opt = *opt;
@@ -948,6 +949,10 @@ extern "C" rix_status rix_setup(const rix_system *sys, const rix_options *opt, r
   if ((s = rix_alloc(ctx, &ctx->d_keepC, np)) != RIX_OK) return fail(s);
   if ((s = rix_alloc(ctx, &ctx->d_keepV, np)) != RIX_OK) return fail(s);
   if ((s = rix_alloc(ctx, &ctx->d_keepD, np)) != RIX_OK) return fail(s);
+  if ((s = rix_alloc(ctx, &ctx->d_normC, np)) != RIX_OK) return fail(s);
+  if ((s = rix_alloc(ctx, &ctx->d_normV, np)) != RIX_OK) return fail(s);
+  if ((s = rix_alloc(ctx, &ctx->d_normD, np)) != RIX_OK) return fail(s);
+  if ((s = rix_alloc(ctx, &ctx->d_maxCatom, ctx->nat)) != RIX_OK) return fail(s);
   {
     // pair vectors (the geometry the force and stress chain differentiates through)
     std::vector<double> rv(3 * (size_t)np);
@@ -1021,8 +1026,10 @@ extern "C" rix_status rix_set_CV(rix_ctx *ctx, const double *C, const double *V,
     return RIX_ENOTSYM;
   }
   ctx->fwd_valid = false;
-  if ((s = rix_launch_flags(ctx, ctx->d_C, ctx->d_offC, ctx->np, ctx->d_keepC, st)) != RIX_OK) return s;
-  if ((s = rix_launch_flags(ctx, ctx->d_V, ctx->d_offV, ctx->np, ctx->d_keepV, st)) != RIX_OK) return s;
+  if ((s = rix_launch_flags(ctx, ctx->d_C, ctx->d_offC, ctx->np, ctx->d_keepC, st, ctx->d_normC)) != RIX_OK) return s;
+  if ((s = rix_launch_flags(ctx, ctx->d_V, ctx->d_offV, ctx->np, ctx->d_keepV, st, ctx->d_normV)) != RIX_OK) return s;
+  if (ctx->opt.product_tau > 0 && (s = rix_launch_atom_max(ctx, ctx->d_normC, ctx->d_maxCatom, st)) != RIX_OK)
+    return s;
   ctx->have_cv = true;
   return RIX_OK;
 }

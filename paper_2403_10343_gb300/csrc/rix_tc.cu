@@ -1057,15 +1057,18 @@ struct SrcAcc {
 };
 
 // live[r] = 1 if any pair of row tile r has a kept V and a kept D block
+// (product screening: a pair (B, G') also counts as dead when |V| |D| times the largest C
+// block of G' is below the product threshold)
 __global__ void k_rt_live(int64_t n, const int2 *rt, const int32_t *rtq, const uint8_t *keepV, const uint8_t *keepD,
-                          uint8_t *live) {
+                          const int32_t *pB, const float *maxCatom, rix::PScreen ps, uint8_t *live) {
   const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= n) return;
   const int2 e = rt[r];
   uint8_t v = 0;
   for (int i = 0; i < e.y; i++) {
     const int q = rtq[e.x + i];
-    v |= keepV[q] & keepD[q];
+    const bool small = ps.tau > 0.f && ps.nV[q] * ps.nD[q] * maxCatom[pB[q]] < ps.tau;
+    v |= keepV[q] & keepD[q] & (uint8_t)!small;
   }
   live[r] = v;
 }
@@ -1666,8 +1669,9 @@ rix_status rix_mixed_z(rix_ctx *ctx, int blk, int64_t zbase, const double *D, cu
   const Operand rows{ctx->d_V, 0, D, ctx->d_keepV, ctx->d_keepD};
   const Operand cols{ctx->d_C, 0, nullptr, ctx->d_keepC, nullptr};
   if (pl->n_rt > 0) {
-    rixtc::k_rt_live<<<(unsigned)((pl->n_rt + 255) / 256), 256, 0, st>>>(pl->n_rt, pl->d_rt, pl->d_rtq, ctx->d_keepV,
-                                                                         ctx->d_keepD, pl->d_rtlive);
+    rixtc::k_rt_live<<<(unsigned)((pl->n_rt + 255) / 256), 256, 0, st>>>(
+        pl->n_rt, pl->d_rt, pl->d_rtq, ctx->d_keepV, ctx->d_keepD, ctx->d_pB, ctx->d_maxCatom, rix_pscreen(ctx),
+        pl->d_rtlive);
   }
   for (size_t g = 0; g + 1 < pl->grp.size(); g++) {
     if (pl->grp_blk[g] != blk) continue;
@@ -2185,7 +2189,7 @@ struct TTColAcc {
 // One warp per T block.
 __global__ void k_tt_mask(int64_t n2, const int64_t *ptrT, const int2 *LT, const int32_t *pB, const int32_t *atomB2,
                           const int32_t *nb, const uint8_t *keepC, const uint8_t *keepD, const int32_t *kpos1,
-                          const int2 *tmask, const int32_t *tmw, unsigned long long *mask) {
+                          const int2 *tmask, const int32_t *tmw, rix::PScreen ps, unsigned long long *mask) {
   const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (t >= n2) return;
@@ -2195,7 +2199,7 @@ __global__ void k_tt_mask(int64_t n2, const int64_t *ptrT, const int2 *LT, const
   const int nt0 = tm.x / TN, nt1 = (tm.x + nb[atomB2[t]] - 1) / TN;
   for (int64_t e = ptrT[t] + lane; e < ptrT[t + 1]; e += 32) {
     const int2 en = LT[e];
-    if (!keepC[en.x] || !keepD[en.y]) continue;
+    if (!keepC[en.x] || !keepD[en.y] || ps.drop2(en.x, en.y)) continue;
     const int k0 = kpos1[en.x];
     const int c0 = k0 / KC, c1 = (k0 + nb[pB[en.x]] - 1) / KC;
     for (int nt = nt0; nt <= nt1; nt++)
@@ -2456,7 +2460,7 @@ rix_status rix_mixed_T(rix_ctx *ctx, int b, int64_t tbase, const double *D, cuda
     RIX_CUDA_TRY(ctx, cudaMemsetAsync(pl->d_mask, 0, sizeof(unsigned long long) * pl->n_mask, st));
     k_tt_mask<<<(unsigned)((ctx->n2 * 32 + 255) / 256), 256, 0, st>>>(
         ctx->n2, ctx->d_ptrT, ctx->d_LT, ctx->d_pB, ctx->d_atomB2, ctx->d_nb, ctx->d_keepC, ctx->d_keepD,
-        pl->d_kpos1, pl->d_tmask, pl->d_tmw, pl->d_mask);
+        pl->d_kpos1, pl->d_tmask, pl->d_tmw, rix_pscreen(ctx), pl->d_mask);
   }
   for (size_t g = 0; g + 1 < pl->grp_prob.size(); g++) {
     if (pl->grp_blk[g] != b || pl->grp_prob[g + 1] == pl->grp_prob[g]) continue;
