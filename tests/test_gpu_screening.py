@@ -50,7 +50,7 @@ def test_product_screening(prec):
     o.set_data(pk.C, pk.V, pk.D)
     kr = o.kpattern(ROWS)
     Kr = o.build_K()
-    for ptau in (1e-12, 1e-9):
+    for ptau in (1e-10, 1e-8):
         K, E, f, _ = _run(s, pk, prec, ptau)
         sub_keys, sub = rows_of(s, keys, K, ROWS)
         assert np.array_equal(sub_keys, kr)
