@@ -130,6 +130,12 @@ typedef struct {
                                       block of G').  An approximation whose error is the skipped
                                       products'; 0 = off (only input blocks below screen_tau are
                                       dropped).  The adjoint does not apply it. */
+  int32_t deterministic;           /* mixed mode: 1 = bitwise reproducible builds.  The tensor-core
+                                      contributions to K are added as 128-bit fixed-point integers
+                                      (units of 2^-80, |K| < 2^47; integer addition does not depend on
+                                      order) instead of FP64 atomics, and the term-4 intermediate runs
+                                      on the output-stationary FP64 kernel.  (The FP64 path is always
+                                      reproducible.) */
 } rix_options;
 
 typedef struct {

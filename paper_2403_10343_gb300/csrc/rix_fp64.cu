@@ -447,18 +447,25 @@ __global__ void __launch_bounds__(NT) k_X34(const int32_t *ord, const int64_t *p
 }
 
 // ------------------------------------------------------------------ K = X + X^T (image flipped)
-// K(A,E,n) = X(A,E,n) + X(E,A,-n)^T (accumulate: added to K)
+// K(A,E,n) = X(A,E,n) + X(E,A,-n)^T (accumulate: added to K); a deterministic mixed
+// build keeps the tensor-core part of X in 128-bit fixed point (X128) beside the FP64 part
 __global__ void k_sym(int64_t nk, const int32_t *atomA3, const int32_t *atomB3, const int32_t *partner3,
-                      const int32_t *nb, const int64_t *offK, const double *__restrict__ X, double *K,
-                      int accumulate) {
+                      const int32_t *nb, const int64_t *offK, const double *__restrict__ X,
+                      const unsigned long long *X128, double *K, int accumulate) {
   const int64_t x = blockIdx.x;
   if (x >= nk) return;
   const int nbA = nb[atomA3[x]], nbE = nb[atomB3[x]];
-  const double *xa = X + offK[x], *xb = X + offK[partner3[x]];
-  double *k = K + offK[x];
+  const int64_t oa = offK[x], ob = offK[partner3[x]];
+  double *k = K + oa;
   for (int el = threadIdx.x; el < nbA * nbE; el += blockDim.x) {
     const int i = el / nbE, l = el - i * nbE;
-    const double v = xa[el] + xb[l * nbA + i];
+    const int64_t ea = oa + el, eb = ob + l * nbA + i;
+    double va = X[ea], vb = X[eb];
+    if (X128) {
+      va += from_x128(X128 + 2 * ea);
+      vb += from_x128(X128 + 2 * eb);
+    }
+    const double v = va + vb;
     k[el] = accumulate ? k[el] + v : v;
   }
 }
@@ -664,6 +671,8 @@ rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t
   if ((s = rix_launch_flags(ctx, D, ctx->d_offD, ctx->np, ctx->d_keepD, st, ctx->d_normD)) != RIX_OK) return s;
   if ((s = rix_prof_mark(ctx, 1, st)) != RIX_OK) return s;
   RIX_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_X, 0, sizeof(double) * ctx->offK[ctx->nk], st));
+  if (ctx->d_X128)
+    RIX_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_X128, 0, 2 * sizeof(unsigned long long) * ctx->offK[ctx->nk], st));
   // terms 1 and 2, one block of row atoms at a time (T resident for the block)
   for (int b = 0; b < ctx->nblk; b++) {
     const int64_t tbase = ctx->blk_base[b];
@@ -701,7 +710,7 @@ rix_status rix_fp64_build(rix_ctx *ctx, const double *D, double *K, cudaStream_t
   }
   if ((s = rix_prof_mark(ctx, 7, st)) != RIX_OK) return s;
   k_sym<<<(unsigned)ctx->nk, 128, 0, st>>>(ctx->nk, ctx->d_atomA3, ctx->d_atomB3, ctx->d_partner3, ctx->d_nb,
-                                           ctx->d_offK, ctx->d_X, K, accumulate);
+                                           ctx->d_offK, ctx->d_X, ctx->d_X128, K, accumulate);
   if ((s = last(ctx, "k_sym")) != RIX_OK) return s;
   return rix_prof_mark(ctx, 8, st);
 }

@@ -20,6 +20,38 @@ namespace rix {
 
 // Product screening (rix_options.product_tau): a product of blocks whose max-norms
 // multiply to less than tau is skipped.  tau = 0: off.
+// 128-bit fixed point in units of 2^-X128_FRAC (deterministic accumulation: integer
+// addition does not depend on the order of the additions).  |x| < 2^(127 - X128_FRAC).
+constexpr int X128_FRAC = 80;
+
+// x * 2^X128_FRAC as a 128-bit integer (truncated toward minus infinity below the unit)
+__device__ __forceinline__ __int128 to_x128(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0) return 0;  // zero and subnormals lie below the unit
+  const long long m = (long long)((b & ((1ull << 52) - 1)) | (1ull << 52));
+  const int sh = ex - 1075 + X128_FRAC;  // x = m 2^(ex - 1075)
+  __int128 v;
+  if (sh >= 0) v = sh < 74 ? ((__int128)m << sh) : ((__int128)m << 74);  // beyond the range: saturate
+  else v = sh > -64 ? (__int128)(m >> -sh) : 0;
+  return (b >> 63) ? -v : v;
+}
+
+// the value of a 128-bit fixed-point number (two roundings, the same for the same bits)
+__device__ __forceinline__ double from_x128(const unsigned long long *p) {
+  const long long hi = (long long)p[1];
+  const unsigned long long lo = p[0];
+  return (double)hi * 0x1p-16 + (double)lo * 0x1p-80;
+}
+
+// *p += v (two 64-bit atomics; the carries out of the low word are counted exactly)
+__device__ __forceinline__ void add_x128(unsigned long long *p, __int128 v) {
+  const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+  const unsigned long long old = atomicAdd(p, lo);
+  const unsigned long long h = hi + (old + lo < old ? 1ull : 0ull);
+  if (h) atomicAdd(p + 1, h);
+}
+
 struct PScreen {
   const float *nC, *nV, *nD;
   float tau;
@@ -124,6 +156,7 @@ struct rix_ctx {
   float *d_maxCatom = nullptr;          // per atom G: the largest norm of its C blocks (G, .)
   double *d_T = nullptr, *d_Z = nullptr, *d_U = nullptr, *d_X = nullptr;
   double *d_epart = nullptr;            // energy partial sums
+  unsigned long long *d_X128 = nullptr; // deterministic mixed builds: tensor-core part of X, 128-bit fixed point
   int32_t *d_flag = nullptr;            // device status word
   int64_t n_epart = 0;
   // fold-gamma groups (consecutive K blocks with the same atom pair)

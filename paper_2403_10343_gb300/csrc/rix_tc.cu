@@ -464,9 +464,18 @@ struct GemmArgs {
   // zero, (Kpad / 32 + 63) / 64 words at kmask + tiles[t].w; stages without a bit are skipped
   const unsigned long long *kmask = nullptr;
   unsigned long long *chunks = nullptr;  // profiling: K stages (tile x 32 K) issued times slice pairs, all CTAs
+  unsigned long long *X128 = nullptr;  // deterministic mode: X additions as 128-bit fixed point (2 words each)
   uint64_t wait_ns = WAIT_NS;  // limit of every bounded wait
   int stall = 0;           // 1: the MMA issuer waits on a barrier nothing completes (timeout test)
 };
+
+// X(output block x)[el] += v: an FP64 atomic, or the 128-bit fixed-point addition of a
+// deterministic build
+__device__ __forceinline__ void x_add(const GemmArgs &g, int x, int64_t el, double v) {
+  const int64_t o = g.offK[x] + el;
+  if (g.X128) rix::add_x128(g.X128 + 2 * o, rix::to_x128(v));
+  else atomicAdd(g.X + o, v);
+}
 
 // Bits the fixed-point sum needs: products below 2^14, at most Kpad of them in
 // the leading diagonal, scaled up by 7(S-1), plus sign and the lower
@@ -743,7 +752,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
                   const int4 ci = g.colinfo[pr->coloff + gc];  // (l, Q, nbE, naE)
                   if (ci.x >= 0) {
                     if (ci.x != lcur) {
-                      if (lcur >= 0) atomicAdd(xb + (int64_t)i * nbE + lcur, g.oscale * part);
+                      if (lcur >= 0) x_add(g, qi.x, (int64_t)i * nbE + lcur, g.oscale * part);
                       lcur = ci.x;
                       nbE = ci.z;
                       part = 0.0;
@@ -753,7 +762,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
                   }
                 }
               }
-              if (lcur >= 0) atomicAdd(xb + (int64_t)i * nbE + lcur, g.oscale * part);
+              if (lcur >= 0) x_add(g, qi.x, (int64_t)i * nbE + lcur, g.oscale * part);
             }
           }
         } else {
@@ -768,7 +777,9 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
                 if (ci.x >= 0) {
                   const int sc = er + geB[gc] - 7 * (S + 1) + drop;
                   const double v = fixed_to_double(acc[n], sc);
-                  atomicAdd(g.X + (g.offK[xrow[ci.x]] - g.xshift) + (int64_t)ri.y * ci.z + ci.y, g.oscale * v);
+                  const int64_t o = (g.offK[xrow[ci.x]] - g.xshift) + (int64_t)ri.y * ci.z + ci.y;
+                  if (g.X128) rix::add_x128(g.X128 + 2 * o, rix::to_x128(g.oscale * v));
+                  else atomicAdd(g.X + o, g.oscale * v);
                 }
               }
             }
@@ -1181,7 +1192,9 @@ rix_status plan_host(rix_ctx *ctx, int kind, const std::vector<int64_t> &ptrZ, P
       const double Mp = std::ceil(M / TM) * TM, Np = std::ceil(sE / TN) * TN,
                    Kp = std::ceil(naG * nbG / KC) * KC;
       const double tc = 2.0 * Mp * Np * Kp * npairs;
-      if (sE > 0 && tc / TC_RATE < f64 / FP64_RATE_Z) {
+      // (a deterministic build keeps Z on the output-stationary FP64 kernel: Z adds the
+      // contributions of many middle atoms, which the tensor-core plan does with atomics)
+      if (sE > 0 && tc / TC_RATE < f64 / FP64_RATE_Z && !ctx->opt.deterministic) {
         h.use[g] = 1;
         h.fl64 += f64;
       }
@@ -1508,6 +1521,9 @@ rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
   }
   if ((s = rix_dev_alloc(ctx, (void **)&ctx->d_mx_buf, std::max<int64_t>(buf, 16))) != RIX_OK) return s;
   ctx->d_mx_err = ctx->d_err;
+  if (ctx->opt.deterministic) {
+    if ((s = rix_alloc(ctx, &ctx->d_X128, 2 * ctx->offK[ctx->nk])) != RIX_OK) return s;
+  }
   if ((s = rix_alloc(ctx, &ctx->d_gemm_chunks, 1)) != RIX_OK) return s;
   RIX_CUDA_TRY(ctx, cudaMemset(ctx->d_gemm_chunks, 0, sizeof(unsigned long long)));
   ctx->mx_buf_bytes = buf;
@@ -1581,6 +1597,7 @@ rix_status run_group(rix_ctx *ctx, const rix_mx_plan *pl, size_t g, const Operan
     ga.xshift = oshift;
     ga.ntiles = (int)(t1 - t0);
     ga.row_live = pl->d_rtlive;  // kind 2: skip row tiles of screened (V, D) blocks
+    if (out == ctx->d_X && ctx->d_X128) ga.X128 = ctx->d_X128;  // deterministic: X as 128-bit fixed point
     rix_status ls = launch_gemm(ctx, ga, t1 - t0, S, st);
     if (ls != RIX_OK) return ls;
   }
@@ -2066,6 +2083,7 @@ rix_status rix_mixed_t1(rix_ctx *ctx, int b, int64_t tbase, cudaStream_t st) {
                   pl->d_tiles + t0, pl->d_probs, pl->d_rowinfo, pl->d_colinfo, nullptr, ctx->d_offK, ctx->d_X,
                   1, pl->d_qinfo, ctx->d_V, ctx->d_keepV, 0.5};
       ga.ntiles = (int)(t1 - t0);
+      ga.X128 = ctx->d_X128;  // deterministic builds: 128-bit fixed-point additions
       rix_status ls = launch_gemm(ctx, ga, t1 - t0, S, st);
       if (ls != RIX_OK) return ls;
     }

@@ -38,7 +38,7 @@ class _Options(ctypes.Structure):
                 ("max_workspace_bytes", ctypes.c_int64), ("verbose", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("backward", ctypes.c_int32), ("block_atoms", ctypes.c_int32),
                 ("n_slices_regrouped", ctypes.c_int32), ("reuse_forward", ctypes.c_int32),
-                ("product_tau", ctypes.c_double)]
+                ("product_tau", ctypes.c_double), ("deterministic", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -155,7 +155,8 @@ def _sizes(ctx):
 
 def setup(xyz_bohr, species, nbas, naux, cell_bohr=None, cutoff_bohr=0.0, screen_tau=0.0,
           precision="fp64", n_slices=0, max_workspace_bytes=0, verbose=0, profile=0, backward=0,
-          block_atoms=0, n_slices_regrouped=0, pairs=None, reuse_forward=0, product_tau=0.0):
+          block_atoms=0, n_slices_regrouped=0, pairs=None, reuse_forward=0, product_tau=0.0,
+          deterministic=0):
     """rix_setup: returns an opaque context handle (int).  pairs: optional [n, 5] (A, B, n1, n2, n3)."""
     lib = load()
     keep = [np.ascontiguousarray(xyz_bohr, dtype=np.float64), np.ascontiguousarray(species, dtype=np.int32),
@@ -168,7 +169,8 @@ def setup(xyz_bohr, species, nbas, naux, cell_bohr=None, cutoff_bohr=0.0, screen
                    None if pl is None else pl.ctypes.data)
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     opt = _Options(prec, int(n_slices), int(max_workspace_bytes), int(verbose), int(profile), int(backward),
-                   int(block_atoms), int(n_slices_regrouped), int(reuse_forward), float(product_tau))
+                   int(block_atoms), int(n_slices_regrouped), int(reuse_forward), float(product_tau),
+                   int(deterministic))
     h = ctypes.c_void_p()
     _check(lib.rix_setup(ctypes.byref(sysd), ctypes.byref(opt), ctypes.byref(h)))
     return h.value
@@ -389,10 +391,11 @@ class Exchange:
 
     def __init__(self, xyz_bohr, species, nbas, naux, cell_bohr=None, cutoff_bohr=0.0, screen_tau=0.0,
                  precision="fp64", n_slices=0, max_workspace_bytes=0, verbose=0, profile=0, backward=0,
-                 block_atoms=0, n_slices_regrouped=0, pairs=None, reuse_forward=0, product_tau=0.0):
+                 block_atoms=0, n_slices_regrouped=0, pairs=None, reuse_forward=0, product_tau=0.0,
+                 deterministic=0):
         self.ctx = setup(xyz_bohr, species, nbas, naux, cell_bohr, cutoff_bohr, screen_tau, precision,
                          n_slices, max_workspace_bytes, verbose, profile, backward, block_atoms,
-                         n_slices_regrouped, pairs, reuse_forward, product_tau)
+                         n_slices_regrouped, pairs, reuse_forward, product_tau, deterministic)
         self.c_elems, self.v_elems, self.d_elems, self.k_elems = layout_sizes(self.ctx)
 
     @classmethod

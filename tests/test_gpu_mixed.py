@@ -91,3 +91,22 @@ def test_mixed_full_size_cluster():
     print(f"(H2O)64 mixed vs FP64: K rel err {err:.2e}, dE {E - E64:.2e} Ha")
     assert err < K_TOL
     assert abs(E - E64) < E_TOL_HA
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_deterministic_mixed_builds(cfg):
+    """rix_options.deterministic: the tensor-core contributions to K are added as 128-bit fixed-point
+    integers, so two builds give the same bits; the result keeps the mixed bar against FP64."""
+    s = ri.config(cfg)
+    pk = ri.generate(s)
+    _, _, K64, E64 = _run(s, pk)
+    ex = Exchange.from_system(s, precision="mixed", deterministic=1)
+    ex.set_CV(_dev(pk.C), _dev(pk.V))
+    D = _dev(pk.D)
+    Ks = [ex.build_K(D).cpu().numpy() for _ in range(3)]
+    E = ex.energy(D, ex.build_K(D)).item()
+    assert all(np.array_equal(Ks[0], k) for k in Ks[1:])
+    err = _rel(Ks[0], K64)
+    print(f"config {cfg}: deterministic mixed vs FP64 {err:.2e}, dE {E - E64:.2e} Ha")
+    assert err < K_TOL and abs(E - E64) < E_TOL_HA
+    ex.close()
