@@ -1,4 +1,7 @@
-"""Several independent clusters in one exchange context (one launch per stage).
+"""Several independent systems in one exchange context (one launch per stage).
+
+ClusterBatch places clusters far apart; PeriodicBatch joins periodic cells
+through the union of their pair lists.
 
 Clusters placed further apart than three pair cutoffs share no pair, no
 2-hop and no 3-hop block, so one context over their union computes each
@@ -57,3 +60,60 @@ class ClusterBatch:
         """Element ranges of each cluster in a packed array with block offsets [n+1]."""
         off = np.asarray(offsets)
         return [(int(off[b0]), int(off[b1])) for b0, b1 in block_ranges]
+
+
+class PeriodicBatch:
+    """Several independent periodic cells in one exchange context.
+
+    Cells with different lattices cannot share a cutoff pair builder, but
+    every later stage of the build only follows the pair list and the image
+    vectors n of its pairs.  So the batch hands the context the union of the
+    cells' own pair lists (rix_system.pairs), with the atoms of cell c after
+    those of cell c-1: no pair crosses two cells, every 2- and 3-hop block
+    stays inside one cell with that cell's images, and each cell's K is
+    computed exactly as in a context of its own while every stage is one
+    launch over all cells (one CUDA graph replays the batch).  The union's
+    packed arrays are the cells' packed arrays back to back; E_x of the
+    union is the sum of the cells' (per cell of each).
+
+    cells: list of (xyz [n][3] bohr, species [n], keys) with keys the cell's
+    own sorted pair keys (rix_layout / rix_inputs.pair_list).  The context's
+    cell_bohr only marks it periodic (use the first cell); the force/stress
+    chain, which needs each atom's lattice, is not available on a batch.
+    """
+
+    def __init__(self, cells):
+        if not cells:
+            raise ValueError("no cells")
+        xyz, sp, rows = [], [], []
+        self.atom_offsets = [0]
+        for x, s, keys in cells:
+            x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+            s = np.asarray(s, dtype=np.int32)
+            if len(s) != len(x):
+                raise ValueError("species and coordinates differ in length")
+            k = np.asarray(keys, dtype=np.int64)
+            A = (k >> 44) & 0xFFFFF
+            B = (k >> 24) & 0xFFFFF
+            n = np.stack([((k >> 16) & 0xFF) - 128, ((k >> 8) & 0xFF) - 128, (k & 0xFF) - 128], axis=1)
+            if len(k) and (A.max() >= len(x) or B.max() >= len(x)):
+                raise ValueError("a pair key names an atom outside its cell")
+            off = self.atom_offsets[-1]
+            rows.append(np.concatenate([(A + off)[:, None], (B + off)[:, None], n], axis=1))
+            xyz.append(x)
+            sp.append(s)
+            self.atom_offsets.append(off + len(x))
+        self.xyz = np.concatenate(xyz)
+        self.species = np.concatenate(sp)
+        self.pairs = np.concatenate(rows).astype(np.int32)
+
+    @property
+    def n_cells(self):
+        return len(self.atom_offsets) - 1
+
+    def ranges(self, keys):
+        """Block ranges [first, last) of each cell in a sorted key list (rix_layout keys)."""
+        first_atom = (np.asarray(keys, dtype=np.int64) >> 44) & 0xFFFFF
+        return [(int(np.searchsorted(first_atom, self.atom_offsets[c], side="left")),
+                 int(np.searchsorted(first_atom, self.atom_offsets[c + 1], side="left")))
+                for c in range(self.n_cells)]

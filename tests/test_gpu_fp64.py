@@ -375,3 +375,43 @@ def test_caller_supplied_pair_list():
     assert rel(K.cpu().numpy(), Ko) < K_TOL
     ex.close()
     ex_ref.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_periodic_batch_equals_separate_cells(precision):
+    """Two periodic cells with different lattices in one context (PeriodicBatch): each cell's K blocks
+    equal its own context's (bitwise in FP64), E_x is the sum, one launch per stage for both."""
+    from paper_2403_10343_gb300.batch import PeriodicBatch
+    cells = [_small_waters([[1.0, 1.2, 0.8], [3.9, 3.1, 3.3]], 11, side=6.0, cut=4.5),
+             _small_waters([[1.0, 1.2, 0.8]], 12, side=4.6, cut=4.8)]
+    pks = [ri.generate(s) for s in cells]
+    b = PeriodicBatch([(s.xyz, s.species, pk.keys) for s, pk in zip(cells, pks)])
+    s0 = cells[0]
+    ex = Exchange(b.xyz, b.species, s0.nbas, s0.naux, s0.cell, s0.cutoff, 0.0, precision=precision, pairs=b.pairs)
+    C = np.concatenate([p.C for p in pks])
+    V = np.concatenate([p.V for p in pks])
+    D = np.concatenate([p.D for p in pks])
+    assert (ex.c_elems, ex.v_elems, ex.d_elems) == (C.size, V.size, D.size)
+    ex.set_CV(C, V)
+    Dd = _dev(D)
+    K = ex.build_K(Dd)
+    E = ex.energy(Dd, K).item()
+    K = K.cpu().numpy()
+    keys = ex.k_keys()
+    nb = s0.nbas[b.species].astype(np.int64)
+    A, Ek, _ = ri.unpack_key(keys)
+    koff = np.concatenate([[0], np.cumsum(nb[A] * nb[Ek])])
+    e_sum = 0.0
+    for c, (s, pk) in enumerate(zip(cells, pks)):
+        exs, keys_s, K_s, E_s, _ = run_gpu(s, pk, precision=precision)
+        b0, b1 = b.ranges(keys)[c]
+        assert b1 - b0 == len(keys_s)
+        e0, e1 = int(koff[b0]), int(koff[b1])
+        if precision == "fp64":
+            assert np.array_equal(K[e0:e1], K_s)
+        else:
+            assert rel(K[e0:e1], K_s) < 1e-12
+        e_sum += E_s
+        exs.close()
+    assert abs(E - e_sum) < 1e-12 * abs(e_sum)
+    ex.close()
