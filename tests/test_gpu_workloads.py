@@ -49,7 +49,7 @@ def _perovskite_rows(s):
     names = list(s.species_names)
     h = int(np.nonzero(s.species == names.index("H"))[0][0])
     c = int(np.nonzero(s.species == names.index("C"))[0][0])
-    return [c, h]
+    return sorted([c, h])
 
 
 def _mixed(s, pk):
