@@ -1018,6 +1018,70 @@ __global__ void k_slice_dig(int64_t n0, int64_t n, Acc acc, __nv_bfloat16 *plane
   }
 }
 
+// One pass instead of two: a CTA gathers 8 rows into shared memory (one warp per row,
+// which also takes the row's exponent), then writes their digit planes as k_slice_dig
+// does (lane -> row lane & 7, 8 consecutive K values; the 8 warps take 32-wide K chunks
+// in turn).  For operands whose rows fit: ld = the largest Kpad + 2 doubles per row.
+constexpr int FUSED_KMAX = 3328;  // 8 rows x (3328 + 2) doubles = 208 KB of shared memory
+
+template <class Acc, int S>
+__global__ void __launch_bounds__(256) k_slice_fused(int64_t n0, int64_t n, Acc acc, __nv_bfloat16 *planes, int *e,
+                                                     int ld) {
+  extern __shared__ double sv[];
+  __shared__ int se[8];
+  const int64_t g8 = blockIdx.x;
+  if (g8 * 8 >= n) return;  // n is a multiple of 8
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  {
+    const typename Acc::Row R = acc.row(n0 + g8 * 8 + warp);
+    double *row = sv + (int64_t)warp * ld;
+    int m = -2000;
+    // four elements per lane in flight (their gathers are independent)
+    for (int k = lane; k < R.pr.Kpad; k += 128) {
+      double v[4];
+#pragma unroll
+      for (int j = 0; j < 4; j++) v[j] = k + 32 * j < R.pr.Kpad ? acc.at(R, k + 32 * j) : 0.0;
+#pragma unroll
+      for (int j = 0; j < 4; j++)
+        if (k + 32 * j < R.pr.Kpad) {
+          row[k + 32 * j] = v[j];
+          m = max(m, exp_of(fabs(v[j])));
+        }
+    }
+    for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) {
+      se[warp] = m;
+      e[(acc.is_b ? R.pr.eboff : R.pr.eaoff) + R.r] = m;
+    }
+  }
+  __syncthreads();
+  const int rr8 = lane & 7;
+  const typename Acc::Row R = acc.row(n0 + g8 * 8 + rr8);
+  const int m = se[rr8];
+  const double *row = sv + (int64_t)rr8 * ld;
+  const int trows = acc.is_b ? TN : TM, tbytes = acc.is_b ? B_TILE : A_TILE;
+  const int rows_pad = acc.is_b ? R.pr.Npad : R.pr.Mpad;
+  const int nkt = R.pr.Kpad / KC;
+  char *base = (char *)planes + (acc.is_b ? R.pr.boff : R.pr.aoff);
+  const int64_t plane = (int64_t)(rows_pad / trows) * nkt * tbytes;
+  const int rt = R.r / trows, rr = R.r % trows;
+  for (int k0 = warp * 32 + (lane >> 3) * 8; k0 < R.pr.Kpad; k0 += 256) {
+    uint32_t pk[4][S];
+#pragma unroll
+    for (int j = 0; j < 4; j++) digit_pairs<S>(row[k0 + 2 * j], row[k0 + 2 * j + 1], m, pk[j]);
+    const int64_t off = ((int64_t)rt * nkt + k0 / KC) * tbytes + tile_off(rr, k0 % KC);
+#pragma unroll
+    for (int t = 0; t < S; t++)
+      *reinterpret_cast<uint4 *>(base + t * plane + off) = make_uint4(pk[0][t], pk[1][t], pk[2][t], pk[3][t]);
+  }
+}
+
+// exponents and digit planes of rows [n0, n0 + n) (n a multiple of 8): one fused pass when
+// the longest row (kmax) fits in shared memory, else the exponent pass and the digit pass
+template <class Acc>
+void slice_rows(int64_t n0, int64_t n, const Acc &acc, int S, __nv_bfloat16 *planes, int *e, int kmax,
+                cudaStream_t st);
+
 // k_slice_dig over rows [n0, n0 + n) (n a multiple of 8) for S slices
 template <class Acc>
 void launch_slice_dig(int64_t n0, int64_t n, const Acc &acc, int S, __nv_bfloat16 *planes, const int *e,
@@ -1033,6 +1097,40 @@ void launch_slice_dig(int64_t n0, int64_t n, const Acc &acc, int S, __nv_bfloat1
     case 7: k_slice_dig<Acc, 7><<<grid, 256, 0, st>>>(n0, n, acc, planes, e); break;
     default: k_slice_dig<Acc, 8><<<grid, 256, 0, st>>>(n0, n, acc, planes, e); break;
   }
+}
+
+template <class Acc, int S>
+void launch_fused(int64_t n0, int64_t n, const Acc &acc, __nv_bfloat16 *planes, int *e, int ld, cudaStream_t st) {
+  const size_t smem = (size_t)8 * ld * sizeof(double);
+  static bool attr = false;  // per instantiation
+  if (!attr) {
+    cudaFuncSetAttribute(k_slice_fused<Acc, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         8 * (FUSED_KMAX + 2) * (int)sizeof(double));
+    attr = true;
+  }
+  k_slice_fused<Acc, S><<<(unsigned)(n / 8), 256, smem, st>>>(n0, n, acc, planes, e, ld);
+}
+
+template <class Acc>
+void slice_rows(int64_t n0, int64_t n, const Acc &acc, int S, __nv_bfloat16 *planes, int *e, int kmax,
+                cudaStream_t st) {
+  if (n <= 0) return;
+  if (kmax > 0 && kmax <= FUSED_KMAX) {
+    const int ld = kmax + 2;  // a 16-byte skew between rows against bank conflicts
+    switch (S) {
+      case 1: launch_fused<Acc, 1>(n0, n, acc, planes, e, ld, st); break;
+      case 2: launch_fused<Acc, 2>(n0, n, acc, planes, e, ld, st); break;
+      case 3: launch_fused<Acc, 3>(n0, n, acc, planes, e, ld, st); break;
+      case 4: launch_fused<Acc, 4>(n0, n, acc, planes, e, ld, st); break;
+      case 5: launch_fused<Acc, 5>(n0, n, acc, planes, e, ld, st); break;
+      case 6: launch_fused<Acc, 6>(n0, n, acc, planes, e, ld, st); break;
+      case 7: launch_fused<Acc, 7>(n0, n, acc, planes, e, ld, st); break;
+      default: launch_fused<Acc, 8>(n0, n, acc, planes, e, ld, st); break;
+    }
+    return;
+  }
+  k_slice_exp<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(n0, n, acc, e);
+  launch_slice_dig(n0, n, acc, S, planes, e, st);
 }
 
 // element access of the generic plans (Src records)
@@ -1098,6 +1196,7 @@ __global__ void k_flag_set(int n, const int32_t *idx, uint8_t *flags) {
 struct rix_mx_plan {
   int kind = 0;                          // 0: terms 3+4, 1: term 2, 2: term-4 intermediate Z
   int S = 6;                             // slices of this plan
+  int kmax = 0;                          // longest K (padded) of its problems
   std::vector<int32_t> grp;              // problems [grp[g], grp[g+1])
   std::vector<int32_t> grp_blk;          // memory-plan block of each group (-1: any)
   std::vector<int64_t> tile_seg, row_seg, col_seg;
@@ -1468,6 +1567,7 @@ rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
     }
     pl->tflops = h.tflops;
     pl->fl64 = h.fl64;
+    for (const Prob &pr : h.probs) pl->kmax = std::max(pl->kmax, pr.Kpad);
     tflops += h.tflops;
     ctx->stats.tensor_flops_stage[kind == 0 ? 0 : kind == 1 ? 1 : 3] = h.tflops;
     if ((s = rix_upload(ctx, &pl->d_probs, h.probs)) != RIX_OK) return s;
@@ -1539,8 +1639,11 @@ int32_t rix_launch_count(const rix_ctx *ctx) {
   int32_t n = 2 + 3 * ctx->nblk;
   if (ctx->have_mx) {
     // per group: exponents and digits of both operands, then the GEMM
-    n += 5 * (int32_t)(ctx->mx34->grp.size() - 1) + 5 * (int32_t)(ctx->mx2->grp.size() - 1) +
-         5 * (int32_t)(ctx->mxz->grp.size() - 1) + rix_t1_launches(ctx) + rix_tt_launches(ctx);
+    // per group: the slicing of both operands (one fused kernel each, or two) and the GEMM
+    auto per = [](int kmax) { return kmax <= rixtc::FUSED_KMAX ? 3 : 5; };
+    n += per(ctx->mx34->kmax) * (int32_t)(ctx->mx34->grp.size() - 1) +
+         per(ctx->mx2->kmax) * (int32_t)(ctx->mx2->grp.size() - 1) +
+         per(ctx->mxz->kmax) * (int32_t)(ctx->mxz->grp.size() - 1) + rix_t1_launches(ctx) + rix_tt_launches(ctx);
     if (ctx->n_t1tc < ctx->nat) n += ctx->nblk;  // k_X12 for the other column atoms
     if (ctx->mxz->n_rt > 0) n += ctx->nblk;      // row-tile liveness of the Z plan
   } else {
@@ -1581,13 +1684,11 @@ rix_status run_group(rix_ctx *ctx, const rix_mx_plan *pl, size_t g, const Operan
   __nv_bfloat16 *buf = (__nv_bfloat16 *)ctx->d_mx_buf;
   if (r1 > r0) {
     const SrcAcc a{pl->d_rowprob, pl->d_probs, pl->d_rowsrc, ra.x, ra.shift, ra.x2, ra.keep, ra.keep2, 0};
-    k_slice_exp<<<(unsigned)(((r1 - r0) * 32 + 255) / 256), 256, 0, st>>>(r0, r1 - r0, a, pl->d_eA);
-    launch_slice_dig(r0, r1 - r0, a, S, buf, pl->d_eA, st);
+    slice_rows(r0, r1 - r0, a, S, buf, pl->d_eA, pl->kmax, st);
   }
   if (c1 > c0) {
     const SrcAcc b{pl->d_colprob, pl->d_probs, pl->d_colsrc, cb.x, cb.shift, cb.x2, cb.keep, cb.keep2, 1};
-    k_slice_exp<<<(unsigned)(((c1 - c0) * 32 + 255) / 256), 256, 0, st>>>(c0, c1 - c0, b, pl->d_eB);
-    launch_slice_dig(c0, c1 - c0, b, S, buf, pl->d_eB, st);
+    slice_rows(c0, c1 - c0, b, S, buf, pl->d_eB, pl->kmax, st);
   }
   if (t1 > t0) {
     GemmArgs ga{buf, buf, pl->d_eA, pl->d_eB, nullptr, 0, 0, 0, 0, 0, 0, S, 1, 0, ctx->d_mx_err,
@@ -1808,6 +1909,7 @@ struct T1ColAcc {
 }  // namespace rixtc
 
 struct rix_t1_plan {
+  int kmax = 0;                           // longest K (padded) of its problems
   std::vector<int32_t> grp_prob;          // groups of problems [grp_prob[g], grp_prob[g+1])
   std::vector<int32_t> grp_blk;           // memory-plan block of each group
   std::vector<int64_t> tile_seg, row_seg, col_seg;
@@ -1975,6 +2077,7 @@ rix_status rix_t1_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
   }
   rix_t1_plan *pl = new rix_t1_plan;
   ctx->mx1 = pl;
+  for (const Prob &pr : probs) pl->kmax = std::max(pl->kmax, pr.Kpad);
   pl->fl64 = fl64_tc;
   pl->tflops = tflops;
   const int64_t budget = std::max(maxp, std::min(total, (int64_t)8 << 30));
@@ -2069,14 +2172,12 @@ rix_status rix_mixed_t1(rix_ctx *ctx, int b, int64_t tbase, cudaStream_t st) {
     if (r1 > r0) {
       const T1RowAcc a{pl->d_rowprob, pl->d_probs, pl->d_ext, pl->d_rowinfo, pl->d_qinfo, pl->d_kmap, pl->d_segT,
                        ctx->d_T, tbase};
-      k_slice_exp<<<(unsigned)(((r1 - r0) * 32 + 255) / 256), 256, 0, st>>>(r0, r1 - r0, a, pl->d_eA);
-      launch_slice_dig(r0, r1 - r0, a, S, buf, pl->d_eA, st);
+      slice_rows(r0, r1 - r0, a, S, buf, pl->d_eA, pl->kmax, st);
     }
     if (c1 > c0) {
       const T1ColAcc b{pl->d_colprob, pl->d_probs, pl->d_ext, pl->d_colinfo, pl->d_kmap, pl->d_segC, pl->d_gpair,
                        ctx->d_keepC, ctx->d_C};
-      k_slice_exp<<<(unsigned)(((c1 - c0) * 32 + 255) / 256), 256, 0, st>>>(c0, c1 - c0, b, pl->d_eB);
-      launch_slice_dig(c0, c1 - c0, b, S, buf, pl->d_eB, st);
+      slice_rows(c0, c1 - c0, b, S, buf, pl->d_eB, pl->kmax, st);
     }
     if (t1 > t0) {
       GemmArgs ga{buf, buf, pl->d_eA, pl->d_eB, nullptr, 0, 0, 0, 0, 0, 0, S, 1, 0, ctx->d_mx_err,
@@ -2097,7 +2198,8 @@ rix_status rix_mixed_t1(rix_ctx *ctx, int b, int64_t tbase, cudaStream_t st) {
 }
 
 int32_t rix_t1_launches(const rix_ctx *ctx) {
-  return ctx->mx1 ? 5 * (int32_t)(ctx->mx1->grp_prob.size() - 1) : 0;
+  if (!ctx->mx1) return 0;
+  return (ctx->mx1->kmax <= rixtc::FUSED_KMAX ? 3 : 5) * (int32_t)(ctx->mx1->grp_prob.size() - 1);
 }
 
 // ==========================================================================
@@ -2234,6 +2336,7 @@ __global__ void k_skip_flags(int n, const int32_t *idx, uint8_t *flags) {
 }  // namespace rixtc
 
 struct rix_tt_plan {
+  int kmax = 0;                           // longest K (padded) of its problems
   std::vector<int32_t> grp_prob, grp_blk;
   std::vector<int64_t> tile_seg, row_seg, col_seg;
   int64_t buf_bytes = 0;
@@ -2385,6 +2488,7 @@ rix_status rix_tt_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
   }
   rix_tt_plan *pl = new rix_tt_plan;
   ctx->mxt = pl;
+  for (const Prob &pr : probs) pl->kmax = std::max(pl->kmax, pr.Kpad);
   pl->S = S;
   const int64_t budget = std::max(maxp, std::min(total, (int64_t)8 << 30));
   pl->grp_prob.assign(1, 0);
@@ -2488,14 +2592,12 @@ rix_status rix_mixed_T(rix_ctx *ctx, int b, int64_t tbase, const double *D, cuda
     if (r1 > r0) {
       const TTRowAcc a{pl->d_rowprob, pl->d_probs, pl->d_ext, pl->d_rowinfo, pl->d_kmap, ctx->d_offC, ctx->d_keepC,
                        ctx->d_C};
-      k_slice_exp<<<(unsigned)(((r1 - r0) * 32 + 255) / 256), 256, 0, st>>>(r0, r1 - r0, a, pl->d_eA);
-      launch_slice_dig(r0, r1 - r0, a, S, buf, pl->d_eA, st);
+      slice_rows(r0, r1 - r0, a, S, buf, pl->d_eA, pl->kmax, st);
     }
     if (c1 > c0) {
       const TTColAcc bb{pl->d_colprob, pl->d_probs, pl->d_ext, pl->d_colinfo, pl->d_kmap, ctx->d_ptrT, ctx->d_LT,
                         ctx->d_offD, ctx->d_keepD, D};
-      k_slice_exp<<<(unsigned)(((c1 - c0) * 32 + 255) / 256), 256, 0, st>>>(c0, c1 - c0, bb, pl->d_eB);
-      launch_slice_dig(c0, c1 - c0, bb, S, buf, pl->d_eB, st);
+      slice_rows(c0, c1 - c0, bb, S, buf, pl->d_eB, pl->kmax, st);
     }
     if (t1 > t0) {
       GemmArgs ga{buf, buf, pl->d_eA, pl->d_eB, nullptr, 0, 0, 0, 0, 0, 0, S, 1, 0, ctx->d_mx_err,
@@ -2518,7 +2620,9 @@ rix_status rix_mixed_T(rix_ctx *ctx, int b, int64_t tbase, const double *D, cuda
 }
 
 int32_t rix_tt_launches(const rix_ctx *ctx) {
-  return ctx->mxt ? 5 * (int32_t)(ctx->mxt->grp_prob.size() - 1) + (ctx->mxt->n_mask > 0 ? 1 : 0) : 0;
+  if (!ctx->mxt) return 0;
+  return (ctx->mxt->kmax <= rixtc::FUSED_KMAX ? 3 : 5) * (int32_t)(ctx->mxt->grp_prob.size() - 1) +
+         (ctx->mxt->n_mask > 0 ? 1 : 0);
 }
 
 extern "C" rix_status rix_gemm_profile(rix_ctx *ctx, double *ms, int64_t *launches, int64_t *chunks) {
