@@ -1218,6 +1218,23 @@ struct rix_mx_plan {
 
 namespace {
 
+// The output tiles of one problem, in the order the persistent CTAs take them:
+// the panels of the larger operand outer, so that each of its row (or column)
+// panels is read from memory once while the ~150 tiles in flight share it through
+// L2, and the smaller operand's panels are the ones re-read.  w(mt, nt) fills the
+// tile's fourth field.
+template <class W>
+void push_tiles(std::vector<int4> &tiles, int pidx, int mtn, int ntn, W w) {
+  if (mtn >= ntn) {
+    for (int mt = 0; mt < mtn; mt++)
+      for (int nt = 0; nt < ntn; nt++) tiles.push_back(make_int4(pidx, mt, nt, w(mt, nt)));
+  } else {
+    for (int nt = 0; nt < ntn; nt++)
+      for (int mt = 0; mt < mtn; mt++) tiles.push_back(make_int4(pidx, mt, nt, w(mt, nt)));
+  }
+}
+
+
 using rix::key_a;
 using rix::key_b;
 using rix::key_n;
@@ -1457,8 +1474,7 @@ rix_status plan_host(rix_ctx *ctx, int kind, const std::vector<int64_t> &ptrZ, P
           h.rt.push_back(make_int2(first, (int)h.rtq.size() - first));
         }
       }
-      for (int nt = 0; nt < Npad / TN; nt++)
-        for (int mt = 0; mt < Mpad / TM; mt++) h.tiles.push_back(make_int4(pidx, mt, nt, kind == 2 ? rt0 + mt : 0));
+      push_tiles(h.tiles, pidx, Mpad / TM, Npad / TN, [&](int mt, int) { return kind == 2 ? rt0 + mt : 0; });
       h.probs.push_back(pr);
       h.pbytes.push_back(bytes);
       // Z of terms 3+4 is resident per block of its middle atom; kind 2 rows per block
@@ -2064,8 +2080,7 @@ rix_status rix_t1_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
         colinfo.push_back(make_int4(-1, 0, 1, 1));
         colprob.push_back(pidx);
       }
-      for (int mt = 0; mt < Mpad / TM; mt++)
-        for (int nt = 0; nt < Npad / TN; nt++) tiles.push_back(make_int4(pidx, mt, nt, 0));
+      push_tiles(tiles, pidx, Mpad / TM, Npad / TN, [](int, int) { return 0; });
       probs.push_back(pr);
       ext.push_back(ex);
       pbytes.push_back(bytes);
@@ -2476,8 +2491,7 @@ rix_status rix_tt_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
       colinfo.push_back(make_int4(-1, 0, 1, 0));
       colprob.push_back(pidx);
     }
-    for (int mt = 0; mt < Mpad / TM; mt++)
-      for (int nt = 0; nt < Npad / TN; nt++) tiles.push_back(make_int4(pidx, mt, nt, (int)(mbase + nt * mwords)));
+    push_tiles(tiles, pidx, Mpad / TM, Npad / TN, [&](int, int nt) { return (int)(mbase + nt * mwords); });
     probs.push_back(pr);
     pbytes.push_back(bytes);
     pblk.push_back(blk_of[a]);
