@@ -277,11 +277,10 @@ def max_over_ranks(x, world, dev):
     return t.item()
 
 
-# DRAM bytes per issued slice-pair K stage of k_gemm_sliced (one 128 x 80 tile x 32 K
-# values x one slice pair), from the ncu capture summarised in profiles/ (None: not measured
-# for the kernel as it stands)
+# DRAM bytes per MMA of k_gemm_sliced (one 128 x 80 x 16 product of one slice pair), from the
+# ncu capture summarised in profiles/ (None: not measured for the kernel as it stands)
 GEMM_DRAM_BYTES_PER_STAGE_PAIR = None
-GEMM_STAGE_PAIR_FLOPS = 2.0 * 128 * 80 * 32
+GEMM_STAGE_PAIR_FLOPS = 2.0 * 128 * 80 * 16
 
 
 def measure(args, s, pk, precision, dev, world, steps, warmup, graph, e2e_steps):

@@ -375,9 +375,9 @@ rix_status rix_stage_times(rix_ctx *ctx, double *ms, int32_t n, int32_t *n_build
  * and mixed precision): device time of every k_gemm_sliced launch enqueued
  * since the previous call, from the event pairs around each launch (none are
  * recorded while a stream is being captured), summed into *ms; *launches the
- * number of launches; *chunks the K stages they issued (one output tile of
- * 128 x 80 by 32 K values) times the slice pairs per stage, so that the BF16
- * FLOPs issued are *chunks x 2 x 128 x 80 x 32.  Synchronises on the last event; resets the
+ * number of launches; *chunks the MMAs they issued (one 128 x 80 x 16 product
+ * of one slice pair each), so that the BF16 FLOPs issued are
+ * *chunks x 2 x 128 x 80 x 16.  Synchronises on the last event; resets the
  * counts.  EUNSUPPORTED otherwise. */
 rix_status rix_gemm_profile(rix_ctx *ctx, double *ms, int64_t *launches, int64_t *chunks);
 

@@ -44,12 +44,12 @@ namespace rixtc {
 
 constexpr int TM = 128;         // output rows per tile (one TMEM lane each)
 constexpr int TN = 80;          // output columns per tile
-constexpr int KC = 32;          // K per pipeline stage
+constexpr int KC = 16;          // K per pipeline stage (one MMA K step: short stages keep more of them in flight)
 // Accumulation groups of GROUP K stages (512 K values).  Accumulator a < NACC-1
 // holds diagonal a: pairs (0, a) and (a, 0) with a leading digit (<= 128)
 // and a balanced one (<= 64), and a - 1 pairs of balanced digits (a = 0: the
 // one pair of leading digits), so its sum stays an integer below 2^24.
-constexpr int GROUP = 16;
+constexpr int GROUP = 32;
 constexpr int64_t diag_bound(int a) {  // largest |sum over one K value| of diagonal a
   return a == 0 ? 128 * 128 : 2 * 128 * 64 + (int64_t)(a - 1) * 64 * 64;
 }
@@ -65,7 +65,7 @@ constexpr uint64_t WAIT_NS = 2000000000ull;  // a wait gives up after 2 s
 constexpr int A_TILE = TM * KC * 2;  // 8 KB
 constexpr int B_TILE = TN * KC * 2;  // 5 KB
 
-constexpr int NSTAGE = 3;            // pipeline stages when they fit in shared memory
+constexpr int NSTAGE = 6;            // pipeline stages when they fit in shared memory
 constexpr int SMEM_LIMIT = 227 * 1024;
 
 // stages that fit for S slices, and the dynamic shared memory they need
@@ -461,9 +461,9 @@ struct GemmArgs {
   int ntiles;              // output tiles of the launch (persistent CTAs loop over them)
   const uint8_t *row_live = nullptr;  // batched mode: per row tile (tiles[t].w), 0 = all its rows are zero
   // batched mode: per (problem, column tile) a bit mask of the K stages whose B tile is not all
-  // zero, (Kpad / 32 + 63) / 64 words at kmask + tiles[t].w; stages without a bit are skipped
+  // zero, (Kpad / KC + 63) / 64 words at kmask + tiles[t].w; stages without a bit are skipped
   const unsigned long long *kmask = nullptr;
-  unsigned long long *chunks = nullptr;  // profiling: K stages (tile x 32 K) issued times slice pairs, all CTAs
+  unsigned long long *chunks = nullptr;  // profiling: 128 x 80 x 16 MMAs issued (K stages x K steps x slice pairs)
   unsigned long long *X128 = nullptr;  // deterministic mode: X additions as 128-bit fixed point (2 words each)
   uint64_t wait_ns = WAIT_NS;  // limit of every bounded wait
   int stall = 0;           // 1: the MMA issuer waits on a barrier nothing completes (timeout test)
@@ -623,7 +623,8 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
       if (*(volatile int *)abort_flag) aborted = true;
     }
     issued_chunks = cg;
-    if (g.chunks && cg) atomicAdd(g.chunks, (unsigned long long)cg * (unsigned long long)(S * (S + 1) / 2));
+    if (g.chunks && cg)
+      atomicAdd(g.chunks, (unsigned long long)cg * (unsigned long long)(S * (S + 1) / 2) * (KC / 16));
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------ MMA issuer
     const uint32_t idesc = idesc_bf16(TM, TN);

@@ -96,6 +96,6 @@ def test_tensor_roofline_uses_algorithmic_flops_over_kernel_time():
     assert roof["kernel"] == "k_gemm_sliced" and roof["bound"] == "tensor"
     assert abs(roof["achieved"] - alg / 2e-3 / 1e12) < 1e-24
     assert abs(roof["frac"] - roof["achieved"] / roof["peak"]) < 1e-24
-    issued = 1000.0 * 2 * 128 * 80 * 32
+    issued = 1000.0 * 2 * 128 * 80 * 16
     assert roof["issued_bf16_flops_per_build"] == issued
     assert abs(roof["issued_tflops"] - issued / 2e-3 / 1e12) < 1e-9
