@@ -1019,66 +1019,8 @@ __global__ void k_slice_dig(int64_t n0, int64_t n, Acc acc, __nv_bfloat16 *plane
   }
 }
 
-// One pass instead of two: a CTA gathers 8 rows into shared memory (one warp per row,
-// which also takes the row's exponent), then writes their digit planes as k_slice_dig
-// does (lane -> row lane & 7, 8 consecutive K values; the 8 warps take 32-wide K chunks
-// in turn).  For operands whose rows fit: ld = the largest Kpad + 2 doubles per row.
-constexpr int FUSED_KMAX = 3328;  // 8 rows x (3328 + 2) doubles = 208 KB of shared memory
-
-template <class Acc, int S>
-__global__ void __launch_bounds__(256) k_slice_fused(int64_t n0, int64_t n, Acc acc, __nv_bfloat16 *planes, int *e,
-                                                     int ld) {
-  extern __shared__ double sv[];
-  __shared__ int se[8];
-  const int64_t g8 = blockIdx.x;
-  if (g8 * 8 >= n) return;  // n is a multiple of 8
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  {
-    const typename Acc::Row R = acc.row(n0 + g8 * 8 + warp);
-    double *row = sv + (int64_t)warp * ld;
-    int m = -2000;
-    // four elements per lane in flight (their gathers are independent)
-    for (int k = lane; k < R.pr.Kpad; k += 128) {
-      double v[4];
-#pragma unroll
-      for (int j = 0; j < 4; j++) v[j] = k + 32 * j < R.pr.Kpad ? acc.at(R, k + 32 * j) : 0.0;
-#pragma unroll
-      for (int j = 0; j < 4; j++)
-        if (k + 32 * j < R.pr.Kpad) {
-          row[k + 32 * j] = v[j];
-          m = max(m, exp_of(fabs(v[j])));
-        }
-    }
-    for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) {
-      se[warp] = m;
-      e[(acc.is_b ? R.pr.eboff : R.pr.eaoff) + R.r] = m;
-    }
-  }
-  __syncthreads();
-  const int rr8 = lane & 7;
-  const typename Acc::Row R = acc.row(n0 + g8 * 8 + rr8);
-  const int m = se[rr8];
-  const double *row = sv + (int64_t)rr8 * ld;
-  const int trows = acc.is_b ? TN : TM, tbytes = acc.is_b ? B_TILE : A_TILE;
-  const int rows_pad = acc.is_b ? R.pr.Npad : R.pr.Mpad;
-  const int nkt = R.pr.Kpad / KC;
-  char *base = (char *)planes + (acc.is_b ? R.pr.boff : R.pr.aoff);
-  const int64_t plane = (int64_t)(rows_pad / trows) * nkt * tbytes;
-  const int rt = R.r / trows, rr = R.r % trows;
-  for (int k0 = warp * 32 + (lane >> 3) * 8; k0 < R.pr.Kpad; k0 += 256) {
-    uint32_t pk[4][S];
-#pragma unroll
-    for (int j = 0; j < 4; j++) digit_pairs<S>(row[k0 + 2 * j], row[k0 + 2 * j + 1], m, pk[j]);
-    const int64_t off = ((int64_t)rt * nkt + k0 / KC) * tbytes + tile_off(rr, k0 % KC);
-#pragma unroll
-    for (int t = 0; t < S; t++)
-      *reinterpret_cast<uint4 *>(base + t * plane + off) = make_uint4(pk[0][t], pk[1][t], pk[2][t], pk[3][t]);
-  }
-}
-
-// exponents and digit planes of rows [n0, n0 + n) (n a multiple of 8): one fused pass when
-// the longest row (kmax) fits in shared memory, else the exponent pass and the digit pass
+// exponents and digit planes of rows [n0, n0 + n) (n a multiple of 8): the exponent pass,
+// then the digit pass
 template <class Acc>
 void slice_rows(int64_t n0, int64_t n, const Acc &acc, int S, __nv_bfloat16 *planes, int *e, int kmax,
                 cudaStream_t st);
@@ -1100,36 +1042,10 @@ void launch_slice_dig(int64_t n0, int64_t n, const Acc &acc, int S, __nv_bfloat1
   }
 }
 
-template <class Acc, int S>
-void launch_fused(int64_t n0, int64_t n, const Acc &acc, __nv_bfloat16 *planes, int *e, int ld, cudaStream_t st) {
-  const size_t smem = (size_t)8 * ld * sizeof(double);
-  static bool attr = false;  // per instantiation
-  if (!attr) {
-    cudaFuncSetAttribute(k_slice_fused<Acc, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         8 * (FUSED_KMAX + 2) * (int)sizeof(double));
-    attr = true;
-  }
-  k_slice_fused<Acc, S><<<(unsigned)(n / 8), 256, smem, st>>>(n0, n, acc, planes, e, ld);
-}
-
 template <class Acc>
-void slice_rows(int64_t n0, int64_t n, const Acc &acc, int S, __nv_bfloat16 *planes, int *e, int kmax,
+void slice_rows(int64_t n0, int64_t n, const Acc &acc, int S, __nv_bfloat16 *planes, int *e, int,
                 cudaStream_t st) {
   if (n <= 0) return;
-  if (kmax > 0 && kmax <= FUSED_KMAX) {
-    const int ld = kmax + 2;  // a 16-byte skew between rows against bank conflicts
-    switch (S) {
-      case 1: launch_fused<Acc, 1>(n0, n, acc, planes, e, ld, st); break;
-      case 2: launch_fused<Acc, 2>(n0, n, acc, planes, e, ld, st); break;
-      case 3: launch_fused<Acc, 3>(n0, n, acc, planes, e, ld, st); break;
-      case 4: launch_fused<Acc, 4>(n0, n, acc, planes, e, ld, st); break;
-      case 5: launch_fused<Acc, 5>(n0, n, acc, planes, e, ld, st); break;
-      case 6: launch_fused<Acc, 6>(n0, n, acc, planes, e, ld, st); break;
-      case 7: launch_fused<Acc, 7>(n0, n, acc, planes, e, ld, st); break;
-      default: launch_fused<Acc, 8>(n0, n, acc, planes, e, ld, st); break;
-    }
-    return;
-  }
   k_slice_exp<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(n0, n, acc, e);
   launch_slice_dig(n0, n, acc, S, planes, e, st);
 }
@@ -1656,8 +1572,8 @@ int32_t rix_launch_count(const rix_ctx *ctx) {
   int32_t n = 2 + 3 * ctx->nblk;
   if (ctx->have_mx) {
     // per group: exponents and digits of both operands, then the GEMM
-    // per group: the slicing of both operands (one fused kernel each, or two) and the GEMM
-    auto per = [](int kmax) { return kmax <= rixtc::FUSED_KMAX ? 3 : 5; };
+    // per group: exponents and digits of both operands, then the GEMM
+    auto per = [](int) { return 5; };
     n += per(ctx->mx34->kmax) * (int32_t)(ctx->mx34->grp.size() - 1) +
          per(ctx->mx2->kmax) * (int32_t)(ctx->mx2->grp.size() - 1) +
          per(ctx->mxz->kmax) * (int32_t)(ctx->mxz->grp.size() - 1) + rix_t1_launches(ctx) + rix_tt_launches(ctx);
@@ -2215,7 +2131,7 @@ rix_status rix_mixed_t1(rix_ctx *ctx, int b, int64_t tbase, cudaStream_t st) {
 
 int32_t rix_t1_launches(const rix_ctx *ctx) {
   if (!ctx->mx1) return 0;
-  return (ctx->mx1->kmax <= rixtc::FUSED_KMAX ? 3 : 5) * (int32_t)(ctx->mx1->grp_prob.size() - 1);
+  return 5 * (int32_t)(ctx->mx1->grp_prob.size() - 1);
 }
 
 // ==========================================================================
@@ -2636,7 +2552,7 @@ rix_status rix_mixed_T(rix_ctx *ctx, int b, int64_t tbase, const double *D, cuda
 
 int32_t rix_tt_launches(const rix_ctx *ctx) {
   if (!ctx->mxt) return 0;
-  return (ctx->mxt->kmax <= rixtc::FUSED_KMAX ? 3 : 5) * (int32_t)(ctx->mxt->grp_prob.size() - 1) +
+  return 5 * (int32_t)(ctx->mxt->grp_prob.size() - 1) +
          (ctx->mxt->n_mask > 0 ? 1 : 0);
 }
 
