@@ -1572,11 +1572,8 @@ int32_t rix_launch_count(const rix_ctx *ctx) {
   int32_t n = 2 + 3 * ctx->nblk;
   if (ctx->have_mx) {
     // per group: exponents and digits of both operands, then the GEMM
-    // per group: exponents and digits of both operands, then the GEMM
-    auto per = [](int) { return 5; };
-    n += per(ctx->mx34->kmax) * (int32_t)(ctx->mx34->grp.size() - 1) +
-         per(ctx->mx2->kmax) * (int32_t)(ctx->mx2->grp.size() - 1) +
-         per(ctx->mxz->kmax) * (int32_t)(ctx->mxz->grp.size() - 1) + rix_t1_launches(ctx) + rix_tt_launches(ctx);
+    n += 5 * (int32_t)(ctx->mx34->grp.size() - 1) + 5 * (int32_t)(ctx->mx2->grp.size() - 1) +
+         5 * (int32_t)(ctx->mxz->grp.size() - 1) + rix_t1_launches(ctx) + rix_tt_launches(ctx);
     if (ctx->n_t1tc < ctx->nat) n += ctx->nblk;  // k_X12 for the other column atoms
     if (ctx->mxz->n_rt > 0) n += ctx->nblk;      // row-tile liveness of the Z plan
   } else {
