@@ -219,7 +219,8 @@ def test_ice_3072_atoms_forward_and_adjoint():
     print(f"[{s.name} mixed] directional derivative over 32 entries (h = {h}): FD {fd:.10e}, "
           f"adjoint {an:.10e}, |diff| / sum|g| = {abs(fd - an) / scale:.2e}", flush=True)
     # E_x ~ 1e6 Ha: its rounding (~1e-8 Ha) over 2h bounds what the difference can resolve
-    assert abs(fd - an) <= 1e-4 * scale
+    # (measured 1.7e-7 of sum |g|)
+    assert abs(fd - an) <= 1e-6 * scale
     ex.close()
     del C, V, D
     torch.cuda.empty_cache()
