@@ -44,12 +44,12 @@ namespace rixtc {
 
 constexpr int TM = 128;         // output rows per tile (one TMEM lane each)
 constexpr int TN = 80;          // output columns per tile
-constexpr int KC = 16;          // K per pipeline stage (one MMA K step: short stages keep more of them in flight)
+constexpr int KC = 32;          // K per pipeline stage (two MMA K steps)
 // Accumulation groups of GROUP K stages (512 K values).  Accumulator a < NACC-1
 // holds diagonal a: pairs (0, a) and (a, 0) with a leading digit (<= 128)
 // and a balanced one (<= 64), and a - 1 pairs of balanced digits (a = 0: the
 // one pair of leading digits), so its sum stays an integer below 2^24.
-constexpr int GROUP = 32;
+constexpr int GROUP = 16;
 constexpr int64_t diag_bound(int a) {  // largest |sum over one K value| of diagonal a
   return a == 0 ? 128 * 128 : 2 * 128 * 64 + (int64_t)(a - 1) * 64 * 64;
 }
@@ -65,7 +65,7 @@ constexpr uint64_t WAIT_NS = 2000000000ull;  // a wait gives up after 2 s
 constexpr int A_TILE = TM * KC * 2;  // 8 KB
 constexpr int B_TILE = TN * KC * 2;  // 5 KB
 
-constexpr int NSTAGE = 6;            // pipeline stages when they fit in shared memory
+constexpr int NSTAGE = 3;            // pipeline stages when they fit in shared memory
 constexpr int SMEM_LIMIT = 227 * 1024;
 
 // stages that fit for S slices, and the dynamic shared memory they need

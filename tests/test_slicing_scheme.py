@@ -24,7 +24,7 @@ import struct
 import numpy as np
 import pytest
 
-KC, GROUP = 16, 32  # the kernel's K stage and stages per accumulation group (512 K values)
+KC, GROUP = 32, 16  # the kernel's K stage and stages per accumulation group (512 K values)
 
 
 def row_exponent(row):
