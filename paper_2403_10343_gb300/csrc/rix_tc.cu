@@ -67,14 +67,21 @@ constexpr int B_TILE = TN * KC * 2;  // 5 KB
 
 constexpr int NSTAGE = 3;            // pipeline stages when they fit in shared memory
 constexpr int SMEM_LIMIT = 227 * 1024;
+// Scatter epilogue staging: per drain warp 32 rows x EPI_CW values plus each row's
+// output-block base and in-block row offset
+constexpr int EPI_CW = 4;
+constexpr int EPI_WARP_BYTES = 32 * EPI_CW * 8 + 32 * 8 + 32 * 4;
+constexpr int EPI_BYTES = 8 * EPI_WARP_BYTES;
 
 // stages that fit for S slices, and the dynamic shared memory they need
 __host__ __device__ inline int n_stages(int S) {
   const int st = S * (A_TILE + B_TILE);
-  const int fit = (SMEM_LIMIT - 256) / st;
+  const int fit = (SMEM_LIMIT - 256 - EPI_BYTES) / st;
   return fit >= NSTAGE ? NSTAGE : (fit >= 2 ? fit : 1);
 }
-__host__ __device__ inline int smem_bytes(int S) { return n_stages(S) * S * (A_TILE + B_TILE) + 8 * (2 * NSTAGE + 4) + 16; }
+__host__ __device__ inline int smem_bytes(int S) {
+  return n_stages(S) * S * (A_TILE + B_TILE) + EPI_BYTES + 8 * (2 * NSTAGE + 4) + 16;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -545,11 +552,13 @@ __device__ __forceinline__ TileInfo tile_info(const GemmArgs &g, int t) {
 // tensor memory before they convert and scatter their sums).
 __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  // layout: [stage][A tiles S][B tiles S], then barriers, then TMEM address
+  // layout: [stage][A tiles S][B tiles S], the scatter staging of the drain warps,
+  // then barriers, then TMEM address
   const int S = g.S;
   const int stage_bytes = S * (A_TILE + B_TILE);
   const int nst = n_stages(S);
-  uint64_t *full = (uint64_t *)(smem + nst * stage_bytes);
+  uint8_t *epi = smem + nst * stage_bytes;
+  uint64_t *full = (uint64_t *)(epi + EPI_BYTES);
   uint64_t *empty = full + NSTAGE;
   uint64_t *accfull = empty + NSTAGE;
   uint64_t *accempty = accfull + 1;
@@ -692,7 +701,8 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
 #pragma unroll
       for (int n = 0; n < HN; n++) acc[n] = 0;
       for (int grp = 0; grp < ngroups; grp++, gg++) {
-        if (!mbar_wait(accfull, gg & 1, g.wait_ns)) {
+        // warp-uniform outcome: the tensor-memory loads and the scatter below are warp-collective
+        if (!__all_sync(0xffffffffu, mbar_wait(accfull, gg & 1, g.wait_ns))) {
           atomicExch(abort_flag, 1);
           ok = false;
           break;
@@ -722,7 +732,57 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
       }
       if (!ok) break;
       const int gr = mt * TM + row;
-      if (gr < ti.M) {
+      if (pr && g.mode == 0) {
+        // Batched scatter.  A lane holds one output row; the rows of a warp lie nbE (or nbG)
+        // elements apart in the output, so row-wise additions touch one sector each.  The
+        // warp therefore stages EPI_CW columns of its 32 rows in shared memory and adds them
+        // with the lanes running along the columns: EPI_CW consecutive output elements per
+        // row, a few sectors per warp-wide reduction.
+        uint8_t *wb = epi + (warp - 4) * EPI_WARP_BYTES;
+        double *sv = (double *)wb;
+        int64_t *sxb = (int64_t *)(wb + 32 * EPI_CW * 8);
+        int *sry = (int *)(wb + 32 * EPI_CW * 8 + 32 * 8);
+        int64_t xbase = -1;
+        int ry = 0, er = 0;
+        if (gr < ti.M) {
+          const int2 ri = g.rowinfo[pr->rowoff + gr];
+          if (ri.x >= 0) {
+            xbase = pr->xoff + (int64_t)ri.x * pr->nz;
+            ry = ri.y;
+            er = geA[gr];
+          }
+        }
+        sxb[lane] = xbase;
+        sry[lane] = ry;
+        const int cbase = nt * TN + h * HN;
+#pragma unroll
+        for (int c0 = 0; c0 < HN; c0 += EPI_CW) {
+#pragma unroll
+          for (int j = 0; j < EPI_CW; j++) {
+            const int gc = cbase + c0 + j;
+            double v = 0.0;
+            if (xbase >= 0 && gc < Ncols) v = fixed_to_double(acc[c0 + j], er + geB[gc] - 7 * (S + 1) + drop);
+            sv[lane * EPI_CW + j] = v;
+          }
+          __syncwarp();
+#pragma unroll
+          for (int it = 0; it < EPI_CW; it++) {
+            const int r = it * (32 / EPI_CW) + lane / EPI_CW, j = lane % EPI_CW;
+            const int gc = cbase + c0 + j;
+            const int64_t xb = sxb[r];
+            if (xb >= 0 && gc < Ncols) {
+              const int4 ci = g.colinfo[pr->coloff + gc];
+              if (ci.x >= 0) {
+                const int64_t o = (g.offK[g.xmap[xb + ci.x]] - g.xshift) + (int64_t)sry[r] * ci.z + ci.y;
+                const double v = g.oscale * sv[r * EPI_CW + j];
+                if (g.X128) rix::add_x128(g.X128 + 2 * o, rix::to_x128(v));
+                else atomicAdd(g.X + o, v);
+              }
+            }
+          }
+          __syncwarp();
+        }
+      } else if (gr < ti.M) {
         const int er = geA[gr];
         // fully unrolled with predicates so acc[] stays in registers
         if (!pr) {
@@ -743,7 +803,6 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
             const QInfo qi = g.qinfo[pr->xoff + ri.x];
             if (g.keepV[qi.vpair]) {
               const int P = ri.y / qi.nbA, i = ri.y - P * qi.nbA;
-              double *xb = g.X + g.offK[qi.x];
               int lcur = -1, nbE = 0;
               double part = 0.0;
 #pragma unroll
@@ -764,25 +823,6 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
                 }
               }
               if (lcur >= 0) x_add(g, qi.x, (int64_t)i * nbE + lcur, g.oscale * part);
-            }
-          }
-        } else {
-          const int2 ri = g.rowinfo[pr->rowoff + gr];
-          if (ri.x >= 0) {
-            const int32_t *xrow = g.xmap + pr->xoff + (int64_t)ri.x * pr->nz;
-#pragma unroll
-            for (int n = 0; n < HN; n++) {
-              const int gc = nt * TN + h * HN + n;
-              if (gc < Ncols) {
-                const int4 ci = g.colinfo[pr->coloff + gc];
-                if (ci.x >= 0) {
-                  const int sc = er + geB[gc] - 7 * (S + 1) + drop;
-                  const double v = fixed_to_double(acc[n], sc);
-                  const int64_t o = (g.offK[xrow[ci.x]] - g.xshift) + (int64_t)ri.y * ci.z + ci.y;
-                  if (g.X128) rix::add_x128(g.X128 + 2 * o, rix::to_x128(g.oscale * v));
-                  else atomicAdd(g.X + o, g.oscale * v);
-                }
-              }
             }
           }
         }
@@ -990,6 +1030,19 @@ __device__ __forceinline__ void digit_pairs(double x0, double x1, int e, uint32_
   }
 }
 
+// Element access of the digit pass, eight consecutive K values at a time, and whether
+// the GEMM reads the K stage at all.  Accessors with cheaper forms overload these
+// (found by argument-dependent lookup when the kernel is instantiated).
+template <class Acc>
+__device__ __forceinline__ void load8(const Acc &acc, const typename Acc::Row &R, int k0, double (&v)[8]) {
+#pragma unroll
+  for (int j = 0; j < 8; j++) v[j] = acc.at(R, k0 + j);
+}
+template <class Acc>
+__device__ __forceinline__ bool dig_live(const Acc &, const typename Acc::Row &, int) {
+  return true;
+}
+
 template <class Acc, int S>
 __global__ void k_slice_dig(int64_t n0, int64_t n, Acc acc, __nv_bfloat16 *planes, const int *e) {
   const int64_t g8 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -1005,10 +1058,10 @@ __global__ void k_slice_dig(int64_t n0, int64_t n, Acc acc, __nv_bfloat16 *plane
   const int64_t plane = (int64_t)(rows_pad / trows) * nkt * tbytes;
   const int rt = R.r / trows, rr = R.r % trows;
   for (int k0 = (lane >> 3) * 8; k0 < R.pr.Kpad; k0 += 32) {
+    if (!dig_live(acc, R, k0)) continue;  // a stage the GEMM skips: its tile is never read
     // the eight loads first (independent, so their latencies overlap), then the digits
     double v[8];
-#pragma unroll
-    for (int j = 0; j < 8; j++) v[j] = acc.at(R, k0 + j);
+    load8(acc, R, k0, v);
     uint32_t pk[4][S];
 #pragma unroll
     for (int j = 0; j < 4; j++) digit_pairs<S>(v[2 * j], v[2 * j + 1], m, pk[j]);
@@ -1836,6 +1889,48 @@ struct T1ColAcc {
   }
 };
 
+// Row exponents of the T window once per block: rexp[roff2[t] - rbase + r] = the
+// largest exponent of row r of the 2-hop block T(A', G') (its nbG values), one
+// CTA per block t in [t0, t1).
+__global__ void k_rowexp(int64_t t0, const int64_t *off2, const int64_t *roff2, const int32_t *atomA2,
+                         const int32_t *atomB2, const int32_t *nb, const int32_t *na, const double *T,
+                         int64_t tbase, int64_t rbase, int *rexp) {
+  const int64_t t = t0 + blockIdx.x;
+  const int a = atomA2[t], nbG = nb[atomB2[t]];
+  const int rows = na[a] * nb[a];
+  const double *Tb = T + (off2[t] - tbase);
+  int *out = rexp + (roff2[t] - rbase);
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+    int m = -2000;
+    for (int k = 0; k < nbG; k++) m = max(m, exp_of(fabs(Tb[(int64_t)r * nbG + k])));
+    out[r] = m;
+  }
+}
+
+// Exponents of the term-1 packed rows from the row exponents of their T blocks:
+// the row (A'_q, P, i) of a problem spans the blocks T(A'_q, G'_g) of its ng
+// neighbours G', so its largest exponent is the largest of theirs (the same value
+// the element-wise pass finds: padding and absent blocks hold zeros).
+__global__ void k_t1_exp(int64_t n0, int64_t n, T1RowAcc acc, const int64_t *segR, const int *rexp,
+                         int64_t rbase, int *e) {
+  const int64_t w = n0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= n0 + n) return;
+  const T1RowAcc::Row R = acc.row(w);
+  int m = -2000;
+  if (R.seg) {
+    const int64_t *rs = segR + (R.seg - acc.segT);
+    const int ng = acc.ext[acc.prob_of[w]].ng;
+    const int r = R.P * R.nbA + R.i;
+    for (int g = lane; g < ng; g += 32) {
+      const int64_t so = rs[g];
+      if (so >= 0) m = max(m, rexp[so - rbase + r]);
+    }
+  }
+  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) e[R.pr.eaoff + R.r] = m;
+}
+
 }  // namespace rixtc
 
 struct rix_t1_plan {
@@ -1850,6 +1945,9 @@ struct rix_t1_plan {
   int2 *d_rowinfo = nullptr;
   int4 *d_colinfo = nullptr, *d_tiles = nullptr, *d_kmap = nullptr;
   int64_t *d_rowprob = nullptr, *d_colprob = nullptr, *d_segT = nullptr, *d_segC = nullptr;
+  int64_t *d_segR = nullptr;              // [nq][ng] like d_segT: row offset of T(A'_q, G'_g) in the row exponents
+  int64_t *d_roff2 = nullptr;             // per 2-hop block: its first row among all T rows
+  std::vector<int64_t> roff2;
   int32_t *d_gpair = nullptr;
   QInfo *d_qinfo = nullptr;
   int *d_eA = nullptr, *d_eB = nullptr;
@@ -1904,7 +2002,13 @@ rix_status rix_t1_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
   std::vector<T1Ext> ext;
   std::vector<int2> rowinfo;
   std::vector<int4> colinfo, tiles, kmap;
-  std::vector<int64_t> rowprob, colprob, segT, segC, pbytes;
+  std::vector<int64_t> rowprob, colprob, segT, segR, segC, pbytes;
+  // rows of every 2-hop block T(A', G') (na_A nb_A each) and their prefix offsets
+  std::vector<int64_t> roff2(ctx->n2 + 1, 0);
+  for (int64_t t = 0; t < ctx->n2; t++) {
+    const int a = key_a(ctx->keys2[t]);
+    roff2[t + 1] = roff2[t] + (int64_t)ctx->na_at[a] * ctx->nb_at[a];
+  }
   std::vector<int32_t> gpair, pblk;
   std::vector<QInfo> qinfo;
   int64_t eaoff = 0, eboff = 0, maps = 0, maxp = 0, total = 0;
@@ -1929,7 +2033,7 @@ rix_status rix_t1_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
       total += bytes;
       maxp = std::max(maxp, bytes);
       maps += (int64_t)Mpad * (8 + 8 + 4) + (int64_t)Npad * (16 + 8 + 4) + (int64_t)Kpad * 16 +
-              (int64_t)qs.size() * ng * 8 + (int64_t)ng * 12 + (int64_t)qs.size() * 24 +
+              (int64_t)qs.size() * ng * 16 + (int64_t)ng * 12 + (int64_t)qs.size() * 24 +
               (int64_t)(Mpad / TM) * (Npad / TN) * 16 + (int64_t)(sizeof(Prob) + sizeof(T1Ext));
       tflops += 2.0 * Mpad * Npad * Kpad * npairs;
       if (count_only) continue;
@@ -1975,6 +2079,7 @@ rix_status rix_t1_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
           const int64_t t =
               find_sorted(ctx->keys2, row2[a], row2[a + 1], pair_key(a, ctx->pB[g], d[0], d[1], d[2]));
           segT.push_back(t < 0 ? -1 : ctx->off2[t]);
+          segR.push_back(t < 0 ? -1 : roff2[t]);
         }
         for (int r = 0; r < naA * nbA; r++) {
           rowinfo.push_back(make_int2(qi, r));
@@ -2000,6 +2105,7 @@ rix_status rix_t1_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
       pbytes.push_back(bytes);
       pblk.push_back(b);
     }
+  maps += (ctx->n2 + 1) * 8;  // roff2
   if (count_only) {
     if (bytes_out) *bytes_out = maps + (total ? std::max(maxp, std::min(total, (int64_t)8 << 30)) : 0);
     return RIX_OK;
@@ -2053,6 +2159,9 @@ rix_status rix_t1_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
   if ((s = rix_upload(ctx, &pl->d_rowprob, rowprob)) != RIX_OK) return s;
   if ((s = rix_upload(ctx, &pl->d_colprob, colprob)) != RIX_OK) return s;
   if ((s = rix_upload(ctx, &pl->d_segT, segT)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &pl->d_segR, segR)) != RIX_OK) return s;
+  if ((s = rix_upload(ctx, &pl->d_roff2, roff2)) != RIX_OK) return s;
+  pl->roff2.swap(roff2);
   if ((s = rix_upload(ctx, &pl->d_segC, segC)) != RIX_OK) return s;
   if ((s = rix_upload(ctx, &pl->d_gpair, gpair)) != RIX_OK) return s;
   if ((s = rix_upload(ctx, &pl->d_qinfo, qinfo)) != RIX_OK) return s;
@@ -2093,15 +2202,28 @@ rix_status rix_mixed_t1(rix_ctx *ctx, int b, int64_t tbase, cudaStream_t st) {
   gemm_attr();
   const int S = rix_plan_slices(ctx, 3);
   __nv_bfloat16 *buf = (__nv_bfloat16 *)ctx->d_mx_buf;
+  // row exponents of the block's T window, kept in the Z buffer (Z of this block is
+  // built after term 1; the T window has at most as many rows as elements)
+  const int64_t w0 = ctx->row2[ctx->blk_atom[b]], w1 = ctx->row2[ctx->blk_atom[b + 1]];
+  const int64_t rbase = pl->roff2[w0];
+  int *rexp = (int *)ctx->d_Z;
+  bool have_rexp = false;
   for (size_t g = 0; g + 1 < pl->grp_prob.size(); g++) {
     if (pl->grp_blk[g] != b || pl->grp_prob[g + 1] == pl->grp_prob[g]) continue;
     const int64_t r0 = pl->row_seg[g], r1 = pl->row_seg[g + 1];
     const int64_t c0 = pl->col_seg[g], c1 = pl->col_seg[g + 1];
     const int64_t t0 = pl->tile_seg[g], t1 = pl->tile_seg[g + 1];
     if (r1 > r0) {
+      if (!have_rexp && w1 > w0) {
+        k_rowexp<<<(unsigned)(w1 - w0), 128, 0, st>>>(w0, ctx->d_off2, pl->d_roff2, ctx->d_atomA2, ctx->d_atomB2,
+                                                      ctx->d_nb, ctx->d_na, ctx->d_T, tbase, rbase, rexp);
+        have_rexp = true;
+      }
       const T1RowAcc a{pl->d_rowprob, pl->d_probs, pl->d_ext, pl->d_rowinfo, pl->d_qinfo, pl->d_kmap, pl->d_segT,
                        ctx->d_T, tbase};
-      slice_rows(r0, r1 - r0, a, S, buf, pl->d_eA, pl->kmax, st);
+      k_t1_exp<<<(unsigned)(((r1 - r0) * 32 + 255) / 256), 256, 0, st>>>(r0, r1 - r0, a, pl->d_segR, rexp, rbase,
+                                                                          pl->d_eA);
+      launch_slice_dig(r0, r1 - r0, a, S, buf, pl->d_eA, st);
     }
     if (c1 > c0) {
       const T1ColAcc b{pl->d_colprob, pl->d_probs, pl->d_ext, pl->d_colinfo, pl->d_kmap, pl->d_segC, pl->d_gpair,
@@ -2128,7 +2250,15 @@ rix_status rix_mixed_t1(rix_ctx *ctx, int b, int64_t tbase, cudaStream_t st) {
 
 int32_t rix_t1_launches(const rix_ctx *ctx) {
   if (!ctx->mx1) return 0;
-  return 5 * (int32_t)(ctx->mx1->grp_prob.size() - 1);
+  const rix_t1_plan *pl = ctx->mx1;
+  int32_t n = 0, last_blk = -1;
+  for (size_t g = 0; g + 1 < pl->grp_prob.size(); g++) {
+    if (pl->grp_prob[g + 1] == pl->grp_prob[g]) continue;
+    n += 5;  // row exponents and digits, column exponents and digits, the GEMM
+    if (pl->grp_blk[g] != last_blk) n++;  // k_rowexp, once per block (groups are in block order)
+    last_blk = pl->grp_blk[g];
+  }
+  return n;
 }
 
 // ==========================================================================
@@ -2143,7 +2273,8 @@ namespace rixtc {
 struct TTExt {
   int64_t koff;    // kmap offset (Kpad entries: (g, j, nb_B, -), g < 0 past K)
   int64_t p1base;  // first pair (A, .) of the row atom
-  int32_t nbA, pad_;
+  int32_t nbA;
+  int32_t mbase;   // first K-stage mask word of the problem (column tile nt at mbase + nt * words)
 };
 
 // rows: element (P, i ; g, j) = C(A, B'_g)[P][i][j]
@@ -2196,6 +2327,7 @@ struct TTColAcc {
   const int64_t *offD;
   const uint8_t *keepD;
   const double *D;
+  const unsigned long long *mask;  // K-stage masks of the plan (nullptr: every stage live)
   static constexpr int is_b = 1;
   struct Row {
     Prob pr;
@@ -2204,6 +2336,18 @@ struct TTColAcc {
     int r;
     int64_t e0, e1;
   };
+  // offset of D(B'_g, G') for problem atom pair p1 = (A, B'_g), -1 if that product is absent or screened
+  __device__ int64_t dblock(const Row &R, int p1) const {
+    int64_t lo = R.e0, hi = R.e1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (LT[mid].x < p1) lo = mid + 1;
+      else hi = mid;
+    }
+    if (lo >= R.e1 || LT[lo].x != p1) return -1;
+    const int pD = LT[lo].y;
+    return keepD[pD] ? offD[pD] : -1;
+  }
   __device__ Row row(int64_t w) const {
     Row R;
     const int64_t pi = prob_of[w];
@@ -2219,19 +2363,72 @@ struct TTColAcc {
     if (R.ci.x < 0) return 0.0;
     const int4 km = kmap[R.ex.koff + kk];
     if (km.x < 0) return 0.0;
-    const int p1 = (int)(R.ex.p1base + km.x);
-    int64_t lo = R.e0, hi = R.e1;
-    while (lo < hi) {
-      const int64_t mid = (lo + hi) >> 1;
-      if (LT[mid].x < p1) lo = mid + 1;
-      else hi = mid;
-    }
-    if (lo >= R.e1 || LT[lo].x != p1) return 0.0;
-    const int pD = LT[lo].y;
-    if (!keepD[pD]) return 0.0;
-    return D[offD[pD] + (int64_t)km.y * R.ci.z + R.ci.y];  // j nbG + k
+    const int64_t o = dblock(R, (int)(R.ex.p1base + km.x));
+    return o < 0 ? 0.0 : D[o + (int64_t)km.y * R.ci.z + R.ci.y];  // j nbG + k
   }
 };
+
+// eight consecutive K values of a T column: one search per B' block met (not per value)
+__device__ __forceinline__ void load8(const TTColAcc &acc, const TTColAcc::Row &R, int k0, double (&v)[8]) {
+  int lastg = -1;
+  int64_t o = -1;
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    v[j] = 0.0;
+    if (R.ci.x < 0) continue;
+    const int4 km = acc.kmap[R.ex.koff + k0 + j];
+    if (km.x < 0) continue;
+    if (km.x != lastg) {
+      lastg = km.x;
+      o = acc.dblock(R, (int)(R.ex.p1base + km.x));
+    }
+    if (o >= 0) v[j] = acc.D[o + (int64_t)km.y * R.ci.z + R.ci.y];
+  }
+}
+
+// the GEMM skips the K stages of a column tile that meet no kept D block
+__device__ __forceinline__ bool dig_live(const TTColAcc &acc, const TTColAcc::Row &R, int k0) {
+  if (!acc.mask) return true;
+  const int c = k0 / KC, words = (R.pr.Kpad / KC + 63) / 64;
+  const unsigned long long w = acc.mask[R.ex.mbase + (int64_t)(R.r / TN) * words + (c >> 6)];
+  return (w >> (c & 63)) & 1ull;
+}
+
+// Column maxima of the D blocks for the T columns' exponents: dcolexp[dcoff[p] + k] =
+// the largest exponent of column k of D(pair p) (one warp per pair, lanes over k).
+__global__ void k_dcolexp(int64_t np, const int32_t *pA, const int32_t *pB, const int32_t *nb, const double *D,
+                          const int64_t *offD, const int64_t *dcoff, int *dcolexp) {
+  const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (p >= np) return;
+  const int nbB = nb[pA[p]], nbG = nb[pB[p]];
+  const double *Db = D + offD[p];
+  for (int k = lane; k < nbG; k += 32) {
+    int m = -2000;
+    for (int j = 0; j < nbB; j++) m = max(m, exp_of(fabs(Db[(int64_t)j * nbG + k])));
+    dcolexp[dcoff[p] + k] = m;
+  }
+}
+
+// Exponents of the T plan's columns (G'_t, k): the largest over the kept D blocks
+// D(B', G'_t) of the column's T block (its product list) of their column-k maxima,
+// which is the largest exponent over the column's K values (the rest are zero).
+__global__ void k_tt_colexp(int64_t n0, int64_t n, TTColAcc acc, const int64_t *dcoff, const int *dcolexp,
+                            int *e) {
+  const int64_t w = n0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= n0 + n) return;
+  const TTColAcc::Row R = acc.row(w);
+  int m = -2000;
+  if (R.ci.x >= 0) {
+    for (int64_t x = R.e0 + lane; x < R.e1; x += 32) {
+      const int pD = acc.LT[x].y;
+      if (acc.keepD[pD]) m = max(m, dcolexp[dcoff[pD] + R.ci.y]);
+    }
+  }
+  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) e[R.pr.eboff + R.r] = m;
+}
 
 // K-stage masks of the T plan: for every product (C(A,B'), D(B',G')) of a T block with kept
 // blocks, the stages covering B' in problem A and the column tiles covering G' get their bit.
@@ -2284,6 +2481,8 @@ struct rix_tt_plan {
   int32_t *d_kpos1 = nullptr;   // per pair (A, B'): K offset of B' in problem A (-1: A not here)
   int2 *d_tmask = nullptr;      // per T block (A, G'): (column offset in problem A, mask base), -1 if none
   int32_t *d_tmw = nullptr;     // per T block: mask words per column tile of its problem
+  int64_t *d_dcoff = nullptr;   // per pair p: offset of its nb(pB) column exponents
+  int *d_dcolexp = nullptr;     // column exponents of the D blocks, per build
 };
 
 // T plan: decide per row atom, build one problem per chosen atom (its block is the atom's).
@@ -2364,8 +2563,8 @@ rix_status rix_tt_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
     pr.xoff = (int64_t)xmap.size();
     eaoff += Mpad;
     eboff += Npad;
-    ext.push_back(TTExt{(int64_t)kmap.size(), row1[a], nbA, 0});
     const int64_t mbase = n_mask;
+    ext.push_back(TTExt{(int64_t)kmap.size(), row1[a], nbA, (int32_t)mbase});
     n_mask += (int64_t)(Npad / TN) * mwords;
     {
       int kp = 0;
@@ -2410,6 +2609,7 @@ rix_status rix_tt_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
     pbytes.push_back(bytes);
     pblk.push_back(blk_of[a]);
   }
+  maps += (ctx->np + 1) * 8 + (int64_t)ctx->np * 64 * 4;  // dcoff and (at most) the D column exponents
   if (count_only) {
     if (bytes_out) *bytes_out = maps + (total ? std::max(maxp, std::min(total, (int64_t)8 << 30)) : 0) + nat;
     return RIX_OK;
@@ -2471,6 +2671,12 @@ rix_status rix_tt_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
   }
   if ((s = rix_alloc(ctx, &pl->d_eA, std::max<int64_t>(eaoff, 1))) != RIX_OK) return s;
   if ((s = rix_alloc(ctx, &pl->d_eB, std::max<int64_t>(eboff, 1))) != RIX_OK) return s;
+  {
+    std::vector<int64_t> dcoff(ctx->np + 1, 0);
+    for (int64_t p = 0; p < ctx->np; p++) dcoff[p + 1] = dcoff[p] + ctx->nb_at[ctx->pB[p]];
+    if ((s = rix_upload(ctx, &pl->d_dcoff, dcoff)) != RIX_OK) return s;
+    if ((s = rix_alloc(ctx, &pl->d_dcolexp, std::max<int64_t>(dcoff[ctx->np], 1))) != RIX_OK) return s;
+  }
   std::vector<int32_t> on;
   for (int a = 0; a < nat; a++)
     if (use[a]) on.push_back(a);
@@ -2512,6 +2718,9 @@ rix_status rix_mixed_T(rix_ctx *ctx, int b, int64_t tbase, const double *D, cuda
         ctx->n2, ctx->d_ptrT, ctx->d_LT, ctx->d_pB, ctx->d_atomB2, ctx->d_nb, ctx->d_keepC, ctx->d_keepD,
         pl->d_kpos1, pl->d_tmask, pl->d_tmw, rix_pscreen(ctx), pl->d_mask);
   }
+  if (b == 0 && !pl->grp_blk.empty())
+    k_dcolexp<<<(unsigned)((ctx->np * 32 + 255) / 256), 256, 0, st>>>(ctx->np, ctx->d_pA, ctx->d_pB, ctx->d_nb, D,
+                                                                      ctx->d_offD, pl->d_dcoff, pl->d_dcolexp);
   for (size_t g = 0; g + 1 < pl->grp_prob.size(); g++) {
     if (pl->grp_blk[g] != b || pl->grp_prob[g + 1] == pl->grp_prob[g]) continue;
     const int64_t r0 = pl->row_seg[g], r1 = pl->row_seg[g + 1];
@@ -2524,8 +2733,10 @@ rix_status rix_mixed_T(rix_ctx *ctx, int b, int64_t tbase, const double *D, cuda
     }
     if (c1 > c0) {
       const TTColAcc bb{pl->d_colprob, pl->d_probs, pl->d_ext, pl->d_colinfo, pl->d_kmap, ctx->d_ptrT, ctx->d_LT,
-                        ctx->d_offD, ctx->d_keepD, D};
-      slice_rows(c0, c1 - c0, bb, S, buf, pl->d_eB, pl->kmax, st);
+                        ctx->d_offD, ctx->d_keepD, D, pl->n_mask > 0 ? pl->d_mask : nullptr};
+      k_tt_colexp<<<(unsigned)(((c1 - c0) * 32 + 255) / 256), 256, 0, st>>>(c0, c1 - c0, bb, pl->d_dcoff,
+                                                                             pl->d_dcolexp, pl->d_eB);
+      launch_slice_dig(c0, c1 - c0, bb, S, buf, pl->d_eB, st);
     }
     if (t1 > t0) {
       GemmArgs ga{buf, buf, pl->d_eA, pl->d_eB, nullptr, 0, 0, 0, 0, 0, 0, S, 1, 0, ctx->d_mx_err,
@@ -2549,8 +2760,8 @@ rix_status rix_mixed_T(rix_ctx *ctx, int b, int64_t tbase, const double *D, cuda
 
 int32_t rix_tt_launches(const rix_ctx *ctx) {
   if (!ctx->mxt) return 0;
-  return 5 * (int32_t)(ctx->mxt->grp_prob.size() - 1) +
-         (ctx->mxt->n_mask > 0 ? 1 : 0);
+  const int32_t ng = (int32_t)(ctx->mxt->grp_prob.size() - 1);
+  return 5 * ng + (ctx->mxt->n_mask > 0 ? 1 : 0) + (ng > 0 ? 1 : 0);  // + k_tt_mask, k_dcolexp
 }
 
 extern "C" rix_status rix_gemm_profile(rix_ctx *ctx, double *ms, int64_t *launches, int64_t *chunks) {
