@@ -422,14 +422,21 @@ void launch_pack(const double *X, int64_t sr, int64_t sk, int R, int Kd, int Rpa
 }
 
 // ------------------------------------------------------------------ the GEMM
+// Middle atoms batched into one problem of the plans of terms 2, 3+4 and Z (at most).
+constexpr int GMAX = 4;
+
 // One problem of a batched launch: its packed operands, exponents and the
 // scatter maps of its output (rows (row block q, i), columns (col block z, l)).
+// In the plans of terms 2, 3+4 and Z a problem sums over ng middle atoms: its K
+// axis is their contraction ranges back to back, member m at [kb[m], kb[m+1]).
 struct Prob {
   int64_t aoff, boff;      // byte offsets of the A and B slice planes
   int64_t eaoff, eboff;    // offsets into the exponent arrays
   int64_t rowoff, coloff;  // offsets into rowinfo / colinfo
   int64_t xoff;            // offset into xmap ([nq][nz])
   int32_t Mpad, Npad, Kpad, M, N, nz, drop, pad_;
+  int32_t ng;              // middle atoms of the problem (grouped plans)
+  int32_t kb[GMAX + 1];    // their K ranges; kb[ng] = K
 };
 
 // Output row block of a term-1 problem: the K block X(A',E'), the pair (A',E')
@@ -470,6 +477,7 @@ struct GemmArgs {
   // batched mode: per (problem, column tile) a bit mask of the K stages whose B tile is not all
   // zero, (Kpad / KC + 63) / 64 words at kmask + tiles[t].w; stages without a bit are skipped
   const unsigned long long *kmask = nullptr;
+  const int64_t *kmask_off = nullptr;  // grouped plans: word offset of the mask of row tile tiles[t].w
   unsigned long long *chunks = nullptr;  // profiling: 128 x 80 x 16 MMAs issued (K stages x K steps x slice pairs)
   unsigned long long *X128 = nullptr;  // deterministic mode: X additions as 128-bit fixed point (2 words each)
   uint64_t wait_ns = WAIT_NS;  // limit of every bounded wait
@@ -526,11 +534,11 @@ __device__ __forceinline__ TileInfo tile_info(const GemmArgs &g, int t) {
     ti.km = nullptr;
     ti.nlive = ti.Kpad / KC;
     if (g.kmask) {
-      ti.km = g.kmask + tt.w;
+      ti.km = g.kmask + (g.kmask_off ? g.kmask_off[tt.w] : (int64_t)tt.w);
       int n = 0;
       for (int w = 0; w < (ti.nlive + 63) / 64; w++) n += __popcll(ti.km[w]);
       ti.nlive = n;
-      ti.live = n > 0;
+      ti.live = ti.live && n > 0;
     }
   } else {
     const int mtiles = g.Mpad / TM;
@@ -772,8 +780,10 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
             const int64_t xb = sxb[r];
             if (xb >= 0 && gc < Ncols) {
               const int4 ci = g.colinfo[pr->coloff + gc];
-              if (ci.x >= 0) {
-                const int64_t o = (g.offK[g.xmap[xb + ci.x]] - g.xshift) + (int64_t)sry[r] * ci.z + ci.y;
+              // xmap < 0: no middle atom of the problem joins this row and column block
+              const int32_t xi = ci.x >= 0 ? g.xmap[xb + ci.x] : -1;
+              if (xi >= 0) {
+                const int64_t o = (g.offK[xi] - g.xshift) + (int64_t)sry[r] * ci.z + ci.y;
                 const double v = g.oscale * sv[r * EPI_CW + j];
                 if (g.X128) rix::add_x128(g.X128 + 2 * o, rix::to_x128(v));
                 else atomicAdd(g.X + o, v);
@@ -1103,11 +1113,15 @@ void slice_rows(int64_t n0, int64_t n, const Acc &acc, int S, __nv_bfloat16 *pla
   launch_slice_dig(n0, n, acc, S, planes, e, st);
 }
 
-// element access of the generic plans (Src records)
+// element access of the plans of terms 2, 3+4 and Z: packed row (or column) w
+// has one Src record per middle atom of its problem (G records per row, off < 0
+// where the atom does not meet the row), and K value k lies in the range of
+// member m, kb[m] <= k < kb[m+1]
 struct SrcAcc {
   const int64_t *prob_of;
   const Prob *probs;
   const Src *src;
+  int G;
   const double *X;
   int64_t shift;
   const double *X2;
@@ -1115,39 +1129,60 @@ struct SrcAcc {
   int is_b;
   struct Row {
     Prob pr;
-    Src sr;
+    const Src *s;
     int r;
-    bool live;
   };
   __device__ Row row(int64_t w) const {
     Row R;
     R.pr = probs[prob_of[w]];
-    R.sr = src[w];
+    R.s = src + w * G;
     R.r = (int)(w - (is_b ? R.pr.coloff : R.pr.rowoff));
-    R.live = R.sr.off >= 0 && (R.sr.flag < 0 || (keep[R.sr.flag] && (!keep2 || keep2[R.sr.flag])));
     return R;
   }
   __device__ double at(const Row &R, int k) const {
-    if (!R.live || k >= R.pr.pad_) return 0.0;
-    const int o = k / R.sr.inner_n, in = k - o * R.sr.inner_n;
-    const double v = X[R.sr.off - shift + (int64_t)o * R.sr.outer + (int64_t)in * R.sr.inner_st];
-    return R.sr.off2 >= 0 ? v * X2[R.sr.off2 + in] : v;
+    if (k >= R.pr.pad_) return 0.0;
+    // member of k (kb[j] = K for j >= ng; constant indices keep the record in registers)
+    static_assert(GMAX == 4, "member search");
+    const int m = (k >= R.pr.kb[1]) + (k >= R.pr.kb[2]) + (k >= R.pr.kb[3]);
+    const int k0 = m == 0 ? 0 : m == 1 ? R.pr.kb[1] : m == 2 ? R.pr.kb[2] : R.pr.kb[3];
+    const Src sr = R.s[m];
+    if (sr.off < 0 || (sr.flag >= 0 && !(keep[sr.flag] && (!keep2 || keep2[sr.flag])))) return 0.0;
+    const int kl = k - k0;
+    const int o = kl / sr.inner_n, in = kl - o * sr.inner_n;
+    const double v = X[sr.off - shift + (int64_t)o * sr.outer + (int64_t)in * sr.inner_st];
+    return sr.off2 >= 0 ? v * X2[sr.off2 + in] : v;
   }
 };
 
-// live[r] = 1 if any pair of row tile r has a kept V and a kept D block
-// (product screening: a pair (B, G') also counts as dead when |V| |D| times the largest C
-// block of G' is below the product threshold)
-__global__ void k_rt_live(int64_t n, const int2 *rt, const int32_t *rtq, const uint8_t *keepV, const uint8_t *keepD,
-                          const int32_t *pB, const float *maxCatom, rix::PScreen ps, uint8_t *live) {
+// Per row tile r of a grouped plan, for this build: bit c of its K-stage mask is set
+// when a row of the tile has a kept block with a middle atom whose K range meets
+// stage c (entries (pair, first stage | last stage << 16) in rtq), and live[r] tells
+// whether any bit is.  A pair is kept when keep (and keep2) flag it; with product
+// screening (Z plan) a pair (B, G') also counts as dead when |V| |D| times the
+// largest C block of G' is below the threshold.
+__global__ void k_rt_mask(int64_t n, const int2 *rt, const int2 *rtq, const int64_t *rtkw, const uint8_t *keep,
+                          const uint8_t *keep2, const int32_t *pB, const float *maxCatom, rix::PScreen ps,
+                          unsigned long long *kmask, uint8_t *live) {
   const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= n) return;
   const int2 e = rt[r];
+  unsigned long long *m = kmask + rtkw[r];
+  const int nw = (int)(rtkw[r + 1] - rtkw[r]);
+  for (int w = 0; w < nw; w++) m[w] = 0ull;
   uint8_t v = 0;
   for (int i = 0; i < e.y; i++) {
-    const int q = rtq[e.x + i];
-    const bool small = ps.tau > 0.f && ps.nV[q] * ps.nD[q] * maxCatom[pB[q]] < ps.tau;
-    v |= keepV[q] & keepD[q] & (uint8_t)!small;
+    const int2 x = rtq[e.x + i];
+    const int q = x.x;
+    bool ok = keep[q] && (!keep2 || keep2[q]);
+    if (ok && ps.tau > 0.f && ps.nD) ok = !(ps.nV[q] * ps.nD[q] * maxCatom[pB[q]] < ps.tau);
+    if (!ok) continue;
+    v = 1;
+    const int lo = x.y & 0xFFFF, hi = x.y >> 16;  // stages lo..hi
+    for (int w = lo >> 6; w <= hi >> 6; w++) {
+      const int a = max(lo - 64 * w, 0), b = min(hi - 64 * w, 63);
+      const unsigned long long bits = (b == 63 ? ~0ull : ((1ull << (b + 1)) - 1)) & ~((1ull << a) - 1);
+      m[w] |= bits;
+    }
   }
   live[r] = v;
 }
@@ -1160,12 +1195,16 @@ __global__ void k_flag_set(int n, const int32_t *idx, uint8_t *flags) {
 }  // namespace rixtc
 
 #include <algorithm>
+#include <array>
+#include <cmath>
+#include <map>
 #include <vector>
 
 // Host and device state of one batched plan.
 struct rix_mx_plan {
   int kind = 0;                          // 0: terms 3+4, 1: term 2, 2: term-4 intermediate Z
   int S = 6;                             // slices of this plan
+  int G = 1;                             // Src records per packed row / column (largest group)
   int kmax = 0;                          // longest K (padded) of its problems
   std::vector<int32_t> grp;              // problems [grp[g], grp[g+1])
   std::vector<int32_t> grp_blk;          // memory-plan block of each group (-1: any)
@@ -1179,10 +1218,13 @@ struct rix_mx_plan {
   rixtc::Src *d_rowsrc = nullptr, *d_colsrc = nullptr;
   int32_t *d_xmap = nullptr;
   int *d_eA = nullptr, *d_eB = nullptr;
-  // kind 2: row tiles whose rows all come from screened (V, D) blocks are skipped per build
+  // row tiles: per build, the K stages that meet a kept block of their rows (a member
+  // of the problem whose blocks with these rows are all screened or absent is skipped)
   int64_t n_rt = 0;
   int2 *d_rt = nullptr;
-  int32_t *d_rtq = nullptr;
+  int2 *d_rtq = nullptr;
+  int64_t *d_rtkw = nullptr;
+  unsigned long long *d_kmask = nullptr;
   uint8_t *d_rtlive = nullptr;
 };
 
@@ -1219,8 +1261,10 @@ struct PlanHost {
   std::vector<rixtc::Src> rowsrc, colsrc;
   std::vector<int32_t> xmap;
   std::vector<uint8_t> use;                // kind 2: middle atoms that run here
-  std::vector<int2> rt;                    // kind 2: per row tile, (first, count) of its pairs in rtq
-  std::vector<int32_t> rtq;                // kind 2: pair (B, G') of each row group, per row tile
+  std::vector<int2> rt;                    // per row tile, (first, count) of its entries in rtq
+  std::vector<int2> rtq;                   // (pair, first | last K stage << 16) of each row block and member
+  std::vector<int64_t> rtkw;               // per row tile (and one past the last): first word of its mask
+  int G = 1;                               // Src records per packed row / column
   int64_t eaoff = 0, eboff = 0;
   double tflops = 0, fl64 = 0;
 };
@@ -1246,6 +1290,9 @@ int plan_slices(const rix_ctx *ctx, int kind) { return rix_plan_slices(ctx, kind
 // of term 1 (k_X12, ~0.7 TFLOP/s), of Z (k_Z, ~1.2) and of T (k_T, ~1.0), and
 // the sliced GEMM with its slicing kernels (~0.75 PFLOP/s issued).
 constexpr double FP64_RATE_T1 = 0.7e12, FP64_RATE_Z = 1.2e12, FP64_RATE_T = 1.0e12, TC_RATE = 7.5e14;
+
+// Middle atoms within this distance of a group's first atom join its problem (2.5 A).
+constexpr double GROUP_R = 2.5 / 0.529177210903;
 
 // Build the problems of one plan (see the section comment for the three kinds).
 // count_only: no host arrays, just the map bytes, the largest problem's slices
@@ -1289,131 +1336,242 @@ rix_status plan_host(rix_ctx *ctx, int kind, const std::vector<int64_t> &ptrZ, P
   // the row blocks of the memory plan (one block while it is not known yet)
   const bool have_blocks = (int)ctx->blk_atom.size() == ctx->nblk + 1;
   const int nblk = (kind == 2 && have_blocks) ? ctx->nblk : 1;
-  std::vector<int32_t> blk_of(nat, 0);
-  if (kind == 2 && have_blocks)
-    for (int b = 0; b < nblk; b++)
-      for (int a = ctx->blk_atom[b]; a < ctx->blk_atom[b + 1]; a++) blk_of[a] = b;
-  std::vector<int64_t> qs, zs;
-  for (int blk = 0; blk < nblk; blk++)
-    for (int b = 0; b < nat; b++) {
-      if (!h.use[b]) continue;
-      qs.clear();
-      zs.clear();
-      // rows: pairs (b, A', m); terms 3+4 skip on-site (P on B' != A)
+  std::vector<int32_t> mblk(nat, 0);
+  if (have_blocks)
+    for (int b = 0; b < ctx->nblk; b++)
+      for (int a = ctx->blk_atom[b]; a < ctx->blk_atom[b + 1]; a++) mblk[a] = b;
+  // Problems: groups of middle atoms that share most of their neighbours (atoms
+  // consecutive in index order within GROUP_R of the first, in one memory-plan
+  // block: the atoms of a molecule).  A group's contraction ranges are
+  // concatenated on the K axis, its rows and columns are the union of its
+  // members', so the output of the group is added once instead of once per atom.
+  // Member k sits at image o_k from the first (its shortest pair); row (A', M)
+  // means A' at image M from the first member, i.e. at M - o_k from member k,
+  // and the output block of (row (A', M), column (E', N)) is (A', E', N - M).
+  struct Member {
+    int b;
+    int o[3];
+  };
+  std::vector<std::vector<Member>> groups;
+  for (int b = 0; b < nat;) {
+    if (!h.use[b]) {
+      b++;
+      continue;
+    }
+    std::vector<Member> gm(1, Member{b, {0, 0, 0}});
+    int c = b + 1;
+    for (; c < nat && (int)gm.size() < GMAX && h.use[c] && mblk[c] == mblk[b]; c++) {
+      double best = GROUP_R;
+      int64_t qb = -1;
       for (int64_t q = row1[b]; q < row1[b + 1]; q++) {
-        if (kind == 0 && ctx->onsite[q]) continue;
-        if (kind == 2 && blk_of[ctx->pB[q]] != blk) continue;
-        qs.push_back(q);
+        if (ctx->pB[q] != c) continue;
+        double d2 = 0.0;
+        for (int x = 0; x < 3; x++) {
+          double sh = 0.0;
+          if (ctx->periodic)
+            for (int d = 0; d < 3; d++) sh += (double)ctx->pn[3 * q + d] * ctx->cell[3 * d + x];
+          const double r = (ctx->xyz[3 * c + x] + sh) - ctx->xyz[3 * b + x];
+          d2 += r * r;
+        }
+        if (std::sqrt(d2) < best) {
+          best = std::sqrt(d2);
+          qb = q;
+        }
       }
-      if (qs.empty()) continue;
-      if (kind == 0) {
-        for (int64_t z = row2[b]; z < row2[b + 1]; z++)
-          if (ptrZ[z + 1] > ptrZ[z]) zs.push_back(z);
-      } else {
-        for (int64_t q = row1[b]; q < row1[b + 1]; q++)
-          if (!ctx->onsite[q]) zs.push_back(q);
+      if (qb < 0) break;
+      gm.push_back(Member{c, {ctx->pn[3 * qb], ctx->pn[3 * qb + 1], ctx->pn[3 * qb + 2]}});
+    }
+    h.G = std::max(h.G, (int)gm.size());
+    groups.push_back(std::move(gm));
+    b = c;
+  }
+  const int G = h.G;
+  const Src absent{-1, -1, 1, 1, 1, -1};
+  // (atom, image) as a sortable key; images stay well inside the key's 8-bit fields
+  auto node_key = [](int a, const int *m) { return pair_key(0, a, m[0], m[1], m[2]); };
+  using Slots = std::array<int64_t, GMAX>;
+  for (int blk = 0; blk < nblk; blk++)
+    for (const auto &gm : groups) {
+      const int ng = (int)gm.size();
+      // rows: (A', M) from the members' pairs (b_k, A', m), M = m + o_k (terms 3+4 skip
+      // the on-site pair: P on B' != A); the pair of each member, or -1
+      std::map<int64_t, Slots> rm, cm;
+      auto slot = [](std::map<int64_t, Slots> &m, int64_t key) -> Slots & {
+        auto it = m.find(key);
+        if (it == m.end()) {
+          Slots e;
+          e.fill(-1);
+          it = m.emplace(key, e).first;
+        }
+        return it->second;
+      };
+      for (int k = 0; k < ng; k++) {
+        const int b = gm[k].b;
+        for (int64_t q = row1[b]; q < row1[b + 1]; q++) {
+          if (kind == 0 && ctx->onsite[q]) continue;
+          if (kind == 2 && mblk[ctx->pB[q]] != blk && nblk > 1) continue;
+          int M[3];
+          for (int c = 0; c < 3; c++) M[c] = ctx->pn[3 * q + c] + gm[k].o[c];
+          slot(rm, node_key(ctx->pB[q], M))[k] = q;
+        }
+        // columns: (E', N) from the 2-hop blocks Z(b_k, E', n) with products (terms 3+4),
+        // or from the pairs (b_k, E', n) that are not on-site (term 2, Z)
+        if (kind == 0) {
+          for (int64_t z = row2[b]; z < row2[b + 1]; z++) {
+            if (ptrZ[z + 1] <= ptrZ[z]) continue;
+            int N[3];
+            for (int c = 0; c < 3; c++) N[c] = key_n(ctx->keys2[z], c) + gm[k].o[c];
+            slot(cm, node_key(key_b(ctx->keys2[z]), N))[k] = z;
+          }
+        } else {
+          for (int64_t q = row1[b]; q < row1[b + 1]; q++) {
+            if (ctx->onsite[q]) continue;
+            int N[3];
+            for (int c = 0; c < 3; c++) N[c] = ctx->pn[3 * q + c] + gm[k].o[c];
+            slot(cm, node_key(ctx->pB[q], N))[k] = q;
+          }
+        }
       }
-      int M = 0, N = 0;
-      for (auto q : qs) {
-        const int a = ctx->pB[q];
+      if (rm.empty()) continue;
+      int M = 0, N = 0, K = 0;
+      for (const auto &r : rm) {
+        const int a = key_b(r.first);
         M += kind == 2 ? ctx->na_at[a] * ctx->nb_at[a] : ctx->nb_at[a];
       }
-      for (auto z : zs) N += ctx->nb_at[kind == 0 ? key_b(ctx->keys2[z]) : ctx->pB[z]];
-      const int K = ctx->na_at[b] * ctx->nb_at[b];
+      for (const auto &c : cm) N += ctx->nb_at[key_b(c.first)];
+      int kb[GMAX + 1] = {0};
+      for (int k = 0; k < ng; k++) kb[k + 1] = kb[k] + ctx->na_at[gm[k].b] * ctx->nb_at[gm[k].b];
+      K = kb[ng];
       const int Mpad = std::max(TM, (M + TM - 1) / TM * TM);
       const int Npad = std::max(TN, (N + TN - 1) / TN * TN);
       const int Kpad = std::max(KC, (K + KC - 1) / KC * KC);
       const int64_t bytes = (int64_t)S * (Mpad + Npad) * Kpad * 2;
       total += bytes;
       maxp = std::max(maxp, bytes);
+      // row tiles (the kept blocks of their rows decide, per build, which K stages run)
+      std::vector<int2> rt_here, rtq_here;
+      {
+        // row tile t covers rows [128 t, 128 t + 128): the (pair, member) of the row blocks there
+        std::vector<std::pair<int, const Slots *>> blocks;  // (end row, pairs of the members)
+        int acc = 0;
+        for (const auto &r : rm) {
+          const int a = key_b(r.first);
+          acc += kind == 2 ? ctx->na_at[a] * ctx->nb_at[a] : ctx->nb_at[a];
+          blocks.push_back(std::make_pair(acc, &r.second));
+        }
+        size_t i0 = 0;
+        for (int t = 0; t < Mpad / TM; t++) {
+          const int lo = t * TM, hi = std::min(M, lo + TM);
+          while (i0 < blocks.size() && blocks[i0].first <= lo) i0++;
+          const int first = (int)rtq_here.size();
+          for (size_t i = i0; i < blocks.size() && (i == 0 ? 0 : blocks[i - 1].first) < hi; i++)
+            for (int k = 0; k < ng; k++) {
+              const int64_t q = (*blocks[i].second)[k];
+              if (q < 0 || kb[k + 1] == kb[k]) continue;
+              // the block's flag: C(A', b_k) (terms 3+4), V(A', G) (term 2), V and D (B, G') (Z)
+              const int stages = (kb[k] / KC) | (((kb[k + 1] - 1) / KC) << 16);
+              rtq_here.push_back(make_int2(ctx->partner1[q], stages));
+            }
+          rt_here.push_back(make_int2(first, (int)rtq_here.size() - first));
+        }
+      }
+      const int nkw = (Kpad / KC + 63) / 64;  // mask words per row tile
       // xmap, rowinfo + rowprob + rowsrc + exponent, colinfo + colprob + colsrc + exponent, tiles
-      maps += (kind == 2 ? (int64_t)(Mpad / TM) * 21 : 0) +
-              (int64_t)qs.size() * zs.size() * 4 + (int64_t)Mpad * (8 + 8 + 32 + 4) +
-              (int64_t)Npad * (16 + 8 + 32 + 4) + (int64_t)(Mpad / TM) * (Npad / TN) * 16 + (int64_t)sizeof(Prob);
+      maps += (int64_t)rt_here.size() * (8 + 8 + 1 + 8 * nkw) + (int64_t)rtq_here.size() * 8 +
+              (int64_t)rm.size() * cm.size() * 4 + (int64_t)Mpad * (8 + 8 + 32 * G + 4) +
+              (int64_t)Npad * (16 + 8 + 32 * G + 4) + (int64_t)(Mpad / TM) * (Npad / TN) * 16 + (int64_t)sizeof(Prob);
       h.tflops += 2.0 * Mpad * Npad * Kpad * npairs;
       if (count_only) continue;
       const int pidx = (int)h.probs.size();
       Prob pr{};
       pr.M = M; pr.N = N; pr.Mpad = Mpad; pr.Npad = Npad; pr.Kpad = Kpad;
-      pr.pad_ = K;  // true K (the pack kernel zero-fills K..Kpad)
-      pr.nz = (int32_t)zs.size();
+      pr.pad_ = K;  // true K (the slicing zero-fills K..Kpad)
+      pr.nz = (int32_t)cm.size();
       pr.drop = fixed_point_drop(Kpad, S);
+      pr.ng = ng;
+      for (int k = 0; k <= GMAX; k++) pr.kb[k] = kb[std::min(k, ng)];
       pr.eaoff = h.eaoff; pr.eboff = h.eboff;
       pr.rowoff = (int64_t)h.rowinfo.size();
       pr.coloff = (int64_t)h.colinfo.size();
       pr.xoff = (int64_t)h.xmap.size();
       h.eaoff += Mpad;
       h.eboff += Npad;
-      const int nbB = ctx->nb_at[b], naB = ctx->na_at[b];
-      for (int qi = 0; qi < (int)qs.size(); qi++) {
-        const int64_t q = qs[qi];
-        const int a = ctx->pB[q];
+      int qi = 0;
+      for (const auto &r : rm) {
+        const int a = key_b(r.first);
         const int nbA = ctx->nb_at[a], naA = ctx->na_at[a];
-        const int64_t pq = ctx->partner1[q];  // pair (A', b)
-        if (kind == 2) {  // rows (P, j) of V(B,G')[P][.] x D(B,G')[j][.]
-          for (int P = 0; P < naA; P++)
-            for (int j = 0; j < nbA; j++) {
-              h.rowinfo.push_back(make_int2(qi, P * nbA + j));
-              h.rowsrc.push_back(Src{ctx->offV[pq] + (int64_t)P * naB, ctx->offD[pq] + (int64_t)j * nbB, 1, 0,
-                                     nbB, (int32_t)pq});
-              h.rowprob.push_back(pidx);
-            }
-          continue;
-        }
-        for (int i = 0; i < nbA; i++) {
-          h.rowinfo.push_back(make_int2(qi, i));
-          Src sr;
-          sr.off2 = -1;
-          if (kind == 0) {  // C(A,B)[naA + P][i][j]
-            sr.off = ctx->offC[pq] + ((int64_t)naA * nbA + i) * nbB;
-            sr.outer = nbA * nbB; sr.inner_st = 1; sr.inner_n = nbB; sr.flag = (int32_t)pq;
-          } else {          // U2(A,G)[Q][i][k]
-            sr.off = ctx->offU_h[pq] + (int64_t)i * nbB;
-            sr.outer = nbA * nbB; sr.inner_st = 1; sr.inner_n = nbB; sr.flag = (int32_t)pq;
-          }
-          h.rowsrc.push_back(sr);
+        const int nrow = kind == 2 ? naA * nbA : nbA;
+        for (int y = 0; y < nrow; y++) {
+          h.rowinfo.push_back(make_int2(qi, y));
           h.rowprob.push_back(pidx);
+          for (int k = 0; k < G; k++) {
+            const int64_t q = k < ng ? r.second[k] : -1;
+            if (q < 0) {
+              h.rowsrc.push_back(absent);
+              continue;
+            }
+            const int64_t pq = ctx->partner1[q];  // pair (A', b_k)
+            const int nbB = ctx->nb_at[gm[k].b], naB = ctx->na_at[gm[k].b];
+            Src sr;
+            if (kind == 2) {  // rows (P, j) of V(B,G')[P][.] x D(B,G')[j][.]
+              const int P = y / nbA, j = y - P * nbA;
+              sr = Src{ctx->offV[pq] + (int64_t)P * naB, ctx->offD[pq] + (int64_t)j * nbB, 1, 0, nbB, (int32_t)pq};
+            } else if (kind == 0) {  // C(A,B)[naA + P][i][j]
+              sr = Src{ctx->offC[pq] + ((int64_t)naA * nbA + y) * nbB, -1, nbA * nbB, 1, nbB, (int32_t)pq};
+            } else {  // U2(A,G)[Q][i][k]
+              sr = Src{ctx->offU_h[pq] + (int64_t)y * nbB, -1, nbA * nbB, 1, nbB, (int32_t)pq};
+            }
+            h.rowsrc.push_back(sr);
+          }
         }
+        qi++;
       }
       for (int r = M; r < Mpad; r++) {
         h.rowinfo.push_back(make_int2(-1, 0));
-        h.rowsrc.push_back(Src{-1, -1, 1, 1, 1, -1});
         h.rowprob.push_back(pidx);
+        for (int k = 0; k < G; k++) h.rowsrc.push_back(absent);
       }
-      for (int zi = 0; zi < (int)zs.size(); zi++) {
-        const int64_t z = zs[zi];
-        const int e = kind == 0 ? key_b(ctx->keys2[z]) : ctx->pB[z];
+      int zi = 0;
+      for (const auto &c : cm) {
+        const int e = key_b(c.first);
         const int nbE = ctx->nb_at[e];
         for (int l = 0; l < nbE; l++) {
           h.colinfo.push_back(make_int4(zi, l, nbE, 0));
-          Src sr;
-          sr.off2 = -1;
-          if (kind == 0) {  // Z(B,E')[P][j][l]
-            sr.off = ctx->off2[z] + l;
-            sr.outer = nbB * nbE; sr.inner_st = nbE; sr.inner_n = nbB; sr.flag = -1;
-          } else {          // C(G,E')[Q][k][l], Q on G
-            sr.off = ctx->offC[z] + l;
-            sr.outer = nbB * nbE; sr.inner_st = nbE; sr.inner_n = nbB; sr.flag = (int32_t)z;
-          }
-          h.colsrc.push_back(sr);
           h.colprob.push_back(pidx);
+          for (int k = 0; k < G; k++) {
+            const int64_t z = k < ng ? c.second[k] : -1;
+            if (z < 0) {
+              h.colsrc.push_back(absent);
+              continue;
+            }
+            const int nbB = ctx->nb_at[gm[k].b];
+            if (kind == 0)  // Z(B,E')[P][j][l]
+              h.colsrc.push_back(Src{ctx->off2[z] + l, -1, nbB * nbE, nbE, nbB, -1});
+            else  // C(G,E')[Q][k][l], Q on G
+              h.colsrc.push_back(Src{ctx->offC[z] + l, -1, nbB * nbE, nbE, nbB, (int32_t)z});
+          }
         }
+        zi++;
       }
       for (int c = N; c < Npad; c++) {
         h.colinfo.push_back(make_int4(-1, 0, 0, 0));
-        h.colsrc.push_back(Src{-1, -1, 1, 1, 1, -1});
         h.colprob.push_back(pidx);
+        for (int k = 0; k < G; k++) h.colsrc.push_back(absent);
       }
-      // output block of (row block q, column block z): A' at image m_q from the middle
-      // atom, E' at n_z from it, so E' sits at n_z - m_q from A' (a K block, or for
-      // kind 2 a Z block of the 2-hop list)
-      for (auto q : qs) {
-        const int a = ctx->pB[q];
-        for (auto z : zs) {
-          const int e = kind == 0 ? key_b(ctx->keys2[z]) : ctx->pB[z];
+      // output block of (row block, column block): a K block, or for kind 2 a Z block of
+      // the 2-hop list; -1 where no member meets both (the product is zero there)
+      for (const auto &r : rm) {
+        const int a = key_b(r.first);
+        for (const auto &c : cm) {
+          bool meet = false;
+          for (int k = 0; k < ng; k++) meet |= r.second[k] >= 0 && c.second[k] >= 0;
+          if (!meet) {
+            h.xmap.push_back(-1);
+            continue;
+          }
+          const int e = key_b(c.first);
           int nz3[3];
-          for (int c = 0; c < 3; c++)
-            nz3[c] = (kind == 0 ? key_n(ctx->keys2[z], c) : (int)ctx->pn[3 * z + c]) - ctx->pn[3 * q + c];
+          for (int x = 0; x < 3; x++) nz3[x] = key_n(c.first, x) - key_n(r.first, x);
           const int64_t key = pair_key(a, e, nz3[0], nz3[1], nz3[2]);
           const int64_t x = kind == 2 ? find_sorted(ctx->keys2, row2[a], row2[a + 1], key)
                                       : find_sorted(ctx->keys3, row3[a], row3[a + 1], key);
@@ -1425,35 +1583,17 @@ rix_status plan_host(rix_ctx *ctx, int kind, const std::vector<int64_t> &ptrZ, P
         }
       }
       const int rt0 = (int)h.rt.size();
-      if (kind == 2) {
-        // row tile mt covers rows [128 mt, 128 mt + 128): the pairs (B, G') of the row groups there
-        std::vector<int> qend(qs.size());
-        int acc = 0;
-        for (size_t qi = 0; qi < qs.size(); qi++) {
-          const int a = ctx->pB[qs[qi]];
-          acc += ctx->na_at[a] * ctx->nb_at[a];
-          qend[qi] = acc;
-        }
-        size_t q0 = 0;
-        for (int mt = 0; mt < Mpad / TM; mt++) {
-          const int lo = mt * TM, hi = std::min(M, lo + TM);
-          while (q0 < qs.size() && qend[q0] <= lo) q0++;
-          const int first = (int)h.rtq.size();
-          for (size_t qi = q0; qi < qs.size() && (qi == 0 ? 0 : qend[qi - 1]) < hi; qi++)
-            h.rtq.push_back(ctx->partner1[qs[qi]]);
-          h.rt.push_back(make_int2(first, (int)h.rtq.size() - first));
-        }
+      if (h.rtkw.empty()) h.rtkw.push_back(0);
+      for (const int2 &t : rt_here) {
+        h.rt.push_back(make_int2((int)h.rtq.size() + t.x, t.y));
+        h.rtkw.push_back(h.rtkw.back() + nkw);
       }
-      push_tiles(h.tiles, pidx, Mpad / TM, Npad / TN, [&](int mt, int) { return kind == 2 ? rt0 + mt : 0; });
+      h.rtq.insert(h.rtq.end(), rtq_here.begin(), rtq_here.end());
+      push_tiles(h.tiles, pidx, Mpad / TM, Npad / TN, [&](int mt, int) { return rt0 + mt; });
       h.probs.push_back(pr);
       h.pbytes.push_back(bytes);
-      // Z of terms 3+4 is resident per block of its middle atom; kind 2 rows per block
-      h.pblk.push_back(kind == 0 ? -1 : (kind == 2 ? blk : -1));
-      if (kind == 0) {
-        int bb = 0;
-        while (b >= ctx->blk_atom[bb + 1]) bb++;
-        h.pblk.back() = bb;
-      }
+      // Z of terms 3+4 is resident per block of its middle atoms; kind 2 rows per block
+      h.pblk.push_back(kind == 0 ? mblk[gm[0].b] : (kind == 2 ? blk : -1));
     }
   if (maps_out) *maps_out = maps;
   if (maxp_out) *maxp_out = maxp;
@@ -1512,6 +1652,7 @@ rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
     rix_mx_plan *pl = new rix_mx_plan;
     pl->kind = kind;
     pl->S = plan_slices(ctx, kind);
+    pl->G = h.G;
     (kind == 0 ? ctx->mx34 : kind == 1 ? ctx->mx2 : ctx->mxz) = pl;
     const int64_t budget = group_budget(maxp, total);
     // groups of consecutive problems within the budget and within one memory-plan block
@@ -1567,10 +1708,12 @@ rix_status rix_mixed_plan(rix_ctx *ctx, const std::vector<int64_t> &ptrZ) {
     if ((s = rix_upload(ctx, &pl->d_xmap, h.xmap)) != RIX_OK) return s;
     if ((s = rix_alloc(ctx, &pl->d_eA, std::max<int64_t>(h.eaoff, 1))) != RIX_OK) return s;
     if ((s = rix_alloc(ctx, &pl->d_eB, std::max<int64_t>(h.eboff, 1))) != RIX_OK) return s;
-    if (kind == 2 && !h.rt.empty()) {
+    if (!h.rt.empty()) {
       pl->n_rt = (int64_t)h.rt.size();
       if ((s = rix_upload(ctx, &pl->d_rt, h.rt)) != RIX_OK) return s;
-      if ((s = rix_upload(ctx, &pl->d_rtq, h.rtq)) != RIX_OK) return s;
+      if (!h.rtq.empty() && (s = rix_upload(ctx, &pl->d_rtq, h.rtq)) != RIX_OK) return s;
+      if ((s = rix_upload(ctx, &pl->d_rtkw, h.rtkw)) != RIX_OK) return s;
+      if ((s = rix_alloc(ctx, &pl->d_kmask, std::max<int64_t>(h.rtkw.back(), 1))) != RIX_OK) return s;
       if ((s = rix_alloc(ctx, &pl->d_rtlive, pl->n_rt)) != RIX_OK) return s;
     }
     if (kind == 2) {
@@ -1628,7 +1771,10 @@ int32_t rix_launch_count(const rix_ctx *ctx) {
     n += 5 * (int32_t)(ctx->mx34->grp.size() - 1) + 5 * (int32_t)(ctx->mx2->grp.size() - 1) +
          5 * (int32_t)(ctx->mxz->grp.size() - 1) + rix_t1_launches(ctx) + rix_tt_launches(ctx);
     if (ctx->n_t1tc < ctx->nat) n += ctx->nblk;  // k_X12 for the other column atoms
-    if (ctx->mxz->n_rt > 0) n += ctx->nblk;      // row-tile liveness of the Z plan
+    // row-tile K-stage masks: once per Z block, once per terms-3+4 block, once for term 2
+    if (ctx->mxz->n_rt > 0) n += ctx->nblk;
+    if (ctx->mx34->n_rt > 0) n += ctx->nblk;
+    if (ctx->mx2->n_rt > 0) n++;
   } else {
     n += 2 * ctx->nblk;  // k_X12, k_X34
   }
@@ -1666,11 +1812,11 @@ rix_status run_group(rix_ctx *ctx, const rix_mx_plan *pl, size_t g, const Operan
   const int64_t t0 = pl->tile_seg[g], t1 = pl->tile_seg[g + 1];
   __nv_bfloat16 *buf = (__nv_bfloat16 *)ctx->d_mx_buf;
   if (r1 > r0) {
-    const SrcAcc a{pl->d_rowprob, pl->d_probs, pl->d_rowsrc, ra.x, ra.shift, ra.x2, ra.keep, ra.keep2, 0};
+    const SrcAcc a{pl->d_rowprob, pl->d_probs, pl->d_rowsrc, pl->G, ra.x, ra.shift, ra.x2, ra.keep, ra.keep2, 0};
     slice_rows(r0, r1 - r0, a, S, buf, pl->d_eA, pl->kmax, st);
   }
   if (c1 > c0) {
-    const SrcAcc b{pl->d_colprob, pl->d_probs, pl->d_colsrc, cb.x, cb.shift, cb.x2, cb.keep, cb.keep2, 1};
+    const SrcAcc b{pl->d_colprob, pl->d_probs, pl->d_colsrc, pl->G, cb.x, cb.shift, cb.x2, cb.keep, cb.keep2, 1};
     slice_rows(c0, c1 - c0, b, S, buf, pl->d_eB, pl->kmax, st);
   }
   if (t1 > t0) {
@@ -1680,7 +1826,9 @@ rix_status run_group(rix_ctx *ctx, const rix_mx_plan *pl, size_t g, const Operan
     ga.oscale = oscale;
     ga.xshift = oshift;
     ga.ntiles = (int)(t1 - t0);
-    ga.row_live = pl->d_rtlive;  // kind 2: skip row tiles of screened (V, D) blocks
+    ga.row_live = pl->d_rtlive;  // row tiles and K stages whose blocks are all screened are skipped
+    ga.kmask = pl->d_kmask;
+    ga.kmask_off = pl->d_rtkw;
     if (out == ctx->d_X && ctx->d_X128) ga.X128 = ctx->d_X128;  // deterministic: X as 128-bit fixed point
     rix_status ls = launch_gemm(ctx, ga, t1 - t0, S, st);
     if (ls != RIX_OK) return ls;
@@ -1735,12 +1883,27 @@ void gemm_attr() {
 
 }  // namespace
 
+namespace {
+// The K-stage masks and liveness of a plan's row tiles for the current flags (product
+// screening applies to the Z plan's (V, D) rows).
+void rt_masks(rix_ctx *ctx, const rix_mx_plan *pl, const uint8_t *keep, const uint8_t *keep2, bool pscreen,
+              cudaStream_t st) {
+  if (pl->n_rt <= 0) return;
+  rix::PScreen ps = rix_pscreen(ctx);
+  if (!pscreen) ps.tau = 0.f;
+  rixtc::k_rt_mask<<<(unsigned)((pl->n_rt + 255) / 256), 256, 0, st>>>(
+      pl->n_rt, pl->d_rt, pl->d_rtq, pl->d_rtkw, keep, keep2, ctx->d_pB, ctx->d_maxCatom, ps, pl->d_kmask,
+      pl->d_rtlive);
+}
+}  // namespace
+
 // Terms 3+4 for the middle atoms of memory-plan block blk (Z resident, zbase).
 rix_status rix_mixed_x34(rix_ctx *ctx, int blk, int64_t zbase, cudaStream_t st) {
   gemm_attr();
   const rix_mx_plan *pl = ctx->mx34;
   const Operand rows{ctx->d_C, 0, nullptr, ctx->d_keepC, nullptr};
   const Operand cols{ctx->d_Z, zbase, nullptr, nullptr, nullptr};
+  rt_masks(ctx, pl, ctx->d_keepC, nullptr, false, st);
   for (size_t g = 0; g + 1 < pl->grp.size(); g++) {
     if (pl->grp_blk[g] != blk) continue;
     rix_status s = run_group(ctx, pl, g, rows, cols, ctx->d_offK, ctx->d_X, 0, 1.0, st);
@@ -1755,6 +1918,7 @@ rix_status rix_mixed_t2(rix_ctx *ctx, cudaStream_t st) {
   const rix_mx_plan *pl = ctx->mx2;
   const Operand rows{ctx->d_U, 0, nullptr, ctx->d_keepV, nullptr};
   const Operand cols{ctx->d_C, 0, nullptr, ctx->d_keepC, nullptr};
+  rt_masks(ctx, pl, ctx->d_keepV, nullptr, false, st);
   for (size_t g = 0; g + 1 < pl->grp.size(); g++) {
     rix_status s = run_group(ctx, pl, g, rows, cols, ctx->d_offK, ctx->d_X, 0, 1.0, st);
     if (s != RIX_OK) return s;
@@ -1769,11 +1933,7 @@ rix_status rix_mixed_z(rix_ctx *ctx, int blk, int64_t zbase, const double *D, cu
   const rix_mx_plan *pl = ctx->mxz;
   const Operand rows{ctx->d_V, 0, D, ctx->d_keepV, ctx->d_keepD};
   const Operand cols{ctx->d_C, 0, nullptr, ctx->d_keepC, nullptr};
-  if (pl->n_rt > 0) {
-    rixtc::k_rt_live<<<(unsigned)((pl->n_rt + 255) / 256), 256, 0, st>>>(
-        pl->n_rt, pl->d_rt, pl->d_rtq, ctx->d_keepV, ctx->d_keepD, ctx->d_pB, ctx->d_maxCatom, rix_pscreen(ctx),
-        pl->d_rtlive);
-  }
+  rt_masks(ctx, pl, ctx->d_keepV, ctx->d_keepD, true, st);
   for (size_t g = 0; g + 1 < pl->grp.size(); g++) {
     if (pl->grp_blk[g] != blk) continue;
     rix_status s = run_group(ctx, pl, g, rows, cols, ctx->d_off2, ctx->d_Z, zbase, 0.5, st);
