@@ -63,12 +63,12 @@ __global__ void k_cnt_U2(int64_t np, const int32_t *pA, const int32_t *pB, const
 __global__ void k_cnt_X12(int64_t n2, const int64_t *ptr, const rix::X12Entry *L, const int32_t *atomA2,
                           const int32_t *atomB2, const int32_t *map2to1, const int32_t *pA,
                           const int32_t *nb, const int32_t *na, const uint8_t *keepC, const uint8_t *keepV,
-                          const uint8_t *t1tc, double *out) {
+                          const uint8_t *t1tc, const uint8_t *rep1, double *out) {
   double all = 0.0, t2 = 0.0, t1tc_s = 0.0;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n2; s += (int64_t)gridDim.x * blockDim.x) {
     const int a = atomA2[s], e = atomB2[s];
     const int pae = map2to1[s];
-    const bool has1 = pae >= 0 && keepV[pae];
+    const bool has1 = pae >= 0 && keepV[pae] && rep1[pae];  // one orientation per pair
     double s1 = 0.0;
     for (int64_t it = ptr[s]; it < ptr[s + 1]; it++) {
       const rix::X12Entry en = L[it];
@@ -109,9 +109,10 @@ __global__ void k_cnt_Z(int64_t n2, const int64_t *ptrZ, const int2 *LZ, const i
 // X(A,E') <- C(A,B') Z(B,E'): 2 na_B nb_B nb_A nb_E per product with a kept C.
 __global__ void k_cnt_X34(int64_t nk, const int64_t *ptr, const int2 *L, const int32_t *atomA3,
                           const int32_t *atomB3, const int32_t *pB, const int32_t *nb, const int32_t *na,
-                          const uint8_t *keepC, double *out) {
+                          const uint8_t *keepC, const uint8_t *rep3, double *out) {
   double s = 0.0;
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nk; x += (int64_t)gridDim.x * blockDim.x) {
+    if (!rep3[x]) continue;  // one orientation per K block
     const int a = atomA3[x], e = atomB3[x];
     for (int64_t it = ptr[x]; it < ptr[x + 1]; it++) {
       const int2 en = L[it];
@@ -155,13 +156,13 @@ extern "C" rix_status rix_count_flops(rix_ctx *ctx, const double *D, double *flo
                                                         ctx->d_keepV, d_out);
     k_cnt_X12<<<grid_for(n2), CNT_THREADS, 0, st>>>(n2, ctx->d_ptrX12, ctx->d_LX12, ctx->d_atomA2,
                                                     ctx->d_atomB2, ctx->d_map2to1, ctx->d_pA, ctx->d_nb, ctx->d_na, ctx->d_keepC, ctx->d_keepV,
-                                                    ctx->d_t1tc, d_out);
+                                                    ctx->d_t1tc, ctx->d_rep1, d_out);
     k_cnt_Z<<<grid_for(n2), CNT_THREADS, 0, st>>>(n2, ctx->d_ptrZ, ctx->d_LZ, ctx->d_atomA2, ctx->d_atomB2,
                                                   ctx->d_pB, ctx->d_nb, ctx->d_na, ctx->d_keepC, ctx->d_keepV,
                                                   ctx->d_keepD, ctx->d_ztc, rix_pscreen(ctx), d_out);
     k_cnt_X34<<<grid_for(nk), CNT_THREADS, 0, st>>>(nk, ctx->d_ptrX34, ctx->d_LX34, ctx->d_atomA3,
                                                     ctx->d_atomB3, ctx->d_pB, ctx->d_nb, ctx->d_na, ctx->d_keepC,
-                                                    d_out);
+                                                    ctx->d_rep3, d_out);
     if (cudaGetLastError() != cudaSuccess) { r = RIX_ECUDA; break; }
     if (cudaMemcpyAsync(flops, d_out, 10 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {

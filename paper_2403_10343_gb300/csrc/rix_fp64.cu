@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(NT) k_X12(const int32_t *ord, const int64_t *p
                                             const double *__restrict__ T, const int64_t *off2,
                                             const double *__restrict__ U, const int64_t *offU,
                                             const int64_t *offK, double *X, int64_t tbase, int smb, int t2,
-                                            const uint8_t *t1tc) {
+                                            const uint8_t *t1tc, const uint8_t *rep1) {
   extern __shared__ double sm[];
   const int tid = threadIdx.x;
   const int s = ord[blockIdx.x];
@@ -244,7 +244,10 @@ __global__ void __launch_bounds__(NT) k_X12(const int32_t *ord, const int64_t *p
   const int nbA = nb[a], naA = na[a], nbE = nb[e], naE = na[e];
   const int nel = nbA * nbE;
   const int pae = map2to1[s];
-  const bool has1 = pae >= 0 && keepV[pae] && !(t1tc && t1tc[e]);  // else term 1 runs on the tensor cores
+  // term 1 in one orientation of each pair (rep1; else the transpose partner's block
+  // carries it), and not for the column atoms whose term 1 runs on the tensor cores
+  const bool has1 = pae >= 0 && keepV[pae] && rep1[pae] && !(t1tc && t1tc[e]);
+  const double w1 = has1 && rep1[pae] == 2 ? 0.5 : 1.0;
   if (!has1 && !t2) return;
   double acc[XMAXE];
 #pragma unroll
@@ -283,7 +286,7 @@ __global__ void __launch_bounds__(NT) k_X12(const int32_t *ord, const int64_t *p
               const double *uq = sm + (q * nbA + i) * nbG;
               for (int k = 0; k < nbG; k++) v = fma(uq[k], __ldg(cq + k * nbE), v);
             }
-            acc[r] = fma(0.5, v, acc[r]);
+            acc[r] = fma(w1, v, acc[r]);
           }
         }
       }
@@ -396,10 +399,15 @@ __global__ void __launch_bounds__(NT) k_X34(const int32_t *ord, const int64_t *p
                                             const double *__restrict__ C, const int64_t *offC,
                                             const uint8_t *keepC, const double *__restrict__ Z,
                                             const int64_t *off2, const int64_t *offK, double *X, int64_t zbase,
-                                            int64_t zlo, int64_t zhi, int smb) {
+                                            int64_t zlo, int64_t zhi, int smb, const uint8_t *rep3) {
   extern __shared__ double sm[];
   const int tid = threadIdx.x;
   const int x = ord[blockIdx.x];
+  // one orientation of each K block (the transpose partner carries the other), with
+  // twice the weight of Z's 1/2; the self block keeps it
+  const uint8_t r3 = rep3[x];
+  if (!r3) return;
+  const double w4 = r3 == 2 ? 1.0 : 2.0;
   const int a = atomA3[x], e = atomB3[x];
   const int nbA = nb[a], naA = na[a], nbE = nb[e];
   const int nel = nbA * nbE;
@@ -442,7 +450,7 @@ __global__ void __launch_bounds__(NT) k_X34(const int32_t *ord, const int64_t *p
 #pragma unroll
   for (int r = 0; r < XMAXE; r++) {
     const int el = tid + r * NT;
-    if (el < nel) out[el] += acc[r];
+    if (el < nel) out[el] += w4 * acc[r];
   }
 }
 
@@ -616,7 +624,7 @@ rix_status launch_X12_items(rix_ctx *ctx, int b, int64_t first, int64_t count, i
       ctx->d_ordX12 + ctx->segX12[b] + first, ctx->d_ptrX12, ctx->d_LX12, ctx->d_atomA2, ctx->d_atomB2,
       ctx->d_map2to1, ctx->d_map2to3, ctx->d_pA, ctx->d_onsite, ctx->d_nb, ctx->d_na, ctx->d_C, ctx->d_offC,
       ctx->d_V, ctx->d_offV, ctx->d_keepC, ctx->d_keepV, ctx->d_T, ctx->d_off2, ctx->d_U, ctx->d_offU, ctx->d_offK,
-      ctx->d_X, ctx->blk_base[b], smb, ctx->have_mx ? 0 : 1, ctx->have_mx ? ctx->d_t1tc : nullptr);
+      ctx->d_X, ctx->blk_base[b], smb, ctx->have_mx ? 0 : 1, ctx->have_mx ? ctx->d_t1tc : nullptr, ctx->d_rep1);
   return last(ctx, "k_X12");
 }
 
@@ -628,7 +636,7 @@ rix_status launch_X34_items(rix_ctx *ctx, int b, int64_t first, int64_t count, i
   k_X34<<<(unsigned)count, NT, smb * 8, st>>>(ctx->d_ordX34 + first, ctx->d_ptrX34, ctx->d_LX34, ctx->d_atomA3,
                                               ctx->d_atomB3, ctx->d_pB, ctx->d_nb, ctx->d_na, ctx->d_C, ctx->d_offC,
                                               ctx->d_keepC, ctx->d_Z, ctx->d_off2, ctx->d_offK, ctx->d_X,
-                                              ctx->blk_base[b], zlo, zhi, smb);
+                                              ctx->blk_base[b], zlo, zhi, smb, ctx->d_rep3);
   return last(ctx, "k_X34");
 }
 

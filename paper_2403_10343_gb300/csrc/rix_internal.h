@@ -129,6 +129,15 @@ struct rix_ctx {
   // pair list
   int32_t *d_pA = nullptr, *d_pB = nullptr, *d_partner1 = nullptr;
   uint8_t *d_onsite = nullptr;
+  // term 1 per pair (A, E', n): 1 = computed (representative orientation), 2 = computed
+  // with weight 1/2 (on-site pair), 0 = left to the transpose partner
+  std::vector<uint8_t> rep1;
+  uint8_t *d_rep1 = nullptr;
+  // the same for term 4 per K block (A, E', n) of the 3-hop pattern: 1 = computed with
+  // twice the weight of the four-term grouping, 2 = the self block (A, A, 0), weight as
+  // in the grouping, 0 = left to the transpose partner
+  std::vector<uint8_t> rep3;
+  uint8_t *d_rep3 = nullptr;
   int64_t *d_offC = nullptr, *d_offV = nullptr, *d_offD = nullptr, *d_offU = nullptr;
   int32_t *d_map1to2 = nullptr, *d_map1to3 = nullptr;
   // 2-hop and 3-hop lists

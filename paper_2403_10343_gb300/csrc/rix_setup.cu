@@ -373,6 +373,16 @@ static rix_status build_lists(rix_ctx *ctx) {
     return RIX_EINVAL;
   }
   for (int64_t x = 0; x < nk; x++) ctx->offK[x + 1] = ctx->offK[x] + szk[x];
+  // Term 4 (like term 1) is symmetric under (A, E', n) -> (E', A, -n) with
+  // transposition: it is computed for one orientation of each K block (twice the 1/2
+  // of the grouping), the self block (A, A, 0) being its own partner.
+  ctx->rep3.assign(nk, 0);
+  for (int64_t x = 0; x < nk; x++) {
+    const int a = key_a(keys3[x]), e = key_b(keys3[x]);
+    const int n0 = key_n(keys3[x], 0), n1 = key_n(keys3[x], 1), n2 = key_n(keys3[x], 2);
+    const bool pos = n0 > 0 || (n0 == 0 && (n1 > 0 || (n1 == 0 && n2 > 0)));
+    ctx->rep3[x] = partner3[x] == x ? 2 : (a < e || (a == e && pos)) ? 1 : 0;
+  }
   std::vector<int32_t> map1to2(np), map1to3(np);
   std::vector<int64_t> offU(np + 1, 0);
   for (int64_t p = 0; p < np; p++) {
@@ -456,7 +466,9 @@ static rix_status build_lists(rix_ctx *ctx) {
         j++;
       }
       int e = pB[en.p3], g = pA[en.p3];
-      if (en.t1) flX12 += 2.0 * NA(e) * NA(a) * NB(a) * NB(g) + 2.0 * NA(e) * NB(a) * NB(g) * NB(e);
+      // term 1 runs in one orientation of each pair (the list keeps both for the adjoint)
+      if (en.t1 && ctx->rep1[map2to1[r[i].s]])
+        flX12 += 2.0 * NA(e) * NA(a) * NB(a) * NB(g) + 2.0 * NA(e) * NB(a) * NB(g) * NB(e);
       if (en.u2 >= 0) {
         flX12 += 2.0 * NA(g) * NB(a) * NB(g) * NB(e);
         flT2 += 2.0 * NA(g) * NB(a) * NB(g) * NB(e);
@@ -541,9 +553,10 @@ static rix_status build_lists(rix_ctx *ctx) {
         int e = key_b(keys2[z]);
         int8_t m[3];
         decode_n(keys2[z], m);
-        key.push_back(find3(key_add(a, e, &pn[3 * p1], m, &lok)));
+        const int64_t x3 = find3(key_add(a, e, &pn[3 * p1], m, &lok));
+        key.push_back(x3);
         pay.push_back(make_int2((int)p1, (int)z));
-        flX34 += 2.0 * NA(b) * NB(b) * NB(a) * NB(e);
+        if (x3 >= 0 && ctx->rep3[x3]) flX34 += 2.0 * NA(b) * NB(b) * NB(a) * NB(e);  // one orientation
       }
     }
     std::vector<int64_t> rel(row3[a + 1] - row3[a] + 1);
@@ -682,6 +695,7 @@ static rix_status build_lists(rix_ctx *ctx) {
   TRY(rix_upload(ctx, &ctx->d_map2to1, map2to1));
   TRY(rix_upload(ctx, &ctx->d_map2to3, map2to3));
   TRY(rix_upload(ctx, &ctx->d_atomA3, atomA3));
+  TRY(rix_upload(ctx, &ctx->d_rep3, ctx->rep3));
   TRY(rix_upload(ctx, &ctx->d_atomB3, atomB3));
   TRY(rix_upload(ctx, &ctx->d_offK, ctx->offK));
   TRY(rix_upload(ctx, &ctx->d_partner3, partner3));
@@ -941,6 +955,19 @@ extern "C" rix_status rix_setup(const rix_system *sys, const rix_options *opt, r
   if ((s = rix_upload(ctx, &ctx->d_pB, ctx->pB)) != RIX_OK) return fail(s);
   if ((s = rix_upload(ctx, &ctx->d_partner1, ctx->partner1)) != RIX_OK) return fail(s);
   if ((s = rix_upload(ctx, &ctx->d_onsite, ctx->onsite)) != RIX_OK) return fail(s);
+  // Term 1 is symmetric under (A, E', n) -> (E', A, -n) with transposition (C, V and D
+  // are pair-symmetric), and K = X + X^T adds the transpose of every block of X; so
+  // term 1 is computed for one orientation of each pair only, with weight 1 instead
+  // of the 1/2 of the four-term grouping (weight 1/2 on the on-site pair, its own
+  // partner).  Representative: A < E', or A == E' with n lexicographically positive.
+  ctx->rep1.assign(np, 0);
+  for (int64_t p = 0; p < np; p++) {
+    const int a = ctx->pA[p], b = ctx->pB[p];
+    const int n0 = ctx->pn[3 * p], n1 = ctx->pn[3 * p + 1], n2 = ctx->pn[3 * p + 2];
+    const bool pos = n0 > 0 || (n0 == 0 && (n1 > 0 || (n1 == 0 && n2 > 0)));
+    ctx->rep1[p] = ctx->onsite[p] ? 2 : (a < b || (a == b && pos)) ? 1 : 0;
+  }
+  if ((s = rix_upload(ctx, &ctx->d_rep1, ctx->rep1)) != RIX_OK) return fail(s);
   if ((s = rix_upload(ctx, &ctx->d_offC, ctx->offC)) != RIX_OK) return fail(s);
   if ((s = rix_upload(ctx, &ctx->d_offV, ctx->offV)) != RIX_OK) return fail(s);
   if ((s = rix_upload(ctx, &ctx->d_offD, ctx->offD)) != RIX_OK) return fail(s);

@@ -424,6 +424,9 @@ void launch_pack(const double *X, int64_t sr, int64_t sk, int R, int Kd, int Rpa
 // ------------------------------------------------------------------ the GEMM
 // Middle atoms batched into one problem of the plans of terms 2, 3+4 and Z (at most).
 constexpr int GMAX = 4;
+// xmap entries of the terms-3+4 plan: output block index, with this bit set for the self
+// block (A, A, 0), which takes half the weight of the other blocks
+constexpr int32_t XHALF = 1 << 30;
 
 // One problem of a batched launch: its packed operands, exponents and the
 // scatter maps of its output (rows (row block q, i), columns (col block z, l)).
@@ -440,10 +443,12 @@ struct Prob {
 };
 
 // Output row block of a term-1 problem: the K block X(A',E'), the pair (A',E')
-// carrying V(A',E') (offset voff), and nb of A'.
+// carrying V(A',E') (offset voff), nb of A', and whether the block takes term 1
+// with weight 1/2 (the on-site pair; every other pair takes it with weight 1 in
+// one orientation).
 struct QInfo {
   int64_t voff;
-  int32_t x, vpair, nbA, pad_;
+  int32_t x, vpair, nbA, half;
 };
 
 struct GemmArgs {
@@ -465,7 +470,7 @@ struct GemmArgs {
   const int64_t *offK;
   double *X;               // X[offK[x] + i * nbE + l] += value (atomic)
   // mode 1 (term 1): rows (q, P nbA + i), columns (l, Q, nbE, naE) l-major;
-  // X(A',E')[i][l] += oscale * sum_Q V(A',E')[P][Q] R[row][col], one atomic per l
+  // X(A',E')[i][l] += oscale w sum_Q V(A',E')[P][Q] R[row][col], one atomic per l (w: QInfo)
   int mode;
   const QInfo *qinfo;      // per row block, indexed from Prob::xoff
   const double *V;
@@ -780,11 +785,12 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
             const int64_t xb = sxb[r];
             if (xb >= 0 && gc < Ncols) {
               const int4 ci = g.colinfo[pr->coloff + gc];
-              // xmap < 0: no middle atom of the problem joins this row and column block
+              // xmap < 0: no middle atom of the problem joins this row and column block, or
+              // the block is left to its transpose partner
               const int32_t xi = ci.x >= 0 ? g.xmap[xb + ci.x] : -1;
               if (xi >= 0) {
-                const int64_t o = (g.offK[xi] - g.xshift) + (int64_t)sry[r] * ci.z + ci.y;
-                const double v = g.oscale * sv[r * EPI_CW + j];
+                const int64_t o = (g.offK[xi & ~XHALF] - g.xshift) + (int64_t)sry[r] * ci.z + ci.y;
+                const double v = (xi & XHALF ? 0.5 * g.oscale : g.oscale) * sv[r * EPI_CW + j];
                 if (g.X128) rix::add_x128(g.X128 + 2 * o, rix::to_x128(v));
                 else atomicAdd(g.X + o, v);
               }
@@ -812,6 +818,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
           if (ri.x >= 0) {
             const QInfo qi = g.qinfo[pr->xoff + ri.x];
             if (g.keepV[qi.vpair]) {
+              const double osc = qi.half ? 0.5 * g.oscale : g.oscale;
               const int P = ri.y / qi.nbA, i = ri.y - P * qi.nbA;
               int lcur = -1, nbE = 0;
               double part = 0.0;
@@ -822,7 +829,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
                   const int4 ci = g.colinfo[pr->coloff + gc];  // (l, Q, nbE, naE)
                   if (ci.x >= 0) {
                     if (ci.x != lcur) {
-                      if (lcur >= 0) x_add(g, qi.x, (int64_t)i * nbE + lcur, g.oscale * part);
+                      if (lcur >= 0) x_add(g, qi.x, (int64_t)i * nbE + lcur, osc * part);
                       lcur = ci.x;
                       nbE = ci.z;
                       part = 0.0;
@@ -832,7 +839,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_gemm_sliced(GemmArgs g) {
                   }
                 }
               }
-              if (lcur >= 0) x_add(g, qi.x, (int64_t)i * nbE + lcur, g.oscale * part);
+              if (lcur >= 0) x_add(g, qi.x, (int64_t)i * nbE + lcur, osc * part);
             }
           }
         }
@@ -1245,6 +1252,19 @@ void push_tiles(std::vector<int4> &tiles, int pidx, int mtn, int ntn, W w) {
       for (int mt = 0; mt < mtn; mt++) tiles.push_back(make_int4(pidx, mt, nt, w(mt, nt)));
   }
 }
+// the same, keeping only the tiles for which live(mt, nt) holds
+template <class W, class L>
+void push_tiles_if(std::vector<int4> &tiles, int pidx, int mtn, int ntn, W w, L live) {
+  if (mtn >= ntn) {
+    for (int mt = 0; mt < mtn; mt++)
+      for (int nt = 0; nt < ntn; nt++)
+        if (live(mt, nt)) tiles.push_back(make_int4(pidx, mt, nt, w(mt, nt)));
+  } else {
+    for (int nt = 0; nt < ntn; nt++)
+      for (int mt = 0; mt < mtn; mt++)
+        if (live(mt, nt)) tiles.push_back(make_int4(pidx, mt, nt, w(mt, nt)));
+  }
+}
 
 
 using rix::key_a;
@@ -1575,11 +1595,14 @@ rix_status plan_host(rix_ctx *ctx, int kind, const std::vector<int64_t> &ptrZ, P
           const int64_t key = pair_key(a, e, nz3[0], nz3[1], nz3[2]);
           const int64_t x = kind == 2 ? find_sorted(ctx->keys2, row2[a], row2[a + 1], key)
                                       : find_sorted(ctx->keys3, row3[a], row3[a + 1], key);
-          if (x < 0) {
+          if (x < 0 || x >= XHALF) {
             ctx->last_error = "mixed plan: output block outside its list";
             return RIX_EINVAL;
           }
-          h.xmap.push_back((int32_t)x);
+          if (kind == 0)  // term 4 in one orientation of each K block
+            h.xmap.push_back(ctx->rep3[x] == 0 ? -1 : ctx->rep3[x] == 2 ? (int32_t)x | XHALF : (int32_t)x);
+          else
+            h.xmap.push_back((int32_t)x);
         }
       }
       const int rt0 = (int)h.rt.size();
@@ -1589,7 +1612,25 @@ rix_status plan_host(rix_ctx *ctx, int kind, const std::vector<int64_t> &ptrZ, P
         h.rtkw.push_back(h.rtkw.back() + nkw);
       }
       h.rtq.insert(h.rtq.end(), rtq_here.begin(), rtq_here.end());
-      push_tiles(h.tiles, pidx, Mpad / TM, Npad / TN, [&](int mt, int) { return rt0 + mt; });
+      {
+        // terms 3+4: only the tiles with an output block (one orientation of each K block)
+        std::vector<int> rs(1, 0), cs(1, 0);
+        for (const auto &r : rm) rs.push_back(rs.back() + ctx->nb_at[key_b(r.first)]);
+        for (const auto &c : cm) cs.push_back(cs.back() + ctx->nb_at[key_b(c.first)]);
+        const int nq = (int)rm.size(), nzb = (int)cm.size();
+        auto live = [&](int mt, int nt) {
+          if (kind != 0) return true;
+          const int rlo = mt * TM, rhi = std::min(M, rlo + TM), clo = nt * TN, chi = std::min(N, clo + TN);
+          if (rlo >= rhi || clo >= chi) return false;
+          const int q0 = (int)(std::upper_bound(rs.begin(), rs.end(), rlo) - rs.begin()) - 1;
+          const int z0 = (int)(std::upper_bound(cs.begin(), cs.end(), clo) - cs.begin()) - 1;
+          for (int q = q0; q < nq && rs[q] < rhi; q++)
+            for (int z = z0; z < nzb && cs[z] < chi; z++)
+              if (h.xmap[pr.xoff + (int64_t)q * nzb + z] >= 0) return true;
+          return false;
+        };
+        push_tiles_if(h.tiles, pidx, Mpad / TM, Npad / TN, [&](int mt, int) { return rt0 + mt; }, live);
+      }
       h.probs.push_back(pr);
       h.pbytes.push_back(bytes);
       // Z of terms 3+4 is resident per block of its middle atoms; kind 2 rows per block
@@ -1906,7 +1947,8 @@ rix_status rix_mixed_x34(rix_ctx *ctx, int blk, int64_t zbase, cudaStream_t st) 
   rt_masks(ctx, pl, ctx->d_keepC, nullptr, false, st);
   for (size_t g = 0; g + 1 < pl->grp.size(); g++) {
     if (pl->grp_blk[g] != blk) continue;
-    rix_status s = run_group(ctx, pl, g, rows, cols, ctx->d_offK, ctx->d_X, 0, 1.0, st);
+    // weight 2: term 4 in one orientation of each K block (Z carries the grouping's 1/2)
+    rix_status s = run_group(ctx, pl, g, rows, cols, ctx->d_offK, ctx->d_X, 0, 2.0, st);
     if (s != RIX_OK) return s;
   }
   return RIX_OK;
@@ -1947,9 +1989,12 @@ rix_status rix_mixed_z(rix_ctx *ctx, int blk, int64_t zbase, const double *D, cu
 // block of row atoms):
 //
 //   R(A',E')[(P,i)][(l,Q)] = sum_{G' near E'} sum_k T(A',G')[P][i][k] C(G',E')[Q on E'][k][l]
-//   X(A',E')[i][l]        += 1/2 sum_{P,Q} V(A',E')[P][Q] R[(P,i)][(l,Q)]
+//   X(A',E')[i][l]        += w sum_{P,Q} V(A',E')[P][Q] R[(P,i)][(l,Q)]
 //
-// rows (A', P, i) over the row atoms A' near E', K = (G', k) over E's
+// with w = 1 for the pairs (A', E') in their representative orientation, w = 1/2
+// for the on-site pair and no row for the others (term 1 is symmetric under the
+// transposition of its pair, and K = X + X^T restores the other orientation).
+// Rows (A', P, i) over those row atoms A' near E', K = (G', k) over E's
 // neighbours G', columns (l, Q).  The V contraction (a few FLOPs per R
 // element) runs in the GEMM epilogue in FP64.  This costs about nb_E times
 // the FLOPs of the FP64 grouping (which applies V per (A', G', E') triple),
@@ -2134,6 +2179,7 @@ rix_status rix_t1_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
     int64_t M = 0, K = 0;
     double f64 = 0;
     for (int64_t q = row1[e]; q < row1[e + 1]; q++) {
+      if (!ctx->rep1[ctx->partner1[q]]) continue;  // term 1 of (A', E') in one orientation
       const int a = ctx->pB[q];
       M += (int64_t)ctx->na_at[a] * ctx->nb_at[a];
       for (int64_t g = row1[e]; g < row1[e + 1]; g++) {
@@ -2179,7 +2225,7 @@ rix_status rix_t1_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
       if (!use[e]) continue;
       qs.clear();
       for (int64_t q = row1[e]; q < row1[e + 1]; q++)
-        if (blk_of[ctx->pB[q]] == b) qs.push_back(q);
+        if (blk_of[ctx->pB[q]] == b && ctx->rep1[ctx->partner1[q]]) qs.push_back(q);
       if (qs.empty()) continue;
       const int nbE = ctx->nb_at[e], naE = ctx->na_at[e];
       const int ng = (int)(row1[e + 1] - row1[e]);
@@ -2232,7 +2278,7 @@ rix_status rix_t1_plan_build(rix_ctx *ctx, bool count_only, int64_t *bytes_out) 
           ctx->last_error = "term-1 plan: output block outside the K pattern";
           return RIX_EINVAL;
         }
-        qinfo.push_back(QInfo{ctx->offV[vp], (int32_t)x, (int32_t)vp, nbA, 0});
+        qinfo.push_back(QInfo{ctx->offV[vp], (int32_t)x, (int32_t)vp, nbA, ctx->rep1[vp] == 2 ? 1 : 0});
         for (int64_t g = row1[e]; g < row1[e + 1]; g++) {
           int d[3];
           for (int c = 0; c < 3; c++) d[c] = (int)ctx->pn[3 * g + c] - (int)ctx->pn[3 * q + c];
@@ -2393,7 +2439,7 @@ rix_status rix_mixed_t1(rix_ctx *ctx, int b, int64_t tbase, cudaStream_t st) {
     if (t1 > t0) {
       GemmArgs ga{buf, buf, pl->d_eA, pl->d_eB, nullptr, 0, 0, 0, 0, 0, 0, S, 1, 0, ctx->d_mx_err,
                   pl->d_tiles + t0, pl->d_probs, pl->d_rowinfo, pl->d_colinfo, nullptr, ctx->d_offK, ctx->d_X,
-                  1, pl->d_qinfo, ctx->d_V, ctx->d_keepV, 0.5};
+                  1, pl->d_qinfo, ctx->d_V, ctx->d_keepV, 1.0};
       ga.ntiles = (int)(t1 - t0);
       ga.X128 = ctx->d_X128;  // deterministic builds: 128-bit fixed-point additions
       rix_status ls = launch_gemm(ctx, ga, t1 - t0, S, st);
