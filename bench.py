@@ -62,10 +62,16 @@ def screened(stats, cnt):
 
 
 def stage_flops(stats, st, precision):
-    """Algorithmic FP64-equivalent FLOPs of one stage as the path runs it."""
+    """Algorithmic FP64-equivalent FLOPs of one stage as the path runs it.
+
+    In mixed precision the TC12 stage holds term 2 on the tensor cores and, with a
+    single row block, term 1 on the tensor cores; with several row blocks term 1 runs
+    per block while T is resident, inside the X12 stage.
+    """
     fs = stats["flops_stage"]
-    tc12 = stats["flops_term2"] + stats["flops_term1_tc"]
     mixed = precision == "mixed"
+    t1_in_x12 = mixed and stats.get("n_row_blocks", 1) > 1
+    tc12 = stats["flops_term2"] + (0.0 if t1_in_x12 else stats["flops_term1_tc"])
     return {"T": fs[0], "U2": fs[1], "X12": fs[2] - tc12 if mixed else fs[2], "TC12": tc12 if mixed else 0.0,
             "Z": fs[3], "X34": fs[4]}.get(st, 0.0)
 
@@ -277,9 +283,12 @@ def max_over_ranks(x, world, dev):
     return t.item()
 
 
-# DRAM bytes per MMA of k_gemm_sliced (one 128 x 80 x 16 product of one slice pair), from the
-# ncu capture summarised in profiles/ (None: not measured for the kernel as it stands)
-GEMM_DRAM_BYTES_PER_STAGE_PAIR = None
+# DRAM bytes (read + write) per MMA of k_gemm_sliced (one 128 x 80 x 16 product of one slice
+# pair): ncu dram__bytes_read.sum + dram__bytes_write.sum over the 13 GEMM launches of a
+# (H2O)64 cluster build (192 atoms; 1.59e11 bytes for 4.65e8 MMAs, three builds 337-343),
+# scaled to a launch of the bench workload by its MMA count (None: not measured for the
+# kernel as it stands)
+GEMM_DRAM_BYTES_PER_STAGE_PAIR = 340.0
 GEMM_STAGE_PAIR_FLOPS = 2.0 * 128 * 80 * 16
 
 
@@ -423,6 +432,8 @@ def roofline(precision, r):
         return {"bound": "tensor", "kernel": "k_gemm_sliced", "achieved": alg / t / 1e12, "peak": peak,
                 "unit": "TFLOP/s", "frac": alg / t / 1e12 / peak, "traffic": traffic,
                 "traffic_unit": "bytes per launch",
+                "traffic_source": "ncu DRAM bytes per 128x80x16 MMA over the GEMM launches of the 192-atom cluster "
+                                  "build, times the MMAs of an average launch here",
                 "peak_source": f"bf16 sustained (a kernel timed inside a long step), {src}",
                 "alg_flops_per_build": alg, "kernel_ms_per_build": gm["ms_per_build"],
                 "launches_per_build": gm["launches_per_build"],

@@ -667,7 +667,14 @@ rix_status rix_launch_T_block(rix_ctx *ctx, const double *D, int b, cudaStream_t
 // Z(B;E') for the middle atoms of block b (Z buffer holds that block): the FP64
 // kernel stores its part, then in mixed precision the tensor cores add theirs.
 rix_status rix_launch_Z_block(rix_ctx *ctx, const double *D, int b, cudaStream_t st) {
-  rix_status s = launch_Z_items(ctx, D, b, 0, ctx->segZ[b + 1] - ctx->segZ[b], ctx->tile_Z, st);
+  rix_status s = RIX_OK;
+  if (ctx->have_mx && ctx->n_ztc == ctx->nat) {
+    // every middle atom runs on the tensor cores: the FP64 kernel would only write zeros
+    const int64_t n = ctx->off2[ctx->row2[ctx->blk_atom[b + 1]]] - ctx->blk_base[b];
+    RIX_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_Z, 0, sizeof(double) * n, st));
+  } else {
+    s = launch_Z_items(ctx, D, b, 0, ctx->segZ[b + 1] - ctx->segZ[b], ctx->tile_Z, st);
+  }
   if (s == RIX_OK && ctx->have_mx) s = rix_mixed_z(ctx, b, ctx->blk_base[b], D, st);
   return s;
 }

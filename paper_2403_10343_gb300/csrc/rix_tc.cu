@@ -1161,6 +1161,31 @@ struct SrcAcc {
   }
 };
 
+// Row exponents of the Z plan's Kronecker rows, one thread per packed row: row
+// (B, P, j) holds V(B,G'_k)[P][Q] D(B,G'_k)[j][k'] over member k's range, so its
+// largest magnitude is max_k (max_Q |V[P][Q]|) (max_k' |D[j][k']|), attained by
+// the product of the two maximising entries: the same FP64 product, hence the same
+// exponent, as the element-wise pass, from na + nb loads per member instead of
+// na nb products.
+__global__ void k_kron_exp(int64_t n0, int64_t n, SrcAcc acc, int *e) {
+  const int64_t w = n0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (w >= n0 + n) return;
+  const SrcAcc::Row R = acc.row(w);
+  int m = -2000;
+  for (int k = 0; k < R.pr.ng; k++) {
+    const Src sr = R.s[k];
+    if (sr.off < 0 || (sr.flag >= 0 && !(acc.keep[sr.flag] && (!acc.keep2 || acc.keep2[sr.flag])))) continue;
+    const int kn = (k == 0 ? R.pr.kb[1] : k == 1 ? R.pr.kb[2] - R.pr.kb[1] : k == 2 ? R.pr.kb[3] - R.pr.kb[2]
+                                                                                   : R.pr.kb[4] - R.pr.kb[3]);
+    const int nq = kn / sr.inner_n;
+    double mv = 0.0, md = 0.0;
+    for (int q = 0; q < nq; q++) mv = fmax(mv, fabs(acc.X[sr.off - acc.shift + (int64_t)q * sr.outer]));
+    for (int i = 0; i < sr.inner_n; i++) md = fmax(md, fabs(acc.X2[sr.off2 + i]));
+    m = max(m, exp_of(mv * md));
+  }
+  e[R.pr.eaoff + R.r] = m;
+}
+
 // Per row tile r of a grouped plan, for this build: bit c of its K-stage mask is set
 // when a row of the tile has a kept block with a middle atom whose K range meets
 // stage c (entries (pair, first stage | last stage << 16) in rtq), and live[r] tells
@@ -1812,6 +1837,7 @@ int32_t rix_launch_count(const rix_ctx *ctx) {
     n += 5 * (int32_t)(ctx->mx34->grp.size() - 1) + 5 * (int32_t)(ctx->mx2->grp.size() - 1) +
          5 * (int32_t)(ctx->mxz->grp.size() - 1) + rix_t1_launches(ctx) + rix_tt_launches(ctx);
     if (ctx->n_t1tc < ctx->nat) n += ctx->nblk;  // k_X12 for the other column atoms
+    if (ctx->n_ztc == ctx->nat) n -= ctx->nblk;   // no k_Z: the Z buffer is zeroed by a memset
     // row-tile K-stage masks: once per Z block, once per terms-3+4 block, once for term 2
     if (ctx->mxz->n_rt > 0) n += ctx->nblk;
     if (ctx->mx34->n_rt > 0) n += ctx->nblk;
@@ -1854,7 +1880,12 @@ rix_status run_group(rix_ctx *ctx, const rix_mx_plan *pl, size_t g, const Operan
   __nv_bfloat16 *buf = (__nv_bfloat16 *)ctx->d_mx_buf;
   if (r1 > r0) {
     const SrcAcc a{pl->d_rowprob, pl->d_probs, pl->d_rowsrc, pl->G, ra.x, ra.shift, ra.x2, ra.keep, ra.keep2, 0};
-    slice_rows(r0, r1 - r0, a, S, buf, pl->d_eA, pl->kmax, st);
+    if (pl->kind == 2) {  // Kronecker rows: exponents from the factors' maxima
+      k_kron_exp<<<(unsigned)((r1 - r0 + 127) / 128), 128, 0, st>>>(r0, r1 - r0, a, pl->d_eA);
+      launch_slice_dig(r0, r1 - r0, a, S, buf, pl->d_eA, st);
+    } else {
+      slice_rows(r0, r1 - r0, a, S, buf, pl->d_eA, pl->kmax, st);
+    }
   }
   if (c1 > c0) {
     const SrcAcc b{pl->d_colprob, pl->d_probs, pl->d_colsrc, pl->G, cb.x, cb.shift, cb.x2, cb.keep, cb.keep2, 1};
