@@ -122,6 +122,40 @@ def test_term3_is_transpose_of_term2():
         assert np.abs(b - partner.T).max() < 1e-12 * scale
 
 
+def _term_blocks(s, pk, t):
+    orc = Oracle(s)
+    orc.set_data(pk.C, pk.V, pk.D)
+    orc.set_terms(1 << (t - 1))
+    kk = orc.kpattern()
+    return k_blocks(s, kk, orc.build_K())
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_terms_1_and_4_are_each_symmetric(periodic):
+    """Terms 1 and 4 alone satisfy K_t(A,E,n) = K_t(E,A,-n)^T (term 2 alone does not).
+
+    The library computes terms 1 and 4 for one orientation of each block and
+    restores the other through K = X + X^T; this pins that each term carries the
+    symmetry by itself (self-images included in the periodic cell).
+    """
+    if periodic:
+        o = np.array([[1.0, 1.2, 0.8], [3.9, 3.1, 3.3]])
+        s = _waters_system(o, seed=19, cell_side=6.0, cutoff_ang=5.0)
+    else:
+        s = ri.config(0)
+    pk = ri.generate(s)
+    for t in (1, 4):
+        blocks = _term_blocks(s, pk, t)
+        scale = max(np.abs(b).max() for b in blocks.values())
+        assert scale > 0
+        for (a, e, n), b in blocks.items():
+            assert np.abs(b - blocks[(e, a, tuple(-v for v in n))].T).max() < 1e-13 * scale, (t, a, e, n)
+    k2 = _term_blocks(s, pk, 2)
+    scale = max(np.abs(b).max() for b in k2.values())
+    worst = max(np.abs(b - k2[(e, a, tuple(-v for v in n))].T).max() for (a, e, n), b in k2.items())
+    assert worst > 1e-3 * scale
+
+
 def test_closed_form_single_function():
     """One atom, one basis function, one aux function: K = c^2 V D, E = -c^2 V D^2 / 4."""
     s = S.System(name="x", seed=0, xyz=np.zeros((1, 3)), species=np.zeros(1, np.int32),
