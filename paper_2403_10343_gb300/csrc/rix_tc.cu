@@ -479,10 +479,12 @@ struct GemmArgs {
   int64_t xshift;          // mode 0: X + offK[x] - xshift is the output block
   int ntiles;              // output tiles of the launch (persistent CTAs loop over them)
   const uint8_t *row_live = nullptr;  // batched mode: per row tile (tiles[t].w), 0 = all its rows are zero
-  // batched mode: per (problem, column tile) a bit mask of the K stages whose B tile is not all
-  // zero, (Kpad / KC + 63) / 64 words at kmask + tiles[t].w; stages without a bit are skipped
+  // batched mode: a bit mask of the K stages to run, (Kpad / KC + 63) / 64 words per tile:
+  // per (problem, column tile) at kmask + tiles[t].w (T plan: stages whose B tile is not all
+  // zero), or per row tile at kmask + kmask_off[tiles[t].w] (grouped plans: stages of the
+  // members that meet a kept block of the tile's rows); stages without a bit are skipped
   const unsigned long long *kmask = nullptr;
-  const int64_t *kmask_off = nullptr;  // grouped plans: word offset of the mask of row tile tiles[t].w
+  const int64_t *kmask_off = nullptr;
   unsigned long long *chunks = nullptr;  // profiling: 128 x 80 x 16 MMAs issued (K stages x K steps x slice pairs)
   unsigned long long *X128 = nullptr;  // deterministic mode: X additions as 128-bit fixed point (2 words each)
   uint64_t wait_ns = WAIT_NS;  // limit of every bounded wait

@@ -78,6 +78,26 @@ def test_stage_split_between_pipes():
     assert bench.stage_fp64_share(STATS, "T", "mixed") == 0.0
 
 
+def test_term1_flops_follow_the_stage_that_runs_them():
+    # several row blocks: term 1 on the tensor cores runs per block inside the X12 stage, so
+    # TC12 holds term 2 only and X12 holds the FP64 remainder plus the tensor-core term 1
+    st = dict(STATS, n_row_blocks=3)
+    assert bench.stage_flops(st, "TC12", "mixed") == 6.0
+    assert bench.stage_flops(st, "X12", "mixed") == 34.0
+    assert bench.stage_flops(dict(STATS, n_row_blocks=1), "TC12", "mixed") == 36.0
+    # the FP64 build is unaffected by the block count
+    assert bench.stage_flops(st, "X12", "fp64") == 40.0
+
+
+def test_traffic_scales_with_the_mmas_of_a_launch():
+    gemm = {"ms_per_build": 2.0, "launches_per_build": 4.0, "stage_pairs_per_build": 1000.0}
+    roof = bench.roofline("mixed", {"stats": STATS, "stage_ms": {}, "gemm": gemm})
+    if bench.GEMM_DRAM_BYTES_PER_STAGE_PAIR is None:
+        assert roof["traffic"] is None
+    else:
+        assert roof["traffic"] == bench.GEMM_DRAM_BYTES_PER_STAGE_PAIR * 250.0
+
+
 def test_roofline_picks_the_longest_stage():
     r = {"stats": STATS, "stage_ms": {"T": 1.0, "U2": 0.5, "X12": 10.0, "Z": 4.0, "X34": 2.0}}
     roof = bench.roofline("fp64", r)
