@@ -141,7 +141,8 @@ typedef struct {
 typedef struct {
   int64_t n_atoms, n_pairs, n_pairs2, n_kblocks;
   int64_t c_elems, v_elems, d_elems, k_elems;
-  double flops_fp64;               /* algorithmic FLOPs of one rix_build_K (unpadded products) */
+  double flops_fp64;               /* algorithmic FLOPs of one rix_build_K (unpadded products; terms 1
+                                      and 4 counted once per pair / K block, as the build runs them) */
   double flops_stage[6];           /* T, U2, X12 (terms 1+2), Z (term 4), X34, symmetrise */
   double min_bytes;                /* 8 (nnz C + V + D) + 8 nnz K */
   double tensor_flops;             /* mixed mode: tensor-core FLOPs issued per build */
@@ -350,7 +351,9 @@ rix_status rix_stats(const rix_ctx *ctx, rix_stats_t *out);
 /* Algorithmic FLOPs (2 per multiply-add, the FP64 grouping of Eqs. 12a-d) that
  * one rix_build_K with the density matrix D_dev (device, packed) performs
  * after block screening (Sec. "Screening": products whose C, V or D block has
- * no element of magnitude >= tau are skipped).  The counts of rix_stats_t
+ * no element of magnitude >= tau are skipped).  Terms 1 and 4 are symmetric
+ * under the transposition of their block (Eq. 11), so the build evaluates them
+ * for one orientation of each pair / K block and these counts do the same.  The counts of rix_stats_t
  * include every product; these depend on D.  flops (host, 10 doubles):
  * [0] T, [1] U2, [2] terms 1+2, [3] Z, [4] terms 3+4, [5] symmetrise, [6] the
  * term-2 part of [2], [7] the part of [2] for the column atoms whose term 1
