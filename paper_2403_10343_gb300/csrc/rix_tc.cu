@@ -1426,6 +1426,11 @@ rix_status plan_host(rix_ctx *ctx, int kind, const std::vector<int64_t> &ptrZ, P
         }
       }
       if (qb < 0) break;
+      // the member's image relative to the first atom: a neighbour within GROUP_R, so at
+      // most one cell away unless a cell edge is shorter than GROUP_R
+      bool near = true;
+      for (int x = 0; x < 3; x++) near &= ctx->pn[3 * qb + x] >= -1 && ctx->pn[3 * qb + x] <= 1;
+      if (!near) break;
       gm.push_back(Member{c, {ctx->pn[3 * qb], ctx->pn[3 * qb + 1], ctx->pn[3 * qb + 2]}});
     }
     h.G = std::max(h.G, (int)gm.size());
@@ -1434,8 +1439,14 @@ rix_status plan_host(rix_ctx *ctx, int kind, const std::vector<int64_t> &ptrZ, P
   }
   const int G = h.G;
   const Src absent{-1, -1, 1, 1, 1, -1};
-  // (atom, image) as a sortable key; images stay well inside the key's 8-bit fields
-  auto node_key = [](int a, const int *m) { return pair_key(0, a, m[0], m[1], m[2]); };
+  // (atom, image) as a sortable key; member images are within one cell, so a pair's image
+  // shifted by one stays in the key's 8-bit fields unless the pair list's own images reach
+  // their limit, which the check below reports
+  bool img_ok = true;
+  auto node_key = [&img_ok](int a, const int *m) {
+    for (int x = 0; x < 3; x++) img_ok &= m[x] > -128 && m[x] < 128;
+    return pair_key(0, a, m[0], m[1], m[2]);
+  };
   using Slots = std::array<int64_t, GMAX>;
   for (int blk = 0; blk < nblk; blk++)
     for (const auto &gm : groups) {
@@ -1478,6 +1489,10 @@ rix_status plan_host(rix_ctx *ctx, int kind, const std::vector<int64_t> &ptrZ, P
             slot(cm, node_key(ctx->pB[q], N))[k] = q;
           }
         }
+      }
+      if (!img_ok) {
+        ctx->last_error = "mixed plan: an image index outside the pair key's range";
+        return RIX_EINVAL;
       }
       if (rm.empty()) continue;
       int M = 0, N = 0, K = 0;
