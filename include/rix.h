@@ -201,9 +201,15 @@ rix_status rix_autotune(rix_ctx *ctx, const double *D_dev, const char *cache_pat
                         void *stream);
 
 /* K = exchange matrix of D (device, packed, FP64) into K_dev (device, packed
- * on the K list, FP64, fully overwritten).  Asynchronous on `stream`; no host
- * synchronisation, no allocation; may be captured in a CUDA graph once one
- * call has completed.  ESTATE before rix_set_CV. */
+ * on the K list, FP64, fully overwritten): Eq. 4 with the RI-LVL restriction
+ * of Eqs. 6-7, evaluated in the four-term grouping of Eq. 11 and Eqs. 12a-d.
+ * D must be pair-symmetric, D(B,A,-n) = D(A,B,n)^T, as a density matrix is:
+ * K is formed as X + X^T with term 3 taken as the transpose of term 2 and
+ * terms 1 and 4 evaluated for one orientation of each block, all of which
+ * rest on that symmetry (C and V are checked by rix_set_CV; D is not).
+ * Asynchronous on `stream`; no host synchronisation, no allocation; may be
+ * captured in a CUDA graph once one call has completed.  ESTATE before
+ * rix_set_CV. */
 rix_status rix_build_K(rix_ctx *ctx, const double *D_dev, double *K_dev, void *stream);
 
 /* Incremental build for the SCF loop (the paper's exchange matrix is rebuilt
